@@ -1,0 +1,150 @@
+/*
+ * hdi.h -- C ABI of libhdi: homogeneous diffusion inpainting and its data
+ * optimisation on one NVIDIA B300 (sm_103a).
+ *
+ * Method: Kaemper, Chizhov, Weickert, "Efficient Parallel Data Optimization
+ * for Homogeneous Diffusion Inpainting of 4K Images" (arXiv 2401.06747).
+ *
+ * Conventions shared by every call
+ *  - Images are planar: channel c, row y, column x lives at
+ *      data[c * channel_stride + y * row_stride + x]   (strides in ELEMENTS).
+ *  - Masks are uint8 (0 or 1), one per pixel, shared by all channels
+ *    (Sec. 2.1: colour channels are inpainted with the same matrix).
+ *  - `location` says whether a buffer is device memory of the context's GPU
+ *    (HDI_DEVICE) or host memory (HDI_HOST; pinned or pageable). Host
+ *    buffers are staged through the context's workspace with cudaMemcpyAsync.
+ *  - The caller owns every buffer it passes. The library owns only its
+ *    context workspace (grown on demand, released by hdi_destroy).
+ *  - Every call is stream-ordered on the context's stream and returns after
+ *    the work has completed (synchronous). Calls on one context must not
+ *    overlap (one host thread at a time per context).
+ *  - Return value: HDI_OK (0) or a negative hdi_status; hdi_last_error()
+ *    gives a one-line message. Output buffers are unspecified on error,
+ *    except HDI_ERR_NOT_CONVERGED, where they hold the last iterate.
+ */
+#ifndef HDI_H
+#define HDI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdi_ctx hdi_ctx;
+
+typedef enum {
+    HDI_OK = 0,
+    HDI_ERR_INVALID_ARG = -1,   /* null pointer, shape/dtype mismatch, tol not in (0,1), mask value not 0/1, k < 0 */
+    HDI_ERR_EMPTY_MASK = -2,    /* inpaint/tonal with c = 0: A is singular (Sec. 2.1) */
+    HDI_ERR_NOT_CONVERGED = -3, /* iteration cap reached; output holds the last iterate, stats filled */
+    HDI_ERR_OUT_OF_MEMORY = -4, /* workspace would exceed the context's HBM budget or cudaMalloc failed */
+    HDI_ERR_CUDA = -5,          /* CUDA runtime error */
+    HDI_ERR_NONFINITE = -6,     /* non-finite input or residual */
+    HDI_ERR_TIMEOUT = -7,       /* a bounded device-side wait gave up */
+    HDI_ERR_UNSUPPORTED = -8    /* a configuration this build does not handle */
+} hdi_status;
+
+typedef enum { HDI_F32 = 0, HDI_F64 = 1 } hdi_dtype;
+typedef enum { HDI_DEVICE = 0, HDI_HOST = 1 } hdi_location;
+
+typedef struct {
+    void* data;
+    int32_t height, width, channels;
+    int32_t dtype;            /* hdi_dtype */
+    int64_t row_stride;       /* elements between rows */
+    int64_t channel_stride;   /* elements between channels */
+    int32_t location;         /* hdi_location */
+} hdi_image;
+
+typedef struct {
+    uint8_t* data;            /* 0/1 per pixel */
+    int32_t height, width;
+    int64_t row_stride;       /* bytes between rows */
+    int32_t location;         /* hdi_location */
+} hdi_mask;
+
+typedef struct {
+    int32_t status;           /* same value the call returned */
+    int32_t iterations;       /* refinement steps (inpaint) or RAS iterations (tonal) */
+    int32_t vcycles;          /* V-cycles run in total, all inner solves included */
+    int32_t reserved;
+    int64_t local_iters;      /* local CG iterations summed over all subdomains and sweeps */
+    double rel_res;           /* max over channels of the achieved relative residual */
+    double mse;               /* tonal: MSE of B g against f at the last residual evaluation */
+    double seconds;           /* wall time of the call */
+} hdi_stats;
+
+/* Create a context on `device`, ordered on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream). */
+int hdi_create(hdi_ctx** ctx, int device, void* cuda_stream);
+
+/* Release the context and its workspace. NULL is accepted. */
+int hdi_destroy(hdi_ctx* ctx);
+
+/* Set / get a solver parameter by name (table at the end of this file).
+ * Unknown names return HDI_ERR_INVALID_ARG. */
+int hdi_set_param(hdi_ctx* ctx, const char* name, double value);
+int hdi_get_param(const hdi_ctx* ctx, const char* name, double* value);
+
+/* Homogeneous diffusion inpainting (Sec. 2.1, Eq. "inp-discrete-lsi"):
+ * solve (C + (I - C) L) u = C f, L the 5-point negated Laplacian with
+ * reflecting boundaries, by multigrid with ORAS smoothing (Sec. 3).
+ *   f     in : image (F32 or F64), H x W x ch
+ *   mask  in : 0/1, H x W
+ *   u0    in : initial guess (same shape/dtype as f), or NULL for the cold
+ *              start by reduced full multigrid (Sec. 3.2). Values on the mask
+ *              are ignored (u_K = f_K is enforced).
+ *   u     out: solution, same shape and dtype as f (may alias u0).
+ *   tol      : per-channel relative residual ||C f - A u|| / ||C f||, in (0,1),
+ *              evaluated in FP64 on the FP64 iterate kept on the GPU.
+ *   st   out : statistics, may be NULL. */
+int hdi_inpaint(hdi_ctx* ctx, const hdi_image* f, const hdi_mask* mask,
+                const hdi_image* u0, hdi_image* u, double tol, hdi_stats* st);
+
+/* Tonal optimisation (Sec. 5, Eq. "tonal-opt-minimisation"): g minimising
+ * ||f - A^{-1} C g||_2 with g = 0 off the mask, by restricted additive
+ * Schwarz on the normal equations B^T B g = B^T f (Sec. 5.2, Alg. 2); each
+ * application of B and B^T is an inpainting solve (Sec. 5.1).
+ *   f, mask  in : as for hdi_inpaint
+ *   g0       in : initial tonal values (same shape/dtype as f) or NULL (g0 = f)
+ *   g       out : optimised values, zero off the mask (may alias g0)
+ *   tol         : per-channel ||B^T (f - B g)|| / ||B^T f||, in (0,1) */
+int hdi_tonal_opt(hdi_ctx* ctx, const hdi_image* f, const hdi_mask* mask,
+                  const hdi_image* g0, hdi_image* g, double tol, hdi_stats* st);
+
+/* One densification step (Sec. 4.1, Alg. 1 with the Delaunay partition;
+ * initial mask by random dithering of |L f|, Sec. 4.2).
+ *   f     in     : reference image
+ *   mask  in/out : current mask; only new 1-bits are written
+ *   u     in     : inpainting of f from the current mask (ignored when the
+ *                  mask is empty)
+ *   k            : number of pixels to add (k >= 0)
+ *   seed         : seed of the counter-based generator used on an empty mask
+ *   added   out  : pixels actually added (<= k for a non-empty mask) */
+int hdi_densify_step(hdi_ctx* ctx, const hdi_image* f, hdi_mask* mask,
+                     const hdi_image* u, int64_t k, uint64_t seed, int64_t* added);
+
+/* One-line description of the last error on this context ("" if none). */
+const char* hdi_last_error(const hdi_ctx* ctx);
+
+/* Library version string. */
+const char* hdi_version(void);
+
+/*
+ * Parameters (hdi_set_param names), defaults in brackets:
+ *   oras_theta        [0.3]   Robin weight at inner subdomain boundaries (Sec. 3.1)
+ *   oras_eta          [1e-3]  local CG stop: ||r_i||^2 <= eta * ||r||^2 / n_subdomains (Sec. 3.3)
+ *   oras_max_local    [48]    local CG iteration cap per subdomain and sweep
+ *   coarse_eta        [1e-8]  relative squared-residual target of the single-block coarsest solve
+ *   max_vcycles       [60]    refinement steps per inpainting solve
+ *   tonal_max_iter    [400]   RAS iterations per tonal solve
+ *   tonal_inner_ratio [0.05]  inner solves target: ratio * current outer relative residual
+ *   hbm_budget_gb     [200]   workspace cap for this context
+ */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HDI_H */

@@ -1,0 +1,96 @@
+// common.cuh -- shared device helpers of libhdi (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define HDI_FULL 0xffffffffu
+
+// Bit-packed mask: one uint32 word per 32 pixels along x, `wpitch` words per
+// row (ceil(W/32) + 1; the extra zero word lets a 32-wide window starting at
+// any x read two words without a bounds check). Bit set = known pixel (c = 1).
+struct MaskView {
+    const uint32_t* bits;
+    int H, W, wpitch;
+    __device__ __forceinline__ bool known(int x, int y) const {
+        return (bits[(size_t)y * wpitch + (x >> 5)] >> (x & 31)) & 1u;
+    }
+    // 32 mask bits for columns x0 .. x0+31 of row y (bit i = column x0+i).
+    __device__ __forceinline__ uint32_t window(int x0, int y) const {
+        const uint32_t* row = bits + (size_t)y * wpitch + (x0 >> 5);
+        return __funnelshift_r(row[0], row[1], x0 & 31);
+    }
+};
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(HDI_FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(HDI_FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int linear_tid() {
+    return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+}
+
+// Block-wide FP64 sum in a fixed tree order; result valid in thread 0.
+// All threads of the block must call it.
+__device__ __forceinline__ double block_sum_d(double v) {
+    __shared__ double sh[32];
+    const int tid = linear_tid();
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    __syncthreads();
+    const int nw = (nt + 31) >> 5;
+    v = (tid < nw) ? sh[tid] : 0.0;
+    if (tid < 32) v = warp_sum_d(v);
+    return v;
+}
+
+// Deterministic grid reduction: every CTA deposits one FP64 partial per
+// (channel, part); the last CTA to arrive sums each channel's partials in a
+// fixed order and writes out[ch]. `nparts` CTAs per channel, `nch` channels;
+// all nparts*nch CTAs of the launch call grid_reduce_commit exactly once.
+struct GridReduce {
+    double* partials;   // [nch * nparts]
+    double* out;        // [nch]
+    unsigned* ticket;   // zero before the launch; reset to zero by the last CTA
+    int nparts;
+    int nch;
+};
+
+__device__ __forceinline__ void grid_reduce_commit(const GridReduce& R, int ch, int part, double block_total) {
+    __shared__ bool last_cta;
+    const int tid = linear_tid();
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    if (tid == 0) {
+        R.partials[(size_t)ch * R.nparts + part] = block_total;
+        __threadfence();
+        unsigned t = atomicAdd(R.ticket, 1u);
+        last_cta = (t == (unsigned)(R.nparts * R.nch - 1));
+    }
+    __syncthreads();
+    if (!last_cta) return;
+    __threadfence();
+    for (int c = 0; c < R.nch; ++c) {
+        double acc = 0.0;
+        for (int i = tid; i < R.nparts; i += nt) acc += __ldcg(R.partials + (size_t)c * R.nparts + i);
+        acc = block_sum_d(acc);
+        if (tid == 0) R.out[c] = acc;
+    }
+    if (tid == 0) *R.ticket = 0u;
+}
+
+// Number of overlapping subdomains of side `size` with overlap `ov` along an
+// axis of n pixels: ceil((n - ov) / (size - ov)), at least 1 (Sec. 3.3).
+__host__ __device__ __forceinline__ int tile_count(int n, int size, int ov) {
+    const int s = size - ov;
+    const int c = (n - ov + s - 1) / s;
+    return c < 1 ? 1 : c;
+}
