@@ -1,0 +1,198 @@
+"""B300-native homogeneous diffusion inpainting and data optimisation.
+
+Thin Python binding over libhdi.so (include/hdi.h). Every step of the solvers
+runs in the library's CUDA kernels; this module only marshals arguments.
+PyTorch tensors (CUDA or CPU) and NumPy arrays are accepted: CUDA tensors
+are passed as device pointers, CPU tensors / arrays as host buffers, which
+the library stages through its own workspace. There is no CPU fallback:
+loading fails loudly if the library is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+HDI_OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "EMPTY_MASK", -3: "NOT_CONVERGED", -4: "OUT_OF_MEMORY",
+    -5: "CUDA", -6: "NONFINITE", -7: "TIMEOUT", -8: "UNSUPPORTED",
+}
+F32, F64 = 0, 1
+DEVICE, HOST = 0, 1
+
+
+class HdiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hdi error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Image(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("channels", ctypes.c_int32), ("dtype", ctypes.c_int32), ("row_stride", ctypes.c_int64),
+                ("channel_stride", ctypes.c_int64), ("location", ctypes.c_int32)]
+
+
+class Mask(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("row_stride", ctypes.c_int64), ("location", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("vcycles", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("local_iters", ctypes.c_int64), ("rel_res", ctypes.c_double),
+                ("mse", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+SYMBOLS = ["hdi_create", "hdi_destroy", "hdi_set_param", "hdi_get_param", "hdi_inpaint",
+           "hdi_tonal_opt", "hdi_densify_step", "hdi_last_error", "hdi_version"]
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libhdi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhdi.so not found at {path}; run paper_2401_06747_b300/build.py")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    lib.hdi_create.argtypes = [P(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p]
+    lib.hdi_destroy.argtypes = [ctypes.c_void_p]
+    lib.hdi_set_param.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_double]
+    lib.hdi_get_param.argtypes = [ctypes.c_void_p, ctypes.c_char_p, P(ctypes.c_double)]
+    lib.hdi_inpaint.argtypes = [ctypes.c_void_p, P(Image), P(Mask), P(Image), P(Image), ctypes.c_double, P(Stats)]
+    lib.hdi_tonal_opt.argtypes = [ctypes.c_void_p, P(Image), P(Mask), P(Image), P(Image), ctypes.c_double, P(Stats)]
+    lib.hdi_densify_step.argtypes = [ctypes.c_void_p, P(Image), P(Mask), P(Image), ctypes.c_int64,
+                                     ctypes.c_uint64, P(ctypes.c_int64)]
+    lib.hdi_last_error.argtypes = [ctypes.c_void_p]
+    lib.hdi_last_error.restype = ctypes.c_char_p
+    lib.hdi_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def image_of(x) -> Image:
+    """Describe a (H, W) or (C, H, W) float32/float64 tensor or array."""
+    if _is_torch(x):
+        import torch
+        if x.dim() == 2:
+            x = x.unsqueeze(0)
+        dt = {torch.float32: F32, torch.float64: F64}.get(x.dtype)
+        if dt is None:
+            raise TypeError("image must be float32 or float64")
+        if x.stride(2) != 1:
+            raise ValueError("image rows must be contiguous")
+        loc = DEVICE if x.is_cuda else HOST
+        return Image(x.data_ptr(), x.shape[1], x.shape[2], x.shape[0], dt, x.stride(1), x.stride(0), loc)
+    a = x if x.ndim == 3 else x[None]
+    if a.dtype not in (np.float32, np.float64):
+        raise TypeError("image must be float32 or float64")
+    es = a.itemsize
+    if a.strides[2] != es:
+        raise ValueError("image rows must be contiguous")
+    return Image(a.ctypes.data, a.shape[1], a.shape[2], a.shape[0], F64 if a.dtype == np.float64 else F32,
+                 a.strides[1] // es, a.strides[0] // es, HOST)
+
+
+def mask_of(m) -> Mask:
+    if _is_torch(m):
+        import torch
+        if m.dtype != torch.uint8 or m.dim() != 2 or m.stride(1) != 1:
+            raise TypeError("mask must be a 2-D uint8 tensor with contiguous rows")
+        return Mask(m.data_ptr(), m.shape[0], m.shape[1], m.stride(0), DEVICE if m.is_cuda else HOST)
+    if m.dtype != np.uint8 or m.ndim != 2 or m.strides[1] != 1:
+        raise TypeError("mask must be a 2-D uint8 array with contiguous rows")
+    return Mask(m.ctypes.data, m.shape[0], m.shape[1], m.strides[0], HOST)
+
+
+class Context:
+    """One libhdi context (device, stream, workspace)."""
+
+    def __init__(self, device: int = 0, stream=None, **params):
+        self.lib = load()
+        self.h = ctypes.c_void_p()
+        s = 0
+        if stream is not None:
+            s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        rc = self.lib.hdi_create(ctypes.byref(self.h), device, ctypes.c_void_p(s))
+        if rc != HDI_OK:
+            raise HdiError(rc, "hdi_create failed")
+        for k, v in params.items():
+            self.set_param(k, v)
+
+    def close(self):
+        if self.h:
+            self.lib.hdi_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow_not_converged=False):
+        if rc == HDI_OK or (allow_not_converged and rc == -3):
+            return rc
+        raise HdiError(rc, self.lib.hdi_last_error(self.h).decode())
+
+    def set_param(self, name: str, value: float):
+        self._check(self.lib.hdi_set_param(self.h, name.encode(), float(value)))
+
+    def get_param(self, name: str) -> float:
+        v = ctypes.c_double()
+        self._check(self.lib.hdi_get_param(self.h, name.encode(), ctypes.byref(v)))
+        return v.value
+
+    def inpaint(self, f, mask, out, u0=None, tol: float = 1e-6, allow_not_converged=False) -> dict:
+        """Solve (C + (I-C)L) u = C f into `out` (same shape/dtype as f)."""
+        fi, mi, oi = image_of(f), mask_of(mask), image_of(out)
+        ui = image_of(u0) if u0 is not None else None
+        st = Stats()
+        rc = self.lib.hdi_inpaint(self.h, ctypes.byref(fi), ctypes.byref(mi),
+                                  ctypes.byref(ui) if ui is not None else None, ctypes.byref(oi),
+                                  float(tol), ctypes.byref(st))
+        self._check(rc, allow_not_converged)
+        return st.as_dict()
+
+    def tonal_opt(self, f, mask, out, g0=None, tol: float = 1e-6, allow_not_converged=False) -> dict:
+        """Optimised tonal values g (zero off the mask) into `out`."""
+        fi, mi, oi = image_of(f), mask_of(mask), image_of(out)
+        gi = image_of(g0) if g0 is not None else None
+        st = Stats()
+        rc = self.lib.hdi_tonal_opt(self.h, ctypes.byref(fi), ctypes.byref(mi),
+                                    ctypes.byref(gi) if gi is not None else None, ctypes.byref(oi),
+                                    float(tol), ctypes.byref(st))
+        self._check(rc, allow_not_converged)
+        return st.as_dict()
+
+    def densify_step(self, f, mask, u, k: int, seed: int = 0) -> int:
+        """Add up to k mask pixels in place; returns the number added."""
+        fi, mi = image_of(f), mask_of(mask)
+        ui = image_of(u) if u is not None else None
+        added = ctypes.c_int64()
+        rc = self.lib.hdi_densify_step(self.h, ctypes.byref(fi), ctypes.byref(mi),
+                                       ctypes.byref(ui) if ui is not None else None, int(k),
+                                       ctypes.c_uint64(seed), ctypes.byref(added))
+        self._check(rc)
+        return added.value
+
+
+def version() -> str:
+    return load().hdi_version().decode()

@@ -1,0 +1,661 @@
+// hdi.cu -- libhdi: C ABI, context/workspace management and the solver
+// drivers (multigrid ORAS inpainting, RAS tonal optimisation,
+// densification) for one B300 (sm_103a).
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <string>
+#include <vector>
+#include <algorithm>
+#include <chrono>
+
+#include "../../include/hdi.h"
+#include "common.cuh"
+#include "oras.cuh"
+#include "stencil.cuh"
+#include "solver.h"
+#include "tonal.cuh"
+#include "densify.cuh"
+
+// ----------------------------------------------------------------- params ---
+
+namespace {
+
+struct ParamDef {
+    const char* name;
+    double Params::*field;
+    double lo, hi;
+};
+
+const ParamDef kParams[] = {
+    {"oras_theta", &Params::oras_theta, 0.0, 1.0},
+    {"oras_eta", &Params::oras_eta, 1e-12, 1.0},
+    {"oras_max_local", &Params::oras_max_local, 1, 1024},
+    {"coarse_eta", &Params::coarse_eta, 1e-16, 1.0},
+    {"coarse_max_local", &Params::coarse_max_local, 1, 4096},
+    {"max_vcycles", &Params::max_vcycles, 1, 10000},
+    {"tonal_max_iter", &Params::tonal_max_iter, 1, 100000},
+    {"tonal_inner_ratio", &Params::tonal_inner_ratio, 1e-6, 1.0},
+    {"tonal_echo_rtol", &Params::tonal_echo_rtol, 1e-12, 1.0},
+    {"tonal_echo_max_iter", &Params::tonal_echo_max_iter, 1, 4096},
+    {"hbm_budget_gb", &Params::hbm_budget_gb, 0.001, 1e6},
+};
+
+}  // namespace
+
+// ------------------------------------------------------------- utilities ---
+
+int Ctx::fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+}
+
+int Ctx::cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return HDI_OK;
+    return fail(HDI_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int Ctx::sync(const char* what) {
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return cuda_check(e, what);
+}
+
+void Arena::release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = used = 0;
+}
+
+int Arena::reserve(Ctx& c, size_t bytes, const char* what) {
+    if (bytes <= cap) {
+        used = 0;
+        return HDI_OK;
+    }
+    release();
+    const double budget = c.p.hbm_budget_gb * 1e9;
+    if ((double)(bytes + c.other_bytes()) > budget)
+        return c.fail(HDI_ERR_OUT_OF_MEMORY, "%s: %.3f GB workspace exceeds the %.3f GB budget", what,
+                      (bytes + c.other_bytes()) / 1e9, c.p.hbm_budget_gb);
+    cudaError_t e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) {
+        base = nullptr;
+        cudaGetLastError();
+        return c.fail(HDI_ERR_OUT_OF_MEMORY, "%s: cudaMalloc(%zu) failed: %s", what, bytes, cudaGetErrorString(e));
+    }
+    cap = bytes;
+    used = 0;
+    return HDI_OK;
+}
+
+void* Arena::take(size_t bytes) {
+    size_t off = (used + 255) & ~(size_t)255;
+    used = off + bytes;
+    return (char*)base + off;
+}
+
+size_t Ctx::other_bytes() const { return ws.cap + tws.cap + dws.cap + stage.cap; }
+
+// ------------------------------------------------------------ hierarchy ---
+
+static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Plans the level sizes, reserves the workspace and carves the buffers.
+int Ctx::setup(int H_, int W_, int nch_) {
+    if (H_ == H && W_ == W && nch_ == nch && ws.base) return HDI_OK;
+    std::vector<std::pair<int, int>> sizes;
+    int h = H_, w = W_;
+    sizes.push_back({h, w});
+    while (std::max(h, w) > 32 && (int)sizes.size() < kMaxLevels) {
+        h = (h + 1) / 2;
+        w = (w + 1) / 2;
+        sizes.push_back({h, w});
+    }
+    const int nl = (int)sizes.size();
+    // bytes
+    size_t bytes = 0;
+    auto acc = [&](size_t b) { bytes += ((b + 255) & ~(size_t)255); };
+    int maxparts = 1;
+    for (int l = 0; l < nl; ++l) {
+        const int P = round_up(sizes[l].second, 32);
+        const int wp = (sizes[l].second + 31) / 32 + 1;
+        acc((size_t)sizes[l].first * wp * 4);            // bits
+        acc((size_t)nch_ * sizes[l].first * P * 4 * 3);   // xa, xb, b
+        const int parts = ((sizes[l].second + 31) / 32) * ((sizes[l].first + 7) / 8);
+        maxparts = std::max(maxparts, parts);
+    }
+    const int P0 = round_up(W_, 32);
+    const size_t n64 = (size_t)nch_ * H_ * P0;
+    acc(n64 * 8 * kNumF64);                                   // FP64 vectors
+    acc((size_t)kSlots * maxparts * nch_ * 8);                // reduction partials
+    acc((size_t)kSlots * 4 * 8);                              // reduction outputs
+    acc((size_t)kSlots * 4);                                  // tickets
+    acc(64 * 8);                                              // counters / flags
+    int rc = ws.reserve(*this, bytes, "inpainting workspace");
+    if (rc) { H = W = nch = 0; return rc; }
+    H = H_; W = W_; nch = nch_; nlev = nl;
+    for (int l = 0; l < nl; ++l) {
+        Level& L = lev[l];
+        L.H = sizes[l].first;
+        L.W = sizes[l].second;
+        L.P = round_up(L.W, 32);
+        L.wp = (L.W + 31) / 32 + 1;
+        L.cs = (long long)L.H * L.P;
+        L.bits = (uint32_t*)ws.take((size_t)L.H * L.wp * 4);
+        L.xa = (float*)ws.take((size_t)nch * L.cs * 4);
+        L.xb = (float*)ws.take((size_t)nch * L.cs * 4);
+        L.b = (float*)ws.take((size_t)nch * L.cs * 4);
+        L.nbx = tile_count(L.W, 32, kOv);
+        L.nby = tile_count(L.H, 32, kOv);
+    }
+    for (int i = 0; i < kNumF64; ++i) f64[i] = (double*)ws.take(n64 * 8);
+    maxparts_ = maxparts;
+    partials = (double*)ws.take((size_t)kSlots * maxparts * nch * 8);
+    scal = (double*)ws.take((size_t)kSlots * 4 * 8);
+    tickets = (unsigned*)ws.take((size_t)kSlots * 4);
+    counters = (unsigned long long*)ws.take(64 * 8);
+    cudaMemsetAsync(tickets, 0, (size_t)kSlots * 4, stream);
+    cudaMemsetAsync(counters, 0, 64 * 8, stream);
+    cudaMemsetAsync(scal, 0, (size_t)kSlots * 4 * 8, stream);
+    // zero-fill mask padding words once per setup
+    for (int l = 0; l < nl; ++l) cudaMemsetAsync(lev[l].bits, 0, (size_t)lev[l].H * lev[l].wp * 4, stream);
+    mask_key_valid = false;
+    return cuda_check(cudaGetLastError(), "workspace setup");
+}
+
+GridReduce Ctx::reducer(int slot, int nparts) const {
+    GridReduce r;
+    r.partials = partials + (size_t)slot * maxparts_ * nch;
+    r.out = scal + slot * 4;
+    r.ticket = tickets + slot;
+    r.nparts = nparts;
+    r.nch = nch;
+    return r;
+}
+
+LevelArr Ctx::arr(int l) const {
+    LevelArr a;
+    a.H = lev[l].H;
+    a.W = lev[l].W;
+    a.pitch = lev[l].P;
+    a.cs = lev[l].cs;
+    return a;
+}
+
+MaskView Ctx::mview(int l) const {
+    MaskView m;
+    m.bits = lev[l].bits;
+    m.H = lev[l].H;
+    m.W = lev[l].W;
+    m.wpitch = lev[l].wp;
+    return m;
+}
+
+// Builds the coarse masks from the level-0 bits (any-of-4, Sec. 3.3).
+void Ctx::build_mask_pyramid() {
+    for (int l = 0; l + 1 < nlev; ++l) {
+        const Level& C = lev[l + 1];
+        dim3 blk(64), grd((C.wp + 63) / 64, C.H);
+        k_restrict_mask<<<grd, blk, 0, stream>>>(mview(l), C.bits, C.H, C.W, C.wp);
+    }
+}
+
+// ---------------------------------------------------------- multigrid ---
+
+void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rnorm2, bool coarsest,
+               unsigned long long* iters) {
+    const Level& L = lev[l];
+    OrasArgs a;
+    a.m = mview(l);
+    a.H = L.H;
+    a.W = L.W;
+    a.pitch = L.P;
+    a.cstride = L.cs;
+    a.nch = nch;
+    a.nbx = L.nbx;
+    a.nby = L.nby;
+    a.stride = 32 - kOv;
+    a.ov = kOv;
+    a.theta = (float)p.oras_theta;
+    a.maxit = coarsest ? (int)p.coarse_max_local : (int)p.oras_max_local;
+    a.thresh_scale = coarsest ? p.coarse_eta : p.oras_eta / (double)(L.nbx * L.nby);
+    a.xin = xin;
+    a.xout = xout;
+    a.b = L.b;
+    a.rnorm2 = rnorm2;
+    a.iters = iters;
+    const int warps = L.nbx * L.nby * nch;
+    const int blocks = (warps + 3) / 4;
+    if (zero) k_oras<true><<<blocks, 128, 0, stream>>>(a);
+    else k_oras<false><<<blocks, 128, 0, stream>>>(a);
+}
+
+static dim3 tiles_of(const Level& L, int nch) { return dim3((L.W + PT_W - 1) / PT_W, (L.H + PT_H - 1) / PT_H, nch); }
+
+// One V-cycle (Sec. 3.2) on the correction equation A_l x = b_l, x from 0.
+// Result in lev[l].xa.
+void Ctx::vcycle(int l) {
+    Level& L = lev[l];
+    const double* pre_norm = (l == 0) ? scal + kSlotR64 * 4 : scal + l * 4;
+    unsigned long long* it = (l == 0) ? counters + kCntLocal : nullptr;
+    if (l == nlev - 1) {
+        oras(l, true, nullptr, L.xa, pre_norm, true, it);
+        return;
+    }
+    oras(l, true, nullptr, L.xa, pre_norm, false, it);
+    Level& C = lev[l + 1];
+    {
+        dim3 blk(32, 8), grd((C.W + 31) / 32, (C.H + 7) / 8, nch);
+        k_restrict_residual<<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, arr(l + 1), mview(l + 1), C.b,
+                                                     reducer(l + 1, grd.x * grd.y));
+    }
+    vcycle(l + 1);
+    {
+        dim3 grd = tiles_of(L, nch), blk(PT_W, PT_H);
+        k_prolong<0><<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, L.xb, arr(l + 1), C.xa,
+                                              reducer(l, grd.x * grd.y));
+    }
+    oras(l, false, L.xb, L.xa, scal + l * 4, false, it);
+    ++vcycles_run;
+}
+
+// Reduced full multigrid (Sec. 3.2, Fig. "multigrid_reduced"): data pyramid,
+// coarsest solve, then one ORAS sweep per finer level after prolongation.
+// `d` is the level-0 Dirichlet data in FP64. Result (FP32) in lev[0].xa.
+void Ctx::fmg(const double* d) {
+    {
+        dim3 grd((W + 127) / 128, H, nch);
+        k_data_to_f32<<<grd, 128, 0, stream>>>(d, arr(0), mview(0), lev[0].b);
+    }
+    for (int l = 1; l < nlev; ++l) {
+        dim3 blk(32, 8), grd((lev[l].W + 31) / 32, (lev[l].H + 7) / 8, nch);
+        k_restrict_data<<<grd, blk, 0, stream>>>(arr(l - 1), mview(l - 1), lev[l - 1].b, arr(l), lev[l].b);
+    }
+    const int L = nlev - 1;
+    {
+        dim3 grd = tiles_of(lev[L], nch), blk(PT_W, PT_H);
+        k_prolong<2><<<grd, blk, 0, stream>>>(arr(L), mview(L), nullptr, lev[L].b, lev[L].xb, arr(L), nullptr,
+                                              reducer(L, grd.x * grd.y));
+        oras(L, false, lev[L].xb, lev[L].xa, scal + L * 4, true, nullptr);
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        dim3 grd = tiles_of(lev[l], nch), blk(PT_W, PT_H);
+        k_prolong<1><<<grd, blk, 0, stream>>>(arr(l), mview(l), nullptr, lev[l].b, lev[l].xb, arr(l + 1),
+                                              lev[l + 1].xa, reducer(l, grd.x * grd.y));
+        oras(l, false, lev[l].xb, lev[l].xa, scal + l * 4, l == L, l == 0 ? counters + kCntLocal : nullptr);
+    }
+}
+
+template <int RHS, int INIT>
+static void launch_res64(Ctx& c, const double* uin, double* uout, const float* x32, const double* d, const double* y,
+                         bool want_b) {
+    Res64Args a;
+    a.F = c.arr(0);
+    a.m = c.mview(0);
+    a.uin = uin;
+    a.uout = uout;
+    a.x32 = x32;
+    a.d = d;
+    a.y = y;
+    a.r32 = c.lev[0].b;
+    dim3 grd = tiles_of(c.lev[0], c.nch), blk(PT_W, PT_H);
+    a.red_r = c.reducer(kSlotR64, grd.x * grd.y);
+    a.red_b = c.reducer(kSlotB64, grd.x * grd.y);
+    a.want_b = want_b ? 1 : 0;
+    k_residual64<RHS, INIT><<<grd, blk, 0, c.stream>>>(a);
+}
+
+void Ctx::residual64(int rhs, int init, const double* uin, double* uout, const float* x32, const double* d,
+                     const double* y, bool want_b) {
+#define HDI_R64(R, I) \
+    if (rhs == R && init == I) { launch_res64<R, I>(*this, uin, uout, x32, d, y, want_b); return; }
+    HDI_R64(RHS_DATA, INIT_KEEP) HDI_R64(RHS_DATA, INIT_UPDATE) HDI_R64(RHS_DATA, INIT_FROM32)
+    HDI_R64(RHS_DATA, INIT_ZERO) HDI_R64(RHS_SOURCE, INIT_KEEP) HDI_R64(RHS_SOURCE, INIT_UPDATE)
+    HDI_R64(RHS_SOURCE, INIT_FROM32) HDI_R64(RHS_SOURCE, INIT_ZERO)
+#undef HDI_R64
+}
+
+// Solves A u = b on level 0 with iterative refinement in FP64 (pattern:
+// FP32 V-cycles on the correction, FP64 residual and update).
+//   spec.u[0/1]  : ping-pong FP64 buffers; spec.cur selects the one holding
+//                  the iterate on entry (warm) and receives it on exit.
+//   spec.rhs     : RHS_DATA (b = C d) or RHS_SOURCE (b = (I-C)(d - y)).
+//   spec.start   : START_FMG, START_WARM (iterate in u[cur]) or START_ZERO.
+//   spec.tol     : relative residual per channel; spec.bnorm2 receives ||b||^2.
+int Ctx::solve(SolveSpec& s) {
+    int rc;
+    double* ub[2] = {s.u[0], s.u[1]};
+    int cur = s.cur;
+    if (s.start == START_FMG) {
+        fmg(s.d);
+        residual64(s.rhs, INIT_FROM32, nullptr, ub[cur], lev[0].xa, s.d, s.y, true);
+    } else if (s.start == START_WARM) {
+        residual64(s.rhs, INIT_KEEP, ub[cur], ub[1 - cur], nullptr, s.d, s.y, true);
+        cur = 1 - cur;
+    } else {
+        residual64(s.rhs, INIT_ZERO, nullptr, ub[cur], nullptr, s.d, s.y, true);
+    }
+    double r2[4], b2[4];
+    s.iterations = 0;
+    for (;;) {
+        cudaMemcpyAsync(hscal, scal + kSlotR64 * 4, 4 * 8, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(hscal + 4, scal + kSlotB64 * 4, 4 * 8, cudaMemcpyDeviceToHost, stream);
+        if ((rc = sync("inpainting residual"))) return rc;
+        double worst = 0.0;
+        for (int c = 0; c < nch; ++c) {
+            r2[c] = hscal[c];
+            b2[c] = hscal[4 + c];
+            if (!std::isfinite(r2[c])) {
+                s.cur = cur;
+                return fail(HDI_ERR_NONFINITE, "non-finite residual in channel %d", c);
+            }
+            const double rel = b2[c] > 0 ? std::sqrt(r2[c] / b2[c]) : (r2[c] > 0 ? INFINITY : 0.0);
+            s.rel[c] = rel;
+            worst = std::max(worst, rel);
+        }
+        s.rel_max = worst;
+        for (int c = 0; c < nch; ++c) s.bnorm2[c] = b2[c];
+        if (worst <= s.tol) break;
+        if (s.iterations >= s.max_iter) {
+            s.cur = cur;
+            return HDI_ERR_NOT_CONVERGED;
+        }
+        vcycle(0);
+        residual64(s.rhs, INIT_UPDATE, ub[cur], ub[1 - cur], lev[0].xa, s.d, s.y, false);
+        cur = 1 - cur;
+        ++s.iterations;
+        // ||b||^2 is unchanged; keep the slot value from the first evaluation.
+    }
+    s.cur = cur;
+    return HDI_OK;
+}
+
+// --------------------------------------------------------- input checks ---
+
+int Ctx::check_image(const hdi_image* im, const char* name, int H_, int W_, int nch_) {
+    if (!im || !im->data) return fail(HDI_ERR_INVALID_ARG, "%s: null image", name);
+    if (im->dtype != HDI_F32 && im->dtype != HDI_F64) return fail(HDI_ERR_INVALID_ARG, "%s: bad dtype", name);
+    if (im->location != HDI_DEVICE && im->location != HDI_HOST)
+        return fail(HDI_ERR_INVALID_ARG, "%s: bad location", name);
+    if (im->height <= 0 || im->width <= 0 || im->channels <= 0 || im->channels > 4)
+        return fail(HDI_ERR_INVALID_ARG, "%s: bad shape %dx%dx%d (1..4 channels)", name, im->height, im->width,
+                    im->channels);
+    if (H_ >= 0 && (im->height != H_ || im->width != W_ || im->channels != nch_))
+        return fail(HDI_ERR_INVALID_ARG, "%s: shape %dx%dx%d does not match %dx%dx%d", name, im->height, im->width,
+                    im->channels, H_, W_, nch_);
+    if (im->row_stride < im->width || (im->channels > 1 && im->channel_stride < im->row_stride * im->height))
+        return fail(HDI_ERR_INVALID_ARG, "%s: strides too small", name);
+    return HDI_OK;
+}
+
+// Copies a caller image into the internal FP64 layout (device or host source).
+int Ctx::load_image(const hdi_image* im, double* dst) {
+    const void* src = im->data;
+    long long rs = im->row_stride, cs = im->channel_stride;
+    const size_t es = im->dtype == HDI_F64 ? 8 : 4;
+    if (im->location == HDI_HOST) {
+        const size_t n = (size_t)nch * H * W * es;
+        int rc = stage.reserve(*this, std::max(stage.cap, n + (size_t)H * W + 1024), "staging buffer");
+        if (rc) return rc;
+        char* st = (char*)stage.base;
+        for (int c = 0; c < nch; ++c) {
+            cudaError_t e = cudaMemcpy2DAsync(st + (size_t)c * H * W * es, W * es,
+                                              (const char*)src + (size_t)c * cs * es, rs * es, W * es, H,
+                                              cudaMemcpyHostToDevice, stream);
+            if (e != cudaSuccess) return cuda_check(e, "host-to-device copy");
+        }
+        src = st;
+        rs = W;
+        cs = (long long)H * W;
+    }
+    cudaMemsetAsync(flags, 0, 4, stream);
+    dim3 grd((W + 127) / 128, H, nch);
+    if (im->dtype == HDI_F64)
+        k_load_image<double><<<grd, 128, 0, stream>>>((const double*)src, rs, cs, arr(0), dst, flags);
+    else
+        k_load_image<float><<<grd, 128, 0, stream>>>((const float*)src, rs, cs, arr(0), dst, flags);
+    unsigned bad = 0;
+    cudaMemcpyAsync(&bad, flags, 4, cudaMemcpyDeviceToHost, stream);
+    int rc = sync("image upload");
+    if (rc) return rc;
+    if (bad) return fail(HDI_ERR_NONFINITE, "non-finite value in input image");
+    return HDI_OK;
+}
+
+int Ctx::store_image(const double* src, hdi_image* im, bool zero_off_mask) {
+    void* dst = im->data;
+    long long rs = im->row_stride, cs = im->channel_stride;
+    const size_t es = im->dtype == HDI_F64 ? 8 : 4;
+    const bool host = im->location == HDI_HOST;
+    if (host) {
+        const size_t n = (size_t)nch * H * W * es;
+        int rc = stage.reserve(*this, std::max(stage.cap, n + (size_t)H * W + 1024), "staging buffer");
+        if (rc) return rc;
+        dst = stage.base;
+        rs = W;
+        cs = (long long)H * W;
+    }
+    dim3 grd((W + 127) / 128, H, nch);
+    if (im->dtype == HDI_F64)
+        k_store_image<double><<<grd, 128, 0, stream>>>(src, arr(0), mview(0), zero_off_mask, (double*)dst, rs, cs);
+    else
+        k_store_image<float><<<grd, 128, 0, stream>>>(src, arr(0), mview(0), zero_off_mask, (float*)dst, rs, cs);
+    if (host) {
+        for (int c = 0; c < nch; ++c) {
+            cudaError_t e = cudaMemcpy2DAsync((char*)im->data + (size_t)c * im->channel_stride * es,
+                                              im->row_stride * es, (const char*)dst + (size_t)c * H * W * es, W * es,
+                                              W * es, H, cudaMemcpyDeviceToHost, stream);
+            if (e != cudaSuccess) return cuda_check(e, "device-to-host copy");
+        }
+    }
+    return sync("image download");
+}
+
+// Uploads and bit-packs the mask, builds the mask pyramid; returns the number
+// of known pixels in *ones.
+int Ctx::load_mask(const hdi_mask* m, long long* ones) {
+    if (!m || !m->data) return fail(HDI_ERR_INVALID_ARG, "mask: null");
+    if (m->height != H || m->width != W) return fail(HDI_ERR_INVALID_ARG, "mask: shape does not match the image");
+    if (m->row_stride < m->width) return fail(HDI_ERR_INVALID_ARG, "mask: row stride too small");
+    if (m->location != HDI_DEVICE && m->location != HDI_HOST) return fail(HDI_ERR_INVALID_ARG, "mask: bad location");
+    const uint8_t* src = m->data;
+    long long rs = m->row_stride;
+    if (m->location == HDI_HOST) {
+        const size_t need = (size_t)nch * H * W * 8 + (size_t)H * W + 1024;
+        int rc = stage.reserve(*this, std::max(stage.cap, need), "staging buffer");
+        if (rc) return rc;
+        uint8_t* st = (uint8_t*)stage.base + (size_t)nch * H * W * 8;
+        cudaError_t e = cudaMemcpy2DAsync(st, W, m->data, m->row_stride, W, H, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_check(e, "mask upload");
+        src = st;
+        rs = W;
+    }
+    cudaMemsetAsync(counters + kCntOnes, 0, 8, stream);
+    cudaMemsetAsync(flags, 0, 4, stream);
+    const Level& L = lev[0];
+    dim3 grd((L.wp + 63) / 64, H);
+    k_pack_mask<<<grd, 64, 0, stream>>>(src, rs, H, W, L.bits, L.wp, counters + kCntOnes, flags);
+    build_mask_pyramid();
+    unsigned long long cnt = 0;
+    unsigned bad = 0;
+    cudaMemcpyAsync(&cnt, counters + kCntOnes, 8, cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(&bad, flags, 4, cudaMemcpyDeviceToHost, stream);
+    int rc = sync("mask upload");
+    if (rc) return rc;
+    if (bad) return fail(HDI_ERR_INVALID_ARG, "mask: values must be 0 or 1");
+    *ones = (long long)cnt;
+    mask_ones = (long long)cnt;
+    return HDI_OK;
+}
+
+// ------------------------------------------------------------ C ABI ---
+
+extern "C" {
+
+int hdi_create(hdi_ctx** out, int device, void* stream) {
+    if (!out) return HDI_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return HDI_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return HDI_ERR_CUDA;
+    Ctx* c = new Ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    if (cudaMallocHost(&c->hscal, 64 * 8) != cudaSuccess) {
+        delete c;
+        return HDI_ERR_CUDA;
+    }
+    if (cudaMalloc(&c->flags, 256) != cudaSuccess) {
+        cudaFreeHost(c->hscal);
+        delete c;
+        return HDI_ERR_CUDA;
+    }
+    *out = reinterpret_cast<hdi_ctx*>(c);
+    return HDI_OK;
+}
+
+int hdi_destroy(hdi_ctx* h) {
+    if (!h) return HDI_OK;
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    c->ws.release();
+    c->tws.release();
+    c->dws.release();
+    c->stage.release();
+    if (c->flags) cudaFree(c->flags);
+    if (c->hscal) cudaFreeHost(c->hscal);
+    delete c;
+    return HDI_OK;
+}
+
+int hdi_set_param(hdi_ctx* h, const char* name, double v) {
+    if (!h || !name) return HDI_ERR_INVALID_ARG;
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    for (const auto& d : kParams) {
+        if (!strcmp(d.name, name)) {
+            if (!(v >= d.lo && v <= d.hi))
+                return c->fail(HDI_ERR_INVALID_ARG, "%s=%g outside [%g, %g]", name, v, d.lo, d.hi);
+            c->p.*(d.field) = v;
+            return HDI_OK;
+        }
+    }
+    return c->fail(HDI_ERR_INVALID_ARG, "unknown parameter '%s'", name);
+}
+
+int hdi_get_param(const hdi_ctx* h, const char* name, double* v) {
+    if (!h || !name || !v) return HDI_ERR_INVALID_ARG;
+    const Ctx* c = reinterpret_cast<const Ctx*>(h);
+    for (const auto& d : kParams) {
+        if (!strcmp(d.name, name)) {
+            *v = c->p.*(d.field);
+            return HDI_OK;
+        }
+    }
+    return HDI_ERR_INVALID_ARG;
+}
+
+const char* hdi_last_error(const hdi_ctx* h) {
+    if (!h) return "null context";
+    return reinterpret_cast<const Ctx*>(h)->err.c_str();
+}
+
+const char* hdi_version(void) { return "hdi 0.1 (sm_103a)"; }
+
+int hdi_inpaint(hdi_ctx* h, const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,
+                hdi_stats* st) {
+    if (!h) return HDI_ERR_INVALID_ARG;
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    auto t0 = std::chrono::steady_clock::now();
+    c->err.clear();
+    int rc = c->inpaint(f, mask, u0, u, tol, st);
+    if (st) {
+        st->status = rc;
+        st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return rc;
+}
+
+int hdi_tonal_opt(hdi_ctx* h, const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hdi_image* g,
+                  double tol, hdi_stats* st) {
+    if (!h) return HDI_ERR_INVALID_ARG;
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    auto t0 = std::chrono::steady_clock::now();
+    c->err.clear();
+    int rc = c->tonal(f, mask, g0, g, tol, st);
+    if (st) {
+        st->status = rc;
+        st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return rc;
+}
+
+int hdi_densify_step(hdi_ctx* h, const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t k, uint64_t seed,
+                     int64_t* added) {
+    if (!h) return HDI_ERR_INVALID_ARG;
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    c->err.clear();
+    return c->densify(f, mask, u, k, seed, added);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ inpaint ---
+
+int Ctx::inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,
+                 hdi_stats* st) {
+    int rc;
+    if ((rc = cuda_check(cudaSetDevice(device), "cudaSetDevice"))) return rc;
+    if ((rc = check_image(f, "f", -1, 0, 0))) return rc;
+    if ((rc = check_image(u, "u", f->height, f->width, f->channels))) return rc;
+    if (u->dtype != f->dtype) return fail(HDI_ERR_INVALID_ARG, "u: dtype differs from f");
+    if (u0 && (rc = check_image(u0, "u0", f->height, f->width, f->channels))) return rc;
+    if (!(tol > 0.0 && tol < 1.0)) return fail(HDI_ERR_INVALID_ARG, "tol must lie in (0, 1)");
+    if ((rc = setup(f->height, f->width, f->channels))) return rc;
+    long long ones = 0;
+    if ((rc = load_mask(mask, &ones))) return rc;
+    if (ones == 0) return fail(HDI_ERR_EMPTY_MASK, "empty mask: A is singular");
+    double* F = f64[kF];
+    if ((rc = load_image(f, F))) return rc;
+    SolveSpec s;
+    s.u[0] = f64[kU0];
+    s.u[1] = f64[kU1];
+    s.cur = 0;
+    s.rhs = RHS_DATA;
+    s.d = F;
+    s.y = nullptr;
+    s.tol = tol;
+    s.max_iter = (int)p.max_vcycles;
+    if (u0) {
+        if ((rc = load_image(u0, s.u[0]))) return rc;
+        s.start = START_WARM;
+    } else {
+        s.start = START_FMG;
+    }
+    vcycles_run = 0;
+    cudaMemsetAsync(counters + kCntLocal, 0, 8, stream);
+    const int src = solve(s);
+    if (src != HDI_OK && src != HDI_ERR_NOT_CONVERGED) return src;
+    if ((rc = store_image(s.u[s.cur], u, false))) return rc;
+    if (st) {
+        unsigned long long li = 0;
+        cudaMemcpy(&li, counters + kCntLocal, 8, cudaMemcpyDeviceToHost);
+        st->iterations = s.iterations;
+        st->vcycles = vcycles_run;
+        st->local_iters = (int64_t)li;
+        st->rel_res = s.rel_max;
+        st->mse = 0.0;
+    }
+    if (src == HDI_ERR_NOT_CONVERGED)
+        return fail(HDI_ERR_NOT_CONVERGED, "inpainting: relative residual %.3e after %d refinement steps", s.rel_max,
+                    s.iterations);
+    return HDI_OK;
+}

@@ -1,0 +1,123 @@
+// solver.h -- host-side context of libhdi: parameters, workspace arenas,
+// multigrid hierarchy and the solver drivers' declarations.
+#pragma once
+#include <cstdarg>
+#include <string>
+#include <cuda_runtime.h>
+#include "../../include/hdi.h"
+#include "common.cuh"
+#include "stencil.cuh"
+
+struct Params {
+    double oras_theta = 0.3;        // Robin weight (Sec. 3.1)
+    double oras_eta = 1e-3;         // local stop fraction (Sec. 3.3)
+    double oras_max_local = 48;
+    double coarse_eta = 1e-8;
+    double coarse_max_local = 600;
+    double max_vcycles = 60;
+    double tonal_max_iter = 400;
+    double tonal_inner_ratio = 0.05;
+    double tonal_echo_rtol = 1e-4;
+    double tonal_echo_max_iter = 300;
+    double hbm_budget_gb = 200.0;
+};
+
+struct Level {
+    int H = 0, W = 0, P = 0, wp = 0;
+    long long cs = 0;
+    uint32_t* bits = nullptr;
+    float* xa = nullptr;
+    float* xb = nullptr;
+    float* b = nullptr;
+    int nbx = 0, nby = 0;
+};
+
+struct Ctx;
+
+// One cudaMalloc'd block carved into 256-byte aligned pieces.
+struct Arena {
+    void* base = nullptr;
+    size_t cap = 0, used = 0;
+    int reserve(Ctx& c, size_t bytes, const char* what);
+    void* take(size_t bytes);
+    void release();
+};
+
+enum { START_FMG = 0, START_WARM = 1, START_ZERO = 2 };
+
+struct SolveSpec {
+    double* u[2];
+    int cur = 0;
+    int rhs = 0;
+    const double* d = nullptr;
+    const double* y = nullptr;
+    int start = START_FMG;
+    double tol = 1e-6;
+    int max_iter = 60;
+    int iterations = 0;
+    double rel[4] = {0, 0, 0, 0};
+    double rel_max = 0;
+    double bnorm2[4] = {0, 0, 0, 0};
+};
+
+constexpr int kMaxLevels = 16;
+constexpr int kOv = 6;            // overlap of the 32x32 subdomains (Sec. 3.3)
+constexpr int kSlots = 32;        // reduction slots
+constexpr int kSlotR64 = 16;      // ||r||^2 of the FP64 residual
+constexpr int kSlotB64 = 17;      // ||b||^2 of the FP64 residual
+constexpr int kSlotTonalR = 18;   // ||B^T(f - Bg)||^2
+constexpr int kSlotTonalE = 19;   // ||f - Bg||^2
+constexpr int kCntOnes = 0;
+constexpr int kCntLocal = 1;
+// FP64 vectors of level-0 size
+enum { kF = 0, kU0, kU1, kG, kY0, kY1, kW0, kW1, kR, kNumF64 };
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Params p;
+    std::string err;
+    Arena ws;      // multigrid + FP64 vectors
+    Arena tws;     // tonal local factors
+    Arena dws;     // densification
+    Arena stage;   // host staging
+    int H = 0, W = 0, nch = 0, nlev = 0;
+    Level lev[kMaxLevels];
+    double* f64[kNumF64] = {};
+    double* partials = nullptr;
+    double* scal = nullptr;
+    unsigned* tickets = nullptr;
+    unsigned long long* counters = nullptr;
+    unsigned* flags = nullptr;
+    double* hscal = nullptr;   // pinned host mirror
+    int maxparts_ = 1;
+    bool mask_key_valid = false;
+    long long mask_ones = 0;
+    int vcycles_run = 0;
+
+    int fail(int code, const char* fmt, ...);
+    int cuda_check(cudaError_t e, const char* what);
+    int sync(const char* what);
+    size_t other_bytes() const;
+    int setup(int H, int W, int nch);
+    GridReduce reducer(int slot, int nparts) const;
+    LevelArr arr(int l) const;
+    MaskView mview(int l) const;
+    void build_mask_pyramid();
+    void oras(int l, bool zero, const float* xin, float* xout, const double* rnorm2, bool coarsest,
+              unsigned long long* iters);
+    void vcycle(int l);
+    void fmg(const double* d);
+    void residual64(int rhs, int init, const double* uin, double* uout, const float* x32, const double* d,
+                    const double* y, bool want_b);
+    int solve(SolveSpec& s);
+    int check_image(const hdi_image* im, const char* name, int H, int W, int nch);
+    int load_image(const hdi_image* im, double* dst);
+    int store_image(const double* src, hdi_image* im, bool zero_off_mask);
+    int load_mask(const hdi_mask* m, long long* ones);
+    int inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,
+                hdi_stats* st);
+    int tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hdi_image* g, double tol,
+              hdi_stats* st);
+    int densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t k, uint64_t seed, int64_t* added);
+};

@@ -165,7 +165,8 @@ __device__ __forceinline__ float prolong_at(const float* __restrict__ e, const L
 #define PT_H 8
 
 // MODE 0 (V-cycle): xout = xin + P e on unknown pixels, xin on known ones;
-// MODE 1 (FMG):     xout = b on known pixels, P e on unknown ones.
+// MODE 1 (FMG):     xout = b on known pixels, P e on unknown ones;
+// MODE 2 (start):   xout = b on known pixels, 0 on unknown ones (e unused).
 // Then ||b - A xout||^2 per channel (the next sweep's local stop rule).
 template <int MODE>
 __global__ void __launch_bounds__(PT_W * PT_H) k_prolong(LevelArr F, MaskView fm, const float* __restrict__ xin,
@@ -174,9 +175,9 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_prolong(LevelArr F, MaskView fm
     __shared__ float t[PT_H + 2][PT_W + 2];
     const int ch = blockIdx.z;
     const int bx0 = blockIdx.x * PT_W, by0 = blockIdx.y * PT_H;
-    const float* xc = xin + ch * F.cs;
+    const float* xc = (MODE == 0) ? xin + ch * F.cs : nullptr;
     const float* bc = b + ch * F.cs;
-    const float* ec = e + ch * C.cs;
+    const float* ec = (MODE == 2) ? nullptr : e + ch * C.cs;
     for (int i = threadIdx.y * PT_W + threadIdx.x; i < (PT_W + 2) * (PT_H + 2); i += PT_W * PT_H) {
         const int ty = i / (PT_W + 2), tx = i - ty * (PT_W + 2);
         const int px = min(max(bx0 + tx - 1, 0), F.W - 1);
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_prolong(LevelArr F, MaskView fm
         const size_t idx = (size_t)py * F.pitch + px;
         float v;
         if (fm.known(px, py)) v = (MODE == 0) ? xc[idx] : bc[idx];
+        else if (MODE == 2) v = 0.f;
         else v = (MODE == 0 ? xc[idx] : 0.f) + prolong_at(ec, C, px, py);
         t[ty][tx] = v;
     }

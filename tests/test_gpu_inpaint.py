@@ -1,0 +1,99 @@
+"""Parity of the CUDA inpainting path (multigrid ORAS, FP64 refinement)
+against the FP64 oracle, called through the C ABI."""
+
+import numpy as np
+import pytest
+
+from gpu_util import torch, need_gpu, ctx, dev
+from oracle import inpaint as inpaint_ref, rel_residual
+from synthdata import synth_image, synth_rgb, random_mask
+
+pytestmark = pytest.mark.gpu
+
+
+def run(f, c, tol, u0=None, **params):
+    need_gpu()
+    k = ctx(**params)
+    fd, cd = dev(f), dev(c)
+    out = torch.empty_like(fd)
+    st = k.inpaint(fd, cd, out, u0=None if u0 is None else dev(u0), tol=tol)
+    return out.cpu().numpy(), st
+
+
+def test_c1_256_gray_fp64_tight():
+    """256x256 grey FP64, 4% mask, relative residual 1e-10."""
+    f = synth_image(256, 256, 0)
+    c = random_mask(256, 256, 0.04, 1000)
+    u, st = run(f, c, 1e-10)
+    ref = inpaint_ref(f, c)
+    assert st["rel_res"] <= 1e-10
+    assert rel_residual(u, f, c)[0] <= 1e-10
+    assert np.abs(u - ref).max() <= 1e-6
+    assert st["iterations"] <= 12
+
+
+@pytest.mark.parametrize("H,W,d,seed", [(77, 131, 0.04, 1), (300, 200, 0.1, 2), (33, 33, 0.02, 3),
+                                        (1, 40, 0.1, 4), (41, 1, 0.1, 5), (70, 3, 0.05, 6),
+                                        (520, 97, 0.01, 7)])
+def test_ragged_rgb_fp32(H, W, d, seed):
+    """Ragged sizes spanning several subdomains and a partial last tile."""
+    f = synth_rgb(H, W, seeds=(seed, seed + 10, seed + 20), dtype=np.float32)
+    c = random_mask(H, W, d, seed + 100)
+    u, st = run(f, c, 1e-6)
+    ref = inpaint_ref(f.astype(np.float64), c)
+    assert st["rel_res"] <= 1e-6
+    assert rel_residual(u.astype(np.float64), f.astype(np.float64), c).max() <= 1.5e-6
+    assert np.abs(u - ref).max() <= 1e-3
+
+
+def test_full_mask_and_single_pixel():
+    f = synth_image(40, 50, 9)
+    u, _ = run(f, np.ones((40, 50), np.uint8), 1e-8)
+    np.testing.assert_array_equal(u, f)
+    c = np.zeros((40, 50), np.uint8)
+    c[17, 33] = 1
+    u, _ = run(f, c, 1e-9)
+    assert np.abs(u - f[17, 33]).max() <= 1e-6
+
+
+def test_warm_start_and_host_buffers():
+    need_gpu()
+    f = synth_rgb(96, 128, dtype=np.float32)
+    c = random_mask(96, 128, 0.05, 11)
+    ref = inpaint_ref(f.astype(np.float64), c)
+    k = ctx()
+    out = np.empty_like(f)
+    st = k.inpaint(f, c, out, tol=1e-6)          # host buffers
+    assert np.abs(out - ref).max() <= 1e-3
+    out2 = np.empty_like(f)
+    st2 = k.inpaint(f, c, out2, u0=out, tol=1e-6)
+    assert st2["iterations"] <= 1 and np.abs(out2 - ref).max() <= 1e-3
+
+
+def test_determinism():
+    f = synth_rgb(130, 90, dtype=np.float32)
+    c = random_mask(130, 90, 0.04, 12)
+    u1, _ = run(f, c, 1e-6)
+    u2, _ = run(f, c, 1e-6)
+    np.testing.assert_array_equal(u1, u2)
+
+
+def test_errors():
+    need_gpu()
+    import paper_2401_06747_b300 as hdi
+    k = ctx()
+    f = dev(synth_image(20, 20, 1))
+    out = torch.empty_like(f)
+    with pytest.raises(hdi.HdiError) as e:
+        k.inpaint(f, dev(np.zeros((20, 20), np.uint8)), out)
+    assert e.value.code == -2
+    bad = np.zeros((20, 20), np.uint8)
+    bad[3, 3] = 2
+    with pytest.raises(hdi.HdiError) as e:
+        k.inpaint(f, dev(bad), out)
+    assert e.value.code == -1
+    fn = f.clone()
+    fn[2, 2] = float("nan")
+    with pytest.raises(hdi.HdiError) as e:
+        k.inpaint(fn, dev(random_mask(20, 20, 0.1, 1)), out)
+    assert e.value.code == -6
