@@ -125,13 +125,13 @@ int Ctx::setup(int H_, int W_, int nch_) {
         const int P = round_up(sizes[l].second, 32);
         const int wp = (sizes[l].second + 31) / 32 + 1;
         acc((size_t)sizes[l].first * wp * 4);            // bits
-        acc((size_t)nch_ * sizes[l].first * P * 4 * 3);   // xa, xb, b
+        for (int k = 0; k < 3; ++k) acc((size_t)nch_ * sizes[l].first * P * 4);   // xa, xb, b
         const int parts = ((sizes[l].second + 31) / 32) * ((sizes[l].first + 7) / 8);
         maxparts = std::max(maxparts, parts);
     }
     const int P0 = round_up(W_, 32);
     const size_t n64 = (size_t)nch_ * H_ * P0;
-    acc(n64 * 8 * kNumF64);                                   // FP64 vectors
+    for (int k = 0; k < kNumF64; ++k) acc(n64 * 8);           // FP64 vectors
     acc((size_t)kSlots * maxparts * nch_ * 8);                // reduction partials
     acc((size_t)kSlots * 4 * 8);                              // reduction outputs
     acc((size_t)kSlots * 4);                                  // tickets
@@ -159,6 +159,10 @@ int Ctx::setup(int H_, int W_, int nch_) {
     scal = (double*)ws.take((size_t)kSlots * 4 * 8);
     tickets = (unsigned*)ws.take((size_t)kSlots * 4);
     counters = (unsigned long long*)ws.take(64 * 8);
+    if (ws.used > ws.cap) {
+        H = W = nch = 0;
+        return fail(HDI_ERR_CUDA, "internal: workspace carving exceeds its reservation");
+    }
     cudaMemsetAsync(tickets, 0, (size_t)kSlots * 4, stream);
     cudaMemsetAsync(counters, 0, 64 * 8, stream);
     cudaMemsetAsync(scal, 0, (size_t)kSlots * 4 * 8, stream);
