@@ -249,6 +249,7 @@ void Ctx::vcycle(int l) {
     unsigned long long* it = (l == 0) ? counters + kCntLocal : nullptr;
     if (l == nlev - 1) {
         oras(l, true, nullptr, L.xa, pre_norm, true, it);
+        if (l == 0) ++vcycles_run;
         return;
     }
     oras(l, true, nullptr, L.xa, pre_norm, false, it);
@@ -265,7 +266,7 @@ void Ctx::vcycle(int l) {
                                               reducer(l, grd.x * grd.y));
     }
     oras(l, false, L.xb, L.xa, scal + l * 4, false, it);
-    ++vcycles_run;
+    if (l == 0) ++vcycles_run;
 }
 
 // Reduced full multigrid (Sec. 3.2, Fig. "multigrid_reduced"): data pyramid,

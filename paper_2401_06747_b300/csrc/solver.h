@@ -69,6 +69,7 @@ constexpr int kSlotTonalR = 18;   // ||B^T(f - Bg)||^2
 constexpr int kSlotTonalE = 19;   // ||f - Bg||^2
 constexpr int kCntOnes = 0;
 constexpr int kCntLocal = 1;
+constexpr int kCntEcho = 2;
 // FP64 vectors of level-0 size
 enum { kF = 0, kU0, kU1, kG, kY0, kY1, kW0, kW1, kR, kNumF64 };
 
@@ -94,6 +95,13 @@ struct Ctx {
     bool mask_key_valid = false;
     long long mask_ones = 0;
     int vcycles_run = 0;
+    // tonal local factors (valid for the mask of the current tonal call)
+    int* t_off = nullptr;
+    long long* t_goff = nullptr;
+    uint16_t* t_list = nullptr;
+    float* t_echo = nullptr;
+    float* t_fac = nullptr;
+    long long t_total = 0;
 
     int fail(int code, const char* fmt, ...);
     int cuda_check(cudaError_t e, const char* what);
@@ -115,6 +123,10 @@ struct Ctx {
     int load_image(const hdi_image* im, double* dst);
     int store_image(const double* src, hdi_image* im, bool zero_off_mask);
     int load_mask(const hdi_mask* m, long long* ones);
+    int read_slot(int slot, double* out);
+    int tonal_setup();
+    void tonal_residual(const double* y, const double* w, double* r);
+    void tonal_local(double* g);
     int inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,
                 hdi_stats* st);
     int tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hdi_image* g, double tol,

@@ -233,7 +233,7 @@ struct Res64Args {
     double* uout;         // FP64 iterate after the step
     const float* x32;     // INIT_UPDATE: correction e; INIT_FROM32: x
     const double* d;      // data (RHS_DATA) or minuend (RHS_SOURCE)
-    const double* y;      // subtrahend (RHS_SOURCE)
+    const double* y;      // subtrahend (RHS_SOURCE; nullptr = 0)
     float* r32;           // out: residual in FP32 (V-cycle right-hand side)
     GridReduce red_r;     // ||r||^2 per channel
     GridReduce red_b;     // ||b||^2 per channel (only if want_b)
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_residual64(Res64Args a) {
             bv = (RHS == RHS_DATA) ? a.d[idx] : 0.0;
             r = bv - v;
         } else {
-            bv = (RHS == RHS_DATA) ? 0.0 : (a.d[idx] - a.y[idx]);
+            bv = (RHS == RHS_DATA) ? 0.0 : (a.d[idx] - (a.y ? a.y[idx] : 0.0));
             double lap = 0.0;
             if (px > 0) lap += v - t[ty][tx - 1];
             if (px + 1 < a.F.W) lap += v - t[ty][tx + 1];

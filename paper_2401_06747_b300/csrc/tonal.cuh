@@ -1,5 +1,512 @@
-// tonal.cuh -- RAS tonal optimisation (Sec. 5.2, Alg. 2).
+// tonal.cuh -- tonal optimisation by restricted additive Schwarz on the
+// normal equations (Sec. 5.2, Alg. 2).
+//
+//   1. r = B^T (f - B g): y = B g solves A y = C g; w solves A w = (I-C)(f-y)
+//      (A~ acts on U as L_UU, Sec. 5.1); r_K = (f - y)_K + sum_{n in N(k) cap U} w_n.
+//      Both solves are warm-started from the previous outer iteration
+//      (Sec. 5.2, first paragraph after Alg. 2).
+//   2. For every 32x32 subdomain i (overlap 6, the ORAS tiling of level 0):
+//      B_i^T B_i v_i = R_i r with B_i the subdomain's inpainting operator under
+//      homogeneous Neumann conditions at the subdomain boundary (Sec. 5.2).
+//   3. g <- g + sum_i R_i^T D_i v_i, D_i = 1 / multiplicity ("simple
+//      averaging", Sec. 5.2).
+//
+// Local solves. The mask is fixed during tonal optimisation, so the local
+// matrices B_i^T B_i = I + S_i^T S_i (S_i = L_UU,i^{-1} L_UK,i, in the mask
+// pixel coordinates of the subdomain) are the same in every outer iteration.
+// They are built once per call: S_i e_k (the negated local inpainting echo of
+// mask pixel k) by warp-level CG on the Neumann subdomain problem, the Gram
+// matrix I + S^T S by a small tiled product, and its Cholesky factor in
+// shared memory. Each outer iteration then solves the local systems exactly
+// by two triangular solves instead of the paper's inner CGNR iterations.
 #pragma once
-int Ctx::tonal(const hdi_image*, const hdi_mask*, const hdi_image*, hdi_image*, double, hdi_stats*) {
-    return fail(HDI_ERR_UNSUPPORTED, "tonal optimisation not built yet");
+#include "oras.cuh"
+
+constexpr int kTonalMaxM = 192;   // mask pixels per 32x32 subdomain handled by the dense local solve
+
+// ----------------------------------------------------------- setup kernels ---
+
+// Valid-column mask of a subdomain of width w (bits 0..w-1).
+__device__ __forceinline__ uint32_t cols_valid(int w) { return w >= 32 ? 0xffffffffu : ((1u << w) - 1u); }
+
+// m_i = number of mask pixels in subdomain i (warp per subdomain, lane = row).
+__global__ void k_tonal_count(MaskView m, int nbx, int nby, int stride, int* __restrict__ cnt) {
+    const int wid = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wid >= nbx * nby) return;
+    const int by = wid / nbx, bx = wid - by * nbx;
+    const int x0 = bx * stride, y0 = by * stride;
+    const int w = min(32, m.W - x0), h = min(32, m.H - y0);
+    int c = 0;
+    if (lane < h) c = __popc(m.window(x0, y0 + lane) & cols_valid(w));
+    c = __reduce_add_sync(HDI_FULL, c);
+    if (lane == 0) cnt[wid] = c;
+}
+
+// Local pixel codes (ly * 32 + lx) of the mask pixels of each subdomain, in
+// raster order, at list + off[i].
+__global__ void k_tonal_list(MaskView m, int nbx, int nby, int stride, const int* __restrict__ off,
+                             uint16_t* __restrict__ list) {
+    const int wid = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wid >= nbx * nby) return;
+    const int by = wid / nbx, bx = wid - by * nbx;
+    const int x0 = bx * stride, y0 = by * stride;
+    const int w = min(32, m.W - x0), h = min(32, m.H - y0);
+    uint32_t bits = (lane < h) ? (m.window(x0, y0 + lane) & cols_valid(w)) : 0u;
+    int c = __popc(bits);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(HDI_FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    int pos = off[wid] + incl - c;
+    while (bits) {
+        const int lx = __ffs(bits) - 1;
+        bits &= bits - 1;
+        list[pos++] = (uint16_t)(lane * 32 + lx);
+    }
+}
+
+struct EchoArgs {
+    MaskView m;
+    int nbx, nby, stride, nb;
+    const int* off;          // [nb + 1] exclusive prefix of m_i
+    const uint16_t* list;
+    float* echo;             // [sum m_i][32 rows][32 lanes]
+    float rtol2;
+    int maxit;
+    unsigned long long* iters;
+};
+
+// One warp per (subdomain, mask pixel k): solve the Neumann subdomain problem
+// L_UU x = L_UK e_k by CG; x = S e_k is stored row-major over the 32x32 tile.
+__global__ void __launch_bounds__(128) k_tonal_echo(EchoArgs a) {
+    const long long e = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int total = a.off[a.nb];
+    if (e >= total) return;
+    // subdomain owning echo e: largest i with off[i] <= e
+    int lo = 0, hi = a.nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.off[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const int i = lo;
+    const int by = i / a.nbx, bx = i - by * a.nbx;
+    const int x0 = bx * a.stride, y0 = by * a.stride;
+    const LocalGeom g = make_geom(x0, y0, a.m.H, a.m.W, a.m, 0.f);
+    const int code = a.list[e];
+    const int ky = code >> 5, kx = code & 31;
+    // right-hand side L_UK e_k: -1 at the unknown 4-neighbours of k inside the subdomain
+    float r[32], v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const bool nb = (lane == kx && (j == ky - 1 || j == ky + 1)) || (j == ky && (lane == kx - 1 || lane == kx + 1));
+        r[j] = (nb && ((g.um >> j) & 1u)) ? -1.f : 0.f;
+    }
+    float rr0 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) rr0 += r[j] * r[j];
+    rr0 = warp_sum_f(rr0);
+    const int it = local_cg(g, v, r, a.rtol2 * rr0, a.maxit);
+    if (a.iters && lane == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
+    float* out = a.echo + (size_t)e * 1024;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) out[j * 32 + lane] = v[j];
+}
+
+// G_i = I + S_i^T S_i and its Cholesky factor (packed lower, row-major) at
+// fac + goff[i]. One CTA of 256 threads per subdomain; G lives in dynamic
+// shared memory (m_i <= kTonalMaxM).
+__global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off, const long long* __restrict__ goff,
+                                                    const float* __restrict__ echo, float* __restrict__ fac,
+                                                    unsigned* bad) {
+    extern __shared__ float sm[];
+    const int i = blockIdx.x;
+    const int m = off[i + 1] - off[i];
+    if (m == 0) return;
+    const int tid = threadIdx.x;
+    float* G = sm;                       // m x m, row stride m
+    float* tA = sm + m * m;              // [32 pixels][64] tile of echoes (rows ti)
+    float* tB = tA + 32 * 64;            // [32 pixels][64] (rows tj)
+    const float* E = echo + (size_t)off[i] * 1024;
+    const int nt = (m + 63) / 64;
+    const int tr = tid / 16, tc = tid % 16;   // 16x16 threads, 4x4 outputs each
+    for (int ti = 0; ti < nt; ++ti) {
+        for (int tj = 0; tj <= ti; ++tj) {
+            float acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+            for (int p0 = 0; p0 < 1024; p0 += 32) {
+                __syncthreads();
+                for (int q = tid; q < 32 * 64; q += 256) {
+                    const int pp = q / 64, kk = q % 64;
+                    const int ka = ti * 64 + kk, kb = tj * 64 + kk;
+                    tA[pp * 64 + kk] = (ka < m) ? E[(size_t)ka * 1024 + p0 + pp] : 0.f;
+                    tB[pp * 64 + kk] = (kb < m) ? E[(size_t)kb * 1024 + p0 + pp] : 0.f;
+                }
+                __syncthreads();
+#pragma unroll 8
+                for (int pp = 0; pp < 32; ++pp) {
+                    float av[4], bv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) av[a] = tA[pp * 64 + tr * 4 + a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) bv[b] = tB[pp * 64 + tc * 4 + b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int r = ti * 64 + tr * 4 + a, c = tj * 64 + tc * 4 + b;
+                    if (r < m && c < m && c <= r) G[r * m + c] = acc[a][b] + (r == c ? 1.f : 0.f);
+                }
+        }
+    }
+    __syncthreads();
+    // right-looking Cholesky on the lower triangle
+    for (int j = 0; j < m; ++j) {
+        const float d = sqrtf(G[j * m + j]);
+        __syncthreads();
+        if (tid == 0) {
+            if (!(d > 0.f)) atomicOr(bad, 1u);
+            G[j * m + j] = d;
+        }
+        const float inv = 1.f / d;
+        for (int r = j + 1 + tid; r < m; r += 256) G[r * m + j] *= inv;
+        __syncthreads();
+        const int n = m - j - 1;   // trailing block (j+1..m-1)^2, lower part
+        for (int q = tid; q < n * n; q += 256) {
+            const int r = j + 1 + q / n, c = j + 1 + q % n;
+            if (c <= r) G[r * m + c] -= G[r * m + j] * G[c * m + j];
+        }
+        __syncthreads();
+    }
+    float* L = fac + goff[i];
+    for (int q = tid; q < m * m; q += 256) {
+        const int r = q / m, c = q % m;
+        if (c <= r) L[r * (r + 1) / 2 + c] = G[r * m + c];
+    }
+}
+
+// ------------------------------------------------------- outer iteration ---
+
+// r_K = (f - y)_K + sum of w over the unknown 4-neighbours (B^T (f - y)),
+// and per channel ||r||^2 and ||f - y||^2 (the tonal MSE numerator).
+// y == nullptr means y = 0 (gives B^T f).
+__global__ void __launch_bounds__(256) k_tonal_residual(LevelArr F, MaskView m, const double* __restrict__ f,
+                                                        const double* __restrict__ y, const double* __restrict__ w,
+                                                        double* __restrict__ r, GridReduce red_r, GridReduce red_e) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int yy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int ch = blockIdx.z;
+    double sr = 0.0, se = 0.0;
+    if (x < F.W && yy < F.H) {
+        const size_t idx = ch * F.cs + (size_t)yy * F.pitch + x;
+        const double s = f[idx] - (y ? y[idx] : 0.0);
+        se = s * s;
+        if (m.known(x, yy)) {
+            double acc = s;
+            if (x > 0 && !m.known(x - 1, yy)) acc += w[idx - 1];
+            if (x + 1 < F.W && !m.known(x + 1, yy)) acc += w[idx + 1];
+            if (yy > 0 && !m.known(x, yy - 1)) acc += w[idx - F.pitch];
+            if (yy + 1 < F.H && !m.known(x, yy + 1)) acc += w[idx + F.pitch];
+            r[idx] = acc;
+            sr = acc * acc;
+        }
+    }
+    const double tr = block_sum_d(sr);
+    grid_reduce_commit(red_r, ch, blockIdx.y * gridDim.x + blockIdx.x, tr);
+    const double te = block_sum_d(se);
+    grid_reduce_commit(red_e, ch, blockIdx.y * gridDim.x + blockIdx.x, te);
+}
+
+struct LocalSolveArgs {
+    LevelArr F;
+    int nbx, nby, stride, nch, color;
+    const int* off;
+    const long long* goff;
+    const uint16_t* list;
+    const float* fac;
+    const double* r;
+    double* g;
+};
+
+// Number of subdomains covering coordinate x along an axis (1 or 2).
+__device__ __forceinline__ int cover_count(int x, int nb, int stride) {
+    const int hi = min(nb - 1, x / stride);
+    const int lo = max(0, (x - 31 + stride - 1) / stride);
+    return hi - lo + 1;
+}
+
+// Local solves of one colour class ((bx & 1) | (by & 1) << 1 == color):
+// v = (L L^T)^{-1} R_i r by forward and backward substitution, then
+// g += D_i v. Subdomains of one colour never overlap (stride 26 > 32/2), so
+// the updates need no atomics and their order is fixed. One warp per
+// (subdomain, channel).
+__global__ void __launch_bounds__(128) k_tonal_local(LocalSolveArgs a) {
+    __shared__ float sv[4][kTonalMaxM];
+    const int wl = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int hx = (a.nbx + 1 - (a.color & 1)) / 2;
+    const int hy = (a.nby + 1 - (a.color >> 1)) / 2;
+    const long long wid = (long long)blockIdx.x * 4 + wl;
+    if (wid >= (long long)hx * hy * a.nch) return;
+    const int ch = (int)(wid / (hx * hy));
+    const int q = (int)(wid - (long long)ch * hx * hy);
+    const int bx = 2 * (q % hx) + (a.color & 1);
+    const int by = 2 * (q / hx) + (a.color >> 1);
+    const int i = by * a.nbx + bx;
+    const int m = a.off[i + 1] - a.off[i];
+    if (m == 0) return;
+    const uint16_t* lst = a.list + a.off[i];
+    const float* L = a.fac + a.goff[i];
+    const int x0 = bx * a.stride, y0 = by * a.stride;
+    const double* r = a.r + ch * a.F.cs;
+    float* v = sv[wl];
+    for (int k = lane; k < m; k += 32) {
+        const int code = lst[k];
+        v[k] = (float)r[(size_t)(y0 + (code >> 5)) * a.F.pitch + x0 + (code & 31)];
+    }
+    __syncwarp();
+    // forward: L y = r (column-oriented)
+    for (int j = 0; j < m; ++j) {
+        const float yj = v[j] / L[j * (j + 1) / 2 + j];
+        __syncwarp();
+        if (lane == 0) v[j] = yj;
+        for (int k = j + 1 + lane; k < m; k += 32) v[k] -= L[k * (k + 1) / 2 + j] * yj;
+        __syncwarp();
+    }
+    // backward: L^T x = y (row j of L holds column j of L^T)
+    for (int j = m - 1; j >= 0; --j) {
+        const float xj = v[j] / L[j * (j + 1) / 2 + j];
+        __syncwarp();
+        if (lane == 0) v[j] = xj;
+        const float* Lj = L + j * (j + 1) / 2;
+        for (int k = lane; k < j; k += 32) v[k] -= Lj[k] * xj;
+        __syncwarp();
+    }
+    double* g = a.g + ch * a.F.cs;
+    for (int k = lane; k < m; k += 32) {
+        const int code = lst[k];
+        const int px = x0 + (code & 31), py = y0 + (code >> 5);
+        const int mult = cover_count(px, a.nbx, a.stride) * cover_count(py, a.nby, a.stride);
+        g[(size_t)py * a.F.pitch + px] += (double)v[k] / (double)mult;
+    }
+}
+
+// ------------------------------------------------------------ the driver ---
+
+int Ctx::tonal_setup() {
+    int rc;
+    const Level& L0 = lev[0];
+    const int nb = L0.nbx * L0.nby;
+    const int stride = 32 - kOv;
+    // counts
+    std::vector<int> cnt(nb), off(nb + 1);
+    std::vector<long long> goff(nb + 1);
+    int* dcnt = nullptr;
+    if ((rc = tws.reserve(*this, std::max(tws.cap, (size_t)(nb + 1) * 24 + 4096), "tonal counts"))) return rc;
+    dcnt = (int*)tws.take((size_t)nb * 4);
+    k_tonal_count<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), L0.nbx, L0.nby, stride, dcnt);
+    cudaMemcpyAsync(cnt.data(), dcnt, (size_t)nb * 4, cudaMemcpyDeviceToHost, stream);
+    if ((rc = sync("tonal subdomain counts"))) return rc;
+    off[0] = 0;
+    goff[0] = 0;
+    int maxm = 0;
+    for (int i = 0; i < nb; ++i) {
+        off[i + 1] = off[i] + cnt[i];
+        goff[i + 1] = goff[i] + (long long)cnt[i] * (cnt[i] + 1) / 2;
+        maxm = std::max(maxm, cnt[i]);
+    }
+    if (maxm > kTonalMaxM)
+        return fail(HDI_ERR_UNSUPPORTED, "tonal: a 32x32 subdomain holds %d mask pixels (limit %d)", maxm, kTonalMaxM);
+    const long long total = off[nb];
+    // layout
+    size_t bytes = 0;
+    auto acc = [&](size_t b) { bytes += (b + 255) & ~(size_t)255; };
+    acc((size_t)(nb + 1) * 4);
+    acc((size_t)(nb + 1) * 8);
+    acc((size_t)total * 2);
+    acc((size_t)total * 1024 * 4);
+    acc((size_t)goff[nb] * 4);
+    if ((rc = tws.reserve(*this, bytes, "tonal local factors"))) return rc;
+    t_off = (int*)tws.take((size_t)(nb + 1) * 4);
+    t_goff = (long long*)tws.take((size_t)(nb + 1) * 8);
+    t_list = (uint16_t*)tws.take((size_t)total * 2);
+    t_echo = (float*)tws.take((size_t)total * 1024 * 4);
+    t_fac = (float*)tws.take((size_t)goff[nb] * 4);
+    cudaMemcpyAsync(t_off, off.data(), (size_t)(nb + 1) * 4, cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(t_goff, goff.data(), (size_t)(nb + 1) * 8, cudaMemcpyHostToDevice, stream);
+    k_tonal_list<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), L0.nbx, L0.nby, stride, t_off, t_list);
+    if (total > 0) {
+        EchoArgs ea;
+        ea.m = mview(0);
+        ea.nbx = L0.nbx;
+        ea.nby = L0.nby;
+        ea.stride = stride;
+        ea.nb = nb;
+        ea.off = t_off;
+        ea.list = t_list;
+        ea.echo = t_echo;
+        ea.rtol2 = (float)(p.tonal_echo_rtol * p.tonal_echo_rtol);
+        ea.maxit = (int)p.tonal_echo_max_iter;
+        ea.iters = counters + kCntEcho;
+        k_tonal_echo<<<(unsigned)((total + 3) / 4), 128, 0, stream>>>(ea);
+        const size_t shm = ((size_t)maxm * maxm + 2 * 32 * 64) * 4;
+        cudaFuncSetAttribute(k_tonal_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        cudaMemsetAsync(flags, 0, 4, stream);
+        k_tonal_gram<<<nb, 256, shm, stream>>>(t_off, t_goff, t_echo, t_fac, flags);
+        unsigned bad = 0;
+        cudaMemcpyAsync(&bad, flags, 4, cudaMemcpyDeviceToHost, stream);
+        if ((rc = sync("tonal local factors"))) return rc;
+        if (bad) return fail(HDI_ERR_NONFINITE, "tonal: a local Gram matrix is not positive definite");
+    }
+    t_total = total;
+    return sync("tonal setup");
+}
+
+void Ctx::tonal_residual(const double* y, const double* w, double* r) {
+    dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8, nch);
+    k_tonal_residual<<<grd, blk, 0, stream>>>(arr(0), mview(0), f64[kF], y, w, r, reducer(kSlotTonalR, grd.x * grd.y),
+                                              reducer(kSlotTonalE, grd.x * grd.y));
+}
+
+void Ctx::tonal_local(double* g) {
+    const Level& L0 = lev[0];
+    for (int color = 0; color < 4; ++color) {
+        LocalSolveArgs a;
+        a.F = arr(0);
+        a.nbx = L0.nbx;
+        a.nby = L0.nby;
+        a.stride = 32 - kOv;
+        a.nch = nch;
+        a.color = color;
+        a.off = t_off;
+        a.goff = t_goff;
+        a.list = t_list;
+        a.fac = t_fac;
+        a.r = f64[kR];
+        a.g = g;
+        const int hx = (L0.nbx + 1 - (color & 1)) / 2;
+        const int hy = (L0.nby + 1 - (color >> 1)) / 2;
+        const long long warps = (long long)hx * hy * nch;
+        if (warps <= 0) continue;
+        k_tonal_local<<<(unsigned)((warps + 3) / 4), 128, 0, stream>>>(a);
+    }
+}
+
+int Ctx::read_slot(int slot, double* out) {
+    cudaMemcpyAsync(hscal, scal + slot * 4, 4 * 8, cudaMemcpyDeviceToHost, stream);
+    int rc = sync("reading a reduction");
+    if (rc) return rc;
+    for (int c = 0; c < nch; ++c) out[c] = hscal[c];
+    return HDI_OK;
+}
+
+int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hdi_image* g, double tol,
+               hdi_stats* st) {
+    int rc;
+    if ((rc = cuda_check(cudaSetDevice(device), "cudaSetDevice"))) return rc;
+    if ((rc = check_image(f, "f", -1, 0, 0))) return rc;
+    if ((rc = check_image(g, "g", f->height, f->width, f->channels))) return rc;
+    if (g->dtype != f->dtype) return fail(HDI_ERR_INVALID_ARG, "g: dtype differs from f");
+    if (g0 && (rc = check_image(g0, "g0", f->height, f->width, f->channels))) return rc;
+    if (!(tol > 0.0 && tol < 1.0)) return fail(HDI_ERR_INVALID_ARG, "tol must lie in (0, 1)");
+    if ((rc = setup(f->height, f->width, f->channels))) return rc;
+    long long ones = 0;
+    if ((rc = load_mask(mask, &ones))) return rc;
+    if (ones == 0) return fail(HDI_ERR_EMPTY_MASK, "empty mask: A is singular");
+    double* F = f64[kF];
+    double* G = f64[kG];
+    if ((rc = load_image(f, F))) return rc;
+    if (g0) {
+        if ((rc = load_image(g0, G))) return rc;
+    } else {
+        cudaMemcpyAsync(G, F, (size_t)nch * lev[0].cs * 8, cudaMemcpyDeviceToDevice, stream);
+    }
+    vcycles_run = 0;
+    cudaMemsetAsync(counters + kCntLocal, 0, 16, stream);
+    if ((rc = tonal_setup())) return rc;
+
+    const double ratio = p.tonal_inner_ratio;
+    // ||B^T f||: w_f solves A w = (I - C) f.
+    SolveSpec sw;
+    sw.u[0] = f64[kW0];
+    sw.u[1] = f64[kW1];
+    sw.cur = 0;
+    sw.rhs = RHS_SOURCE;
+    sw.d = F;
+    sw.y = nullptr;
+    sw.start = START_ZERO;
+    sw.tol = std::max(1e-13, ratio * tol);
+    sw.max_iter = (int)p.max_vcycles;
+    rc = solve(sw);
+    if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return rc;
+    tonal_residual(nullptr, sw.u[sw.cur], f64[kR]);
+    double btf2[4], r2[4], e2[4];
+    if ((rc = read_slot(kSlotTonalR, btf2))) return rc;
+
+    SolveSpec sy;
+    sy.u[0] = f64[kY0];
+    sy.u[1] = f64[kY1];
+    sy.cur = 0;
+    sy.rhs = RHS_DATA;
+    sy.d = G;
+    sy.y = nullptr;
+    sy.start = START_FMG;
+    sy.max_iter = (int)p.max_vcycles;
+    sw.start = START_WARM;
+    double rel_prev = 1.0, rel_max = 1.0;
+    int it = 0;
+    const int max_it = (int)p.tonal_max_iter;
+    double mse_last = 0.0;
+    for (;; ++it) {
+        const double tin = std::max(1e-13, std::min(1e-3, ratio * rel_prev));
+        sy.tol = tin;
+        rc = solve(sy);
+        if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return rc;
+        sy.start = START_WARM;
+        sw.tol = tin;
+        sw.y = sy.u[sy.cur];
+        rc = solve(sw);
+        if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return rc;
+        tonal_residual(sy.u[sy.cur], sw.u[sw.cur], f64[kR]);
+        if ((rc = read_slot(kSlotTonalR, r2))) return rc;
+        if ((rc = read_slot(kSlotTonalE, e2))) return rc;
+        rel_max = 0.0;
+        double esum = 0.0;
+        for (int c = 0; c < nch; ++c) {
+            if (!std::isfinite(r2[c])) return fail(HDI_ERR_NONFINITE, "tonal: non-finite residual");
+            const double rel = btf2[c] > 0 ? std::sqrt(r2[c] / btf2[c]) : 0.0;
+            rel_max = std::max(rel_max, rel);
+            esum += e2[c];
+        }
+        mse_last = esum / ((double)nch * H * W);
+        if (rel_max <= tol || it >= max_it) break;
+        rel_prev = rel_max;
+        tonal_local(G);
+    }
+    if ((rc = store_image(G, g, true))) return rc;
+    if (st) {
+        unsigned long long li[2] = {0, 0};
+        cudaMemcpy(li, counters + kCntLocal, 16, cudaMemcpyDeviceToHost);
+        st->iterations = it;
+        st->vcycles = vcycles_run;
+        st->local_iters = (int64_t)li[0];
+        st->rel_res = rel_max;
+        st->mse = mse_last;
+    }
+    if (rel_max > tol)
+        return fail(HDI_ERR_NOT_CONVERGED, "tonal: relative residual %.3e after %d RAS iterations", rel_max, it);
+    return HDI_OK;
 }

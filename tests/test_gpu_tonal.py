@@ -1,0 +1,58 @@
+"""Parity of the CUDA tonal optimisation (RAS, Alg. 2) against the FP64
+oracle (CG on the normal equations), called through the C ABI."""
+
+import numpy as np
+import pytest
+
+from gpu_util import torch, need_gpu, ctx, dev
+from oracle import tonal as tonal_ref, normal_residual, B_apply, inpaint, mse
+from synthdata import synth_image, synth_rgb, random_mask
+
+pytestmark = pytest.mark.gpu
+
+
+def run(f, c, tol, g0=None, **params):
+    need_gpu()
+    k = ctx(**params)
+    fd, cd = dev(f), dev(c)
+    out = torch.empty_like(fd)
+    st = k.tonal_opt(fd, cd, out, g0=None if g0 is None else dev(g0), tol=tol)
+    return out.cpu().numpy(), st
+
+
+def test_c1_256_gray_fp64_tight():
+    """256x256 grey FP64, 4% mask: normal equations to relative residual 1e-10."""
+    f = synth_image(256, 256, 0)
+    c = random_mask(256, 256, 0.04, 1000)
+    g, st = run(f, c, 1e-10)
+    ref = tonal_ref(f, c)
+    assert st["rel_res"] <= 1e-10
+    assert normal_residual(f, c, g)[0] <= 2e-10
+    assert np.abs(g - ref).max() <= 1e-5
+    assert np.all(g[c == 0] == 0)
+
+
+@pytest.mark.parametrize("H,W,d,seed", [(77, 131, 0.04, 1), (130, 60, 0.1, 2), (40, 33, 0.02, 3)])
+def test_ragged_rgb_fp32(H, W, d, seed):
+    f = synth_rgb(H, W, seeds=(seed, seed + 10, seed + 20), dtype=np.float32)
+    c = random_mask(H, W, d, seed + 100)
+    g, st = run(f, c, 1e-6)
+    f64 = f.astype(np.float64)
+    ref = tonal_ref(f64, c)
+    assert st["rel_res"] <= 1e-6
+    assert normal_residual(f64, c, g.astype(np.float64)).max() <= 2e-6
+    assert np.abs(g - ref).max() <= 0.05
+    # never worse than the unoptimised values (Sec. 5)
+    assert mse(B_apply(g.astype(np.float64), c), f64) <= mse(inpaint(f64, c), f64)
+    assert abs(st["mse"] - mse(B_apply(ref, c), f64)) <= 1e-3 * st["mse"] + 1e-6
+
+
+def test_full_mask_and_generated_data():
+    f = synth_image(50, 40, 5)
+    g, _ = run(f, np.ones((50, 40), np.uint8), 1e-8)
+    np.testing.assert_allclose(g, f, atol=1e-9)
+    c = random_mask(64, 64, 0.05, 6)
+    g0 = np.where(c.astype(bool), synth_image(64, 64, 7), 0.0)
+    fb = B_apply(g0, c)
+    g, _ = run(fb, c, 1e-9)
+    assert np.abs(g - g0).max() <= 1e-4
