@@ -79,8 +79,16 @@ __device__ __forceinline__ void grid_reduce_commit(const GridReduce& R, int ch, 
     if (!last_cta) return;
     __threadfence();
     for (int c = 0; c < R.nch; ++c) {
-        double acc = 0.0;
-        for (int i = tid; i < R.nparts; i += nt) acc += __ldcg(R.partials + (size_t)c * R.nparts + i);
+        // eight independent chains hide the L2 latency; fixed combination order
+        const double* pp = R.partials + (size_t)c * R.nparts;
+        double a8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int i = tid;
+        for (; i + 7 * nt < R.nparts; i += 8 * nt) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a8[k] += __ldcg(pp + i + k * nt);
+        }
+        for (int k = 0; i < R.nparts; i += nt, ++k) a8[k & 7] += __ldcg(pp + i);
+        double acc = ((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7]));
         acc = block_sum_d(acc);
         if (tid == 0) R.out[c] = acc;
     }

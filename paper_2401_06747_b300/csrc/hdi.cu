@@ -130,8 +130,9 @@ int Ctx::setup(int H_, int W_, int nch_) {
         maxparts = std::max(maxparts, parts);
     }
     const int P0 = round_up(W_, 32);
-    const size_t n64 = (size_t)nch_ * H_ * P0;
-    for (int k = 0; k < kNumF64; ++k) acc(n64 * 8);           // FP64 vectors
+    const size_t n32 = (size_t)nch_ * H_ * P0;
+    for (int k = 0; k < kNumDF; ++k) acc(n32 * 8);            // double-float vectors
+    acc(n32 * 4);                                             // tonal residual
     acc((size_t)kSlots * maxparts * nch_ * 8);                // reduction partials
     acc((size_t)kSlots * 4 * 8);                              // reduction outputs
     acc((size_t)kSlots * 4);                                  // tickets
@@ -153,7 +154,11 @@ int Ctx::setup(int H_, int W_, int nch_) {
         L.nbx = tile_count(L.W, 32, kOv);
         L.nby = tile_count(L.H, 32, kOv);
     }
-    for (int i = 0; i < kNumF64; ++i) f64[i] = (double*)ws.take(n64 * 8);
+    for (int i = 0; i < kNumDF; ++i) {
+        dfv[i].hi = (float*)ws.take(n32 * 8);
+        dfv[i].lo = dfv[i].hi + n32;
+    }
+    tres = (float*)ws.take(n32 * 4);
     maxparts_ = maxparts;
     partials = (double*)ws.take((size_t)kSlots * maxparts * nch * 8);
     scal = (double*)ws.take((size_t)kSlots * 4 * 8);
@@ -272,7 +277,7 @@ void Ctx::vcycle(int l) {
 // Reduced full multigrid (Sec. 3.2, Fig. "multigrid_reduced"): data pyramid,
 // coarsest solve, then one ORAS sweep per finer level after prolongation.
 // `d` is the level-0 Dirichlet data in FP64. Result (FP32) in lev[0].xa.
-void Ctx::fmg(const double* d) {
+void Ctx::fmg(DFc d) {
     {
         dim3 grd((W + 127) / 128, H, nch);
         k_data_to_f32<<<grd, 128, 0, stream>>>(d, arr(0), mview(0), lev[0].b);
@@ -297,9 +302,8 @@ void Ctx::fmg(const double* d) {
 }
 
 template <int RHS, int INIT>
-static void launch_res64(Ctx& c, const double* uin, double* uout, const float* x32, const double* d, const double* y,
-                         bool want_b) {
-    Res64Args a;
+static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b) {
+    ResArgs a;
     a.F = c.arr(0);
     a.m = c.mview(0);
     a.uin = uin;
@@ -312,17 +316,16 @@ static void launch_res64(Ctx& c, const double* uin, double* uout, const float* x
     a.red_r = c.reducer(kSlotR64, grd.x * grd.y);
     a.red_b = c.reducer(kSlotB64, grd.x * grd.y);
     a.want_b = want_b ? 1 : 0;
-    k_residual64<RHS, INIT><<<grd, blk, 0, c.stream>>>(a);
+    k_residual_df<RHS, INIT><<<grd, blk, 0, c.stream>>>(a);
 }
 
-void Ctx::residual64(int rhs, int init, const double* uin, double* uout, const float* x32, const double* d,
-                     const double* y, bool want_b) {
-#define HDI_R64(R, I) \
-    if (rhs == R && init == I) { launch_res64<R, I>(*this, uin, uout, x32, d, y, want_b); return; }
-    HDI_R64(RHS_DATA, INIT_KEEP) HDI_R64(RHS_DATA, INIT_UPDATE) HDI_R64(RHS_DATA, INIT_FROM32)
-    HDI_R64(RHS_DATA, INIT_ZERO) HDI_R64(RHS_SOURCE, INIT_KEEP) HDI_R64(RHS_SOURCE, INIT_UPDATE)
-    HDI_R64(RHS_SOURCE, INIT_FROM32) HDI_R64(RHS_SOURCE, INIT_ZERO)
-#undef HDI_R64
+void Ctx::residual(int rhs, int init, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b) {
+#define HDI_RES(R, I) \
+    if (rhs == R && init == I) { launch_res<R, I>(*this, uin, uout, x32, d, y, want_b); return; }
+    HDI_RES(RHS_DATA, INIT_KEEP) HDI_RES(RHS_DATA, INIT_UPDATE) HDI_RES(RHS_DATA, INIT_FROM32)
+    HDI_RES(RHS_DATA, INIT_ZERO) HDI_RES(RHS_SOURCE, INIT_KEEP) HDI_RES(RHS_SOURCE, INIT_UPDATE)
+    HDI_RES(RHS_SOURCE, INIT_FROM32) HDI_RES(RHS_SOURCE, INIT_ZERO)
+#undef HDI_RES
 }
 
 // Solves A u = b on level 0 with iterative refinement in FP64 (pattern:
@@ -334,16 +337,17 @@ void Ctx::residual64(int rhs, int init, const double* uin, double* uout, const f
 //   spec.tol     : relative residual per channel; spec.bnorm2 receives ||b||^2.
 int Ctx::solve(SolveSpec& s) {
     int rc;
-    double* ub[2] = {s.u[0], s.u[1]};
+    DF* ub = s.u;
     int cur = s.cur;
+    const DFc none{nullptr, nullptr};
     if (s.start == START_FMG) {
         fmg(s.d);
-        residual64(s.rhs, INIT_FROM32, nullptr, ub[cur], lev[0].xa, s.d, s.y, true);
+        residual(s.rhs, INIT_FROM32, none, ub[cur], lev[0].xa, s.d, s.y, true);
     } else if (s.start == START_WARM) {
-        residual64(s.rhs, INIT_KEEP, ub[cur], ub[1 - cur], nullptr, s.d, s.y, true);
+        residual(s.rhs, INIT_KEEP, cview(ub[cur]), ub[1 - cur], nullptr, s.d, s.y, true);
         cur = 1 - cur;
     } else {
-        residual64(s.rhs, INIT_ZERO, nullptr, ub[cur], nullptr, s.d, s.y, true);
+        residual(s.rhs, INIT_ZERO, none, ub[cur], nullptr, s.d, s.y, true);
     }
     double r2[4], b2[4];
     s.iterations = 0;
@@ -371,7 +375,7 @@ int Ctx::solve(SolveSpec& s) {
             return HDI_ERR_NOT_CONVERGED;
         }
         vcycle(0);
-        residual64(s.rhs, INIT_UPDATE, ub[cur], ub[1 - cur], lev[0].xa, s.d, s.y, false);
+        residual(s.rhs, INIT_UPDATE, cview(ub[cur]), ub[1 - cur], lev[0].xa, s.d, s.y, false);
         cur = 1 - cur;
         ++s.iterations;
         // ||b||^2 is unchanged; keep the slot value from the first evaluation.
@@ -399,7 +403,7 @@ int Ctx::check_image(const hdi_image* im, const char* name, int H_, int W_, int 
 }
 
 // Copies a caller image into the internal FP64 layout (device or host source).
-int Ctx::load_image(const hdi_image* im, double* dst) {
+int Ctx::load_image(const hdi_image* im, DF dst) {
     const void* src = im->data;
     long long rs = im->row_stride, cs = im->channel_stride;
     const size_t es = im->dtype == HDI_F64 ? 8 : 4;
@@ -432,7 +436,7 @@ int Ctx::load_image(const hdi_image* im, double* dst) {
     return HDI_OK;
 }
 
-int Ctx::store_image(const double* src, hdi_image* im, bool zero_off_mask) {
+int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask) {
     void* dst = im->data;
     long long rs = im->row_stride, cs = im->channel_stride;
     const size_t es = im->dtype == HDI_F64 ? 8 : 4;
@@ -628,15 +632,13 @@ int Ctx::inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, 
     long long ones = 0;
     if ((rc = load_mask(mask, &ones))) return rc;
     if (ones == 0) return fail(HDI_ERR_EMPTY_MASK, "empty mask: A is singular");
-    double* F = f64[kF];
-    if ((rc = load_image(f, F))) return rc;
+    if ((rc = load_image(f, dfv[kF]))) return rc;
     SolveSpec s;
-    s.u[0] = f64[kU0];
-    s.u[1] = f64[kU1];
+    s.u[0] = dfv[kU0];
+    s.u[1] = dfv[kU1];
     s.cur = 0;
     s.rhs = RHS_DATA;
-    s.d = F;
-    s.y = nullptr;
+    s.d = cview(dfv[kF]);
     s.tol = tol;
     s.max_iter = (int)p.max_vcycles;
     if (u0) {
@@ -649,7 +651,7 @@ int Ctx::inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, 
     cudaMemsetAsync(counters + kCntLocal, 0, 8, stream);
     const int src = solve(s);
     if (src != HDI_OK && src != HDI_ERR_NOT_CONVERGED) return src;
-    if ((rc = store_image(s.u[s.cur], u, false))) return rc;
+    if ((rc = store_image(cview(s.u[s.cur]), u, false))) return rc;
     if (st) {
         unsigned long long li = 0;
         cudaMemcpy(&li, counters + kCntLocal, 8, cudaMemcpyDeviceToHost);

@@ -45,12 +45,14 @@ struct Arena {
 
 enum { START_FMG = 0, START_WARM = 1, START_ZERO = 2 };
 
+inline DFc cview(const DF& v) { return DFc{v.hi, v.lo}; }
+
 struct SolveSpec {
-    double* u[2];
+    DF u[2];
     int cur = 0;
     int rhs = 0;
-    const double* d = nullptr;
-    const double* y = nullptr;
+    DFc d{nullptr, nullptr};
+    DFc y{nullptr, nullptr};
     int start = START_FMG;
     double tol = 1e-6;
     int max_iter = 60;
@@ -70,8 +72,8 @@ constexpr int kSlotTonalE = 19;   // ||f - Bg||^2
 constexpr int kCntOnes = 0;
 constexpr int kCntLocal = 1;
 constexpr int kCntEcho = 2;
-// FP64 vectors of level-0 size
-enum { kF = 0, kU0, kU1, kG, kY0, kY1, kW0, kW1, kR, kNumF64 };
+// double-float vectors of level-0 size
+enum { kF = 0, kU0, kU1, kG, kY0, kY1, kW0, kW1, kNumDF };
 
 struct Ctx {
     int device = 0;
@@ -84,7 +86,8 @@ struct Ctx {
     Arena stage;   // host staging
     int H = 0, W = 0, nch = 0, nlev = 0;
     Level lev[kMaxLevels];
-    double* f64[kNumF64] = {};
+    DF dfv[kNumDF] = {};
+    float* tres = nullptr;     // tonal residual B^T (f - B g) on mask pixels, FP32
     double* partials = nullptr;
     double* scal = nullptr;
     unsigned* tickets = nullptr;
@@ -115,18 +118,17 @@ struct Ctx {
     void oras(int l, bool zero, const float* xin, float* xout, const double* rnorm2, bool coarsest,
               unsigned long long* iters);
     void vcycle(int l);
-    void fmg(const double* d);
-    void residual64(int rhs, int init, const double* uin, double* uout, const float* x32, const double* d,
-                    const double* y, bool want_b);
+    void fmg(DFc d);
+    void residual(int rhs, int init, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b);
     int solve(SolveSpec& s);
     int check_image(const hdi_image* im, const char* name, int H, int W, int nch);
-    int load_image(const hdi_image* im, double* dst);
-    int store_image(const double* src, hdi_image* im, bool zero_off_mask);
+    int load_image(const hdi_image* im, DF dst);
+    int store_image(DFc src, hdi_image* im, bool zero_off_mask);
     int load_mask(const hdi_mask* m, long long* ones);
     int read_slot(int slot, double* out);
     int tonal_setup();
-    void tonal_residual(const double* y, const double* w, double* r);
-    void tonal_local(double* g);
+    void tonal_residual(DFc y, DFc w);
+    void tonal_local(DF g);
     int inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,
                 hdi_stats* st);
     int tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hdi_image* g, double tol,

@@ -210,39 +210,79 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_prolong(LevelArr F, MaskView fm
     grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
 }
 
-// ------------------------------------------------- FP64 refinement step ---
+// ------------------------------------------- double-float refinement step ---
+//
+// The level-0 iterate, the data and the tonal vectors are held as
+// double-float pairs (hi, lo) of FP32 numbers with value hi + lo and
+// |lo| <= ulp(hi)/2, about 48 significant bits. The refinement residual is
+// formed with error-free transformations (Knuth's TwoSum, Dekker's
+// Fast2Sum), so it is as accurate as an FP64 evaluation while every
+// operation runs on the FP32 pipes (the FP64 rate of the target is a small
+// fraction of its FP32 rate).
 
-// Right-hand side of the fine-level system in FP64:
+struct DF {
+    float* hi;      // [nch][H][pitch]
+    float* lo;      // same layout, second half of the allocation
+};
+struct DFc {
+    const float* hi;
+    const float* lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    e = b - (s - a);
+}
+// (ah, al) + (bh, bl), renormalised.
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& sh, float& sl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e += al + bl;
+    fast_two_sum(s, e, sh, sl);
+}
+// Split of an FP64 value into a double-float pair.
+__device__ __forceinline__ void df_from_d(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+// Right-hand side of the fine-level system:
 //   RHS_DATA   : b = C d            (d = f for inpainting, d = g for B g)
 //   RHS_SOURCE : b = (I - C)(d - y) (the adjoint solve of Sec. 5.1)
 enum { RHS_DATA = 0, RHS_SOURCE = 1 };
-// Value of the FP64 iterate on unknown pixels before the residual:
+// Value of the iterate on unknown pixels before the residual:
 //   INIT_KEEP   : u = uin
 //   INIT_UPDATE : u = uin + e (FP32 correction from the V-cycle)
 //   INIT_FROM32 : u = x (FP32 FMG result)
 //   INIT_ZERO   : u = 0
 // In every mode known pixels take their Dirichlet value (d, or 0 for
-// RHS_SOURCE), so u_K is exact in FP64. The result goes to uout, which must
-// not alias uin (neighbouring tiles read uin as their halo).
+// RHS_SOURCE), so u_K is exact. The result goes to uout, which must not alias
+// uin (neighbouring tiles read uin as their halo).
 enum { INIT_KEEP = 0, INIT_UPDATE = 1, INIT_FROM32 = 2, INIT_ZERO = 3 };
 
-struct Res64Args {
+struct ResArgs {
     LevelArr F;           // level-0 geometry
     MaskView m;
-    const double* uin;    // FP64 iterate before the step
-    double* uout;         // FP64 iterate after the step
+    DFc uin;              // iterate before the step
+    DF uout;              // iterate after the step
     const float* x32;     // INIT_UPDATE: correction e; INIT_FROM32: x
-    const double* d;      // data (RHS_DATA) or minuend (RHS_SOURCE)
-    const double* y;      // subtrahend (RHS_SOURCE; nullptr = 0)
-    float* r32;           // out: residual in FP32 (V-cycle right-hand side)
+    DFc d;                // data (RHS_DATA) or minuend (RHS_SOURCE)
+    DFc y;                // subtrahend (RHS_SOURCE; hi == nullptr means 0)
+    float* r32;           // out: residual rounded to FP32 (V-cycle right-hand side)
     GridReduce red_r;     // ||r||^2 per channel
     GridReduce red_b;     // ||b||^2 per channel (only if want_b)
     int want_b;
 };
 
 template <int RHS, int INIT>
-__global__ void __launch_bounds__(PT_W * PT_H) k_residual64(Res64Args a) {
-    __shared__ double t[PT_H + 2][PT_W + 2];
+__global__ void __launch_bounds__(PT_W * PT_H) k_residual_df(ResArgs a) {
+    __shared__ float th[PT_H + 2][PT_W + 2];
+    __shared__ float tl[PT_H + 2][PT_W + 2];
     const int ch = blockIdx.z;
     const int bx0 = blockIdx.x * PT_W, by0 = blockIdx.y * PT_H;
     const long long co = ch * a.F.cs;
@@ -251,85 +291,120 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_residual64(Res64Args a) {
         const int px = min(max(bx0 + tx - 1, 0), a.F.W - 1);
         const int py = min(max(by0 + ty - 1, 0), a.F.H - 1);
         const size_t idx = co + (size_t)py * a.F.pitch + px;
-        double v;
+        float h, l;
         if (a.m.known(px, py)) {
-            v = (RHS == RHS_DATA) ? a.d[idx] : 0.0;
+            if (RHS == RHS_DATA) { h = a.d.hi[idx]; l = a.d.lo[idx]; }
+            else { h = 0.f; l = 0.f; }
+        } else if (INIT == INIT_KEEP) {
+            h = a.uin.hi[idx]; l = a.uin.lo[idx];
+        } else if (INIT == INIT_UPDATE) {
+            df_add(a.uin.hi[idx], a.uin.lo[idx], a.x32[idx], 0.f, h, l);
+        } else if (INIT == INIT_FROM32) {
+            h = a.x32[idx]; l = 0.f;
         } else {
-            if (INIT == INIT_KEEP) v = a.uin[idx];
-            else if (INIT == INIT_UPDATE) v = a.uin[idx] + (double)a.x32[idx];
-            else if (INIT == INIT_FROM32) v = (double)a.x32[idx];
-            else v = 0.0;
+            h = 0.f; l = 0.f;
         }
-        t[ty][tx] = v;
+        th[ty][tx] = h;
+        tl[ty][tx] = l;
     }
     __syncthreads();
     const int px = bx0 + threadIdx.x, py = by0 + threadIdx.y;
-    double sq = 0.0, sb = 0.0;
+    float rr = 0.f, bb2 = 0.f;
     if (px < a.F.W && py < a.F.H) {
         const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
         const size_t idx = co + (size_t)py * a.F.pitch + px;
-        const double v = t[ty][tx];
-        a.uout[idx] = v;
-        double r, bv;
+        const float ch_ = th[ty][tx], cl = tl[ty][tx];
+        a.uout.hi[idx] = ch_;
+        a.uout.lo[idx] = cl;
+        float r = 0.f;
         if (a.m.known(px, py)) {
-            bv = (RHS == RHS_DATA) ? a.d[idx] : 0.0;
-            r = bv - v;
+            if (RHS == RHS_DATA) { const float bh = a.d.hi[idx] + a.d.lo[idx]; bb2 = bh * bh; }
         } else {
-            bv = (RHS == RHS_DATA) ? 0.0 : (a.d[idx] - (a.y ? a.y[idx] : 0.0));
-            double lap = 0.0;
-            if (px > 0) lap += v - t[ty][tx - 1];
-            if (px + 1 < a.F.W) lap += v - t[ty][tx + 1];
-            if (py > 0) lap += v - t[ty - 1][tx];
-            if (py + 1 < a.F.H) lap += v - t[ty + 1][tx];
-            r = bv - lap;
+            // lap = sum over in-image neighbours of (u_c - u_n), error-free:
+            // the hi differences are summed with TwoSum, every rounding error
+            // and the lo differences go to the low-order accumulator.
+            float sh = 0.f, sl = 0.f;
+            const int nx[4] = {tx - 1, tx + 1, tx, tx};
+            const int ny[4] = {ty, ty, ty - 1, ty + 1};
+            const bool ok[4] = {px > 0, px + 1 < a.F.W, py > 0, py + 1 < a.F.H};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (ok[k]) {
+                    float dh, dl, s2, e2;
+                    two_sum(ch_, -th[ny[k]][nx[k]], dh, dl);
+                    dl += cl - tl[ny[k]][nx[k]];
+                    two_sum(sh, dh, s2, e2);
+                    sh = s2;
+                    sl += e2 + dl;
+                }
+            }
+            float bh = 0.f, bl = 0.f;
+            if (RHS == RHS_SOURCE) {
+                const float yh = a.y.hi ? a.y.hi[idx] : 0.f, yl = a.y.hi ? a.y.lo[idx] : 0.f;
+                df_add(a.d.hi[idx], a.d.lo[idx], -yh, -yl, bh, bl);
+                bb2 = bh * bh;
+            }
+            float rh, rl;
+            df_add(bh, bl, -sh, -sl, rh, rl);
+            r = rh + rl;
         }
-        a.r32[idx] = (float)r;
-        sq = r * r;
-        sb = bv * bv;
+        a.r32[idx] = r;
+        rr = r * r;
     }
-    const double tot = block_sum_d(sq);
+    rr = warp_sum_f(rr);
+    const double tot = block_sum_d((threadIdx.x & 31) == 0 ? (double)rr : 0.0);
     grid_reduce_commit(a.red_r, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
     if (a.want_b) {
-        const double totb = block_sum_d(sb);
+        bb2 = warp_sum_f(bb2);
+        const double totb = block_sum_d((threadIdx.x & 31) == 0 ? (double)bb2 : 0.0);
         grid_reduce_commit(a.red_b, ch, blockIdx.y * gridDim.x + blockIdx.x, totb);
     }
 }
 
 // ------------------------------------------------------------ staging ---
 
-// Caller image (F32/F64, any strides) -> internal FP64 [nch][H][pitch];
+// Caller image (F32/F64, any strides) -> internal double-float pair;
 // flags non-finite values.
 template <typename T>
-__global__ void k_load_image(const T* __restrict__ src, long long rs, long long cs, LevelArr F,
-                             double* __restrict__ dst, unsigned* bad) {
+__global__ void k_load_image(const T* __restrict__ src, long long rs, long long cs, LevelArr F, DF dst,
+                             unsigned* bad) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     const int ch = blockIdx.z;
     if (x >= F.W) return;
-    const double v = (double)src[ch * cs + (size_t)y * rs + x];
+    const T v = src[ch * cs + (size_t)y * rs + x];
     if (!isfinite(v)) atomicOr(bad, 1u);
-    dst[ch * F.cs + (size_t)y * F.pitch + x] = v;
+    float h, l;
+    if (sizeof(T) == 8) df_from_d((double)v, h, l);
+    else { h = (float)v; l = 0.f; }
+    const size_t idx = ch * F.cs + (size_t)y * F.pitch + x;
+    dst.hi[idx] = h;
+    dst.lo[idx] = l;
 }
 
-// Internal FP64 -> caller image; with zero_off_mask, pixels off the mask are 0.
+// Internal double-float -> caller image; with zero_off_mask, pixels off the
+// mask are 0.
 template <typename T>
-__global__ void k_store_image(const double* __restrict__ src, LevelArr F, MaskView m, int zero_off_mask,
-                              T* __restrict__ dst, long long rs, long long cs) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    const int ch = blockIdx.z;
-    if (x >= F.W) return;
-    double v = src[ch * F.cs + (size_t)y * F.pitch + x];
-    if (zero_off_mask && !m.known(x, y)) v = 0.0;
-    dst[ch * cs + (size_t)y * rs + x] = (T)v;
-}
-
-// FP64 data at known pixels -> FP32 (FMG right-hand side on level 0), 0 elsewhere.
-__global__ void k_data_to_f32(const double* __restrict__ d, LevelArr F, MaskView m, float* __restrict__ out) {
+__global__ void k_store_image(DFc src, LevelArr F, MaskView m, int zero_off_mask, T* __restrict__ dst,
+                              long long rs, long long cs) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     const int ch = blockIdx.z;
     if (x >= F.W) return;
     const size_t idx = ch * F.cs + (size_t)y * F.pitch + x;
-    out[idx] = m.known(x, y) ? (float)d[idx] : 0.f;
+    T v;
+    if (sizeof(T) == 8) v = (T)((double)src.hi[idx] + (double)src.lo[idx]);
+    else v = (T)(src.hi[idx] + src.lo[idx]);
+    if (zero_off_mask && !m.known(x, y)) v = (T)0;
+    dst[ch * cs + (size_t)y * rs + x] = v;
+}
+
+// Data at known pixels -> FP32 (FMG right-hand side on level 0), 0 elsewhere.
+__global__ void k_data_to_f32(DFc d, LevelArr F, MaskView m, float* __restrict__ out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int ch = blockIdx.z;
+    if (x >= F.W) return;
+    const size_t idx = ch * F.cs + (size_t)y * F.pitch + x;
+    out[idx] = m.known(x, y) ? d.hi[idx] + d.lo[idx] : 0.f;
 }

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
             for (int p0 = 0; p0 < 1024; p0 += 32) {
                 __syncthreads();
                 for (int q = tid; q < 32 * 64; q += 256) {
-                    const int pp = q / 64, kk = q % 64;
+                    const int kk = q >> 5, pp = q & 31;   // consecutive threads read consecutive pixels
                     const int ka = ti * 64 + kk, kb = tj * 64 + kk;
                     tA[pp * 64 + kk] = (ka < m) ? E[(size_t)ka * 1024 + p0 + pp] : 0.f;
                     tB[pp * 64 + kk] = (kb < m) ? E[(size_t)kb * 1024 + p0 + pp] : 0.f;
@@ -201,32 +201,36 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
 // ------------------------------------------------------- outer iteration ---
 
 // r_K = (f - y)_K + sum of w over the unknown 4-neighbours (B^T (f - y)),
-// and per channel ||r||^2 and ||f - y||^2 (the tonal MSE numerator).
-// y == nullptr means y = 0 (gives B^T f).
-__global__ void __launch_bounds__(256) k_tonal_residual(LevelArr F, MaskView m, const double* __restrict__ f,
-                                                        const double* __restrict__ y, const double* __restrict__ w,
-                                                        double* __restrict__ r, GridReduce red_r, GridReduce red_e) {
+// stored in FP32 for the local solves, and per channel ||r||^2 and
+// ||f - y||^2 (the tonal MSE numerator). y.hi == nullptr means y = 0 (B^T f).
+// The sums on mask pixels (a few percent of the image) are formed in FP64.
+__global__ void __launch_bounds__(256) k_tonal_residual(LevelArr F, MaskView m, DFc f, DFc y, DFc w,
+                                                        float* __restrict__ r, GridReduce red_r, GridReduce red_e) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int yy = blockIdx.y * blockDim.y + threadIdx.y;
     const int ch = blockIdx.z;
-    double sr = 0.0, se = 0.0;
+    float se = 0.f;
+    double sr = 0.0;
     if (x < F.W && yy < F.H) {
         const size_t idx = ch * F.cs + (size_t)yy * F.pitch + x;
-        const double s = f[idx] - (y ? y[idx] : 0.0);
-        se = s * s;
+        float sh, sl;
+        if (y.hi) df_add(f.hi[idx], f.lo[idx], -y.hi[idx], -y.lo[idx], sh, sl);
+        else { sh = f.hi[idx]; sl = f.lo[idx]; }
+        se = sh * sh;
         if (m.known(x, yy)) {
-            double acc = s;
-            if (x > 0 && !m.known(x - 1, yy)) acc += w[idx - 1];
-            if (x + 1 < F.W && !m.known(x + 1, yy)) acc += w[idx + 1];
-            if (yy > 0 && !m.known(x, yy - 1)) acc += w[idx - F.pitch];
-            if (yy + 1 < F.H && !m.known(x, yy + 1)) acc += w[idx + F.pitch];
-            r[idx] = acc;
+            double acc = (double)sh + (double)sl;
+            if (x > 0 && !m.known(x - 1, yy)) acc += (double)w.hi[idx - 1] + (double)w.lo[idx - 1];
+            if (x + 1 < F.W && !m.known(x + 1, yy)) acc += (double)w.hi[idx + 1] + (double)w.lo[idx + 1];
+            if (yy > 0 && !m.known(x, yy - 1)) acc += (double)w.hi[idx - F.pitch] + (double)w.lo[idx - F.pitch];
+            if (yy + 1 < F.H && !m.known(x, yy + 1)) acc += (double)w.hi[idx + F.pitch] + (double)w.lo[idx + F.pitch];
+            r[idx] = (float)acc;
             sr = acc * acc;
         }
     }
     const double tr = block_sum_d(sr);
     grid_reduce_commit(red_r, ch, blockIdx.y * gridDim.x + blockIdx.x, tr);
-    const double te = block_sum_d(se);
+    se = warp_sum_f(se);
+    const double te = block_sum_d((threadIdx.x & 31) == 0 ? (double)se : 0.0);
     grid_reduce_commit(red_e, ch, blockIdx.y * gridDim.x + blockIdx.x, te);
 }
 
@@ -237,8 +241,8 @@ struct LocalSolveArgs {
     const long long* goff;
     const uint16_t* list;
     const float* fac;
-    const double* r;
-    double* g;
+    const float* r;
+    DF g;
 };
 
 // Number of subdomains covering coordinate x along an axis (1 or 2).
@@ -271,11 +275,11 @@ __global__ void __launch_bounds__(128) k_tonal_local(LocalSolveArgs a) {
     const uint16_t* lst = a.list + a.off[i];
     const float* L = a.fac + a.goff[i];
     const int x0 = bx * a.stride, y0 = by * a.stride;
-    const double* r = a.r + ch * a.F.cs;
+    const float* r = a.r + ch * a.F.cs;
     float* v = sv[wl];
     for (int k = lane; k < m; k += 32) {
         const int code = lst[k];
-        v[k] = (float)r[(size_t)(y0 + (code >> 5)) * a.F.pitch + x0 + (code & 31)];
+        v[k] = r[(size_t)(y0 + (code >> 5)) * a.F.pitch + x0 + (code & 31)];
     }
     __syncwarp();
     // forward: L y = r (column-oriented)
@@ -295,12 +299,15 @@ __global__ void __launch_bounds__(128) k_tonal_local(LocalSolveArgs a) {
         for (int k = lane; k < j; k += 32) v[k] -= Lj[k] * xj;
         __syncwarp();
     }
-    double* g = a.g + ch * a.F.cs;
     for (int k = lane; k < m; k += 32) {
         const int code = lst[k];
         const int px = x0 + (code & 31), py = y0 + (code >> 5);
         const int mult = cover_count(px, a.nbx, a.stride) * cover_count(py, a.nby, a.stride);
-        g[(size_t)py * a.F.pitch + px] += (double)v[k] / (double)mult;
+        const size_t idx = ch * a.F.cs + (size_t)py * a.F.pitch + px;
+        float h, l;
+        df_add(a.g.hi[idx], a.g.lo[idx], v[k] / (float)mult, 0.f, h, l);
+        a.g.hi[idx] = h;
+        a.g.lo[idx] = l;
     }
 }
 
@@ -375,13 +382,13 @@ int Ctx::tonal_setup() {
     return sync("tonal setup");
 }
 
-void Ctx::tonal_residual(const double* y, const double* w, double* r) {
+void Ctx::tonal_residual(DFc y, DFc w) {
     dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8, nch);
-    k_tonal_residual<<<grd, blk, 0, stream>>>(arr(0), mview(0), f64[kF], y, w, r, reducer(kSlotTonalR, grd.x * grd.y),
-                                              reducer(kSlotTonalE, grd.x * grd.y));
+    k_tonal_residual<<<grd, blk, 0, stream>>>(arr(0), mview(0), cview(dfv[kF]), y, w, tres,
+                                              reducer(kSlotTonalR, grd.x * grd.y), reducer(kSlotTonalE, grd.x * grd.y));
 }
 
-void Ctx::tonal_local(double* g) {
+void Ctx::tonal_local(DF g) {
     const Level& L0 = lev[0];
     for (int color = 0; color < 4; ++color) {
         LocalSolveArgs a;
@@ -395,7 +402,7 @@ void Ctx::tonal_local(double* g) {
         a.goff = t_goff;
         a.list = t_list;
         a.fac = t_fac;
-        a.r = f64[kR];
+        a.r = tres;
         a.g = g;
         const int hx = (L0.nbx + 1 - (color & 1)) / 2;
         const int hy = (L0.nby + 1 - (color >> 1)) / 2;
@@ -426,13 +433,13 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     long long ones = 0;
     if ((rc = load_mask(mask, &ones))) return rc;
     if (ones == 0) return fail(HDI_ERR_EMPTY_MASK, "empty mask: A is singular");
-    double* F = f64[kF];
-    double* G = f64[kG];
-    if ((rc = load_image(f, F))) return rc;
+    const DFc F = cview(dfv[kF]);
+    DF G = dfv[kG];
+    if ((rc = load_image(f, dfv[kF]))) return rc;
     if (g0) {
         if ((rc = load_image(g0, G))) return rc;
     } else {
-        cudaMemcpyAsync(G, F, (size_t)nch * lev[0].cs * 8, cudaMemcpyDeviceToDevice, stream);
+        cudaMemcpyAsync(G.hi, F.hi, (size_t)nch * lev[0].cs * 8, cudaMemcpyDeviceToDevice, stream);
     }
     vcycles_run = 0;
     cudaMemsetAsync(counters + kCntLocal, 0, 16, stream);
@@ -441,28 +448,27 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     const double ratio = p.tonal_inner_ratio;
     // ||B^T f||: w_f solves A w = (I - C) f.
     SolveSpec sw;
-    sw.u[0] = f64[kW0];
-    sw.u[1] = f64[kW1];
+    sw.u[0] = dfv[kW0];
+    sw.u[1] = dfv[kW1];
     sw.cur = 0;
     sw.rhs = RHS_SOURCE;
     sw.d = F;
-    sw.y = nullptr;
+    sw.y = DFc{nullptr, nullptr};
     sw.start = START_ZERO;
     sw.tol = std::max(1e-13, ratio * tol);
     sw.max_iter = (int)p.max_vcycles;
     rc = solve(sw);
     if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return rc;
-    tonal_residual(nullptr, sw.u[sw.cur], f64[kR]);
+    tonal_residual(DFc{nullptr, nullptr}, cview(sw.u[sw.cur]));
     double btf2[4], r2[4], e2[4];
     if ((rc = read_slot(kSlotTonalR, btf2))) return rc;
 
     SolveSpec sy;
-    sy.u[0] = f64[kY0];
-    sy.u[1] = f64[kY1];
+    sy.u[0] = dfv[kY0];
+    sy.u[1] = dfv[kY1];
     sy.cur = 0;
     sy.rhs = RHS_DATA;
-    sy.d = G;
-    sy.y = nullptr;
+    sy.d = cview(G);
     sy.start = START_FMG;
     sy.max_iter = (int)p.max_vcycles;
     sw.start = START_WARM;
@@ -477,10 +483,10 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
         if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return rc;
         sy.start = START_WARM;
         sw.tol = tin;
-        sw.y = sy.u[sy.cur];
+        sw.y = cview(sy.u[sy.cur]);
         rc = solve(sw);
         if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return rc;
-        tonal_residual(sy.u[sy.cur], sw.u[sw.cur], f64[kR]);
+        tonal_residual(cview(sy.u[sy.cur]), cview(sw.u[sw.cur]));
         if ((rc = read_slot(kSlotTonalR, r2))) return rc;
         if ((rc = read_slot(kSlotTonalE, e2))) return rc;
         rel_max = 0.0;
@@ -496,7 +502,7 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
         rel_prev = rel_max;
         tonal_local(G);
     }
-    if ((rc = store_image(G, g, true))) return rc;
+    if ((rc = store_image(cview(G), g, true))) return rc;
     if (st) {
         unsigned long long li[2] = {0, 0};
         cudaMemcpy(li, counters + kCntLocal, 16, cudaMemcpyDeviceToHost);
