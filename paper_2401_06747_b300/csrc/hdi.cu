@@ -133,6 +133,7 @@ int Ctx::setup(int H_, int W_, int nch_) {
     const size_t n32 = (size_t)nch_ * H_ * P0;
     for (int k = 0; k < kNumDF; ++k) acc(n32 * 8);            // double-float vectors
     acc(n32 * 4);                                             // tonal residual
+    acc(n32 * 4);                                             // third component of f
     acc((size_t)kSlots * maxparts * nch_ * 8);                // reduction partials
     acc((size_t)kSlots * 4 * 8);                              // reduction outputs
     acc((size_t)kSlots * 4);                                  // tickets
@@ -159,6 +160,7 @@ int Ctx::setup(int H_, int W_, int nch_) {
         dfv[i].lo = dfv[i].hi + n32;
     }
     tres = (float*)ws.take(n32 * 4);
+    flo2 = (float*)ws.take(n32 * 4);
     maxparts_ = maxparts;
     partials = (double*)ws.take((size_t)kSlots * maxparts * nch * 8);
     scal = (double*)ws.take((size_t)kSlots * 4 * 8);
@@ -403,7 +405,7 @@ int Ctx::check_image(const hdi_image* im, const char* name, int H_, int W_, int 
 }
 
 // Copies a caller image into the internal FP64 layout (device or host source).
-int Ctx::load_image(const hdi_image* im, DF dst) {
+int Ctx::load_image(const hdi_image* im, DF dst, float* lo2) {
     const void* src = im->data;
     long long rs = im->row_stride, cs = im->channel_stride;
     const size_t es = im->dtype == HDI_F64 ? 8 : 4;
@@ -425,9 +427,9 @@ int Ctx::load_image(const hdi_image* im, DF dst) {
     cudaMemsetAsync(flags, 0, 4, stream);
     dim3 grd((W + 127) / 128, H, nch);
     if (im->dtype == HDI_F64)
-        k_load_image<double><<<grd, 128, 0, stream>>>((const double*)src, rs, cs, arr(0), dst, flags);
+        k_load_image<double><<<grd, 128, 0, stream>>>((const double*)src, rs, cs, arr(0), dst, lo2, flags);
     else
-        k_load_image<float><<<grd, 128, 0, stream>>>((const float*)src, rs, cs, arr(0), dst, flags);
+        k_load_image<float><<<grd, 128, 0, stream>>>((const float*)src, rs, cs, arr(0), dst, lo2, flags);
     unsigned bad = 0;
     cudaMemcpyAsync(&bad, flags, 4, cudaMemcpyDeviceToHost, stream);
     int rc = sync("image upload");
@@ -436,7 +438,7 @@ int Ctx::load_image(const hdi_image* im, DF dst) {
     return HDI_OK;
 }
 
-int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask) {
+int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2) {
     void* dst = im->data;
     long long rs = im->row_stride, cs = im->channel_stride;
     const size_t es = im->dtype == HDI_F64 ? 8 : 4;
@@ -451,9 +453,11 @@ int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask) {
     }
     dim3 grd((W + 127) / 128, H, nch);
     if (im->dtype == HDI_F64)
-        k_store_image<double><<<grd, 128, 0, stream>>>(src, arr(0), mview(0), zero_off_mask, (double*)dst, rs, cs);
+        k_store_image<double><<<grd, 128, 0, stream>>>(src, arr(0), mview(0), zero_off_mask, known_lo2, (double*)dst,
+                                                       rs, cs);
     else
-        k_store_image<float><<<grd, 128, 0, stream>>>(src, arr(0), mview(0), zero_off_mask, (float*)dst, rs, cs);
+        k_store_image<float><<<grd, 128, 0, stream>>>(src, arr(0), mview(0), zero_off_mask, known_lo2, (float*)dst,
+                                                      rs, cs);
     if (host) {
         for (int c = 0; c < nch; ++c) {
             cudaError_t e = cudaMemcpy2DAsync((char*)im->data + (size_t)c * im->channel_stride * es,
@@ -632,7 +636,7 @@ int Ctx::inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, 
     long long ones = 0;
     if ((rc = load_mask(mask, &ones))) return rc;
     if (ones == 0) return fail(HDI_ERR_EMPTY_MASK, "empty mask: A is singular");
-    if ((rc = load_image(f, dfv[kF]))) return rc;
+    if ((rc = load_image(f, dfv[kF], flo2))) return rc;
     SolveSpec s;
     s.u[0] = dfv[kU0];
     s.u[1] = dfv[kU1];
@@ -651,7 +655,7 @@ int Ctx::inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, 
     cudaMemsetAsync(counters + kCntLocal, 0, 8, stream);
     const int src = solve(s);
     if (src != HDI_OK && src != HDI_ERR_NOT_CONVERGED) return src;
-    if ((rc = store_image(cview(s.u[s.cur]), u, false))) return rc;
+    if ((rc = store_image(cview(s.u[s.cur]), u, false, flo2))) return rc;
     if (st) {
         unsigned long long li = 0;
         cudaMemcpy(&li, counters + kCntLocal, 8, cudaMemcpyDeviceToHost);

@@ -87,7 +87,8 @@ struct Ctx {
     int H = 0, W = 0, nch = 0, nlev = 0;
     Level lev[kMaxLevels];
     DF dfv[kNumDF] = {};
-    float* tres = nullptr;     // tonal residual B^T (f - B g) on mask pixels, FP32
+    float* tres = nullptr;
+    float* flo2 = nullptr;     // bits of f below its double-float pair (FP64 input)     // tonal residual B^T (f - B g) on mask pixels, FP32
     double* partials = nullptr;
     double* scal = nullptr;
     unsigned* tickets = nullptr;
@@ -122,8 +123,8 @@ struct Ctx {
     void residual(int rhs, int init, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b);
     int solve(SolveSpec& s);
     int check_image(const hdi_image* im, const char* name, int H, int W, int nch);
-    int load_image(const hdi_image* im, DF dst);
-    int store_image(DFc src, hdi_image* im, bool zero_off_mask);
+    int load_image(const hdi_image* im, DF dst, float* lo2 = nullptr);
+    int store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2 = nullptr);
     int load_mask(const hdi_mask* m, long long* ones);
     int read_slot(int slot, double* out);
     int tonal_setup();

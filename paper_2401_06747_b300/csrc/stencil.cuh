@@ -364,10 +364,12 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_residual_df(ResArgs a) {
 // ------------------------------------------------------------ staging ---
 
 // Caller image (F32/F64, any strides) -> internal double-float pair;
-// flags non-finite values.
+// flags non-finite values. For FP64 input, lo2 (if given) receives the bits
+// below the pair, (v - hi) - lo, which are exact in FP32, so that
+// hi + lo + lo2 reproduces v exactly.
 template <typename T>
 __global__ void k_load_image(const T* __restrict__ src, long long rs, long long cs, LevelArr F, DF dst,
-                             unsigned* bad) {
+                             float* __restrict__ lo2, unsigned* bad) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     const int ch = blockIdx.z;
@@ -380,21 +382,28 @@ __global__ void k_load_image(const T* __restrict__ src, long long rs, long long 
     const size_t idx = ch * F.cs + (size_t)y * F.pitch + x;
     dst.hi[idx] = h;
     dst.lo[idx] = l;
+    if (lo2) lo2[idx] = (sizeof(T) == 8) ? (float)(((double)v - (double)h) - (double)l) : 0.f;
 }
 
 // Internal double-float -> caller image; with zero_off_mask, pixels off the
-// mask are 0.
+// mask are 0. known_lo2 (if given) adds the third component of the data on
+// known pixels, so inpainted FP64 output equals f there bit for bit.
 template <typename T>
-__global__ void k_store_image(DFc src, LevelArr F, MaskView m, int zero_off_mask, T* __restrict__ dst,
-                              long long rs, long long cs) {
+__global__ void k_store_image(DFc src, LevelArr F, MaskView m, int zero_off_mask, const float* __restrict__ known_lo2,
+                              T* __restrict__ dst, long long rs, long long cs) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     const int ch = blockIdx.z;
     if (x >= F.W) return;
     const size_t idx = ch * F.cs + (size_t)y * F.pitch + x;
     T v;
-    if (sizeof(T) == 8) v = (T)((double)src.hi[idx] + (double)src.lo[idx]);
-    else v = (T)(src.hi[idx] + src.lo[idx]);
+    if (sizeof(T) == 8) {
+        double dv = (double)src.hi[idx] + (double)src.lo[idx];
+        if (known_lo2 && m.known(x, y)) dv += (double)known_lo2[idx];
+        v = (T)dv;
+    } else {
+        v = (T)(src.hi[idx] + src.lo[idx]);
+    }
     if (zero_off_mask && !m.known(x, y)) v = (T)0;
     dst[ch * cs + (size_t)y * rs + x] = v;
 }

@@ -458,7 +458,7 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     sw.tol = std::max(1e-13, ratio * tol);
     sw.max_iter = (int)p.max_vcycles;
     rc = solve(sw);
-    if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return rc;
+    if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return fail(rc, "tonal: B^T f solve: %s", err.c_str());
     tonal_residual(DFc{nullptr, nullptr}, cview(sw.u[sw.cur]));
     double btf2[4], r2[4], e2[4];
     if ((rc = read_slot(kSlotTonalR, btf2))) return rc;
@@ -480,12 +480,14 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
         const double tin = std::max(1e-13, std::min(1e-3, ratio * rel_prev));
         sy.tol = tin;
         rc = solve(sy);
-        if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return rc;
+        if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED)
+            return fail(rc, "tonal: B g solve, iteration %d: %s", it, err.c_str());
         sy.start = START_WARM;
         sw.tol = tin;
         sw.y = cview(sy.u[sy.cur]);
         rc = solve(sw);
-        if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return rc;
+        if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED)
+            return fail(rc, "tonal: adjoint solve, iteration %d: %s", it, err.c_str());
         tonal_residual(cview(sy.u[sy.cur]), cview(sw.u[sw.cur]));
         if ((rc = read_slot(kSlotTonalR, r2))) return rc;
         if ((rc = read_slot(kSlotTonalE, e2))) return rc;
