@@ -20,6 +20,7 @@ struct Params {
     double tonal_echo_rtol = 1e-4;
     double tonal_echo_max_iter = 300;
     double hbm_budget_gb = 200.0;
+    double trace = 0;               // 1: one line per outer iteration on stderr
 };
 
 struct Level {

@@ -500,6 +500,9 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
             esum += e2[c];
         }
         mse_last = esum / ((double)nch * H * W);
+        if (p.trace > 0)
+            fprintf(stderr, "[hdi tonal] it %d rel %.3e mse %.6f inner tol %.2e y: %d vc rel %.2e  w: %d vc rel %.2e\n",
+                    it, rel_max, mse_last, tin, sy.iterations, sy.rel_max, sw.iterations, sw.rel_max);
         if (rel_max <= tol || it >= max_it) break;
         rel_prev = rel_max;
         tonal_local(G);
