@@ -1,0 +1,156 @@
+// anderson.cuh -- Anderson acceleration of the RAS fixed-point iteration.
+//
+// Alg. 2 is the stationary iteration g <- g + P r(g), with P the weighted
+// sum of local solves and r(g) = B^T (f - B g) affine in g. Anderson
+// acceleration (type II, window m) replaces the plain step by
+//   g_{n+1} = g_n + f_n - (dX + dF) gamma,  gamma = argmin ||f_n - dF gamma||,
+// where f_n = P r_n and the columns of dX, dF are the last m differences of
+// iterates and of f. For an affine map this is a Krylov method over the
+// same residuals, so it needs no operator application beyond the warm-started
+// residual evaluations Alg. 2 already performs. All vectors live on the mask
+// pixels only, in a compact raster-order list.
+#pragma once
+#include "common.cuh"
+#include "stencil.cuh"
+
+constexpr int kAAMax = 8;   // largest Anderson window
+constexpr int kAAParts = 128;  // CTAs per channel of the dot-product kernel
+
+// Ones per row (warp per row).
+__global__ void k_row_counts(MaskView m, int* __restrict__ cnt) {
+    const int y = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (y >= m.H) return;
+    const int nw = (m.W + 31) / 32;
+    int c = 0;
+    for (int w = lane; w < nw; w += 32) c += __popc(m.bits[(size_t)y * m.wpitch + w]);
+    c = __reduce_add_sync(HDI_FULL, c);
+    if (lane == 0) cnt[y] = c;
+}
+
+// Compact list of known pixels, raster order: idx[rowoff[y] + k] = y*pitch + x.
+__global__ void k_compact_fill(MaskView m, int pitch, const int* __restrict__ rowoff, int* __restrict__ idx) {
+    const int y = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (y >= m.H) return;
+    const int nw = (m.W + 31) / 32;
+    int base = rowoff[y];
+    for (int w0 = 0; w0 < nw; w0 += 32) {
+        const int w = w0 + lane;
+        uint32_t bits = (w < nw) ? m.bits[(size_t)y * m.wpitch + w] : 0u;
+        const int c = __popc(bits);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(HDI_FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int pos = base + incl - c;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            idx[pos++] = y * pitch + w * 32 + b;
+        }
+        base += __shfl_sync(HDI_FULL, incl, 31);
+    }
+}
+
+struct AAArgs {
+    int M;              // known pixels per channel
+    long long cs;       // channel stride of the full-layout arrays
+    int nch, k, slot, mwin;
+    const int* idx;     // [M]
+    const float* fvfull;// P r in full layout (valid on known pixels)
+    float* fv;          // [nch][M] current f_n
+    float* fvprev;      // [nch][M] f_{n-1}
+    float* dF;          // [mwin][nch][M]
+    float* dX;          // [mwin][nch][M]
+    DF g;               // iterate (full layout)
+    const double* gamma;// [nch][kAAMax]
+    double* partials;   // dots: [nch][ndots][nparts]
+    double* out;        // [nch][ndots]
+    unsigned* ticket;
+    int nparts;
+};
+
+// Gather f_n, form dF of the newest slot (f_n - f_{n-1}) when n >= 1, and the
+// dot products dF_i . dF_j (i <= j) and dF_i . f_n of the active window, per
+// channel, reduced deterministically. Grid: (nparts, nch), 256 threads.
+template <int K>
+__global__ void __launch_bounds__(256) k_aa_gather(AAArgs a, int new_slot) {
+    const int ch = blockIdx.y;
+    const int part = blockIdx.x;
+    constexpr int ND = K * (K + 1) / 2 + K;
+    double acc[ND > 0 ? ND : 1];
+#pragma unroll
+    for (int q = 0; q < (ND > 0 ? ND : 1); ++q) acc[q] = 0.0;
+    const size_t co = (size_t)ch * a.M;
+    const size_t vs = (size_t)a.nch * a.M;   // stride between window slots
+    for (int i = part * 256 + threadIdx.x; i < a.M; i += a.nparts * 256) {
+        const float f = a.fvfull[ch * a.cs + a.idx[i]];
+        a.fv[co + i] = f;
+        if (new_slot >= 0) {
+            a.dF[(size_t)new_slot * vs + co + i] = f - a.fvprev[co + i];
+        }
+        a.fvprev[co + i] = f;
+        if (K > 0) {
+            float d[K > 0 ? K : 1];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const int s = (a.slot - j + a.mwin * 4) % a.mwin;
+                d[j] = a.dF[(size_t)s * vs + co + i];
+            }
+            int q = 0;
+#pragma unroll
+            for (int r = 0; r < K; ++r)
+#pragma unroll
+                for (int c = r; c < K; ++c) acc[q++] += (double)(d[r] * d[c]);
+#pragma unroll
+            for (int r = 0; r < K; ++r) acc[q++] += (double)(d[r] * f);
+        }
+    }
+    if (K == 0) return;
+    // block reduce each dot, deposit partials; last CTA per launch sums
+    for (int q = 0; q < ND; ++q) {
+        const double t = block_sum_d(acc[q]);
+        if (threadIdx.x == 0) a.partials[((size_t)ch * ND + q) * a.nparts + part] = t;
+    }
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(a.ticket, 1u);
+        last = (t == (unsigned)(a.nparts * a.nch - 1));
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int c = 0; c < a.nch; ++c)
+        for (int q = 0; q < ND; ++q) {
+            double s = 0.0;
+            for (int p = threadIdx.x; p < a.nparts; p += 256) s += __ldcg(a.partials + ((size_t)c * ND + q) * a.nparts + p);
+            s = block_sum_d(s);
+            if (threadIdx.x == 0) a.out[c * ND + q] = s;
+        }
+    if (threadIdx.x == 0) *a.ticket = 0u;
+}
+
+// step = f_n - sum_j gamma_j (dX_j + dF_j);  g += step;  dX[write_slot] = step.
+__global__ void __launch_bounds__(256) k_aa_update(AAArgs a, int write_slot) {
+    const int ch = blockIdx.y;
+    const size_t co = (size_t)ch * a.M;
+    const size_t vs = (size_t)a.nch * a.M;
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < a.M; i += gridDim.x * 256) {
+        float s = a.fv[co + i];
+        for (int j = 0; j < a.k; ++j) {
+            const int sl = (a.slot - j + a.mwin * 4) % a.mwin;
+            const float gj = (float)a.gamma[ch * kAAMax + j];
+            s -= gj * (a.dX[(size_t)sl * vs + co + i] + a.dF[(size_t)sl * vs + co + i]);
+        }
+        const size_t p = ch * a.cs + a.idx[i];
+        float h, l;
+        df_add(a.g.hi[p], a.g.lo[p], s, 0.f, h, l);
+        a.g.hi[p] = h;
+        a.g.lo[p] = l;
+        a.dX[(size_t)write_slot * vs + co + i] = s;
+    }
+}

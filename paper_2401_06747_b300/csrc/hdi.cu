@@ -40,6 +40,7 @@ const ParamDef kParams[] = {
     {"tonal_echo_max_iter", &Params::tonal_echo_max_iter, 1, 4096},
     {"hbm_budget_gb", &Params::hbm_budget_gb, 0.001, 1e6},
     {"trace", &Params::trace, 0, 1},
+    {"tonal_anderson", &Params::tonal_anderson, 0, 8},
 };
 
 }  // namespace

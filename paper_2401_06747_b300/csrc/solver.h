@@ -16,11 +16,12 @@ struct Params {
     double coarse_max_local = 600;
     double max_vcycles = 60;
     double tonal_max_iter = 400;
-    double tonal_inner_ratio = 0.05;
+    double tonal_inner_ratio = 1e-3;
     double tonal_echo_rtol = 1e-4;
     double tonal_echo_max_iter = 300;
     double hbm_budget_gb = 200.0;
-    double trace = 0;               // 1: one line per outer iteration on stderr
+    double trace = 0;
+    double tonal_anderson = 5;      // Anderson window on the RAS iteration (0 = plain Alg. 2)               // 1: one line per outer iteration on stderr
 };
 
 struct Level {
@@ -107,6 +108,17 @@ struct Ctx {
     float* t_echo = nullptr;
     float* t_fac = nullptr;
     long long t_total = 0;
+    // Anderson acceleration state (compact mask-pixel vectors)
+    int aa_M = 0;
+    int* aa_idx = nullptr;
+    float* aa_fv = nullptr;
+    float* aa_fvprev = nullptr;
+    float* aa_dF = nullptr;
+    float* aa_dX = nullptr;
+    double* aa_part = nullptr;
+    double* aa_out = nullptr;
+    double* aa_gam = nullptr;
+    unsigned* aa_ticket = nullptr;
 
     int fail(int code, const char* fmt, ...);
     int cuda_check(cudaError_t e, const char* what);
@@ -130,7 +142,8 @@ struct Ctx {
     int read_slot(int slot, double* out);
     int tonal_setup();
     void tonal_residual(DFc y, DFc w);
-    void tonal_local(DF g);
+    void tonal_local(float* out);
+    int tonal_aa_step(int n, const float* fvfull, DF G);
     int inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,
                 hdi_stats* st);
     int tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hdi_image* g, double tol,

@@ -21,6 +21,7 @@
 // by two triangular solves instead of the paper's inner CGNR iterations.
 #pragma once
 #include "oras.cuh"
+#include "anderson.cuh"
 
 constexpr int kTonalMaxM = 192;   // mask pixels per 32x32 subdomain handled by the dense local solve
 
@@ -242,7 +243,7 @@ struct LocalSolveArgs {
     const uint16_t* list;
     const float* fac;
     const float* r;
-    DF g;
+    float* out;      // full layout, accumulates D_i v_i (zeroed before the first colour)
 };
 
 // Number of subdomains covering coordinate x along an axis (1 or 2).
@@ -254,7 +255,7 @@ __device__ __forceinline__ int cover_count(int x, int nb, int stride) {
 
 // Local solves of one colour class ((bx & 1) | (by & 1) << 1 == color):
 // v = (L L^T)^{-1} R_i r by forward and backward substitution, then
-// g += D_i v. Subdomains of one colour never overlap (stride 26 > 32/2), so
+// out += D_i v (out = P r after all four colours). Subdomains of one colour never overlap (stride 26 > 32/2), so
 // the updates need no atomics and their order is fixed. One warp per
 // (subdomain, channel).
 __global__ void __launch_bounds__(128) k_tonal_local(LocalSolveArgs a) {
@@ -303,11 +304,7 @@ __global__ void __launch_bounds__(128) k_tonal_local(LocalSolveArgs a) {
         const int code = lst[k];
         const int px = x0 + (code & 31), py = y0 + (code >> 5);
         const int mult = cover_count(px, a.nbx, a.stride) * cover_count(py, a.nby, a.stride);
-        const size_t idx = ch * a.F.cs + (size_t)py * a.F.pitch + px;
-        float h, l;
-        df_add(a.g.hi[idx], a.g.lo[idx], v[k] / (float)mult, 0.f, h, l);
-        a.g.hi[idx] = h;
-        a.g.lo[idx] = l;
+        a.out[ch * a.F.cs + (size_t)py * a.F.pitch + px] += v[k] / (float)mult;
     }
 }
 
@@ -322,8 +319,9 @@ int Ctx::tonal_setup() {
     std::vector<int> cnt(nb), off(nb + 1);
     std::vector<long long> goff(nb + 1);
     int* dcnt = nullptr;
-    if ((rc = tws.reserve(*this, std::max(tws.cap, (size_t)(nb + 1) * 24 + 4096), "tonal counts"))) return rc;
-    dcnt = (int*)tws.take((size_t)nb * 4);
+    const int ncnt = std::max(nb, H) + 1;
+    if ((rc = tws.reserve(*this, std::max(tws.cap, (size_t)ncnt * 24 + 4096), "tonal counts"))) return rc;
+    dcnt = (int*)tws.take((size_t)ncnt * 4);
     k_tonal_count<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), L0.nbx, L0.nby, stride, dcnt);
     cudaMemcpyAsync(cnt.data(), dcnt, (size_t)nb * 4, cudaMemcpyDeviceToHost, stream);
     if ((rc = sync("tonal subdomain counts"))) return rc;
@@ -338,9 +336,27 @@ int Ctx::tonal_setup() {
     if (maxm > kTonalMaxM)
         return fail(HDI_ERR_UNSUPPORTED, "tonal: a 32x32 subdomain holds %d mask pixels (limit %d)", maxm, kTonalMaxM);
     const long long total = off[nb];
+    // compact list of mask pixels (row counts on the device, scan on the host)
+    std::vector<int> rc_h(H), rowoff(H + 1);
+    int* drc = dcnt;
+    k_row_counts<<<(H + 3) / 4, 128, 0, stream>>>(mview(0), drc);
+    cudaMemcpyAsync(rc_h.data(), drc, (size_t)H * 4, cudaMemcpyDeviceToHost, stream);
+    if ((rc = sync("mask row counts"))) return rc;
+    rowoff[0] = 0;
+    for (int y = 0; y < H; ++y) rowoff[y + 1] = rowoff[y] + rc_h[y];
+    const int M = rowoff[H];
+    const int mwin = (int)p.tonal_anderson;
     // layout
     size_t bytes = 0;
     auto acc = [&](size_t b) { bytes += (b + 255) & ~(size_t)255; };
+    acc((size_t)(H + 1) * 4);
+    acc((size_t)M * 4);
+    acc((size_t)nch * M * 4 * 2);
+    acc((size_t)std::max(mwin, 1) * nch * M * 4 * 2);
+    acc((size_t)nch * 64 * kAAParts * 8);
+    acc((size_t)4 * 64 * 8);
+    acc((size_t)4 * kAAMax * 8);
+    acc(256);
     acc((size_t)(nb + 1) * 4);
     acc((size_t)(nb + 1) * 8);
     acc((size_t)total * 2);
@@ -352,6 +368,20 @@ int Ctx::tonal_setup() {
     t_list = (uint16_t*)tws.take((size_t)total * 2);
     t_echo = (float*)tws.take((size_t)total * 1024 * 4);
     t_fac = (float*)tws.take((size_t)goff[nb] * 4);
+    int* drowoff = (int*)tws.take((size_t)(H + 1) * 4);
+    aa_idx = (int*)tws.take((size_t)M * 4);
+    aa_fv = (float*)tws.take((size_t)nch * M * 4);
+    aa_fvprev = (float*)tws.take((size_t)nch * M * 4);
+    aa_dF = (float*)tws.take((size_t)std::max(mwin, 1) * nch * M * 4);
+    aa_dX = (float*)tws.take((size_t)std::max(mwin, 1) * nch * M * 4);
+    aa_part = (double*)tws.take((size_t)nch * 64 * kAAParts * 8);
+    aa_out = (double*)tws.take((size_t)4 * 64 * 8);
+    aa_gam = (double*)tws.take((size_t)4 * kAAMax * 8);
+    aa_ticket = (unsigned*)tws.take(256);
+    cudaMemsetAsync(aa_ticket, 0, 256, stream);
+    aa_M = M;
+    cudaMemcpyAsync(drowoff, rowoff.data(), (size_t)(H + 1) * 4, cudaMemcpyHostToDevice, stream);
+    k_compact_fill<<<(H + 3) / 4, 128, 0, stream>>>(mview(0), lev[0].P, drowoff, aa_idx);
     cudaMemcpyAsync(t_off, off.data(), (size_t)(nb + 1) * 4, cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(t_goff, goff.data(), (size_t)(nb + 1) * 8, cudaMemcpyHostToDevice, stream);
     k_tonal_list<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), L0.nbx, L0.nby, stride, t_off, t_list);
@@ -388,7 +418,7 @@ void Ctx::tonal_residual(DFc y, DFc w) {
                                               reducer(kSlotTonalR, grd.x * grd.y), reducer(kSlotTonalE, grd.x * grd.y));
 }
 
-void Ctx::tonal_local(DF g) {
+void Ctx::tonal_local(float* out) {
     const Level& L0 = lev[0];
     for (int color = 0; color < 4; ++color) {
         LocalSolveArgs a;
@@ -403,13 +433,114 @@ void Ctx::tonal_local(DF g) {
         a.list = t_list;
         a.fac = t_fac;
         a.r = tres;
-        a.g = g;
+        a.out = out;
         const int hx = (L0.nbx + 1 - (color & 1)) / 2;
         const int hy = (L0.nby + 1 - (color >> 1)) / 2;
         const long long warps = (long long)hx * hy * nch;
         if (warps <= 0) continue;
         k_tonal_local<<<(unsigned)((warps + 3) / 4), 128, 0, stream>>>(a);
     }
+}
+
+template <int K>
+static void launch_aa_gather(const AAArgs& a, int new_slot, cudaStream_t s) {
+    k_aa_gather<K><<<dim3(a.nparts, a.nch), 256, 0, s>>>(a, new_slot);
+}
+
+// Solves the k x k least-squares normal equations of one channel by Cholesky
+// in FP64, dropping the oldest columns while the matrix is numerically
+// singular. A is packed as (r <= c) row by row, b follows.
+static void aa_solve(const double* dots, int k, double* gam) {
+    for (int j = 0; j < kAAMax; ++j) gam[j] = 0.0;
+    double A[kAAMax][kAAMax], b[kAAMax];
+    int q = 0;
+    for (int r = 0; r < k; ++r)
+        for (int c = r; c < k; ++c) { A[r][c] = A[c][r] = dots[q++]; }
+    for (int r = 0; r < k; ++r) b[r] = dots[q++];
+    for (int kk = k; kk >= 1; --kk) {
+        double Lm[kAAMax][kAAMax];
+        double dmax = 0.0;
+        for (int r = 0; r < kk; ++r) dmax = std::max(dmax, A[r][r]);
+        if (!(dmax > 0.0)) return;
+        bool ok = true;
+        for (int r = 0; r < kk && ok; ++r) {
+            for (int c = 0; c <= r; ++c) {
+                double s = A[r][c] + (r == c ? 1e-12 * dmax : 0.0);
+                for (int j = 0; j < c; ++j) s -= Lm[r][j] * Lm[c][j];
+                if (r == c) {
+                    if (!(s > 1e-13 * dmax)) { ok = false; break; }
+                    Lm[r][r] = std::sqrt(s);
+                } else {
+                    Lm[r][c] = s / Lm[c][c];
+                }
+            }
+        }
+        if (!ok) continue;
+        double z[kAAMax];
+        for (int r = 0; r < kk; ++r) {
+            double s = b[r];
+            for (int j = 0; j < r; ++j) s -= Lm[r][j] * z[j];
+            z[r] = s / Lm[r][r];
+        }
+        for (int r = kk - 1; r >= 0; --r) {
+            double s = z[r];
+            for (int j = r + 1; j < kk; ++j) s -= Lm[j][r] * gam[j];
+            gam[r] = s / Lm[r][r];
+        }
+        return;
+    }
+}
+
+// One accelerated update g <- g + f_n - (dX + dF) gamma with f_n = P r_n in
+// `fvfull` (iteration n of the outer loop).
+int Ctx::tonal_aa_step(int n, const float* fvfull, DF G) {
+    const int mwin = (int)p.tonal_anderson;
+    const int ring = std::max(mwin, 1);
+    const int k = std::min(mwin, n);
+    AAArgs a;
+    a.M = aa_M;
+    a.cs = lev[0].cs;
+    a.nch = nch;
+    a.k = k;
+    a.slot = n >= 1 ? (n - 1) % ring : 0;
+    a.mwin = ring;
+    a.idx = aa_idx;
+    a.fvfull = fvfull;
+    a.fv = aa_fv;
+    a.fvprev = aa_fvprev;
+    a.dF = aa_dF;
+    a.dX = aa_dX;
+    a.g = G;
+    a.gamma = aa_gam;
+    a.partials = aa_part;
+    a.out = aa_out;
+    a.ticket = aa_ticket;
+    a.nparts = std::max(1, std::min(kAAParts, (aa_M + 255) / 256));
+    if (aa_M == 0) return HDI_OK;
+    const int new_slot = (n >= 1 && mwin > 0) ? (n - 1) % ring : -1;
+    switch (k) {
+        case 0: launch_aa_gather<0>(a, new_slot, stream); break;
+        case 1: launch_aa_gather<1>(a, new_slot, stream); break;
+        case 2: launch_aa_gather<2>(a, new_slot, stream); break;
+        case 3: launch_aa_gather<3>(a, new_slot, stream); break;
+        case 4: launch_aa_gather<4>(a, new_slot, stream); break;
+        case 5: launch_aa_gather<5>(a, new_slot, stream); break;
+        case 6: launch_aa_gather<6>(a, new_slot, stream); break;
+        case 7: launch_aa_gather<7>(a, new_slot, stream); break;
+        default: launch_aa_gather<8>(a, new_slot, stream); break;
+    }
+    if (k > 0) {
+        const int nd = k * (k + 1) / 2 + k;
+        double dots[4 * 64], gam[4 * kAAMax];
+        cudaMemcpyAsync(dots, aa_out, (size_t)nch * nd * 8, cudaMemcpyDeviceToHost, stream);
+        int rc = sync("Anderson dot products");
+        if (rc) return rc;
+        for (int c = 0; c < nch; ++c) aa_solve(dots + c * nd, k, gam + c * kAAMax);
+        cudaMemcpyAsync(aa_gam, gam, (size_t)nch * kAAMax * 8, cudaMemcpyHostToDevice, stream);
+    }
+    const int blocks = std::max(1, std::min(1024, (aa_M + 255) / 256));
+    k_aa_update<<<dim3(blocks, nch), 256, 0, stream>>>(a, mwin > 0 ? n % ring : 0);
+    return cuda_check(cudaGetLastError(), "Anderson update");
 }
 
 int Ctx::read_slot(int slot, double* out) {
@@ -505,7 +636,10 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
                     it, rel_max, mse_last, tin, sy.iterations, sy.rel_max, sw.iterations, sw.rel_max);
         if (rel_max <= tol || it >= max_it) break;
         rel_prev = rel_max;
-        tonal_local(G);
+        float* fvfull = lev[0].xb;   // free between solves
+        cudaMemsetAsync(fvfull, 0, (size_t)nch * lev[0].cs * 4, stream);
+        tonal_local(fvfull);
+        if ((rc = tonal_aa_step(it, fvfull, G))) return rc;
     }
     if ((rc = store_image(cview(G), g, true))) return rc;
     if (st) {
