@@ -351,8 +351,10 @@ int Ctx::tonal_setup() {
     auto acc = [&](size_t b) { bytes += (b + 255) & ~(size_t)255; };
     acc((size_t)(H + 1) * 4);
     acc((size_t)M * 4);
-    acc((size_t)nch * M * 4 * 2);
-    acc((size_t)std::max(mwin, 1) * nch * M * 4 * 2);
+    acc((size_t)nch * M * 4);
+    acc((size_t)nch * M * 4);
+    acc((size_t)std::max(mwin, 1) * nch * M * 4);
+    acc((size_t)std::max(mwin, 1) * nch * M * 4);
     acc((size_t)nch * 64 * kAAParts * 8);
     acc((size_t)4 * 64 * 8);
     acc((size_t)4 * kAAMax * 8);
@@ -378,6 +380,7 @@ int Ctx::tonal_setup() {
     aa_out = (double*)tws.take((size_t)4 * 64 * 8);
     aa_gam = (double*)tws.take((size_t)4 * kAAMax * 8);
     aa_ticket = (unsigned*)tws.take(256);
+    if (tws.used > tws.cap) return fail(HDI_ERR_CUDA, "internal: tonal workspace carving exceeds its reservation");
     cudaMemsetAsync(aa_ticket, 0, 256, stream);
     aa_M = M;
     cudaMemcpyAsync(drowoff, rowoff.data(), (size_t)(H + 1) * 4, cudaMemcpyHostToDevice, stream);
