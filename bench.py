@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark: 4K RGB homogeneous-diffusion inpainting + tonal optimisation.
+
+One step = one cold inpainting solve (C + (I-C)L) u = C f to relative residual
+1e-6 followed by one tonal optimisation (normal equations of
+min_g ||f - A^{-1} C g||) to relative residual 1e-6, on a synthetic
+3840x2160 RGB FP32 image with a fixed 4% random mask shared by the channels.
+The metric is completed steps ("solves") per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hdi|reference]
+
+Under torchrun every rank runs an independent replica on its own GPU (the
+path has no exchange step between images); `value` is the aggregate rate.
+`--impl reference` times the CPU FP64 oracle (the reference arm of this
+project) on a bounded crop of the same workload and scales it to the metric.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H4K, W4K, CH = 2160, 3840, 3
+DENSITY = 0.04
+MASK_SEED = 1001
+IMAGE_SEEDS = (1, 2, 3)
+TOL = 1e-6
+METRIC = "4K RGB inpaint+tonal-opt solves/s at rel-res 1e-6"
+UNIT = "solves/s"
+CROP = 512            # oracle sample: one channel, CROP x CROP, top-left crop of the workload
+REF_CROP = 256        # per-step sample of the reference arm
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "3840x2160 RGB FP32, 4% random mask (seed 1001), channel seeds 1/2/3; "
+                       "cold inpaint to rel-res 1e-6 + tonal optimisation to rel-res 1e-6",
+           "height": H4K, "width": W4K, "channels": CH, "mask_density": DENSITY, "tol": TOL,
+           "l2_policy": "L2 flushed (256 MB write) between timed steps; working set several GB"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------ CPU oracle ---
+
+def oracle_sample_seconds(crop: int) -> float:
+    """Time the oracle (inpaint + tonal, FP64) on one channel of a crop."""
+    import numpy as np
+    from synthdata import synth_image, random_mask
+    from oracle import inpaint, tonal
+    from oracle import laplace as lp
+    f = synth_image(H4K, W4K, IMAGE_SEEDS[0])[:crop, :crop].copy()
+    c = random_mask(H4K, W4K, DENSITY, MASK_SEED)[:crop, :crop].copy()
+    if c.sum() == 0:
+        c[0, 0] = 1
+    lp._cache.clear()
+    t0 = time.perf_counter()
+    inpaint(f, c)
+    tonal(f, c)
+    return time.perf_counter() - t0
+
+
+def scale_to_metric(seconds: float, crop: int) -> float:
+    """Solves/s of the full 4K RGB workload assuming time linear in pixels
+    (the paper reports slope-1 scaling, Sec. 6.2 / 6.3)."""
+    return 1.0 / (seconds * (CH * H4K * W4K) / float(crop * crop))
+
+
+def cpu_baseline() -> dict:
+    """Runs the oracle in a single-threaded subprocess (BLAS threads pinned to 1)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys; sys.path.insert(0, %r); import bench; "
+            "print(bench.oracle_sample_seconds(%d))" % (ROOT, CROP))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    secs = float(out.stdout.strip().splitlines()[-1])
+    return {"value": scale_to_metric(secs, CROP), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle inpaint + tonal (FP64, SuperLU + CG) on channel 0 of the {CROP}x{CROP} top-left crop "
+                      f"of the workload took {secs:.2f} s; scaled by pixel count to 3840x2160x3"}
+
+
+# ---------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ dist ---
+
+def dist_setup(n_gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def all_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ hdi arm ---
+
+# Algorithmic bytes per pixel and channel of one launch of each timed class
+# (FP32 = 4 B, double-float = 8 B, bit-packed mask = 1/8 B):
+#   oras_fine     : read x, b, mask; write x                      12.125
+#   residual_fine : read u (8), e (4), mask; write u (8), r (4)   24.125
+#   prolong_fine  : read x, b, e_H/4, mask; write x               13.125
+#   restrict_fine : read x, b, mask; write b_H/4                   9.125
+ALGO_BYTES_PER_VALUE = {"oras_fine": 12.125, "residual_fine": 24.125, "prolong_fine": 13.125,
+                        "restrict_fine": 9.125}
+
+
+def run_hdi(args, rank, world):
+    import numpy as np
+    import torch
+    import paper_2401_06747_b300 as hdi
+    from synthdata import synth_rgb, random_mask
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    f = synth_rgb(H4K, W4K, seeds=IMAGE_SEEDS, dtype=np.float32)
+    c = random_mask(H4K, W4K, DENSITY, MASK_SEED)
+    stream = torch.cuda.current_stream()
+    ctx = hdi.Context(local, stream=stream)
+    fd = torch.from_numpy(f).cuda()
+    cd = torch.from_numpy(c).cuda()
+    u = torch.empty_like(fd)
+    g = torch.empty_like(fd)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        s1 = ctx.inpaint(fd, cd, u, tol=TOL)
+        s2 = ctx.tonal_opt(fd, cd, g, tol=TOL)
+        return s1, s2
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.timing(enable=True, reset=True)
+    l0 = ctx.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    stats = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = ctx.launch_count() - l0
+    kt = ctx.timing(enable=False, reset=True)
+    clocks = sampler.stop()
+    t_max = all_max(total_ms, world)
+    value = world * args.steps / (t_max / 1e3)
+
+    # dominant kernel class and its roofline
+    name, (ms, n) = max(((k, v) for k, v in kt.items() if k in ALGO_BYTES_PER_VALUE), key=lambda kv: kv[1][0])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    bytes_per_launch = ALGO_BYTES_PER_VALUE[name] * H4K * W4K * CH
+    avg_s = (ms / max(n, 1)) / 1e3
+    achieved = bytes_per_launch / avg_s / 1e9 if n else 0.0
+    share = ms / max(t_max, 1e-9)
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(name)
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": bytes_per_launch, "launches": n, "avg_ms": round(ms / max(n, 1), 4),
+                "share_of_step_time": round(share, 3),
+                "classes_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kt.items()}}
+
+    # end to end through the public API with host buffers
+    fh = torch.from_numpy(f).pin_memory()
+    ch = torch.from_numpy(c).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    gh = torch.empty_like(fh).pin_memory()
+    ctx.inpaint(fh, ch, uh, tol=TOL)
+    ctx.tonal_opt(fh, ch, gh, tol=TOL)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.inpaint(fh, ch, uh, tol=TOL)
+        ctx.tonal_opt(fh, ch, gh, tol=TOL)
+    torch.cuda.synchronize()
+    te = all_max(time.perf_counter() - t0, world)
+    e2e = {"value": world * args.steps / te, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * (f.nbytes + c.nbytes), "d2h_bytes_per_step": 2 * f.nbytes}
+
+    last_inp, last_ton = stats[-1]
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": workload_config({"parallelism": f"replicas{world}",
+                                      "inpaint": {k: last_inp[k] for k in ("iterations", "vcycles", "rel_res")},
+                                      "tonal": {k: last_ton[k] for k in ("iterations", "vcycles", "rel_res", "mse")}}),
+           "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    elif rank == 0 and world > 1:
+        out["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------- reference arm ---
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    secs = []
+    for i in range(args.warmup + args.steps):
+        s = oracle_sample_seconds(REF_CROP)
+        if i >= args.warmup:
+            secs.append(s)
+    per = sum(secs) / len(secs)
+    value = scale_to_metric(per, REF_CROP)
+    cores = 1 if os.environ.get("OMP_NUM_THREADS") == "1" else (os.cpu_count() or 1)
+    sample = (f"oracle inpaint + tonal (FP64) on channel 0 of the {REF_CROP}x{REF_CROP} top-left crop per step, "
+              f"{per:.2f} s per step, scaled by pixel count to 3840x2160x3")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config({"parallelism": "cpu"}),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["hdi", "reference"], default="hdi")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 0)
+    rank, world = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_hdi(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

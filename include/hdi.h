@@ -125,6 +125,28 @@ int hdi_tonal_opt(hdi_ctx* ctx, const hdi_image* f, const hdi_mask* mask,
 int hdi_densify_step(hdi_ctx* ctx, const hdi_image* f, hdi_mask* mask,
                      const hdi_image* u, int64_t k, uint64_t seed, int64_t* added);
 
+/* Number of kernels this context has launched since it was created. */
+int64_t hdi_launch_count(const hdi_ctx* ctx);
+
+/* Device time per kernel class, measured with CUDA events recorded on the
+ * context's stream around each launch of the class (no extra
+ * synchronisation inside a call; events are resolved when a call ends).
+ *   enable : 1 = record from now on, 0 = stop recording
+ *   reset  : 1 = zero the totals after reading them
+ *   ms, launches (out, may be NULL): HDI_TIMING_CLASSES entries each,
+ *   accumulated milliseconds and launch counts; names by hdi_timing_name(i):
+ *   0 oras_fine     ORAS sweep on the finest level (Sec. 3.1)
+ *   1 residual_fine double-float residual / refinement update, finest level
+ *   2 prolong_fine  prolongation + correction onto the finest level (Sec. 3.2)
+ *   3 restrict_fine residual restriction from the finest level (Sec. 3.2)
+ *   4 tonal_echo    local inpainting echoes of the RAS subdomains (Sec. 5.2)
+ *   5 tonal_gram    local Gram matrices and their Cholesky factors
+ *   6 tonal_local   local solves and weighted extension (Alg. 2, steps 2-3)
+ *   7 anderson      Anderson acceleration of the RAS iteration */
+#define HDI_TIMING_CLASSES 8
+int hdi_timing(hdi_ctx* ctx, int enable, int reset, double* ms, int64_t* launches);
+const char* hdi_timing_name(int i);
+
 /* One-line description of the last error on this context ("" if none). */
 const char* hdi_last_error(const hdi_ctx* ctx);
 
@@ -139,7 +161,10 @@ const char* hdi_version(void);
  *   coarse_eta        [1e-8]  relative squared-residual target of the single-block coarsest solve
  *   max_vcycles       [60]    refinement steps per inpainting solve
  *   tonal_max_iter    [400]   RAS iterations per tonal solve
- *   tonal_inner_ratio [0.05]  inner solves target: ratio * current outer relative residual
+ *   tonal_inner_ratio [1e-3]  inner solves target: ratio * current outer relative residual
+ *   tonal_anderson    [5]     Anderson window on the RAS iteration (0 = plain Alg. 2)
+ *   tonal_echo_rtol   [1e-4]  relative CG tolerance of the local echo solves
+ *   trace             [0]     1 = one line per RAS iteration on stderr
  *   hbm_budget_gb     [200]   workspace cap for this context
  */
 

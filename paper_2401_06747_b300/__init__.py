@@ -53,7 +53,9 @@ class Stats(ctypes.Structure):
 
 
 SYMBOLS = ["hdi_create", "hdi_destroy", "hdi_set_param", "hdi_get_param", "hdi_inpaint",
-           "hdi_tonal_opt", "hdi_densify_step", "hdi_last_error", "hdi_version"]
+           "hdi_tonal_opt", "hdi_densify_step", "hdi_last_error", "hdi_version", "hdi_launch_count",
+           "hdi_timing", "hdi_timing_name"]
+TIMING_CLASSES = 8
 
 _lib = None
 
@@ -79,6 +81,10 @@ def load(path: str | None = None):
     lib.hdi_last_error.argtypes = [ctypes.c_void_p]
     lib.hdi_last_error.restype = ctypes.c_char_p
     lib.hdi_version.restype = ctypes.c_char_p
+    lib.hdi_launch_count.argtypes = [ctypes.c_void_p]
+    lib.hdi_launch_count.restype = ctypes.c_int64
+    lib.hdi_timing.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int64)]
+    lib.hdi_timing_name.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -192,6 +198,17 @@ class Context:
                                        ctypes.c_uint64(seed), ctypes.byref(added))
         self._check(rc)
         return added.value
+
+
+    def launch_count(self) -> int:
+        return self.lib.hdi_launch_count(self.h)
+
+    def timing(self, enable: bool = True, reset: bool = False) -> dict:
+        """Per-class device time {name: (ms, launches)} since the last reset."""
+        ms = (ctypes.c_double * TIMING_CLASSES)()
+        n = (ctypes.c_int64 * TIMING_CLASSES)()
+        self._check(self.lib.hdi_timing(self.h, int(enable), int(reset), ms, n))
+        return {self.lib.hdi_timing_name(i).decode(): (ms[i], n[i]) for i in range(TIMING_CLASSES)}
 
 
 def version() -> str:

@@ -103,6 +103,33 @@ void* Arena::take(size_t bytes) {
 
 size_t Ctx::other_bytes() const { return ws.cap + tws.cap + dws.cap + stage.cap; }
 
+// Device-time bookkeeping per kernel class (CUDA events on the context's
+// stream around each timed launch; resolved after the stream drains).
+void Ctx::tstart(int cls) {
+    if (!timing || !tev) return;
+    if (tn >= kMaxTimed && tflush()) return;
+    tcls[tn] = cls;
+    cudaEventRecord(tev[2 * tn], stream);
+}
+void Ctx::tstop() {
+    if (!timing || !tev || tn >= kMaxTimed) return;
+    cudaEventRecord(tev[2 * tn + 1], stream);
+    ++tn;
+}
+int Ctx::tflush() {
+    if (!tev || tn == 0) return HDI_OK;
+    int rc = sync("timing");
+    if (rc) return rc;
+    for (int i = 0; i < tn; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, tev[2 * i], tev[2 * i + 1]);
+        ttot[tcls[i]] += ms;
+        tcnt[tcls[i]] += 1;
+    }
+    tn = 0;
+    return HDI_OK;
+}
+
 // ------------------------------------------------------------ hierarchy ---
 
 static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -215,6 +242,7 @@ void Ctx::build_mask_pyramid() {
         const Level& C = lev[l + 1];
         dim3 blk(64), grd((C.wp + 63) / 64, C.H);
         k_restrict_mask<<<grd, blk, 0, stream>>>(mview(l), C.bits, C.H, C.W, C.wp);
+        ++launches;
     }
 }
 
@@ -244,8 +272,11 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     a.iters = iters;
     const int warps = L.nbx * L.nby * nch;
     const int blocks = (warps + 3) / 4;
+    if (l == 0) tstart(kT_Oras);
     if (zero) k_oras<true><<<blocks, 128, 0, stream>>>(a);
     else k_oras<false><<<blocks, 128, 0, stream>>>(a);
+    ++launches;
+    if (l == 0) tstop();
 }
 
 static dim3 tiles_of(const Level& L, int nch) { return dim3((L.W + PT_W - 1) / PT_W, (L.H + PT_H - 1) / PT_H, nch); }
@@ -265,14 +296,20 @@ void Ctx::vcycle(int l) {
     Level& C = lev[l + 1];
     {
         dim3 blk(32, 8), grd((C.W + 31) / 32, (C.H + 7) / 8, nch);
+        if (l == 0) tstart(kT_Restrict);
         k_restrict_residual<<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, arr(l + 1), mview(l + 1), C.b,
                                                      reducer(l + 1, grd.x * grd.y));
+        ++launches;
+        if (l == 0) tstop();
     }
     vcycle(l + 1);
     {
         dim3 grd = tiles_of(L, nch), blk(PT_W, PT_H);
+        if (l == 0) tstart(kT_Prolong);
         k_prolong<0><<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, L.xb, arr(l + 1), C.xa,
                                               reducer(l, grd.x * grd.y));
+        ++launches;
+        if (l == 0) tstop();
     }
     oras(l, false, L.xb, L.xa, scal + l * 4, false, it);
     if (l == 0) ++vcycles_run;
@@ -285,22 +322,26 @@ void Ctx::fmg(DFc d) {
     {
         dim3 grd((W + 127) / 128, H, nch);
         k_data_to_f32<<<grd, 128, 0, stream>>>(d, arr(0), mview(0), lev[0].b);
+        ++launches;
     }
     for (int l = 1; l < nlev; ++l) {
         dim3 blk(32, 8), grd((lev[l].W + 31) / 32, (lev[l].H + 7) / 8, nch);
         k_restrict_data<<<grd, blk, 0, stream>>>(arr(l - 1), mview(l - 1), lev[l - 1].b, arr(l), lev[l].b);
+        ++launches;
     }
     const int L = nlev - 1;
     {
         dim3 grd = tiles_of(lev[L], nch), blk(PT_W, PT_H);
         k_prolong<2><<<grd, blk, 0, stream>>>(arr(L), mview(L), nullptr, lev[L].b, lev[L].xb, arr(L), nullptr,
                                               reducer(L, grd.x * grd.y));
+        ++launches;
         oras(L, false, lev[L].xb, lev[L].xa, scal + L * 4, true, nullptr);
     }
     for (int l = L - 1; l >= 0; --l) {
         dim3 grd = tiles_of(lev[l], nch), blk(PT_W, PT_H);
         k_prolong<1><<<grd, blk, 0, stream>>>(arr(l), mview(l), nullptr, lev[l].b, lev[l].xb, arr(l + 1),
                                               lev[l + 1].xa, reducer(l, grd.x * grd.y));
+        ++launches;
         oras(l, false, lev[l].xb, lev[l].xa, scal + l * 4, l == L, l == 0 ? counters + kCntLocal : nullptr);
     }
 }
@@ -320,7 +361,10 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
     a.red_r = c.reducer(kSlotR64, grd.x * grd.y);
     a.red_b = c.reducer(kSlotB64, grd.x * grd.y);
     a.want_b = want_b ? 1 : 0;
+    c.tstart(kT_Residual);
     k_residual_df<RHS, INIT><<<grd, blk, 0, c.stream>>>(a);
+    ++c.launches;
+    c.tstop();
 }
 
 void Ctx::residual(int rhs, int init, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b) {
@@ -432,6 +476,7 @@ int Ctx::load_image(const hdi_image* im, DF dst, float* lo2) {
         k_load_image<double><<<grd, 128, 0, stream>>>((const double*)src, rs, cs, arr(0), dst, lo2, flags);
     else
         k_load_image<float><<<grd, 128, 0, stream>>>((const float*)src, rs, cs, arr(0), dst, lo2, flags);
+    ++launches;
     unsigned bad = 0;
     cudaMemcpyAsync(&bad, flags, 4, cudaMemcpyDeviceToHost, stream);
     int rc = sync("image upload");
@@ -460,6 +505,7 @@ int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* kn
     else
         k_store_image<float><<<grd, 128, 0, stream>>>(src, arr(0), mview(0), zero_off_mask, known_lo2, (float*)dst,
                                                       rs, cs);
+    ++launches;
     if (host) {
         for (int c = 0; c < nch; ++c) {
             cudaError_t e = cudaMemcpy2DAsync((char*)im->data + (size_t)c * im->channel_stride * es,
@@ -495,6 +541,7 @@ int Ctx::load_mask(const hdi_mask* m, long long* ones) {
     const Level& L = lev[0];
     dim3 grd((L.wp + 63) / 64, H);
     k_pack_mask<<<grd, 64, 0, stream>>>(src, rs, H, W, L.bits, L.wp, counters + kCntOnes, flags);
+    ++launches;
     build_mask_pyramid();
     unsigned long long cnt = 0;
     unsigned bad = 0;
@@ -547,6 +594,10 @@ int hdi_destroy(hdi_ctx* h) {
     c->dws.release();
     c->stage.release();
     if (c->flags) cudaFree(c->flags);
+    if (c->tev) {
+        for (int i = 0; i < 2 * kMaxTimed; ++i) cudaEventDestroy(c->tev[i]);
+        delete[] c->tev;
+    }
     if (c->hscal) cudaFreeHost(c->hscal);
     delete c;
     return HDI_OK;
@@ -584,6 +635,36 @@ const char* hdi_last_error(const hdi_ctx* h) {
 }
 
 const char* hdi_version(void) { return "hdi 0.1 (sm_103a)"; }
+
+int64_t hdi_launch_count(const hdi_ctx* h) {
+    if (!h) return -1;
+    return reinterpret_cast<const Ctx*>(h)->launches;
+}
+
+const char* hdi_timing_name(int i) {
+    static const char* names[HDI_TIMING_CLASSES] = {"oras_fine", "residual_fine", "prolong_fine", "restrict_fine",
+                                                    "tonal_echo", "tonal_gram", "tonal_local", "anderson"};
+    return (i >= 0 && i < HDI_TIMING_CLASSES) ? names[i] : "";
+}
+
+int hdi_timing(hdi_ctx* h, int enable, int reset, double* ms, int64_t* launches) {
+    if (!h) return HDI_ERR_INVALID_ARG;
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    int rc = c->tflush();
+    if (rc) return rc;
+    if (ms)
+        for (int i = 0; i < HDI_TIMING_CLASSES; ++i) ms[i] = c->ttot[i];
+    if (launches)
+        for (int i = 0; i < HDI_TIMING_CLASSES; ++i) launches[i] = c->tcnt[i];
+    if (reset)
+        for (int i = 0; i < HDI_TIMING_CLASSES; ++i) { c->ttot[i] = 0.0; c->tcnt[i] = 0; }
+    if (enable && !c->tev) {
+        c->tev = new cudaEvent_t[2 * kMaxTimed];
+        for (int i = 0; i < 2 * kMaxTimed; ++i) cudaEventCreate(&c->tev[i]);
+    }
+    c->timing = enable != 0;
+    return HDI_OK;
+}
 
 int hdi_inpaint(hdi_ctx* h, const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,
                 hdi_stats* st) {
@@ -667,6 +748,7 @@ int Ctx::inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, 
         st->rel_res = s.rel_max;
         st->mse = 0.0;
     }
+    if ((rc = tflush())) return rc;
     if (src == HDI_ERR_NOT_CONVERGED)
         return fail(HDI_ERR_NOT_CONVERGED, "inpainting: relative residual %.3e after %d refinement steps", s.rel_max,
                     s.iterations);

@@ -74,6 +74,8 @@ constexpr int kSlotTonalE = 19;   // ||f - Bg||^2
 constexpr int kCntOnes = 0;
 constexpr int kCntLocal = 1;
 constexpr int kCntEcho = 2;
+constexpr int kMaxTimed = 2048;   // timed launches buffered between flushes
+enum { kT_Oras = 0, kT_Residual, kT_Prolong, kT_Restrict, kT_Echo, kT_Gram, kT_Local, kT_Anderson };
 // double-float vectors of level-0 size
 enum { kF = 0, kU0, kU1, kG, kY0, kY1, kW0, kW1, kNumDF };
 
@@ -101,6 +103,17 @@ struct Ctx {
     bool mask_key_valid = false;
     long long mask_ones = 0;
     int vcycles_run = 0;
+    int64_t launches = 0;      // kernels launched by this context
+    // per-class device time (hdi_timing)
+    bool timing = false;
+    cudaEvent_t* tev = nullptr;
+    int tn = 0;
+    int tcls[kMaxTimed];
+    double ttot[HDI_TIMING_CLASSES] = {};
+    int64_t tcnt[HDI_TIMING_CLASSES] = {};
+    void tstart(int cls);
+    void tstop();
+    int tflush();
     // tonal local factors (valid for the mask of the current tonal call)
     int* t_off = nullptr;
     long long* t_goff = nullptr;

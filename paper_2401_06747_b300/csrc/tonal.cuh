@@ -323,6 +323,7 @@ int Ctx::tonal_setup() {
     if ((rc = tws.reserve(*this, std::max(tws.cap, (size_t)ncnt * 24 + 4096), "tonal counts"))) return rc;
     dcnt = (int*)tws.take((size_t)ncnt * 4);
     k_tonal_count<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), L0.nbx, L0.nby, stride, dcnt);
+    ++launches;
     cudaMemcpyAsync(cnt.data(), dcnt, (size_t)nb * 4, cudaMemcpyDeviceToHost, stream);
     if ((rc = sync("tonal subdomain counts"))) return rc;
     off[0] = 0;
@@ -340,6 +341,7 @@ int Ctx::tonal_setup() {
     std::vector<int> rc_h(H), rowoff(H + 1);
     int* drc = dcnt;
     k_row_counts<<<(H + 3) / 4, 128, 0, stream>>>(mview(0), drc);
+    ++launches;
     cudaMemcpyAsync(rc_h.data(), drc, (size_t)H * 4, cudaMemcpyDeviceToHost, stream);
     if ((rc = sync("mask row counts"))) return rc;
     rowoff[0] = 0;
@@ -385,9 +387,11 @@ int Ctx::tonal_setup() {
     aa_M = M;
     cudaMemcpyAsync(drowoff, rowoff.data(), (size_t)(H + 1) * 4, cudaMemcpyHostToDevice, stream);
     k_compact_fill<<<(H + 3) / 4, 128, 0, stream>>>(mview(0), lev[0].P, drowoff, aa_idx);
+    ++launches;
     cudaMemcpyAsync(t_off, off.data(), (size_t)(nb + 1) * 4, cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(t_goff, goff.data(), (size_t)(nb + 1) * 8, cudaMemcpyHostToDevice, stream);
     k_tonal_list<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), L0.nbx, L0.nby, stride, t_off, t_list);
+    ++launches;
     if (total > 0) {
         EchoArgs ea;
         ea.m = mview(0);
@@ -401,11 +405,17 @@ int Ctx::tonal_setup() {
         ea.rtol2 = (float)(p.tonal_echo_rtol * p.tonal_echo_rtol);
         ea.maxit = (int)p.tonal_echo_max_iter;
         ea.iters = counters + kCntEcho;
+        tstart(kT_Echo);
         k_tonal_echo<<<(unsigned)((total + 3) / 4), 128, 0, stream>>>(ea);
+        ++launches;
+        tstop();
         const size_t shm = ((size_t)maxm * maxm + 2 * 32 * 64) * 4;
         cudaFuncSetAttribute(k_tonal_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         cudaMemsetAsync(flags, 0, 4, stream);
+        tstart(kT_Gram);
         k_tonal_gram<<<nb, 256, shm, stream>>>(t_off, t_goff, t_echo, t_fac, flags);
+        ++launches;
+        tstop();
         unsigned bad = 0;
         cudaMemcpyAsync(&bad, flags, 4, cudaMemcpyDeviceToHost, stream);
         if ((rc = sync("tonal local factors"))) return rc;
@@ -419,6 +429,7 @@ void Ctx::tonal_residual(DFc y, DFc w) {
     dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8, nch);
     k_tonal_residual<<<grd, blk, 0, stream>>>(arr(0), mview(0), cview(dfv[kF]), y, w, tres,
                                               reducer(kSlotTonalR, grd.x * grd.y), reducer(kSlotTonalE, grd.x * grd.y));
+    ++launches;
 }
 
 void Ctx::tonal_local(float* out) {
@@ -441,7 +452,10 @@ void Ctx::tonal_local(float* out) {
         const int hy = (L0.nby + 1 - (color >> 1)) / 2;
         const long long warps = (long long)hx * hy * nch;
         if (warps <= 0) continue;
+        tstart(kT_Local);
         k_tonal_local<<<(unsigned)((warps + 3) / 4), 128, 0, stream>>>(a);
+        ++launches;
+        tstop();
     }
 }
 
@@ -521,6 +535,8 @@ int Ctx::tonal_aa_step(int n, const float* fvfull, DF G) {
     a.nparts = std::max(1, std::min(kAAParts, (aa_M + 255) / 256));
     if (aa_M == 0) return HDI_OK;
     const int new_slot = (n >= 1 && mwin > 0) ? (n - 1) % ring : -1;
+    tstart(kT_Anderson);
+    ++launches;
     switch (k) {
         case 0: launch_aa_gather<0>(a, new_slot, stream); break;
         case 1: launch_aa_gather<1>(a, new_slot, stream); break;
@@ -532,6 +548,7 @@ int Ctx::tonal_aa_step(int n, const float* fvfull, DF G) {
         case 7: launch_aa_gather<7>(a, new_slot, stream); break;
         default: launch_aa_gather<8>(a, new_slot, stream); break;
     }
+    tstop();
     if (k > 0) {
         const int nd = k * (k + 1) / 2 + k;
         double dots[4 * 64], gam[4 * kAAMax];
@@ -542,7 +559,10 @@ int Ctx::tonal_aa_step(int n, const float* fvfull, DF G) {
         cudaMemcpyAsync(aa_gam, gam, (size_t)nch * kAAMax * 8, cudaMemcpyHostToDevice, stream);
     }
     const int blocks = std::max(1, std::min(1024, (aa_M + 255) / 256));
+    tstart(kT_Anderson);
     k_aa_update<<<dim3(blocks, nch), 256, 0, stream>>>(a, mwin > 0 ? n % ring : 0);
+    ++launches;
+    tstop();
     return cuda_check(cudaGetLastError(), "Anderson update");
 }
 
@@ -654,6 +674,7 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
         st->rel_res = rel_max;
         st->mse = mse_last;
     }
+    if ((rc = tflush())) return rc;
     if (rel_max > tol)
         return fail(HDI_ERR_NOT_CONVERGED, "tonal: relative residual %.3e after %d RAS iterations", rel_max, it);
     return HDI_OK;
