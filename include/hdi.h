@@ -147,6 +147,34 @@ int64_t hdi_launch_count(const hdi_ctx* ctx);
 int hdi_timing(hdi_ctx* ctx, int enable, int reset, double* ms, int64_t* launches);
 const char* hdi_timing_name(int i);
 
+/* Inpainting that allocates no device memory. The paper has no counterpart;
+ * this entry point exists for callers that cannot call cudaMalloc while they
+ * run, for instance code executing inside a CUDA stream capture, a real-time
+ * or interrupt-like loop with a fixed memory plan, or a host process whose
+ * allocator is owned by another runtime. It solves the same system as
+ * hdi_inpaint (cold start, default parameters) with the same kernels, but
+ * takes no context and keeps its whole workspace in a 24 MiB array in
+ * device global memory that the library declares statically: every GPU that
+ * loads libhdi holds that array until the process exits.
+ *   device, cuda_stream : GPU index and stream (NULL = legacy default)
+ *   f, mask, u          : as for hdi_inpaint, but all three must be DEVICE
+ *                         buffers (host buffers would need staging memory)
+ *   tol, st             : as for hdi_inpaint (st->local_iters is 0)
+ * Size limit: the layout of the image (multigrid levels, three double-float
+ * vectors, reductions) must fit the 24 MiB array, about 500,000 pixel x
+ * channel values (e.g. 400x400 RGB or 700x700 grey); larger images return
+ * HDI_ERR_INVALID_ARG before any GPU work. Host buffers, a null pointer or
+ * tol outside (0,1) also return HDI_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (the device made current first); make that first
+ * call before any stream capture. All calls share the one array and it
+ * keeps the previous call's contents (the entry point clears what must
+ * start at zero): calls that overlap on the GPU, from any thread or stream,
+ * race and corrupt each other. No error message is kept; the return code
+ * (hdi_status) is the only report. */
+int hdi_inpaint_noalloc(int device, void* cuda_stream, const hdi_image* f, const hdi_mask* mask,
+                        hdi_image* u, double tol, hdi_stats* st);
+
 /* One-line description of the last error on this context ("" if none). */
 const char* hdi_last_error(const hdi_ctx* ctx);
 

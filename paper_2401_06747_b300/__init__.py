@@ -54,7 +54,7 @@ class Stats(ctypes.Structure):
 
 SYMBOLS = ["hdi_create", "hdi_destroy", "hdi_set_param", "hdi_get_param", "hdi_inpaint",
            "hdi_tonal_opt", "hdi_densify_step", "hdi_last_error", "hdi_version", "hdi_launch_count",
-           "hdi_timing", "hdi_timing_name"]
+           "hdi_timing", "hdi_timing_name", "hdi_inpaint_noalloc"]
 TIMING_CLASSES = 8
 
 _lib = None
@@ -85,6 +85,8 @@ def load(path: str | None = None):
     lib.hdi_launch_count.restype = ctypes.c_int64
     lib.hdi_timing.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int64)]
     lib.hdi_timing_name.restype = ctypes.c_char_p
+    lib.hdi_inpaint_noalloc.argtypes = [ctypes.c_int, ctypes.c_void_p, P(Image), P(Mask), P(Image),
+                                        ctypes.c_double, P(Stats)]
     _lib = lib
     return lib
 
@@ -209,6 +211,24 @@ class Context:
         n = (ctypes.c_int64 * TIMING_CLASSES)()
         self._check(self.lib.hdi_timing(self.h, int(enable), int(reset), ms, n))
         return {self.lib.hdi_timing_name(i).decode(): (ms[i], n[i]) for i in range(TIMING_CLASSES)}
+
+
+def inpaint_noalloc(f, mask, out, tol: float = 1e-6, device: int = 0, stream=None) -> dict:
+    """hdi_inpaint_noalloc: inpainting for callers that must not allocate
+    device memory (for example inside a stream capture). f, mask and out must
+    be CUDA tensors; the workspace is the library's static 24 MiB device
+    array, so images beyond about 500,000 pixel x channel values are refused
+    and calls that overlap on the GPU race with each other."""
+    lib = load()
+    s = 0
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    st = Stats()
+    rc = lib.hdi_inpaint_noalloc(device, ctypes.c_void_p(s), ctypes.byref(image_of(f)), ctypes.byref(mask_of(mask)),
+                                 ctypes.byref(image_of(out)), float(tol), ctypes.byref(st))
+    if rc != HDI_OK and rc != -3:
+        raise HdiError(rc, "hdi_inpaint_noalloc failed")
+    return st.as_dict()
 
 
 def version() -> str:

@@ -754,3 +754,172 @@ int Ctx::inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, 
                     s.iterations);
     return HDI_OK;
 }
+
+// ----------------------------------------------- allocation-free inpaint ---
+//
+// hdi_inpaint_noalloc: the inpainting solve of hdi_inpaint for callers that
+// must not allocate device memory (see include/hdi.h). Its whole workspace
+// is carved from the file-scope array below; nothing here calls cudaMalloc,
+// cudaFree, cudaMallocHost or any other allocating routine.
+
+constexpr size_t kNoAllocBytes = 24u << 20;   // 24 MiB on every GPU that loads the library
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};   // device address of the scratch, per device
+double g_noalloc_hscal[64];                     // host mirror of the reduction outputs
+
+// Carves the inpainting workspace of an H x W x nch image out of `base`
+// (the same layout rules as Ctx::setup, restricted to the buffers the
+// inpainting solve uses). Returns the bytes needed; carves only if they fit.
+size_t noalloc_layout(Ctx& c, char* base, size_t cap, int H_, int W_, int nch_) {
+    int sizes[kMaxLevels][2];
+    int nl = 0, h = H_, w = W_;
+    sizes[nl][0] = h;
+    sizes[nl][1] = w;
+    ++nl;
+    while (std::max(h, w) > 32 && nl < kMaxLevels) {
+        h = (h + 1) / 2;
+        w = (w + 1) / 2;
+        sizes[nl][0] = h;
+        sizes[nl][1] = w;
+        ++nl;
+    }
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        off = (off + 255) & ~(size_t)255;
+        char* p = base + off;
+        off += bytes;
+        return p;
+    };
+    const bool carve = true;
+    int maxparts = 1;
+    for (int l = 0; l < nl; ++l)
+        maxparts = std::max(maxparts, ((sizes[l][1] + 31) / 32) * ((sizes[l][0] + 7) / 8));
+    // first pass: size only
+    for (int pass = 0; pass < 2; ++pass) {
+        off = 0;
+        for (int l = 0; l < nl; ++l) {
+            Level& L = c.lev[l];
+            const int P = round_up(sizes[l][1], 32);
+            const int wp = (sizes[l][1] + 31) / 32 + 1;
+            const long long cs = (long long)sizes[l][0] * P;
+            char* bits = take((size_t)sizes[l][0] * wp * 4);
+            char* xa = take((size_t)nch_ * cs * 4);
+            char* xb = take((size_t)nch_ * cs * 4);
+            char* b = take((size_t)nch_ * cs * 4);
+            if (pass == 1) {
+                L.H = sizes[l][0];
+                L.W = sizes[l][1];
+                L.P = P;
+                L.wp = wp;
+                L.cs = cs;
+                L.bits = (uint32_t*)bits;
+                L.xa = (float*)xa;
+                L.xb = (float*)xb;
+                L.b = (float*)b;
+                L.nbx = tile_count(L.W, 32, kOv);
+                L.nby = tile_count(L.H, 32, kOv);
+            }
+        }
+        const size_t n32 = (size_t)nch_ * H_ * round_up(W_, 32);
+        const int dfs[3] = {kF, kU0, kU1};
+        for (int i = 0; i < 3; ++i) {
+            char* p = take(n32 * 8);
+            if (pass == 1) {
+                c.dfv[dfs[i]].hi = (float*)p;
+                c.dfv[dfs[i]].lo = (float*)p + n32;
+            }
+        }
+        char* lo2 = take(n32 * 4);
+        char* parts = take((size_t)kSlots * maxparts * nch_ * 8);
+        char* scal = take((size_t)kSlots * 4 * 8);
+        char* tick = take((size_t)kSlots * 4);
+        char* cnt = take(64 * 8);
+        char* flg = take(256);
+        if (pass == 0) {
+            if (off > cap || !carve) return off;
+            continue;
+        }
+        c.flo2 = (float*)lo2;
+        c.partials = (double*)parts;
+        c.scal = (double*)scal;
+        c.tickets = (unsigned*)tick;
+        c.counters = (unsigned long long*)cnt;
+        c.flags = (unsigned*)flg;
+        c.maxparts_ = maxparts;
+        c.H = H_;
+        c.W = W_;
+        c.nch = nch_;
+        c.nlev = nl;
+    }
+    return off;
+}
+}  // namespace
+
+extern "C" int hdi_inpaint_noalloc(int device, void* cuda_stream, const hdi_image* f, const hdi_mask* mask,
+                                   hdi_image* u, double tol, hdi_stats* st) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (device < 0 || device >= kNoAllocMaxDevices) return HDI_ERR_INVALID_ARG;
+    if (!f || !mask || !u || !f->data || !mask->data || !u->data) return HDI_ERR_INVALID_ARG;
+    if (f->location != HDI_DEVICE || mask->location != HDI_DEVICE || u->location != HDI_DEVICE)
+        return HDI_ERR_INVALID_ARG;   // host buffers would need a staging allocation
+    if (!(tol > 0.0 && tol < 1.0)) return HDI_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return HDI_ERR_CUDA;
+    }
+    if (!g_noalloc_ptr[device]) {
+        // One-time set-up on this device, with the device current: the
+        // array's name is only a host-side stand-in, so look up its address.
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return HDI_ERR_CUDA;
+        }
+        g_noalloc_ptr[device] = p;
+    }
+    Ctx c;
+    c.device = device;
+    c.stream = (cudaStream_t)cuda_stream;
+    c.hscal = g_noalloc_hscal;
+    int rc;
+    if ((rc = c.check_image(f, "f", -1, 0, 0))) return rc;
+    if ((rc = c.check_image(u, "u", f->height, f->width, f->channels))) return rc;
+    if (u->dtype != f->dtype) return HDI_ERR_INVALID_ARG;
+    if (noalloc_layout(c, (char*)g_noalloc_ptr[device], kNoAllocBytes, f->height, f->width, f->channels) >
+        kNoAllocBytes)
+        return HDI_ERR_INVALID_ARG;   // image too large for the static scratch
+    // The scratch keeps the previous call's contents: clear what must start at zero.
+    cudaMemsetAsync(c.tickets, 0, (size_t)kSlots * 4, c.stream);
+    cudaMemsetAsync(c.counters, 0, 64 * 8, c.stream);
+    cudaMemsetAsync(c.scal, 0, (size_t)kSlots * 4 * 8, c.stream);
+    long long ones = 0;
+    if ((rc = c.load_mask(mask, &ones))) return rc;
+    if (ones == 0) return HDI_ERR_EMPTY_MASK;
+    if ((rc = c.load_image(f, c.dfv[kF], c.flo2))) return rc;
+    SolveSpec s;
+    s.u[0] = c.dfv[kU0];
+    s.u[1] = c.dfv[kU1];
+    s.cur = 0;
+    s.rhs = RHS_DATA;
+    s.d = cview(c.dfv[kF]);
+    s.tol = tol;
+    s.max_iter = (int)c.p.max_vcycles;
+    s.start = START_FMG;
+    const int src = c.solve(s);
+    if (src != HDI_OK && src != HDI_ERR_NOT_CONVERGED) return src;
+    if ((rc = c.store_image(cview(s.u[s.cur]), u, false, c.flo2))) return rc;
+    if (st) {
+        st->status = src;
+        st->iterations = s.iterations;
+        st->vcycles = c.vcycles_run;
+        st->local_iters = 0;
+        st->rel_res = s.rel_max;
+        st->mse = 0.0;
+        st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return src;
+}
