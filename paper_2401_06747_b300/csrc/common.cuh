@@ -53,6 +53,24 @@ __device__ __forceinline__ double block_sum_d(double v) {
     return v;
 }
 
+// Block-wide FP32 sum in a fixed tree order; result valid in thread 0.
+// (Per-pixel reductions run in FP32: the FP64 pipe of the target is a small
+// fraction of its FP32 pipe. Only one FP64 value per CTA reaches the grid
+// reduction.)
+__device__ __forceinline__ float block_sum_f(float v) {
+    __shared__ float shf[32];
+    const int tid = linear_tid();
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    v = warp_sum_f(v);
+    __syncthreads();
+    if ((tid & 31) == 0) shf[tid >> 5] = v;
+    __syncthreads();
+    const int nw = (nt + 31) >> 5;
+    v = (tid < nw) ? shf[tid] : 0.f;
+    if (tid < 32) v = warp_sum_f(v);
+    return v;
+}
+
 // Deterministic grid reduction: every CTA deposits one FP64 partial per
 // (channel, part); the last CTA to arrive sums each channel's partials in a
 // fixed order and writes out[ch]. `nparts` CTAs per channel, `nch` channels;

@@ -16,7 +16,7 @@ struct Params {
     double coarse_max_local = 600;
     double max_vcycles = 60;
     double tonal_max_iter = 400;
-    double tonal_inner_ratio = 1e-3;
+    double tonal_inner_ratio = 1e-2;
     double tonal_echo_rtol = 1e-4;
     double tonal_echo_max_iter = 300;
     double hbm_budget_gb = 200.0;

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) k_restrict_residual(LevelArr F, MaskView 
     const int ch = blockIdx.z;
     const float* xc = x + ch * F.cs;
     const float* bc = b + ch * F.cs;
-    double sq = 0.0;
+    float sq = 0.f;
     if (X < C.W && Y < C.H) {
         float s = 0.f;
         if (!cm.known(X, Y)) {
@@ -144,9 +144,9 @@ __global__ void __launch_bounds__(256) k_restrict_residual(LevelArr F, MaskView 
                 }
         }
         cb[ch * C.cs + (size_t)Y * C.pitch + X] = s;
-        sq = (double)s * (double)s;
+        sq = s * s;
     }
-    const double tot = block_sum_d(sq);
+    const double tot = (double)block_sum_f(sq);
     grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
 }
 
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_prolong(LevelArr F, MaskView fm
     }
     __syncthreads();
     const int px = bx0 + threadIdx.x, py = by0 + threadIdx.y;
-    double sq = 0.0;
+    float sq = 0.f;
     if (px < F.W && py < F.H) {
         const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
         const float v = t[ty][tx];
@@ -203,10 +203,10 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_prolong(LevelArr F, MaskView fm
             if (py > 0) lap += v - t[ty - 1][tx];
             if (py + 1 < F.H) lap += v - t[ty + 1][tx];
             const float r = bc[(size_t)py * F.pitch + px] - lap;
-            sq = (double)r * (double)r;
+            sq = r * r;
         }
     }
-    const double tot = block_sum_d(sq);
+    const double tot = (double)block_sum_f(sq);
     grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
 }
 
@@ -351,12 +351,10 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_residual_df(ResArgs a) {
         a.r32[idx] = r;
         rr = r * r;
     }
-    rr = warp_sum_f(rr);
-    const double tot = block_sum_d((threadIdx.x & 31) == 0 ? (double)rr : 0.0);
+    const double tot = (double)block_sum_f(rr);
     grid_reduce_commit(a.red_r, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
     if (a.want_b) {
-        bb2 = warp_sum_f(bb2);
-        const double totb = block_sum_d((threadIdx.x & 31) == 0 ? (double)bb2 : 0.0);
+        const double totb = (double)block_sum_f(bb2);
         grid_reduce_commit(a.red_b, ch, blockIdx.y * gridDim.x + blockIdx.x, totb);
     }
 }

@@ -210,8 +210,7 @@ __global__ void __launch_bounds__(256) k_tonal_residual(LevelArr F, MaskView m, 
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int yy = blockIdx.y * blockDim.y + threadIdx.y;
     const int ch = blockIdx.z;
-    float se = 0.f;
-    double sr = 0.0;
+    float se = 0.f, sr = 0.f;
     if (x < F.W && yy < F.H) {
         const size_t idx = ch * F.cs + (size_t)yy * F.pitch + x;
         float sh, sl;
@@ -225,13 +224,12 @@ __global__ void __launch_bounds__(256) k_tonal_residual(LevelArr F, MaskView m, 
             if (yy > 0 && !m.known(x, yy - 1)) acc += (double)w.hi[idx - F.pitch] + (double)w.lo[idx - F.pitch];
             if (yy + 1 < F.H && !m.known(x, yy + 1)) acc += (double)w.hi[idx + F.pitch] + (double)w.lo[idx + F.pitch];
             r[idx] = (float)acc;
-            sr = acc * acc;
+            sr = (float)acc * (float)acc;
         }
     }
-    const double tr = block_sum_d(sr);
+    const double tr = (double)block_sum_f(sr);
     grid_reduce_commit(red_r, ch, blockIdx.y * gridDim.x + blockIdx.x, tr);
-    se = warp_sum_f(se);
-    const double te = block_sum_d((threadIdx.x & 31) == 0 ? (double)se : 0.0);
+    const double te = (double)block_sum_f(se);
     grid_reduce_commit(red_e, ch, blockIdx.y * gridDim.x + blockIdx.x, te);
 }
 
@@ -609,7 +607,7 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     sw.d = F;
     sw.y = DFc{nullptr, nullptr};
     sw.start = START_ZERO;
-    sw.tol = std::max(1e-13, ratio * tol);
+    sw.tol = 1e-3;   // ||B^T f|| only scales the stopping test; 0.1% is ample
     sw.max_iter = (int)p.max_vcycles;
     rc = solve(sw);
     if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return fail(rc, "tonal: B^T f solve: %s", err.c_str());
