@@ -279,7 +279,11 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     if (l == 0) tstop();
 }
 
-static dim3 tiles_of(const Level& L, int nch) { return dim3((L.W + PT_W - 1) / PT_W, (L.H + PT_H - 1) / PT_H, nch); }
+// Grid of the 32x8-tile kernels: each CTA walks TILE_ROWS bands of tiles.
+static dim3 tiles_of(const Level& L, int nch) {
+    const int ty = (L.H + PT_H - 1) / PT_H;
+    return dim3((L.W + PT_W - 1) / PT_W, (ty + TILE_ROWS - 1) / TILE_ROWS, nch);
+}
 
 // One V-cycle (Sec. 3.2) on the correction equation A_l x = b_l, x from 0.
 // Result in lev[l].xa.
@@ -295,7 +299,7 @@ void Ctx::vcycle(int l) {
     oras(l, true, nullptr, L.xa, pre_norm, false, it);
     Level& C = lev[l + 1];
     {
-        dim3 blk(32, 8), grd((C.W + 31) / 32, (C.H + 7) / 8, nch);
+        dim3 blk(32, 8), grd((C.W + 31) / 32, ((C.H + 7) / 8 + TILE_ROWS - 1) / TILE_ROWS, nch);
         if (l == 0) tstart(kT_Restrict);
         k_restrict_residual<<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, arr(l + 1), mview(l + 1), C.b,
                                                      reducer(l + 1, grd.x * grd.y));

@@ -124,27 +124,32 @@ __device__ __forceinline__ float fine_residual(const float* __restrict__ x, cons
 }
 
 // Coarse right-hand side b_H = sum of the children's residuals (0 on coarse
-// known pixels) and ||b_H||^2 per channel. Block 32x8 over coarse pixels.
+// known pixels) and ||b_H||^2 per channel. Block 32x8 over coarse pixels;
+// each CTA walks TILE_ROWS consecutive 8-row bands so that few CTAs take
+// part in the grid reduction.
+#define TILE_ROWS 16
 __global__ void __launch_bounds__(256) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                            const float* __restrict__ b, LevelArr C, MaskView cm,
                                                            float* __restrict__ cb, GridReduce red) {
     const int X = blockIdx.x * blockDim.x + threadIdx.x;
-    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
     const int ch = blockIdx.z;
     const float* xc = x + ch * F.cs;
     const float* bc = b + ch * F.cs;
     float sq = 0.f;
-    if (X < C.W && Y < C.H) {
-        float s = 0.f;
-        if (!cm.known(X, Y)) {
-            for (int dy = 0; dy < 2; ++dy)
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int px = 2 * X + dx, py = 2 * Y + dy;
-                    if (px < F.W && py < F.H) s += fine_residual(xc, bc, F, fm, px, py);
-                }
+    for (int band = 0; band < TILE_ROWS; ++band) {
+        const int Y = (blockIdx.y * TILE_ROWS + band) * blockDim.y + threadIdx.y;
+        if (X < C.W && Y < C.H) {
+            float s = 0.f;
+            if (!cm.known(X, Y)) {
+                for (int dy = 0; dy < 2; ++dy)
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const int px = 2 * X + dx, py = 2 * Y + dy;
+                        if (px < F.W && py < F.H) s += fine_residual(xc, bc, F, fm, px, py);
+                    }
+            }
+            cb[ch * C.cs + (size_t)Y * C.pitch + X] = s;
+            sq += s * s;
         }
-        cb[ch * C.cs + (size_t)Y * C.pitch + X] = s;
-        sq = s * s;
     }
     const double tot = (double)block_sum_f(sq);
     grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
@@ -174,36 +179,41 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_prolong(LevelArr F, MaskView fm
                                                          LevelArr C, const float* __restrict__ e, GridReduce red) {
     __shared__ float t[PT_H + 2][PT_W + 2];
     const int ch = blockIdx.z;
-    const int bx0 = blockIdx.x * PT_W, by0 = blockIdx.y * PT_H;
+    const int bx0 = blockIdx.x * PT_W;
     const float* xc = (MODE == 0) ? xin + ch * F.cs : nullptr;
     const float* bc = b + ch * F.cs;
     const float* ec = (MODE == 2) ? nullptr : e + ch * C.cs;
-    for (int i = threadIdx.y * PT_W + threadIdx.x; i < (PT_W + 2) * (PT_H + 2); i += PT_W * PT_H) {
-        const int ty = i / (PT_W + 2), tx = i - ty * (PT_W + 2);
-        const int px = min(max(bx0 + tx - 1, 0), F.W - 1);
-        const int py = min(max(by0 + ty - 1, 0), F.H - 1);
-        const size_t idx = (size_t)py * F.pitch + px;
-        float v;
-        if (fm.known(px, py)) v = (MODE == 0) ? xc[idx] : bc[idx];
-        else if (MODE == 2) v = 0.f;
-        else v = (MODE == 0 ? xc[idx] : 0.f) + prolong_at(ec, C, px, py);
-        t[ty][tx] = v;
-    }
-    __syncthreads();
-    const int px = bx0 + threadIdx.x, py = by0 + threadIdx.y;
     float sq = 0.f;
-    if (px < F.W && py < F.H) {
-        const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
-        const float v = t[ty][tx];
-        xout[ch * F.cs + (size_t)py * F.pitch + px] = v;
-        if (!fm.known(px, py)) {
-            float lap = 0.f;
-            if (px > 0) lap += v - t[ty][tx - 1];
-            if (px + 1 < F.W) lap += v - t[ty][tx + 1];
-            if (py > 0) lap += v - t[ty - 1][tx];
-            if (py + 1 < F.H) lap += v - t[ty + 1][tx];
-            const float r = bc[(size_t)py * F.pitch + px] - lap;
-            sq = r * r;
+    for (int band = 0; band < TILE_ROWS; ++band) {
+        const int by0 = (blockIdx.y * TILE_ROWS + band) * PT_H;
+        if (by0 >= F.H) break;
+        __syncthreads();
+        for (int i = threadIdx.y * PT_W + threadIdx.x; i < (PT_W + 2) * (PT_H + 2); i += PT_W * PT_H) {
+            const int ty = i / (PT_W + 2), tx = i - ty * (PT_W + 2);
+            const int px = min(max(bx0 + tx - 1, 0), F.W - 1);
+            const int py = min(max(by0 + ty - 1, 0), F.H - 1);
+            const size_t idx = (size_t)py * F.pitch + px;
+            float v;
+            if (fm.known(px, py)) v = (MODE == 0) ? xc[idx] : bc[idx];
+            else if (MODE == 2) v = 0.f;
+            else v = (MODE == 0 ? xc[idx] : 0.f) + prolong_at(ec, C, px, py);
+            t[ty][tx] = v;
+        }
+        __syncthreads();
+        const int px = bx0 + threadIdx.x, py = by0 + threadIdx.y;
+        if (px < F.W && py < F.H) {
+            const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
+            const float v = t[ty][tx];
+            xout[ch * F.cs + (size_t)py * F.pitch + px] = v;
+            if (!fm.known(px, py)) {
+                float lap = 0.f;
+                if (px > 0) lap += v - t[ty][tx - 1];
+                if (px + 1 < F.W) lap += v - t[ty][tx + 1];
+                if (py > 0) lap += v - t[ty - 1][tx];
+                if (py + 1 < F.H) lap += v - t[ty + 1][tx];
+                const float r = bc[(size_t)py * F.pitch + px] - lap;
+                sq += r * r;
+            }
         }
     }
     const double tot = (double)block_sum_f(sq);
@@ -284,8 +294,13 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_residual_df(ResArgs a) {
     __shared__ float th[PT_H + 2][PT_W + 2];
     __shared__ float tl[PT_H + 2][PT_W + 2];
     const int ch = blockIdx.z;
-    const int bx0 = blockIdx.x * PT_W, by0 = blockIdx.y * PT_H;
+    const int bx0 = blockIdx.x * PT_W;
     const long long co = ch * a.F.cs;
+    float rr = 0.f, bb2 = 0.f;
+    for (int band = 0; band < TILE_ROWS; ++band) {
+    const int by0 = (blockIdx.y * TILE_ROWS + band) * PT_H;
+    if (by0 >= a.F.H) break;
+    __syncthreads();
     for (int i = threadIdx.y * PT_W + threadIdx.x; i < (PT_W + 2) * (PT_H + 2); i += PT_W * PT_H) {
         const int ty = i / (PT_W + 2), tx = i - ty * (PT_W + 2);
         const int px = min(max(bx0 + tx - 1, 0), a.F.W - 1);
@@ -309,7 +324,6 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_residual_df(ResArgs a) {
     }
     __syncthreads();
     const int px = bx0 + threadIdx.x, py = by0 + threadIdx.y;
-    float rr = 0.f, bb2 = 0.f;
     if (px < a.F.W && py < a.F.H) {
         const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
         const size_t idx = co + (size_t)py * a.F.pitch + px;
@@ -318,7 +332,7 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_residual_df(ResArgs a) {
         a.uout.lo[idx] = cl;
         float r = 0.f;
         if (a.m.known(px, py)) {
-            if (RHS == RHS_DATA) { const float bh = a.d.hi[idx] + a.d.lo[idx]; bb2 = bh * bh; }
+            if (RHS == RHS_DATA) { const float bh = a.d.hi[idx] + a.d.lo[idx]; bb2 += bh * bh; }
         } else {
             // lap = sum over in-image neighbours of (u_c - u_n), error-free:
             // the hi differences are summed with TwoSum, every rounding error
@@ -342,14 +356,15 @@ __global__ void __launch_bounds__(PT_W * PT_H) k_residual_df(ResArgs a) {
             if (RHS == RHS_SOURCE) {
                 const float yh = a.y.hi ? a.y.hi[idx] : 0.f, yl = a.y.hi ? a.y.lo[idx] : 0.f;
                 df_add(a.d.hi[idx], a.d.lo[idx], -yh, -yl, bh, bl);
-                bb2 = bh * bh;
+                bb2 += bh * bh;
             }
             float rh, rl;
             df_add(bh, bl, -sh, -sl, rh, rl);
             r = rh + rl;
         }
         a.r32[idx] = r;
-        rr = r * r;
+        rr += r * r;
+    }
     }
     const double tot = (double)block_sum_f(rr);
     grid_reduce_commit(a.red_r, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);

@@ -208,23 +208,26 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
 __global__ void __launch_bounds__(256) k_tonal_residual(LevelArr F, MaskView m, DFc f, DFc y, DFc w,
                                                         float* __restrict__ r, GridReduce red_r, GridReduce red_e) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int yy = blockIdx.y * blockDim.y + threadIdx.y;
     const int ch = blockIdx.z;
     float se = 0.f, sr = 0.f;
-    if (x < F.W && yy < F.H) {
-        const size_t idx = ch * F.cs + (size_t)yy * F.pitch + x;
-        float sh, sl;
-        if (y.hi) df_add(f.hi[idx], f.lo[idx], -y.hi[idx], -y.lo[idx], sh, sl);
-        else { sh = f.hi[idx]; sl = f.lo[idx]; }
-        se = sh * sh;
-        if (m.known(x, yy)) {
-            double acc = (double)sh + (double)sl;
-            if (x > 0 && !m.known(x - 1, yy)) acc += (double)w.hi[idx - 1] + (double)w.lo[idx - 1];
-            if (x + 1 < F.W && !m.known(x + 1, yy)) acc += (double)w.hi[idx + 1] + (double)w.lo[idx + 1];
-            if (yy > 0 && !m.known(x, yy - 1)) acc += (double)w.hi[idx - F.pitch] + (double)w.lo[idx - F.pitch];
-            if (yy + 1 < F.H && !m.known(x, yy + 1)) acc += (double)w.hi[idx + F.pitch] + (double)w.lo[idx + F.pitch];
-            r[idx] = (float)acc;
-            sr = (float)acc * (float)acc;
+    for (int band = 0; band < TILE_ROWS; ++band) {
+        const int yy = (blockIdx.y * TILE_ROWS + band) * blockDim.y + threadIdx.y;
+        if (x < F.W && yy < F.H) {
+            const size_t idx = ch * F.cs + (size_t)yy * F.pitch + x;
+            float sh, sl;
+            if (y.hi) df_add(f.hi[idx], f.lo[idx], -y.hi[idx], -y.lo[idx], sh, sl);
+            else { sh = f.hi[idx]; sl = f.lo[idx]; }
+            se += sh * sh;
+            if (m.known(x, yy)) {
+                double acc = (double)sh + (double)sl;
+                if (x > 0 && !m.known(x - 1, yy)) acc += (double)w.hi[idx - 1] + (double)w.lo[idx - 1];
+                if (x + 1 < F.W && !m.known(x + 1, yy)) acc += (double)w.hi[idx + 1] + (double)w.lo[idx + 1];
+                if (yy > 0 && !m.known(x, yy - 1)) acc += (double)w.hi[idx - F.pitch] + (double)w.lo[idx - F.pitch];
+                if (yy + 1 < F.H && !m.known(x, yy + 1))
+                    acc += (double)w.hi[idx + F.pitch] + (double)w.lo[idx + F.pitch];
+                r[idx] = (float)acc;
+                sr += (float)acc * (float)acc;
+            }
         }
     }
     const double tr = (double)block_sum_f(sr);
@@ -424,7 +427,7 @@ int Ctx::tonal_setup() {
 }
 
 void Ctx::tonal_residual(DFc y, DFc w) {
-    dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8, nch);
+    dim3 blk(32, 8), grd((W + 31) / 32, ((H + 7) / 8 + TILE_ROWS - 1) / TILE_ROWS, nch);
     k_tonal_residual<<<grd, blk, 0, stream>>>(arr(0), mview(0), cview(dfv[kF]), y, w, tres,
                                               reducer(kSlotTonalR, grd.x * grd.y), reducer(kSlotTonalE, grd.x * grd.y));
     ++launches;
