@@ -8,6 +8,7 @@
 #include <vector>
 #include <algorithm>
 #include <chrono>
+#include <climits>
 
 #include "../../include/hdi.h"
 #include "common.cuh"

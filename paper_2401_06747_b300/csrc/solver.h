@@ -161,5 +161,6 @@ struct Ctx {
                 hdi_stats* st);
     int tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hdi_image* g, double tol,
               hdi_stats* st);
+    int dens_load(const hdi_image* im, double* dst, void* hstage);
     int densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t k, uint64_t seed, int64_t* added);
 };

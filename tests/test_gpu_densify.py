@@ -1,0 +1,99 @@
+"""Parity of the CUDA densification step (Sec. 4.1, Alg. 1; initial mask of
+Sec. 4.2) against the oracle: new mask bits must match exactly."""
+
+import numpy as np
+import pytest
+
+from gpu_util import torch, need_gpu, ctx, dev
+from oracle import inpaint as inpaint_ref
+from oracle.densify import densify_step as densify_ref, initial_mask
+from synthdata import synth_image, synth_rgb, random_mask
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_step(f, c, u, k, seed=0, host=False):
+    need_gpu()
+    kx = ctx()
+    if host:
+        m = np.ascontiguousarray(c.copy())
+        added = kx.densify_step(f, m, u, k, seed)
+        return m, added
+    md = dev(c.copy())
+    added = kx.densify_step(dev(f), md, None if u is None else dev(u), k, seed)
+    return md.cpu().numpy(), added
+
+
+@pytest.mark.parametrize("H,W,ch,dtype,k,seed", [(77, 131, 3, np.float32, 60, 5), (200, 150, 1, np.float64, 300, 9),
+                                                 (33, 40, 3, np.float32, 2000, 1), (1, 64, 1, np.float64, 5, 2)])
+def test_initial_mask_bit_exact(H, W, ch, dtype, k, seed):
+    f = synth_rgb(H, W, seeds=tuple(range(seed, seed + ch)), dtype=dtype) if ch == 3 else synth_image(H, W, seed).astype(dtype)
+    c = np.zeros((H, W), np.uint8)
+    m, added = gpu_step(f, c, None, k, seed)
+    ref = initial_mask(f.astype(np.float64), k, seed)
+    np.testing.assert_array_equal(m, ref)
+    assert added == int(ref.sum())
+
+
+@pytest.mark.parametrize("H,W,ch,dtype,d,k", [(96, 128, 3, np.float32, 0.02, 40), (300, 200, 1, np.float64, 0.005, 150),
+                                              (64, 80, 3, np.float32, 0.05, 10000), (130, 70, 1, np.float32, 0.01, 0)])
+def test_step_bit_exact(H, W, ch, dtype, d, k):
+    f = synth_rgb(H, W, seeds=(4, 5, 6), dtype=dtype) if ch == 3 else synth_image(H, W, 4).astype(dtype)
+    c = random_mask(H, W, d, 17)
+    u = inpaint_ref(f.astype(np.float64), c).astype(dtype)
+    m, added = gpu_step(f, c, u, k)
+    ref, ref_added = densify_ref(f.astype(np.float64), c, u.astype(np.float64), k)
+    np.testing.assert_array_equal(m, ref)
+    assert added == ref_added
+    assert np.all(m >= c)
+
+
+def test_edge_cases():
+    f = synth_image(40, 30, 3)
+    one = np.zeros((40, 30), np.uint8)
+    one[10, 12] = 1
+    u = np.full_like(f, f[10, 12])
+    m, a = gpu_step(f, one, u, 7)
+    ref, ra = densify_ref(f, one, u, 7)
+    np.testing.assert_array_equal(m, ref)
+    assert a == ra
+    full = np.ones((40, 30), np.uint8)
+    m, a = gpu_step(f, full, f, 5)
+    assert a == 0 and np.all(m == 1)
+    row = synth_image(1, 50, 8)
+    cr = random_mask(1, 50, 0.1, 3)
+    ur = inpaint_ref(row, cr)
+    m, a = gpu_step(row, cr, ur, 3)
+    ref, ra = densify_ref(row, cr, ur, 3)
+    np.testing.assert_array_equal(m, ref)
+
+
+def test_host_buffers():
+    f = synth_rgb(50, 60, seeds=(1, 2, 3), dtype=np.float32)
+    c = random_mask(50, 60, 0.03, 2)
+    u = inpaint_ref(f.astype(np.float64), c).astype(np.float32)
+    m, a = gpu_step(f, c, u, 12, host=True)
+    ref, ra = densify_ref(f.astype(np.float64), c, u.astype(np.float64), 12)
+    np.testing.assert_array_equal(m, ref)
+
+
+def test_densify_loop_matches_oracle_loop():
+    """Empty mask -> 0.5% steps up to 3%, re-inpainting after each step on
+    each side (GPU solver vs oracle solver, FP64 data, tight tolerance)."""
+    need_gpu()
+    H, W = 192, 256
+    f = synth_rgb(H, W, seeds=(1, 2, 3)).astype(np.float64)
+    N = H * W
+    kx = ctx()
+    fd = dev(f)
+    cg = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
+    co = np.zeros((H, W), np.uint8)
+    ug = torch.empty_like(fd)
+    uo = None
+    for s in range(1, 7):
+        k = int(s * 0.005 * N) - int(co.sum())
+        kx.densify_step(fd, cg, None if s == 1 else ug, k, 300)
+        co, _ = densify_ref(f, co, uo, k, 300)
+        np.testing.assert_array_equal(cg.cpu().numpy(), co, err_msg=f"step {s}")
+        kx.inpaint(fd, cg, ug, tol=1e-12)
+        uo = inpaint_ref(f, co)
