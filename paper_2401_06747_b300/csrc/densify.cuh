@@ -236,6 +236,8 @@ __global__ void k_dens_raster(const Tri* __restrict__ list, const unsigned* coun
     }
 }
 
+constexpr int kNoOwner = 0x7F7F7F7F;   // memset(0x7F) sentinel, above every cell id
+
 // Hull cells, cell sums and the per-cell maximum of e.
 __global__ void k_dens_cells(MaskView m, const int* __restrict__ V, int* __restrict__ owner,
                              const long long* __restrict__ eq, const double* __restrict__ e,
@@ -250,7 +252,7 @@ __global__ void k_dens_cells(MaskView m, const int* __restrict__ V, int* __restr
         return;
     }
     int o = owner[i];
-    if (o == INT_MAX) {
+    if (o == kNoOwner) {
         o = hull_base + V[i];
         owner[i] = o;
     }
@@ -327,8 +329,6 @@ __global__ void k_dens_load(const T* __restrict__ src, long long rs, long long c
 }
 
 // ------------------------------------------------------------ the driver ---
-
-constexpr int kNoOwner = 0x7F7F7F7F;   // memset(0x7F) sentinel, above every cell id
 
 // Copies a caller image (device or host) into a plain FP64 [nch][H][W] array.
 int Ctx::dens_load(const hdi_image* im, double* dst, void* hstage) {
