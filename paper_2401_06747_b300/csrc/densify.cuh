@@ -484,7 +484,7 @@ int Ctx::densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t
             }
             Tid = (long long)pid;
         }
-        if (nc) {
+        if (nc && k > 0) {
             k_dens_commit<<<(nc + 255) / 256, 256, 0, stream>>>(cand, ncand, E, T, Tid, arg, W, mptr, mrs, cnt);
             ++launches;
         }
