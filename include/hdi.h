@@ -189,9 +189,10 @@ const char* hdi_version(void);
  *   coarse_eta        [1e-8]  relative squared-residual target of the single-block coarsest solve
  *   max_vcycles       [60]    refinement steps per inpainting solve
  *   tonal_max_iter    [400]   RAS iterations per tonal solve
- *   tonal_inner_ratio [1e-2]  inner solves target: ratio * current outer relative residual
- *   tonal_anderson    [5]     Anderson window on the RAS iteration (0 = plain Alg. 2)
- *   tonal_echo_rtol   [1e-4]  relative CG tolerance of the local echo solves
+ *   tonal_inner_ratio [0.1]   inner solves target: ratio * current outer relative residual
+ *   tonal_anderson    [8]     Anderson window on the RAS iteration (0 = plain Alg. 2)
+ *   tonal_oras_eta    [1e-2]  oras_eta used inside the tonal inner solves
+ *   tonal_echo_rtol   [1e-3]  relative CG tolerance of the local echo solves
  *   trace             [0]     1 = one line per RAS iteration on stderr
  *   hbm_budget_gb     [200]   workspace cap for this context
  */

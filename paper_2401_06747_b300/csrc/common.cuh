@@ -105,7 +105,7 @@ __device__ __forceinline__ void grid_reduce_commit(const GridReduce& R, int ch, 
 #pragma unroll
             for (int k = 0; k < 8; ++k) a8[k] += __ldcg(pp + i + k * nt);
         }
-        for (int k = 0; i < R.nparts; i += nt, ++k) a8[k & 7] += __ldcg(pp + i);
+        for (; i < R.nparts; i += nt) a8[0] += __ldcg(pp + i);
         double acc = ((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7]));
         acc = block_sum_d(acc);
         if (tid == 0) R.out[c] = acc;

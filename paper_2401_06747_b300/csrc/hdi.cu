@@ -42,6 +42,7 @@ const ParamDef kParams[] = {
     {"hbm_budget_gb", &Params::hbm_budget_gb, 0.001, 1e6},
     {"trace", &Params::trace, 0, 1},
     {"tonal_anderson", &Params::tonal_anderson, 0, 8},
+    {"tonal_oras_eta", &Params::tonal_oras_eta, 1e-12, 1.0},
 };
 
 }  // namespace
@@ -280,10 +281,9 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     if (l == 0) tstop();
 }
 
-// Grid of the 32x8-tile kernels: each CTA walks TILE_ROWS bands of tiles.
+// Grid of the column-strip kernels: 128 columns x CS_ROWS rows per CTA.
 static dim3 tiles_of(const Level& L, int nch) {
-    const int ty = (L.H + PT_H - 1) / PT_H;
-    return dim3((L.W + PT_W - 1) / PT_W, (ty + TILE_ROWS - 1) / TILE_ROWS, nch);
+    return dim3((L.W + 127) / 128, (L.H + CS_ROWS - 1) / CS_ROWS, nch);
 }
 
 // One V-cycle (Sec. 3.2) on the correction equation A_l x = b_l, x from 0.
@@ -300,7 +300,7 @@ void Ctx::vcycle(int l) {
     oras(l, true, nullptr, L.xa, pre_norm, false, it);
     Level& C = lev[l + 1];
     {
-        dim3 blk(32, 8), grd((C.W + 31) / 32, ((C.H + 7) / 8 + TILE_ROWS - 1) / TILE_ROWS, nch);
+        dim3 blk(128), grd = tiles_of(L, nch);
         if (l == 0) tstart(kT_Restrict);
         k_restrict_residual<<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, arr(l + 1), mview(l + 1), C.b,
                                                      reducer(l + 1, grd.x * grd.y));
@@ -309,7 +309,7 @@ void Ctx::vcycle(int l) {
     }
     vcycle(l + 1);
     {
-        dim3 grd = tiles_of(L, nch), blk(PT_W, PT_H);
+        dim3 grd = tiles_of(L, nch), blk(128);
         if (l == 0) tstart(kT_Prolong);
         k_prolong<0><<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, L.xb, arr(l + 1), C.xa,
                                               reducer(l, grd.x * grd.y));
@@ -336,14 +336,14 @@ void Ctx::fmg(DFc d) {
     }
     const int L = nlev - 1;
     {
-        dim3 grd = tiles_of(lev[L], nch), blk(PT_W, PT_H);
+        dim3 grd = tiles_of(lev[L], nch), blk(128);
         k_prolong<2><<<grd, blk, 0, stream>>>(arr(L), mview(L), nullptr, lev[L].b, lev[L].xb, arr(L), nullptr,
                                               reducer(L, grd.x * grd.y));
         ++launches;
         oras(L, false, lev[L].xb, lev[L].xa, scal + L * 4, true, nullptr);
     }
     for (int l = L - 1; l >= 0; --l) {
-        dim3 grd = tiles_of(lev[l], nch), blk(PT_W, PT_H);
+        dim3 grd = tiles_of(lev[l], nch), blk(128);
         k_prolong<1><<<grd, blk, 0, stream>>>(arr(l), mview(l), nullptr, lev[l].b, lev[l].xb, arr(l + 1),
                                               lev[l + 1].xa, reducer(l, grd.x * grd.y));
         ++launches;
@@ -362,7 +362,7 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
     a.d = d;
     a.y = y;
     a.r32 = c.lev[0].b;
-    dim3 grd = tiles_of(c.lev[0], c.nch), blk(PT_W, PT_H);
+    dim3 grd((c.W + 127) / 128, (c.H + CS_ROWS - 1) / CS_ROWS, c.nch), blk(128);
     a.red_r = c.reducer(kSlotR64, grd.x * grd.y);
     a.red_b = c.reducer(kSlotB64, grd.x * grd.y);
     a.want_b = want_b ? 1 : 0;

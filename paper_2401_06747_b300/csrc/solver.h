@@ -16,12 +16,13 @@ struct Params {
     double coarse_max_local = 600;
     double max_vcycles = 60;
     double tonal_max_iter = 400;
-    double tonal_inner_ratio = 1e-2;
-    double tonal_echo_rtol = 1e-4;
+    double tonal_inner_ratio = 0.1;
+    double tonal_echo_rtol = 1e-3;
     double tonal_echo_max_iter = 300;
     double hbm_budget_gb = 200.0;
     double trace = 0;
-    double tonal_anderson = 5;      // Anderson window on the RAS iteration (0 = plain Alg. 2)               // 1: one line per outer iteration on stderr
+    double tonal_oras_eta = 1e-2;   // local stop fraction inside the tonal inner solves
+    double tonal_anderson = 8;      // Anderson window on the RAS iteration (0 = plain Alg. 2)               // 1: one line per outer iteration on stderr
 };
 
 struct Level {

@@ -124,31 +124,60 @@ __device__ __forceinline__ float fine_residual(const float* __restrict__ x, cons
 }
 
 // Coarse right-hand side b_H = sum of the children's residuals (0 on coarse
-// known pixels) and ||b_H||^2 per channel. Block 32x8 over coarse pixels;
-// each CTA walks TILE_ROWS consecutive 8-row bands so that few CTAs take
-// part in the grid reduction.
+// known pixels) and ||b_H||^2 per channel. Column strips over the fine grid
+// (see CS_ROWS below): each lane forms the fine residual of its column, two
+// consecutive rows are summed in registers and lane pairs (2j, 2j+1) are
+// combined by a shuffle.
+#define CS_ROWS 64
 #define TILE_ROWS 16
-__global__ void __launch_bounds__(256) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
+__global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                            const float* __restrict__ b, LevelArr C, MaskView cm,
                                                            float* __restrict__ cb, GridReduce red) {
-    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
+    const int px = x0 + lane;
+    const int y0 = blockIdx.y * CS_ROWS;
+    const int y1 = min(y0 + CS_ROWS, F.H);
     const int ch = blockIdx.z;
+    const bool act = px < F.W;
+    const int pxc = act ? px : F.W - 1;
     const float* xc = x + ch * F.cs;
     const float* bc = b + ch * F.cs;
     float sq = 0.f;
-    for (int band = 0; band < TILE_ROWS; ++band) {
-        const int Y = (blockIdx.y * TILE_ROWS + band) * blockDim.y + threadIdx.y;
-        if (X < C.W && Y < C.H) {
-            float s = 0.f;
-            if (!cm.known(X, Y)) {
-                for (int dy = 0; dy < 2; ++dy)
-                    for (int dx = 0; dx < 2; ++dx) {
-                        const int px = 2 * X + dx, py = 2 * Y + dy;
-                        if (px < F.W && py < F.H) s += fine_residual(xc, bc, F, fm, px, py);
-                    }
+    if (x0 < F.W) {
+        const uint32_t* mrow = fm.bits + (x0 >> 5);
+        float up = (y0 > 0) ? xc[(size_t)(y0 - 1) * F.pitch + pxc] : 0.f;
+        float cen = xc[(size_t)y0 * F.pitch + pxc];
+        float pair = 0.f;
+        for (int y = y0; y < y1; ++y) {
+            const float dn = (y + 1 < F.H) ? xc[(size_t)(y + 1) * F.pitch + pxc] : 0.f;
+            float lf = __shfl_up_sync(HDI_FULL, cen, 1);
+            float rt = __shfl_down_sync(HDI_FULL, cen, 1);
+            if (lane == 0 && px > 0) lf = xc[(size_t)y * F.pitch + px - 1];
+            if (lane == 31 && px + 1 < F.W) rt = xc[(size_t)y * F.pitch + px + 1];
+            const bool known = (mrow[(size_t)y * fm.wpitch] >> lane) & 1u;
+            float r = 0.f;
+            if (act && !known) {
+                float lap = 0.f;
+                if (px > 0) lap += cen - lf;
+                if (px + 1 < F.W) lap += cen - rt;
+                if (y > 0) lap += cen - up;
+                if (y + 1 < F.H) lap += cen - dn;
+                r = bc[(size_t)y * F.pitch + px] - lap;
             }
-            cb[ch * C.cs + (size_t)Y * C.pitch + X] = s;
-            sq += s * s;
+            pair += r;
+            if ((y & 1) || y + 1 == F.H) {
+                const float s = pair + __shfl_down_sync(HDI_FULL, pair, 1);
+                const int X = px >> 1, Y = y >> 1;
+                if (!(lane & 1) && act) {
+                    const float v = cm.known(X, Y) ? 0.f : s;
+                    cb[ch * C.cs + (size_t)Y * C.pitch + X] = v;
+                    sq += v * v;
+                }
+                pair = 0.f;
+            }
+            up = cen;
+            cen = dn;
         }
     }
     const double tot = (double)block_sum_f(sq);
@@ -165,55 +194,74 @@ __device__ __forceinline__ float prolong_at(const float* __restrict__ e, const L
     return 0.5625f * r0[X] + 0.1875f * (r0[Xn] + r1[X]) + 0.0625f * r1[Xn];
 }
 
-// Tiles of 32x8 pixels with a one-pixel halo in shared memory.
+// Tiles of 32x8 pixels (used by the staging helpers' grids).
 #define PT_W 32
 #define PT_H 8
+
+template <int MODE>
+__device__ __forceinline__ float prolong_value(const float* __restrict__ xc, const float* __restrict__ bc,
+                                               const float* __restrict__ ec, const LevelArr& F, const LevelArr& C,
+                                               bool known, int px, int py) {
+    const size_t idx = (size_t)py * F.pitch + px;
+    if (known) return (MODE == 0) ? xc[idx] : bc[idx];
+    if (MODE == 2) return 0.f;
+    return (MODE == 0 ? xc[idx] : 0.f) + prolong_at(ec, C, px, py);
+}
 
 // MODE 0 (V-cycle): xout = xin + P e on unknown pixels, xin on known ones;
 // MODE 1 (FMG):     xout = b on known pixels, P e on unknown ones;
 // MODE 2 (start):   xout = b on known pixels, 0 on unknown ones (e unused).
 // Then ||b - A xout||^2 per channel (the next sweep's local stop rule).
+// Column strips: lane = column, three-row register window of xout values.
 template <int MODE>
-__global__ void __launch_bounds__(PT_W * PT_H) k_prolong(LevelArr F, MaskView fm, const float* __restrict__ xin,
-                                                         const float* __restrict__ b, float* __restrict__ xout,
-                                                         LevelArr C, const float* __restrict__ e, GridReduce red) {
-    __shared__ float t[PT_H + 2][PT_W + 2];
+__global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const float* __restrict__ xin,
+                                                 const float* __restrict__ b, float* __restrict__ xout,
+                                                 LevelArr C, const float* __restrict__ e, GridReduce red) {
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
+    const int px = x0 + lane;
+    const int y0 = blockIdx.y * CS_ROWS;
+    const int y1 = min(y0 + CS_ROWS, F.H);
     const int ch = blockIdx.z;
-    const int bx0 = blockIdx.x * PT_W;
+    const bool act = px < F.W;
+    const int pxc = act ? px : F.W - 1;
     const float* xc = (MODE == 0) ? xin + ch * F.cs : nullptr;
     const float* bc = b + ch * F.cs;
     const float* ec = (MODE == 2) ? nullptr : e + ch * C.cs;
     float sq = 0.f;
-    for (int band = 0; band < TILE_ROWS; ++band) {
-        const int by0 = (blockIdx.y * TILE_ROWS + band) * PT_H;
-        if (by0 >= F.H) break;
-        __syncthreads();
-        for (int i = threadIdx.y * PT_W + threadIdx.x; i < (PT_W + 2) * (PT_H + 2); i += PT_W * PT_H) {
-            const int ty = i / (PT_W + 2), tx = i - ty * (PT_W + 2);
-            const int px = min(max(bx0 + tx - 1, 0), F.W - 1);
-            const int py = min(max(by0 + ty - 1, 0), F.H - 1);
-            const size_t idx = (size_t)py * F.pitch + px;
-            float v;
-            if (fm.known(px, py)) v = (MODE == 0) ? xc[idx] : bc[idx];
-            else if (MODE == 2) v = 0.f;
-            else v = (MODE == 0 ? xc[idx] : 0.f) + prolong_at(ec, C, px, py);
-            t[ty][tx] = v;
-        }
-        __syncthreads();
-        const int px = bx0 + threadIdx.x, py = by0 + threadIdx.y;
-        if (px < F.W && py < F.H) {
-            const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
-            const float v = t[ty][tx];
-            xout[ch * F.cs + (size_t)py * F.pitch + px] = v;
-            if (!fm.known(px, py)) {
-                float lap = 0.f;
-                if (px > 0) lap += v - t[ty][tx - 1];
-                if (px + 1 < F.W) lap += v - t[ty][tx + 1];
-                if (py > 0) lap += v - t[ty - 1][tx];
-                if (py + 1 < F.H) lap += v - t[ty + 1][tx];
-                const float r = bc[(size_t)py * F.pitch + px] - lap;
-                sq += r * r;
+    if (x0 < F.W) {
+        const uint32_t* mrow = fm.bits + (x0 >> 5);
+        float up = 0.f;
+        if (y0 > 0) up = prolong_value<MODE>(xc, bc, ec, F, C, fm.known(pxc, y0 - 1), pxc, y0 - 1);
+        uint32_t wc = mrow[(size_t)y0 * fm.wpitch];
+        float cen = prolong_value<MODE>(xc, bc, ec, F, C, (wc >> lane) & 1u, pxc, y0);
+        for (int y = y0; y < y1; ++y) {
+            uint32_t wn = 0;
+            float dn = 0.f;
+            if (y + 1 < F.H) {
+                wn = mrow[(size_t)(y + 1) * fm.wpitch];
+                dn = prolong_value<MODE>(xc, bc, ec, F, C, (wn >> lane) & 1u, pxc, y + 1);
             }
+            float lf = __shfl_up_sync(HDI_FULL, cen, 1);
+            float rt = __shfl_down_sync(HDI_FULL, cen, 1);
+            if (lane == 0 && px > 0) lf = prolong_value<MODE>(xc, bc, ec, F, C, fm.known(px - 1, y), px - 1, y);
+            if (lane == 31 && px + 1 < F.W)
+                rt = prolong_value<MODE>(xc, bc, ec, F, C, fm.known(px + 1, y), px + 1, y);
+            if (act) {
+                xout[ch * F.cs + (size_t)y * F.pitch + px] = cen;
+                if (!((wc >> lane) & 1u)) {
+                    float lap = 0.f;
+                    if (px > 0) lap += cen - lf;
+                    if (px + 1 < F.W) lap += cen - rt;
+                    if (y > 0) lap += cen - up;
+                    if (y + 1 < F.H) lap += cen - dn;
+                    const float r = bc[(size_t)y * F.pitch + px] - lap;
+                    sq += r * r;
+                }
+            }
+            up = cen;
+            cen = dn;
+            wc = wn;
         }
     }
     const double tot = (double)block_sum_f(sq);
@@ -289,82 +337,102 @@ struct ResArgs {
     int want_b;
 };
 
+// Column-strip layout of the streaming kernels: a CTA of four warps covers
+// 128 columns x CS_ROWS rows; lane l of warp w owns one column and walks
+// down the rows with a three-row register window, takes its left and right
+// neighbours by warp shuffles (lanes 0 and 31 read the neighbouring strip
+// from L1/L2), and reads the mask as one broadcast word per row.
+
+// Iterate value at (x, y) after the INIT transform (and the Dirichlet value on
+// known pixels), as a double-float pair.
 template <int RHS, int INIT>
-__global__ void __launch_bounds__(PT_W * PT_H) k_residual_df(ResArgs a) {
-    __shared__ float th[PT_H + 2][PT_W + 2];
-    __shared__ float tl[PT_H + 2][PT_W + 2];
+__device__ __forceinline__ void res_value(const ResArgs& a, long long co, int x, int y, bool known, float& h,
+                                          float& l) {
+    const size_t idx = co + (size_t)y * a.F.pitch + x;
+    if (known) {
+        if (RHS == RHS_DATA) { h = a.d.hi[idx]; l = a.d.lo[idx]; }
+        else { h = 0.f; l = 0.f; }
+    } else if (INIT == INIT_KEEP) {
+        h = a.uin.hi[idx]; l = a.uin.lo[idx];
+    } else if (INIT == INIT_UPDATE) {
+        df_add(a.uin.hi[idx], a.uin.lo[idx], a.x32[idx], 0.f, h, l);
+    } else if (INIT == INIT_FROM32) {
+        h = a.x32[idx]; l = 0.f;
+    } else {
+        h = 0.f; l = 0.f;
+    }
+}
+
+template <int RHS, int INIT>
+__global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
+    const int x = x0 + lane;
+    const int y0 = blockIdx.y * CS_ROWS;
+    const int y1 = min(y0 + CS_ROWS, a.F.H);
     const int ch = blockIdx.z;
-    const int bx0 = blockIdx.x * PT_W;
     const long long co = ch * a.F.cs;
+    const bool act = x < a.F.W;
+    const int xc = act ? x : a.F.W - 1;
+    const bool strip = x0 < a.F.W;
     float rr = 0.f, bb2 = 0.f;
-    for (int band = 0; band < TILE_ROWS; ++band) {
-    const int by0 = (blockIdx.y * TILE_ROWS + band) * PT_H;
-    if (by0 >= a.F.H) break;
-    __syncthreads();
-    for (int i = threadIdx.y * PT_W + threadIdx.x; i < (PT_W + 2) * (PT_H + 2); i += PT_W * PT_H) {
-        const int ty = i / (PT_W + 2), tx = i - ty * (PT_W + 2);
-        const int px = min(max(bx0 + tx - 1, 0), a.F.W - 1);
-        const int py = min(max(by0 + ty - 1, 0), a.F.H - 1);
-        const size_t idx = co + (size_t)py * a.F.pitch + px;
-        float h, l;
-        if (a.m.known(px, py)) {
-            if (RHS == RHS_DATA) { h = a.d.hi[idx]; l = a.d.lo[idx]; }
-            else { h = 0.f; l = 0.f; }
-        } else if (INIT == INIT_KEEP) {
-            h = a.uin.hi[idx]; l = a.uin.lo[idx];
-        } else if (INIT == INIT_UPDATE) {
-            df_add(a.uin.hi[idx], a.uin.lo[idx], a.x32[idx], 0.f, h, l);
-        } else if (INIT == INIT_FROM32) {
-            h = a.x32[idx]; l = 0.f;
-        } else {
-            h = 0.f; l = 0.f;
-        }
-        th[ty][tx] = h;
-        tl[ty][tx] = l;
-    }
-    __syncthreads();
-    const int px = bx0 + threadIdx.x, py = by0 + threadIdx.y;
-    if (px < a.F.W && py < a.F.H) {
-        const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
-        const size_t idx = co + (size_t)py * a.F.pitch + px;
-        const float ch_ = th[ty][tx], cl = tl[ty][tx];
-        a.uout.hi[idx] = ch_;
-        a.uout.lo[idx] = cl;
-        float r = 0.f;
-        if (a.m.known(px, py)) {
-            if (RHS == RHS_DATA) { const float bh = a.d.hi[idx] + a.d.lo[idx]; bb2 += bh * bh; }
-        } else {
-            // lap = sum over in-image neighbours of (u_c - u_n), error-free:
-            // the hi differences are summed with TwoSum, every rounding error
-            // and the lo differences go to the low-order accumulator.
-            float sh = 0.f, sl = 0.f;
-            const int nx[4] = {tx - 1, tx + 1, tx, tx};
-            const int ny[4] = {ty, ty, ty - 1, ty + 1};
-            const bool ok[4] = {px > 0, px + 1 < a.F.W, py > 0, py + 1 < a.F.H};
+    if (strip) {
+        const uint32_t* mrow = a.m.bits + (x0 >> 5);
+        float uh = 0.f, ul = 0.f, ch_ = 0.f, cl = 0.f, dh = 0.f, dl = 0.f;
+        if (y0 > 0) res_value<RHS, INIT>(a, co, xc, y0 - 1, a.m.known(xc, y0 - 1), uh, ul);
+        uint32_t wc = mrow[(size_t)y0 * a.m.wpitch];
+        res_value<RHS, INIT>(a, co, xc, y0, (wc >> lane) & 1u, ch_, cl);
+        for (int y = y0; y < y1; ++y) {
+            uint32_t wn = 0;
+            if (y + 1 < a.F.H) {
+                wn = mrow[(size_t)(y + 1) * a.m.wpitch];
+                res_value<RHS, INIT>(a, co, xc, y + 1, (wn >> lane) & 1u, dh, dl);
+            }
+            float lh = __shfl_up_sync(HDI_FULL, ch_, 1), ll = __shfl_up_sync(HDI_FULL, cl, 1);
+            float rh = __shfl_down_sync(HDI_FULL, ch_, 1), rl = __shfl_down_sync(HDI_FULL, cl, 1);
+            if (lane == 0 && x > 0) res_value<RHS, INIT>(a, co, x - 1, y, a.m.known(x - 1, y), lh, ll);
+            if (lane == 31 && x + 1 < a.F.W) res_value<RHS, INIT>(a, co, x + 1, y, a.m.known(x + 1, y), rh, rl);
+            const bool known = (wc >> lane) & 1u;
+            if (act) {
+                const size_t idx = co + (size_t)y * a.F.pitch + x;
+                a.uout.hi[idx] = ch_;
+                a.uout.lo[idx] = cl;
+                float r = 0.f;
+                if (known) {
+                    if (RHS == RHS_DATA) { const float bh = ch_ + cl; bb2 += bh * bh; }
+                } else {
+                    float sh = 0.f, sl = 0.f;
+                    const float nh[4] = {lh, rh, uh, dh};
+                    const float nl[4] = {ll, rl, ul, dl};
+                    const bool ok[4] = {x > 0, x + 1 < a.F.W, y > 0, y + 1 < a.F.H};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (ok[k]) {
-                    float dh, dl, s2, e2;
-                    two_sum(ch_, -th[ny[k]][nx[k]], dh, dl);
-                    dl += cl - tl[ny[k]][nx[k]];
-                    two_sum(sh, dh, s2, e2);
-                    sh = s2;
-                    sl += e2 + dl;
+                    for (int k = 0; k < 4; ++k) {
+                        if (ok[k]) {
+                            float e1, e2, s2, t2;
+                            two_sum(ch_, -nh[k], e1, e2);
+                            e2 += cl - nl[k];
+                            two_sum(sh, e1, s2, t2);
+                            sh = s2;
+                            sl += t2 + e2;
+                        }
+                    }
+                    float bh = 0.f, bl = 0.f;
+                    if (RHS == RHS_SOURCE) {
+                        const float yh = a.y.hi ? a.y.hi[idx] : 0.f, yl = a.y.hi ? a.y.lo[idx] : 0.f;
+                        df_add(a.d.hi[idx], a.d.lo[idx], -yh, -yl, bh, bl);
+                        bb2 += bh * bh;
+                    }
+                    float rh2, rl2;
+                    df_add(bh, bl, -sh, -sl, rh2, rl2);
+                    r = rh2 + rl2;
                 }
+                a.r32[idx] = r;
+                rr += r * r;
             }
-            float bh = 0.f, bl = 0.f;
-            if (RHS == RHS_SOURCE) {
-                const float yh = a.y.hi ? a.y.hi[idx] : 0.f, yl = a.y.hi ? a.y.lo[idx] : 0.f;
-                df_add(a.d.hi[idx], a.d.lo[idx], -yh, -yl, bh, bl);
-                bb2 += bh * bh;
-            }
-            float rh, rl;
-            df_add(bh, bl, -sh, -sl, rh, rl);
-            r = rh + rl;
+            uh = ch_; ul = cl;
+            ch_ = dh; cl = dl;
+            wc = wn;
         }
-        a.r32[idx] = r;
-        rr += r * r;
-    }
     }
     const double tot = (double)block_sum_f(rr);
     grid_reduce_commit(a.red_r, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);

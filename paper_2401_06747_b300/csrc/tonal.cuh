@@ -600,6 +600,13 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     cudaMemsetAsync(counters + kCntLocal, 0, 16, stream);
     if ((rc = tonal_setup())) return rc;
 
+    // the inner solves use their own local stop fraction (restored on exit)
+    struct EtaSwap {
+        Params& p;
+        double keep;
+        EtaSwap(Params& pp) : p(pp), keep(pp.oras_eta) { p.oras_eta = p.tonal_oras_eta; }
+        ~EtaSwap() { p.oras_eta = keep; }
+    } eta_swap(p);
     const double ratio = p.tonal_inner_ratio;
     // ||B^T f||: w_f solves A w = (I - C) f.
     SolveSpec sw;
