@@ -243,12 +243,11 @@ def run_hdi(args, rank, world):
     achieved = bytes_per_launch / avg_s / 1e9 if n else 0.0
     share = ms / max(t_max, 1e-9)
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    tpath = os.path.join(ROOT, "profiles", f"{name}_4k_rgb.md")
     if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get(name)
-        except Exception:
-            traffic = None
+        for line in open(tpath):
+            if line.startswith("traffic_bytes_per_launch:"):
+                traffic = int(line.split(":")[1])
     roofline = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
