@@ -102,6 +102,19 @@ int hdi_get_param(const hdi_ctx* ctx, const char* name, double* value);
 int hdi_inpaint(hdi_ctx* ctx, const hdi_image* f, const hdi_mask* mask,
                 const hdi_image* u0, hdi_image* u, double tol, hdi_stats* st);
 
+/* Batched inpainting of n independent images of uneven sizes (1..4
+ * channels each, each with its own mask), e.g. a request batch. Images with
+ * the same height and width form one size class and are solved as ONE
+ * system whose channels are all their channels: every solver phase (ORAS
+ * sweep, transfer, residual) is a single kernel launch over all subdomains
+ * and pixels of the class, and the refinement loop runs until every channel
+ * of the class meets tol. Size classes are processed one after another.
+ *   f[n], masks[n], u[n] : as for hdi_inpaint (arrays of descriptors)
+ *   st[n]                : per-image statistics (may be NULL)
+ * Returns HDI_ERR_NOT_CONVERGED if any image missed tol (others are valid). */
+int hdi_inpaint_batch(hdi_ctx* ctx, int n, const hdi_image* f, const hdi_mask* masks, hdi_image* u,
+                      double tol, hdi_stats* st);
+
 /* Tonal optimisation (Sec. 5, Eq. "tonal-opt-minimisation"): g minimising
  * ||f - A^{-1} C g||_2 with g = 0 off the mask, by restricted additive
  * Schwarz on the normal equations B^T B g = B^T f (Sec. 5.2, Alg. 2); each

@@ -54,7 +54,7 @@ class Stats(ctypes.Structure):
 
 SYMBOLS = ["hdi_create", "hdi_destroy", "hdi_set_param", "hdi_get_param", "hdi_inpaint",
            "hdi_tonal_opt", "hdi_densify_step", "hdi_last_error", "hdi_version", "hdi_launch_count",
-           "hdi_timing", "hdi_timing_name", "hdi_inpaint_noalloc"]
+           "hdi_timing", "hdi_timing_name", "hdi_inpaint_noalloc", "hdi_inpaint_batch"]
 TIMING_CLASSES = 8
 
 _lib = None
@@ -85,6 +85,8 @@ def load(path: str | None = None):
     lib.hdi_launch_count.restype = ctypes.c_int64
     lib.hdi_timing.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int64)]
     lib.hdi_timing_name.restype = ctypes.c_char_p
+    lib.hdi_inpaint_batch.argtypes = [ctypes.c_void_p, ctypes.c_int, P(Image), P(Mask), P(Image), ctypes.c_double,
+                                      P(Stats)]
     lib.hdi_inpaint_noalloc.argtypes = [ctypes.c_int, ctypes.c_void_p, P(Image), P(Mask), P(Image),
                                         ctypes.c_double, P(Stats)]
     _lib = lib
@@ -178,6 +180,18 @@ class Context:
                                   float(tol), ctypes.byref(st))
         self._check(rc, allow_not_converged)
         return st.as_dict()
+
+    def inpaint_batch(self, fs, masks, outs, tol: float = 1e-6, allow_not_converged=False) -> list:
+        """Batched inpainting of independent images (lists of tensors/arrays);
+        images of equal size are solved together, one launch per phase."""
+        n = len(fs)
+        FI = (Image * n)(*[image_of(x) for x in fs])
+        MI = (Mask * n)(*[mask_of(x) for x in masks])
+        OI = (Image * n)(*[image_of(x) for x in outs])
+        ST = (Stats * n)()
+        rc = self.lib.hdi_inpaint_batch(self.h, n, FI, MI, OI, float(tol), ST)
+        self._check(rc, allow_not_converged)
+        return [s.as_dict() for s in ST]
 
     def tonal_opt(self, f, mask, out, g0=None, tol: float = 1e-6, allow_not_converged=False) -> dict:
         """Optimised tonal values g (zero off the mask) into `out`."""

@@ -11,6 +11,16 @@
 struct MaskView {
     const uint32_t* bits;
     int H, W, wpitch;
+    // Batched solves give every channel its own mask plane: channel c uses
+    // plane chmask[c], `cstride` words apart. chmask == nullptr: one mask
+    // shared by all channels (Sec. 2.1).
+    const int* chmask;
+    long long cstride;
+    __device__ __forceinline__ MaskView ch(int c) const {
+        MaskView r = *this;
+        if (chmask) r.bits += (size_t)chmask[c] * cstride;
+        return r;
+    }
     __device__ __forceinline__ bool known(int x, int y) const {
         return (bits[(size_t)y * wpitch + (x >> 5)] >> (x & 31)) & 1u;
     }

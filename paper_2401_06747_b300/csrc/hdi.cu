@@ -137,8 +137,9 @@ int Ctx::tflush() {
 static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 // Plans the level sizes, reserves the workspace and carves the buffers.
-int Ctx::setup(int H_, int W_, int nch_) {
-    if (H_ == H && W_ == W && nch_ == nch && ws.base) return HDI_OK;
+int Ctx::setup(int H_, int W_, int nch_, int nmask_) {
+    if (H_ == H && W_ == W && nch_ == nch && nmask_ == nmask && ws.base) return HDI_OK;
+    if (nch_ > kMaxCh || nmask_ > kMaxCh || nmask_ < 1) return fail(HDI_ERR_INVALID_ARG, "too many channels in one solve");
     std::vector<std::pair<int, int>> sizes;
     int h = H_, w = W_;
     sizes.push_back({h, w});
@@ -155,7 +156,7 @@ int Ctx::setup(int H_, int W_, int nch_) {
     for (int l = 0; l < nl; ++l) {
         const int P = round_up(sizes[l].second, 32);
         const int wp = (sizes[l].second + 31) / 32 + 1;
-        acc((size_t)sizes[l].first * wp * 4);            // bits
+        acc((size_t)nmask_ * sizes[l].first * wp * 4);   // bits, one plane per mask
         for (int k = 0; k < 3; ++k) acc((size_t)nch_ * sizes[l].first * P * 4);   // xa, xb, b
         const int parts = ((sizes[l].second + 31) / 32) * ((sizes[l].first + 7) / 8);
         maxparts = std::max(maxparts, parts);
@@ -166,12 +167,12 @@ int Ctx::setup(int H_, int W_, int nch_) {
     acc(n32 * 4);                                             // tonal residual
     acc(n32 * 4);                                             // third component of f
     acc((size_t)kSlots * maxparts * nch_ * 8);                // reduction partials
-    acc((size_t)kSlots * 4 * 8);                              // reduction outputs
+    acc((size_t)kSlots * kMaxCh * 8);                         // reduction outputs
     acc((size_t)kSlots * 4);                                  // tickets
     acc(64 * 8);                                              // counters / flags
     int rc = ws.reserve(*this, bytes, "inpainting workspace");
     if (rc) { H = W = nch = 0; return rc; }
-    H = H_; W = W_; nch = nch_; nlev = nl;
+    H = H_; W = W_; nch = nch_; nlev = nl; nmask = nmask_;
     for (int l = 0; l < nl; ++l) {
         Level& L = lev[l];
         L.H = sizes[l].first;
@@ -179,7 +180,7 @@ int Ctx::setup(int H_, int W_, int nch_) {
         L.P = round_up(L.W, 32);
         L.wp = (L.W + 31) / 32 + 1;
         L.cs = (long long)L.H * L.P;
-        L.bits = (uint32_t*)ws.take((size_t)L.H * L.wp * 4);
+        L.bits = (uint32_t*)ws.take((size_t)nmask * L.H * L.wp * 4);
         L.xa = (float*)ws.take((size_t)nch * L.cs * 4);
         L.xb = (float*)ws.take((size_t)nch * L.cs * 4);
         L.b = (float*)ws.take((size_t)nch * L.cs * 4);
@@ -194,7 +195,7 @@ int Ctx::setup(int H_, int W_, int nch_) {
     flo2 = (float*)ws.take(n32 * 4);
     maxparts_ = maxparts;
     partials = (double*)ws.take((size_t)kSlots * maxparts * nch * 8);
-    scal = (double*)ws.take((size_t)kSlots * 4 * 8);
+    scal = (double*)ws.take((size_t)kSlots * kMaxCh * 8);
     tickets = (unsigned*)ws.take((size_t)kSlots * 4);
     counters = (unsigned long long*)ws.take(64 * 8);
     if (ws.used > ws.cap) {
@@ -203,9 +204,9 @@ int Ctx::setup(int H_, int W_, int nch_) {
     }
     cudaMemsetAsync(tickets, 0, (size_t)kSlots * 4, stream);
     cudaMemsetAsync(counters, 0, 64 * 8, stream);
-    cudaMemsetAsync(scal, 0, (size_t)kSlots * 4 * 8, stream);
+    cudaMemsetAsync(scal, 0, (size_t)kSlots * kMaxCh * 8, stream);
     // zero-fill mask padding words once per setup
-    for (int l = 0; l < nl; ++l) cudaMemsetAsync(lev[l].bits, 0, (size_t)lev[l].H * lev[l].wp * 4, stream);
+    for (int l = 0; l < nl; ++l) cudaMemsetAsync(lev[l].bits, 0, (size_t)nmask * lev[l].H * lev[l].wp * 4, stream);
     mask_key_valid = false;
     return cuda_check(cudaGetLastError(), "workspace setup");
 }
@@ -213,7 +214,7 @@ int Ctx::setup(int H_, int W_, int nch_) {
 GridReduce Ctx::reducer(int slot, int nparts) const {
     GridReduce r;
     r.partials = partials + (size_t)slot * maxparts_ * nch;
-    r.out = scal + slot * 4;
+    r.out = scal + slot * kMaxCh;
     r.ticket = tickets + slot;
     r.nparts = nparts;
     r.nch = nch;
@@ -235,6 +236,8 @@ MaskView Ctx::mview(int l) const {
     m.H = lev[l].H;
     m.W = lev[l].W;
     m.wpitch = lev[l].wp;
+    m.chmask = nmask > 1 ? d_chmask : nullptr;
+    m.cstride = (long long)lev[l].H * lev[l].wp;
     return m;
 }
 
@@ -242,7 +245,7 @@ MaskView Ctx::mview(int l) const {
 void Ctx::build_mask_pyramid() {
     for (int l = 0; l + 1 < nlev; ++l) {
         const Level& C = lev[l + 1];
-        dim3 blk(64), grd((C.wp + 63) / 64, C.H);
+        dim3 blk(64), grd((C.wp + 63) / 64, C.H, nmask);
         k_restrict_mask<<<grd, blk, 0, stream>>>(mview(l), C.bits, C.H, C.W, C.wp);
         ++launches;
     }
@@ -290,7 +293,7 @@ static dim3 tiles_of(const Level& L, int nch) {
 // Result in lev[l].xa.
 void Ctx::vcycle(int l) {
     Level& L = lev[l];
-    const double* pre_norm = (l == 0) ? scal + kSlotR64 * 4 : scal + l * 4;
+    const double* pre_norm = (l == 0) ? scal + kSlotR64 * kMaxCh : scal + l * kMaxCh;
     unsigned long long* it = (l == 0) ? counters + kCntLocal : nullptr;
     if (l == nlev - 1) {
         oras(l, true, nullptr, L.xa, pre_norm, true, it);
@@ -316,7 +319,7 @@ void Ctx::vcycle(int l) {
         ++launches;
         if (l == 0) tstop();
     }
-    oras(l, false, L.xb, L.xa, scal + l * 4, false, it);
+    oras(l, false, L.xb, L.xa, scal + l * kMaxCh, false, it);
     if (l == 0) ++vcycles_run;
 }
 
@@ -340,14 +343,14 @@ void Ctx::fmg(DFc d) {
         k_prolong<2><<<grd, blk, 0, stream>>>(arr(L), mview(L), nullptr, lev[L].b, lev[L].xb, arr(L), nullptr,
                                               reducer(L, grd.x * grd.y));
         ++launches;
-        oras(L, false, lev[L].xb, lev[L].xa, scal + L * 4, true, nullptr);
+        oras(L, false, lev[L].xb, lev[L].xa, scal + L * kMaxCh, true, nullptr);
     }
     for (int l = L - 1; l >= 0; --l) {
         dim3 grd = tiles_of(lev[l], nch), blk(128);
         k_prolong<1><<<grd, blk, 0, stream>>>(arr(l), mview(l), nullptr, lev[l].b, lev[l].xb, arr(l + 1),
                                               lev[l + 1].xa, reducer(l, grd.x * grd.y));
         ++launches;
-        oras(l, false, lev[l].xb, lev[l].xa, scal + l * 4, l == L, l == 0 ? counters + kCntLocal : nullptr);
+        oras(l, false, lev[l].xb, lev[l].xa, scal + l * kMaxCh, l == L, l == 0 ? counters + kCntLocal : nullptr);
     }
 }
 
@@ -402,16 +405,16 @@ int Ctx::solve(SolveSpec& s) {
     } else {
         residual(s.rhs, INIT_ZERO, none, ub[cur], nullptr, s.d, s.y, true);
     }
-    double r2[4], b2[4];
+    double r2[kMaxCh], b2[kMaxCh];
     s.iterations = 0;
     for (;;) {
-        cudaMemcpyAsync(hscal, scal + kSlotR64 * 4, 4 * 8, cudaMemcpyDeviceToHost, stream);
-        cudaMemcpyAsync(hscal + 4, scal + kSlotB64 * 4, 4 * 8, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(hscal, scal + kSlotR64 * kMaxCh, (size_t)nch * 8, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(hscal + kMaxCh, scal + kSlotB64 * kMaxCh, (size_t)nch * 8, cudaMemcpyDeviceToHost, stream);
         if ((rc = sync("inpainting residual"))) return rc;
         double worst = 0.0;
         for (int c = 0; c < nch; ++c) {
             r2[c] = hscal[c];
-            b2[c] = hscal[4 + c];
+            b2[c] = hscal[kMaxCh + c];
             if (!std::isfinite(r2[c])) {
                 s.cur = cur;
                 return fail(HDI_ERR_NONFINITE, "non-finite residual in channel %d", c);
@@ -456,7 +459,14 @@ int Ctx::check_image(const hdi_image* im, const char* name, int H_, int W_, int 
 }
 
 // Copies a caller image into the internal FP64 layout (device or host source).
-int Ctx::load_image(const hdi_image* im, DF dst, float* lo2) {
+int Ctx::load_image(const hdi_image* im, DF dst, float* lo2, int c0) {
+    const int nc = im->channels;
+    if (c0) {
+        const long long off = (long long)c0 * lev[0].cs;
+        dst.hi += off;
+        dst.lo += off;
+        if (lo2) lo2 += off;
+    }
     const void* src = im->data;
     long long rs = im->row_stride, cs = im->channel_stride;
     const size_t es = im->dtype == HDI_F64 ? 8 : 4;
@@ -465,7 +475,7 @@ int Ctx::load_image(const hdi_image* im, DF dst, float* lo2) {
         int rc = stage.reserve(*this, std::max(stage.cap, n + (size_t)H * W + 1024), "staging buffer");
         if (rc) return rc;
         char* st = (char*)stage.base;
-        for (int c = 0; c < nch; ++c) {
+        for (int c = 0; c < nc; ++c) {
             cudaError_t e = cudaMemcpy2DAsync(st + (size_t)c * H * W * es, W * es,
                                               (const char*)src + (size_t)c * cs * es, rs * es, W * es, H,
                                               cudaMemcpyHostToDevice, stream);
@@ -476,7 +486,7 @@ int Ctx::load_image(const hdi_image* im, DF dst, float* lo2) {
         cs = (long long)H * W;
     }
     cudaMemsetAsync(flags, 0, 4, stream);
-    dim3 grd((W + 127) / 128, H, nch);
+    dim3 grd((W + 127) / 128, H, nc);
     if (im->dtype == HDI_F64)
         k_load_image<double><<<grd, 128, 0, stream>>>((const double*)src, rs, cs, arr(0), dst, lo2, flags);
     else
@@ -490,7 +500,14 @@ int Ctx::load_image(const hdi_image* im, DF dst, float* lo2) {
     return HDI_OK;
 }
 
-int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2) {
+int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2, int c0) {
+    const int nc = im->channels;
+    if (c0) {
+        const long long off = (long long)c0 * lev[0].cs;
+        src.hi += off;
+        src.lo += off;
+        if (known_lo2) known_lo2 += off;
+    }
     void* dst = im->data;
     long long rs = im->row_stride, cs = im->channel_stride;
     const size_t es = im->dtype == HDI_F64 ? 8 : 4;
@@ -503,16 +520,16 @@ int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* kn
         rs = W;
         cs = (long long)H * W;
     }
-    dim3 grd((W + 127) / 128, H, nch);
+    dim3 grd((W + 127) / 128, H, nc);
     if (im->dtype == HDI_F64)
         k_store_image<double><<<grd, 128, 0, stream>>>(src, arr(0), mview(0), zero_off_mask, known_lo2, (double*)dst,
-                                                       rs, cs);
+                                                       rs, cs, c0);
     else
         k_store_image<float><<<grd, 128, 0, stream>>>(src, arr(0), mview(0), zero_off_mask, known_lo2, (float*)dst,
-                                                      rs, cs);
+                                                      rs, cs, c0);
     ++launches;
     if (host) {
-        for (int c = 0; c < nch; ++c) {
+        for (int c = 0; c < nc; ++c) {
             cudaError_t e = cudaMemcpy2DAsync((char*)im->data + (size_t)c * im->channel_stride * es,
                                               im->row_stride * es, (const char*)dst + (size_t)c * H * W * es, W * es,
                                               W * es, H, cudaMemcpyDeviceToHost, stream);
@@ -524,7 +541,7 @@ int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* kn
 
 // Uploads and bit-packs the mask, builds the mask pyramid; returns the number
 // of known pixels in *ones.
-int Ctx::load_mask(const hdi_mask* m, long long* ones) {
+int Ctx::load_mask(const hdi_mask* m, long long* ones, int plane, bool pyramid) {
     if (!m || !m->data) return fail(HDI_ERR_INVALID_ARG, "mask: null");
     if (m->height != H || m->width != W) return fail(HDI_ERR_INVALID_ARG, "mask: shape does not match the image");
     if (m->row_stride < m->width) return fail(HDI_ERR_INVALID_ARG, "mask: row stride too small");
@@ -545,9 +562,10 @@ int Ctx::load_mask(const hdi_mask* m, long long* ones) {
     cudaMemsetAsync(flags, 0, 4, stream);
     const Level& L = lev[0];
     dim3 grd((L.wp + 63) / 64, H);
-    k_pack_mask<<<grd, 64, 0, stream>>>(src, rs, H, W, L.bits, L.wp, counters + kCntOnes, flags);
+    k_pack_mask<<<grd, 64, 0, stream>>>(src, rs, H, W, L.bits + (size_t)plane * L.H * L.wp, L.wp, counters + kCntOnes,
+                                        flags);
     ++launches;
-    build_mask_pyramid();
+    if (pyramid) build_mask_pyramid();
     unsigned long long cnt = 0;
     unsigned bad = 0;
     cudaMemcpyAsync(&cnt, counters + kCntOnes, 8, cudaMemcpyDeviceToHost, stream);
@@ -576,15 +594,16 @@ int hdi_create(hdi_ctx** out, int device, void* stream) {
     Ctx* c = new Ctx();
     c->device = device;
     c->stream = (cudaStream_t)stream;
-    if (cudaMallocHost(&c->hscal, 64 * 8) != cudaSuccess) {
+    if (cudaMallocHost(&c->hscal, 2 * kMaxCh * 8) != cudaSuccess) {
         delete c;
         return HDI_ERR_CUDA;
     }
-    if (cudaMalloc(&c->flags, 256) != cudaSuccess) {
+    if (cudaMalloc(&c->flags, 256 + kMaxCh * 4) != cudaSuccess) {
         cudaFreeHost(c->hscal);
         delete c;
         return HDI_ERR_CUDA;
     }
+    c->d_chmask = (int*)((char*)c->flags + 256);
     *out = reinterpret_cast<hdi_ctx*>(c);
     return HDI_OK;
 }
@@ -709,6 +728,104 @@ int hdi_densify_step(hdi_ctx* h, const hdi_image* f, hdi_mask* mask, const hdi_i
 
 }  // extern "C"
 
+// ------------------------------------------------------------ batch ---
+
+// Images of one size class are stacked as the channels of one system (each
+// channel reads its own image's mask plane), so every phase of the solver is
+// one launch over all their subdomains and pixels. Size classes run in turn.
+int Ctx::inpaint_batch(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, hdi_stats* st) {
+    int rc;
+    if ((rc = cuda_check(cudaSetDevice(device), "cudaSetDevice"))) return rc;
+    if (n < 0 || (n > 0 && (!f || !m || !u))) return fail(HDI_ERR_INVALID_ARG, "batch: null arrays");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(HDI_ERR_INVALID_ARG, "tol must lie in (0, 1)");
+    for (int i = 0; i < n; ++i) {
+        if ((rc = check_image(&f[i], "f[i]", -1, 0, 0))) return rc;
+        if ((rc = check_image(&u[i], "u[i]", f[i].height, f[i].width, f[i].channels))) return rc;
+        if (u[i].dtype != f[i].dtype) return fail(HDI_ERR_INVALID_ARG, "u[%d]: dtype differs from f", i);
+        if (m[i].height != f[i].height || m[i].width != f[i].width)
+            return fail(HDI_ERR_INVALID_ARG, "mask[%d]: shape does not match", i);
+    }
+    // group by size, keeping input order inside a class; split classes above kMaxCh channels
+    std::vector<std::vector<int>> groups;
+    std::vector<int> done(n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (done[i]) continue;
+        std::vector<int> g;
+        int chs = 0;
+        for (int j = i; j < n; ++j) {
+            if (done[j] || f[j].height != f[i].height || f[j].width != f[i].width) continue;
+            if (chs + f[j].channels > kMaxCh) break;
+            g.push_back(j);
+            chs += f[j].channels;
+            done[j] = 1;
+        }
+        groups.push_back(g);
+    }
+    int worst = HDI_OK;
+    for (const auto& g : groups) {
+        int C = 0;
+        std::vector<int> chmask, c0s;
+        for (size_t j = 0; j < g.size(); ++j) {
+            c0s.push_back(C);
+            for (int c = 0; c < f[g[j]].channels; ++c) chmask.push_back((int)j);
+            C += f[g[j]].channels;
+        }
+        if ((rc = setup(f[g[0]].height, f[g[0]].width, C, (int)g.size()))) return rc;
+        cudaMemcpyAsync(d_chmask, chmask.data(), chmask.size() * 4, cudaMemcpyHostToDevice, stream);
+        for (size_t j = 0; j < g.size(); ++j) {
+            long long ones = 0;
+            if ((rc = load_mask(&m[g[j]], &ones, (int)j, j + 1 == g.size()))) return rc;
+            if (ones == 0) return fail(HDI_ERR_EMPTY_MASK, "batch image %d: empty mask", g[j]);
+            if ((rc = load_image(&f[g[j]], dfv[kF], flo2, c0s[j]))) return rc;
+        }
+        SolveSpec s;
+        s.u[0] = dfv[kU0];
+        s.u[1] = dfv[kU1];
+        s.cur = 0;
+        s.rhs = RHS_DATA;
+        s.d = cview(dfv[kF]);
+        s.tol = tol;
+        s.max_iter = (int)p.max_vcycles;
+        s.start = START_FMG;
+        vcycles_run = 0;
+        const int src = solve(s);
+        if (src != HDI_OK && src != HDI_ERR_NOT_CONVERGED) return src;
+        if (src == HDI_ERR_NOT_CONVERGED) worst = src;
+        for (size_t j = 0; j < g.size(); ++j) {
+            if ((rc = store_image(cview(s.u[s.cur]), &u[g[j]], false, flo2, c0s[j]))) return rc;
+            if (st) {
+                double rel = 0.0;
+                for (int c = 0; c < f[g[j]].channels; ++c) rel = std::max(rel, s.rel[c0s[j] + c]);
+                hdi_stats& o = st[g[j]];
+                o.status = rel <= tol ? HDI_OK : HDI_ERR_NOT_CONVERGED;
+                o.iterations = s.iterations;
+                o.vcycles = vcycles_run;
+                o.local_iters = 0;
+                o.rel_res = rel;
+                o.mse = 0.0;
+                o.seconds = 0.0;
+            }
+        }
+    }
+    if ((rc = tflush())) return rc;
+    if (worst != HDI_OK) return fail(worst, "batch: some images did not reach the tolerance");
+    return HDI_OK;
+}
+
+extern "C" int hdi_inpaint_batch(hdi_ctx* h, int n, const hdi_image* f, const hdi_mask* masks, hdi_image* u, double tol,
+                                 hdi_stats* st) {
+    if (!h) return HDI_ERR_INVALID_ARG;
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    auto t0 = std::chrono::steady_clock::now();
+    c->err.clear();
+    const int rc = c->inpaint_batch(n, f, masks, u, tol, st);
+    if (st) {
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int i = 0; i < n; ++i) st[i].seconds = secs;
+    }
+    return rc;
+}
+
 // ------------------------------------------------------------ inpaint ---
 
 int Ctx::inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,
@@ -773,7 +890,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 namespace {
 constexpr int kNoAllocMaxDevices = 64;
 void* g_noalloc_ptr[kNoAllocMaxDevices] = {};   // device address of the scratch, per device
-double g_noalloc_hscal[64];                     // host mirror of the reduction outputs
+double g_noalloc_hscal[2 * kMaxCh];             // host mirror of the reduction outputs
 
 // Carves the inpainting workspace of an H x W x nch image out of `base`
 // (the same layout rules as Ctx::setup, restricted to the buffers the
@@ -839,7 +956,7 @@ size_t noalloc_layout(Ctx& c, char* base, size_t cap, int H_, int W_, int nch_) 
         }
         char* lo2 = take(n32 * 4);
         char* parts = take((size_t)kSlots * maxparts * nch_ * 8);
-        char* scal = take((size_t)kSlots * 4 * 8);
+        char* scal = take((size_t)kSlots * kMaxCh * 8);
         char* tick = take((size_t)kSlots * 4);
         char* cnt = take(64 * 8);
         char* flg = take(256);
@@ -900,7 +1017,7 @@ extern "C" int hdi_inpaint_noalloc(int device, void* cuda_stream, const hdi_imag
     // The scratch keeps the previous call's contents: clear what must start at zero.
     cudaMemsetAsync(c.tickets, 0, (size_t)kSlots * 4, c.stream);
     cudaMemsetAsync(c.counters, 0, 64 * 8, c.stream);
-    cudaMemsetAsync(c.scal, 0, (size_t)kSlots * 4 * 8, c.stream);
+    cudaMemsetAsync(c.scal, 0, (size_t)kSlots * kMaxCh * 8, c.stream);
     long long ones = 0;
     if ((rc = c.load_mask(mask, &ones))) return rc;
     if (ones == 0) return HDI_ERR_EMPTY_MASK;

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(128) k_oras(OrasArgs a) {
     const int by = bi / a.nbx;
     const int bx = bi - by * a.nbx;
     const int x0 = bx * a.stride, y0 = by * a.stride;
-    const LocalGeom g = make_geom(x0, y0, a.H, a.W, a.m, a.theta);
+    const LocalGeom g = make_geom(x0, y0, a.H, a.W, a.m.ch(ch), a.theta);
     const int gx = x0 + lane;
     const bool act = lane < g.w;
     const int gxc = act ? gx : (a.W - 1);   // clamped column for safe loads

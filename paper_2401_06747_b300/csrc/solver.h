@@ -47,6 +47,7 @@ struct Arena {
 };
 
 enum { START_FMG = 0, START_WARM = 1, START_ZERO = 2 };
+constexpr int kMaxCh = 256;       // channels of one solve (a batch stacks its images' channels)
 
 inline DFc cview(const DF& v) { return DFc{v.hi, v.lo}; }
 
@@ -60,9 +61,9 @@ struct SolveSpec {
     double tol = 1e-6;
     int max_iter = 60;
     int iterations = 0;
-    double rel[4] = {0, 0, 0, 0};
+    double rel[kMaxCh] = {};
     double rel_max = 0;
-    double bnorm2[4] = {0, 0, 0, 0};
+    double bnorm2[kMaxCh] = {};
 };
 
 constexpr int kMaxLevels = 16;
@@ -90,6 +91,8 @@ struct Ctx {
     Arena dws;     // densification
     Arena stage;   // host staging
     int H = 0, W = 0, nch = 0, nlev = 0;
+    int nmask = 1;             // mask planes (1 = shared by all channels)
+    int* d_chmask = nullptr;   // [kMaxCh] mask plane of each channel (batched solves)
     Level lev[kMaxLevels];
     DF dfv[kNumDF] = {};
     float* tres = nullptr;
@@ -138,7 +141,7 @@ struct Ctx {
     int cuda_check(cudaError_t e, const char* what);
     int sync(const char* what);
     size_t other_bytes() const;
-    int setup(int H, int W, int nch);
+    int setup(int H, int W, int nch, int nmask = 1);
     GridReduce reducer(int slot, int nparts) const;
     LevelArr arr(int l) const;
     MaskView mview(int l) const;
@@ -150,9 +153,10 @@ struct Ctx {
     void residual(int rhs, int init, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b);
     int solve(SolveSpec& s);
     int check_image(const hdi_image* im, const char* name, int H, int W, int nch);
-    int load_image(const hdi_image* im, DF dst, float* lo2 = nullptr);
-    int store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2 = nullptr);
-    int load_mask(const hdi_mask* m, long long* ones);
+    int load_image(const hdi_image* im, DF dst, float* lo2 = nullptr, int c0 = 0);
+    int store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2 = nullptr, int c0 = 0);
+    int load_mask(const hdi_mask* m, long long* ones, int plane = 0, bool pyramid = true);
+    int inpaint_batch(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, hdi_stats* st);
     int read_slot(int slot, double* out);
     int tonal_setup();
     void tonal_residual(DFc y, DFc w);

@@ -65,6 +65,8 @@ __global__ void k_restrict_mask(MaskView f, uint32_t* __restrict__ cbits, int cH
     const int wx = blockIdx.x * blockDim.x + threadIdx.x;
     const int Y = blockIdx.y;
     if (Y >= cH || wx >= cwp) return;
+    f.bits += (size_t)blockIdx.z * f.cstride;           // mask plane
+    cbits += (size_t)blockIdx.z * (size_t)cH * cwp;
     uint32_t out = 0;
     if (wx * 32 < cW) {
         const int fw = 2 * wx;   // fine words 2wx, 2wx+1 hold this word's children
@@ -96,6 +98,7 @@ __global__ void k_restrict_data(LevelArr F, MaskView fm, const float* __restrict
     const int Y = blockIdx.y * blockDim.y + threadIdx.y;
     const int ch = blockIdx.z;
     if (X >= C.W || Y >= C.H) return;
+    fm = fm.ch(ch);
     float s = 0.f;
     int n = 0;
     for (int dy = 0; dy < 2; ++dy)
@@ -139,6 +142,8 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
     const int y0 = blockIdx.y * CS_ROWS;
     const int y1 = min(y0 + CS_ROWS, F.H);
     const int ch = blockIdx.z;
+    fm = fm.ch(ch);
+    cm = cm.ch(ch);
     const bool act = px < F.W;
     const int pxc = act ? px : F.W - 1;
     const float* xc = x + ch * F.cs;
@@ -223,6 +228,7 @@ __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const 
     const int y0 = blockIdx.y * CS_ROWS;
     const int y1 = min(y0 + CS_ROWS, F.H);
     const int ch = blockIdx.z;
+    fm = fm.ch(ch);
     const bool act = px < F.W;
     const int pxc = act ? px : F.W - 1;
     const float* xc = (MODE == 0) ? xin + ch * F.cs : nullptr;
@@ -365,6 +371,7 @@ __device__ __forceinline__ void res_value(const ResArgs& a, long long co, int x,
 
 template <int RHS, int INIT>
 __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
+    a.m = a.m.ch(blockIdx.z);
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
     const int x = x0 + lane;
@@ -471,12 +478,13 @@ __global__ void k_load_image(const T* __restrict__ src, long long rs, long long 
 // known pixels, so inpainted FP64 output equals f there bit for bit.
 template <typename T>
 __global__ void k_store_image(DFc src, LevelArr F, MaskView m, int zero_off_mask, const float* __restrict__ known_lo2,
-                              T* __restrict__ dst, long long rs, long long cs) {
+                              T* __restrict__ dst, long long rs, long long cs, int c0) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     const int ch = blockIdx.z;
     if (x >= F.W) return;
     const size_t idx = ch * F.cs + (size_t)y * F.pitch + x;
+    m = m.ch(c0 + ch);
     T v;
     if (sizeof(T) == 8) {
         double dv = (double)src.hi[idx] + (double)src.lo[idx];
@@ -496,5 +504,5 @@ __global__ void k_data_to_f32(DFc d, LevelArr F, MaskView m, float* __restrict__
     const int ch = blockIdx.z;
     if (x >= F.W) return;
     const size_t idx = ch * F.cs + (size_t)y * F.pitch + x;
-    out[idx] = m.known(x, y) ? d.hi[idx] + d.lo[idx] : 0.f;
+    out[idx] = m.ch(ch).known(x, y) ? d.hi[idx] + d.lo[idx] : 0.f;
 }

@@ -568,7 +568,7 @@ int Ctx::tonal_aa_step(int n, const float* fvfull, DF G) {
 }
 
 int Ctx::read_slot(int slot, double* out) {
-    cudaMemcpyAsync(hscal, scal + slot * 4, 4 * 8, cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(hscal, scal + slot * kMaxCh, (size_t)nch * 8, cudaMemcpyDeviceToHost, stream);
     int rc = sync("reading a reduction");
     if (rc) return rc;
     for (int c = 0; c < nch; ++c) out[c] = hscal[c];
