@@ -312,6 +312,63 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------- batch workload (C3) ---
+
+def run_batch(args, rank, world):
+    """64 images of uneven sizes {256x256, 512x384, 1024x768, 1920x1080,
+    2048x1080}, grey/RGB, mask density U[1%, 10%]: batched solve (one launch
+    per phase per size class) against one solve per image."""
+    import numpy as np
+    import torch
+    import paper_2401_06747_b300 as hdi
+    from synthdata import synth_image, synth_rgb, random_mask, batch_specs
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    specs = batch_specs(args.batch, 200)
+    fs, ms = [], []
+    for s in specs:
+        H, W, ch, sd = s["height"], s["width"], s["channels"], s["seed"]
+        f = synth_rgb(H, W, seeds=(sd, sd + 1000, sd + 2000)) if ch == 3 else synth_image(H, W, sd, np.float32)[None]
+        fs.append(torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).cuda())
+        ms.append(torch.from_numpy(random_mask(H, W, s["density"], sd + 5000)).cuda())
+    outs = [torch.empty_like(x) for x in fs]
+    stream = torch.cuda.current_stream()
+    ctx = hdi.Context(local, stream=stream)
+    pix = sum(x.numel() for x in fs)
+
+    def batched():
+        return ctx.inpaint_batch(fs, ms, outs, tol=TOL)
+
+    def single():
+        return [ctx.inpaint(f, m, o, tol=TOL) for f, m, o in zip(fs, ms, outs)]
+
+    res = {}
+    for name, fn in (("per_image", single), ("batched", batched)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_ = all_max(e0.elapsed_time(e1), world)
+        res[name] = {"images_per_s": world * args.steps * len(fs) / (ms_ / 1e3), "ms_per_batch": ms_ / args.steps,
+                     "max_rel_res": max(s["rel_res"] for s in st)}
+    out = {"metric": "64-image uneven batch: inpaint solves/s at rel-res 1e-6", "value": round(res["batched"]["images_per_s"], 3),
+           "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(res["batched"]["ms_per_batch"], 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{len(fs)} images from batch_specs(seed 200): sizes 256x256..2048x1080, grey/RGB, "
+                                  f"density U[1%,10%]; {pix} values", "per_image_form": res["per_image"],
+                      "batched_form": res["batched"]}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -319,11 +376,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hdi", "reference"], default="hdi")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["4k", "batch"], default="4k")
+    ap.add_argument("--batch", type=int, default=64)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
     rank, world = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch":
+        run_batch(args, rank, world)
     else:
         run_hdi(args, rank, world)
     if world > 1:
