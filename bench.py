@@ -369,6 +369,46 @@ def run_batch(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------ serving (C5) ---
+
+def run_serve(args, rank, world):
+    """Poisson stream of requests (sizes 512^2..4K log-uniform in area,
+    grey/RGB, 70% inpaint / 25% tonal / 5% densify-to-3%) replayed in real
+    time against the continuous-batching server; p50/p99 latency and
+    completed solves per second."""
+    import numpy as np
+    import torch
+    from synthdata import synth_rgb, serving_stream, serving_inputs
+    from paper_2401_06747_b300.serve import Server, Request
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    base = synth_rgb(H4K, W4K, seeds=IMAGE_SEEDS, dtype=np.float32)
+    specs = serving_stream(args.requests, args.rate, 400 + rank)
+    reqs = []
+    for s in specs:
+        f, m = serving_inputs(s, base)
+        reqs.append(Request(id=s["id"], kind=s["kind"], arrival=s["arrival"], f=f, mask=m, density=0.03, seed=s["seed"]))
+    warm = Server(local, budget_gb=args.budget_gb)
+    warm.run([Request(id=-1, kind=r.kind, arrival=0.0, f=r.f, mask=r.mask, seed=r.seed) for r in reqs[:6]])
+    srv = Server(local, budget_gb=args.budget_gb)
+    barrier(world)
+    res = srv.run(reqs)
+    kinds = {k: sum(1 for r in reqs if r.kind == k) for k in ("inpaint", "tonal", "densify")}
+    lat = {k: sorted(r.done - r.arrival for r in srv.done if r.kind == k) for k in kinds}
+    per_kind = {k: {"n": len(v), "p50_ms": float(np.percentile(v, 50) * 1e3), "p99_ms": float(np.percentile(v, 99) * 1e3)}
+                for k, v in lat.items() if v}
+    t = all_max(res["wall_s"], world)
+    out = {"metric": "serving stream: solves/s with p50/p99 latency", "value": round(world * res["requests"] / t, 3),
+           "unit": "solves/s", "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": round(t * 1e3, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "p50_ms": round(res["p50_ms"], 2), "p99_ms": round(res["p99_ms"], 2),
+           "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, 512^2..3840x2160, "
+                                  "70/25/5 inpaint/tonal/densify-to-3%, budget %g GB" % args.budget_gb,
+                      "kinds": kinds, "per_kind": per_kind, "inpaint_batches": res["inpaint_batches"]}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,7 +416,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hdi", "reference"], default="hdi")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["4k", "batch"], default="4k")
+    ap.add_argument("--workload", choices=["4k", "batch", "serve"], default="4k")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--batch", type=int, default=64)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
@@ -385,6 +428,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batch":
         run_batch(args, rank, world)
+    elif args.workload == "serve":
+        run_serve(args, rank, world)
     else:
         run_hdi(args, rank, world)
     if world > 1:

@@ -15,4 +15,5 @@ from .generators import (  # noqa: F401
     random_mask,
     batch_specs,
     serving_stream,
+    serving_inputs,
 )

@@ -110,3 +110,20 @@ def serving_stream(count: int = 2000, rate: float = 200.0, seed: int = 400):
         out.append(dict(id=i, arrival=t, width=w, height=h, channels=ch, kind=kind,
                         density=d, seed=seed + 1 + i))
     return out
+
+
+def serving_inputs(spec: dict, base: np.ndarray):
+    """Image and mask of one serving request: a crop of a shared synthetic
+    RGB base image (at least the request's size) at an offset drawn from the
+    request's seed, channel 0 only for grey requests, and a Bernoulli mask
+    of the request's density (fast to draw for thousands of requests)."""
+    rng = np.random.Generator(np.random.PCG64(spec["seed"]))
+    H, W = spec["height"], spec["width"]
+    y0 = int(rng.integers(0, base.shape[1] - H + 1))
+    x0 = int(rng.integers(0, base.shape[2] - W + 1))
+    f = base[: spec["channels"], y0:y0 + H, x0:x0 + W]
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    m = (rng.random((H, W)) < spec["density"]).astype(np.uint8)
+    if not m.any():
+        m[H // 2, W // 2] = 1
+    return f, m
