@@ -403,7 +403,7 @@ def run_serve(args, rank, world):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "p50_ms": round(res["p50_ms"], 2), "p99_ms": round(res["p99_ms"], 2),
            "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, 512^2..3840x2160, "
-                                  "70/25/5 inpaint/tonal/densify-to-3%, budget %g GB" % args.budget_gb,
+                                  f"70/25/5 inpaint/tonal/densify-to-3 percent, budget {args.budget_gb} GB",
                       "kinds": kinds, "per_kind": per_kind, "inpaint_batches": res["inpaint_batches"]}}
     if rank == 0:
         print(json.dumps(out), flush=True)
