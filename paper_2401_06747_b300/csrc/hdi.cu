@@ -43,6 +43,8 @@ const ParamDef kParams[] = {
     {"trace", &Params::trace, 0, 1},
     {"tonal_anderson", &Params::tonal_anderson, 0, 8},
     {"tonal_oras_eta", &Params::tonal_oras_eta, 1e-12, 1.0},
+    {"fine_pre", &Params::fine_pre, 0, 4},
+    {"fine_post", &Params::fine_post, 0, 4},
 };
 
 }  // namespace
@@ -290,7 +292,8 @@ static dim3 tiles_of(const Level& L, int nch) {
 }
 
 // One V-cycle (Sec. 3.2) on the correction equation A_l x = b_l, x from 0.
-// Result in lev[l].xa.
+// Result in lev[l].xa. Level 0 uses fine_pre / fine_post ORAS sweeps
+// (default 1 and 1, the paper's choice, Sec. 3.3); coarser levels one each.
 void Ctx::vcycle(int l) {
     Level& L = lev[l];
     const double* pre_norm = (l == 0) ? scal + kSlotR64 * kMaxCh : scal + l * kMaxCh;
@@ -300,7 +303,22 @@ void Ctx::vcycle(int l) {
         if (l == 0) ++vcycles_run;
         return;
     }
-    oras(l, true, nullptr, L.xa, pre_norm, false, it);
+    const int npre = (l == 0) ? (int)p.fine_pre : 1;
+    const int npost = (l == 0) ? (int)p.fine_post : 1;
+    // pre-smoothing: the first sweep starts from x = 0
+    bool have_x = false;
+    if (npre > 0) {
+        oras(l, true, nullptr, L.xa, pre_norm, false, it);
+        have_x = true;
+        for (int i = 1; i < npre; ++i) {
+            residual_norm_level(l, L.xa, l);
+            oras(l, false, L.xa, L.xb, scal + l * kMaxCh, false, it);
+            std::swap(L.xa, L.xb);
+        }
+    } else {
+        cudaMemsetAsync(L.xa, 0, (size_t)nch * L.cs * 4, stream);
+    }
+    (void)have_x;
     Level& C = lev[l + 1];
     {
         dim3 blk(128), grd = tiles_of(L, nch);
@@ -319,8 +337,26 @@ void Ctx::vcycle(int l) {
         ++launches;
         if (l == 0) tstop();
     }
-    oras(l, false, L.xb, L.xa, scal + l * kMaxCh, false, it);
+    // x now in xb; post-smoothing sweeps alternate xb -> xa -> xb ...
+    float* cur = L.xb;
+    float* other = L.xa;
+    for (int i = 0; i < npost; ++i) {
+        if (i > 0) residual_norm_level(l, cur, l);
+        oras(l, false, cur, other, scal + l * kMaxCh, false, it);
+        std::swap(cur, other);
+    }
+    if (cur != L.xa) std::swap(L.xa, L.xb);   // result must end in xa
     if (l == 0) ++vcycles_run;
+}
+
+// ||b_l - A_l x||^2 per channel into slot `slot` (prolongation kernel with a
+// zero coarse correction is not available, so reuse k_prolong<0> with the
+// coarse level's zero-filled scratch is avoided: a plain residual pass).
+void Ctx::residual_norm_level(int l, const float* x, int slot) {
+    const Level& L = lev[l];
+    dim3 grd = tiles_of(L, nch), blk(128);
+    k_level_residual_norm<<<grd, blk, 0, stream>>>(arr(l), mview(l), x, L.b, reducer(slot, grd.x * grd.y));
+    ++launches;
 }
 
 // Reduced full multigrid (Sec. 3.2, Fig. "multigrid_reduced"): data pyramid,

@@ -22,6 +22,8 @@ struct Params {
     double hbm_budget_gb = 200.0;
     double trace = 0;
     double tonal_oras_eta = 1e-2;   // local stop fraction inside the tonal inner solves
+    double fine_pre = 1;            // ORAS pre-smoothing sweeps on the finest level
+    double fine_post = 1;           // ORAS post-smoothing sweeps on the finest level
     double tonal_anderson = 8;      // Anderson window on the RAS iteration (0 = plain Alg. 2)               // 1: one line per outer iteration on stderr
 };
 
@@ -149,6 +151,7 @@ struct Ctx {
     void oras(int l, bool zero, const float* xin, float* xout, const double* rnorm2, bool coarsest,
               unsigned long long* iters);
     void vcycle(int l);
+    void residual_norm_level(int l, const float* x, int slot);
     void fmg(DFc d);
     void residual(int rhs, int init, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b);
     int solve(SolveSpec& s);

@@ -189,6 +189,49 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
     grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
 }
 
+// ||b - A x||^2 per channel on one level (column strips, FP32).
+__global__ void __launch_bounds__(128) k_level_residual_norm(LevelArr F, MaskView fm, const float* __restrict__ x,
+                                                             const float* __restrict__ b, GridReduce red) {
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
+    const int px = x0 + lane;
+    const int y0 = blockIdx.y * CS_ROWS;
+    const int y1 = min(y0 + CS_ROWS, F.H);
+    const int ch = blockIdx.z;
+    fm = fm.ch(ch);
+    const bool act = px < F.W;
+    const int pxc = act ? px : F.W - 1;
+    const float* xc = x + ch * F.cs;
+    const float* bc = b + ch * F.cs;
+    float sq = 0.f;
+    if (x0 < F.W) {
+        const uint32_t* mrow = fm.bits + (x0 >> 5);
+        float up = (y0 > 0) ? xc[(size_t)(y0 - 1) * F.pitch + pxc] : 0.f;
+        float cen = xc[(size_t)y0 * F.pitch + pxc];
+        for (int y = y0; y < y1; ++y) {
+            const float dn = (y + 1 < F.H) ? xc[(size_t)(y + 1) * F.pitch + pxc] : 0.f;
+            float lf = __shfl_up_sync(HDI_FULL, cen, 1);
+            float rt = __shfl_down_sync(HDI_FULL, cen, 1);
+            if (lane == 0 && px > 0) lf = xc[(size_t)y * F.pitch + px - 1];
+            if (lane == 31 && px + 1 < F.W) rt = xc[(size_t)y * F.pitch + px + 1];
+            const bool known = (mrow[(size_t)y * fm.wpitch] >> lane) & 1u;
+            if (act && !known) {
+                float lap = 0.f;
+                if (px > 0) lap += cen - lf;
+                if (px + 1 < F.W) lap += cen - rt;
+                if (y > 0) lap += cen - up;
+                if (y + 1 < F.H) lap += cen - dn;
+                const float r = bc[(size_t)y * F.pitch + px] - lap;
+                sq += r * r;
+            }
+            up = cen;
+            cen = dn;
+        }
+    }
+    const double tot = (double)block_sum_f(sq);
+    grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
+}
+
 // Bilinear cell-centred prolongation of coarse e at fine pixel (px, py).
 __device__ __forceinline__ float prolong_at(const float* __restrict__ e, const LevelArr& C, int px, int py) {
     const int X = px >> 1, Y = py >> 1;
