@@ -45,6 +45,8 @@ const ParamDef kParams[] = {
     {"tonal_oras_eta", &Params::tonal_oras_eta, 1e-12, 1.0},
     {"fine_pre", &Params::fine_pre, 0, 4},
     {"fine_post", &Params::fine_post, 0, 4},
+    {"tonal_fine_pre", &Params::tonal_fine_pre, 0, 4},
+    {"tonal_fine_post", &Params::tonal_fine_post, 0, 4},
 };
 
 }  // namespace

@@ -24,6 +24,8 @@ struct Params {
     double tonal_oras_eta = 1e-2;   // local stop fraction inside the tonal inner solves
     double fine_pre = 1;            // ORAS pre-smoothing sweeps on the finest level
     double fine_post = 1;           // ORAS post-smoothing sweeps on the finest level
+    double tonal_fine_pre = 2;      // fine_pre inside the tonal inner solves
+    double tonal_fine_post = 1;     // fine_post inside the tonal inner solves
     double tonal_anderson = 8;      // Anderson window on the RAS iteration (0 = plain Alg. 2)               // 1: one line per outer iteration on stderr
 };
 

@@ -603,9 +603,17 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     // the inner solves use their own local stop fraction (restored on exit)
     struct EtaSwap {
         Params& p;
-        double keep;
-        EtaSwap(Params& pp) : p(pp), keep(pp.oras_eta) { p.oras_eta = p.tonal_oras_eta; }
-        ~EtaSwap() { p.oras_eta = keep; }
+        double keep, kpre, kpost;
+        EtaSwap(Params& pp) : p(pp), keep(pp.oras_eta), kpre(pp.fine_pre), kpost(pp.fine_post) {
+            p.oras_eta = p.tonal_oras_eta;
+            p.fine_pre = p.tonal_fine_pre;
+            p.fine_post = p.tonal_fine_post;
+        }
+        ~EtaSwap() {
+            p.oras_eta = keep;
+            p.fine_pre = kpre;
+            p.fine_post = kpost;
+        }
     } eta_swap(p);
     const double ratio = p.tonal_inner_ratio;
     // ||B^T f||: w_f solves A w = (I - C) f.
