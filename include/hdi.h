@@ -204,7 +204,9 @@ const char* hdi_version(void);
  *   tonal_max_iter    [400]   RAS iterations per tonal solve
  *   tonal_inner_ratio [0.1]   inner solves target: ratio * current outer relative residual
  *   tonal_anderson    [8]     Anderson window on the RAS iteration (0 = plain Alg. 2)
- *   tonal_oras_eta    [1e-2]  oras_eta used inside the tonal inner solves
+ *   tonal_oras_eta    [3e-2]  oras_eta used inside the tonal inner solves
+ *   fine_pre, fine_post [1, 1] ORAS sweeps before / after the coarse correction on the finest level
+ *   tonal_fine_pre, tonal_fine_post [2, 1] the same inside the tonal inner solves
  *   tonal_echo_rtol   [1e-3]  relative CG tolerance of the local echo solves
  *   trace             [0]     1 = one line per RAS iteration on stderr
  *   hbm_budget_gb     [200]   workspace cap for this context

@@ -123,6 +123,16 @@ __device__ __forceinline__ void grid_reduce_commit(const GridReduce& R, int ch, 
     if (tid == 0) *R.ticket = 0u;
 }
 
+// Origin of subdomain b (side 32, stride s) along an axis of n pixels. The
+// last subdomain is shifted back to end at the image border, so that every
+// subdomain is a full 32 pixels whenever n >= 32 (same count and the same
+// owned cores as the plain stride placement).
+__host__ __device__ __forceinline__ int sub_origin(int b, int n, int s) {
+    if (n < 32) return 0;
+    const int o = b * s;
+    return o > n - 32 ? n - 32 : o;
+}
+
 // Number of overlapping subdomains of side `size` with overlap `ov` along an
 // axis of n pixels: ceil((n - ov) / (size - ov)), at least 1 (Sec. 3.3).
 __host__ __device__ __forceinline__ int tile_count(int n, int size, int ov) {

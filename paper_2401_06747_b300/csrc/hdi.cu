@@ -282,8 +282,14 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     const int warps = L.nbx * L.nby * nch;
     const int blocks = (warps + 3) / 4;
     if (l == 0) tstart(kT_Oras);
-    if (zero) k_oras<true><<<blocks, 128, 0, stream>>>(a);
-    else k_oras<false><<<blocks, 128, 0, stream>>>(a);
+    const bool full = L.W >= 32 && L.H >= 32;
+    if (zero) {
+        if (full) k_oras<true, true><<<blocks, 128, 0, stream>>>(a);
+        else k_oras<true, false><<<blocks, 128, 0, stream>>>(a);
+    } else {
+        if (full) k_oras<false, true><<<blocks, 128, 0, stream>>>(a);
+        else k_oras<false, false><<<blocks, 128, 0, stream>>>(a);
+    }
     ++launches;
     if (l == 0) tstop();
 }

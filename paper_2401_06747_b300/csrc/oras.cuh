@@ -23,6 +23,9 @@ struct LocalGeom {
     uint32_t um;          // this lane's column: bit j set = row j is an unknown pixel
     float dh;             // horizontal part of d_j for this lane
     float dtop, dbot;     // weight of the outside neighbour above row 0 / below row h-1
+    // full 32x32 subdomains: the diagonal of row 0, rows 1..30 and row 31,
+    // with lanes 0 and 31 compensated for the shuffle returning their own value
+    float d0, dmid, d31;
 };
 
 __device__ __forceinline__ float local_diag(const LocalGeom& g, int j) {
@@ -55,22 +58,35 @@ __device__ __forceinline__ LocalGeom make_geom(int x0, int y0, int H, int W, con
     g.dh = left + right;
     g.dtop = (y0 > 0) ? theta : 0.f;
     g.dbot = (y0 + g.h < H) ? theta : 0.f;
+    const float dhc = g.dh + ((lane == 0) ? 1.f : 0.f) + ((lane == 31) ? 1.f : 0.f);
+    g.d0 = dhc + 1.f + g.dtop;
+    g.dmid = dhc + 2.f;
+    g.d31 = dhc + 1.f + g.dbot;
     return g;
 }
 
 // q = A_i p on the unknown pixels (p is zero on known / invalid pixels).
+// FULL: the subdomain is 32x32, so the row diagonal is known at compile time
+// and the edge lanes keep the value the shuffle returns (their own p, which
+// d0/dmid/d31 compensate) instead of selecting zero.
+template <bool FULL>
 __device__ __forceinline__ void local_apply(const LocalGeom& g, const float (&p)[32], float (&q)[32]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
         float pl = __shfl_up_sync(HDI_FULL, p[j], 1);
         float pr = __shfl_down_sync(HDI_FULL, p[j], 1);
-        if (lane == 0) pl = 0.f;
-        if (lane == 31) pr = 0.f;
+        if (!FULL) {
+            if (lane == 0) pl = 0.f;
+            if (lane == 31) pr = 0.f;
+        }
         float s = pl + pr;
         if (j > 0) s += p[j - 1];
         if (j < 31) s += p[j + 1];
-        const float v = local_diag(g, j) * p[j] - s;
+        float d;
+        if (FULL) d = (j == 0) ? g.d0 : ((j == 31) ? g.d31 : g.dmid);
+        else d = local_diag(g, j);
+        const float v = d * p[j] - s;
         q[j] = ((g.um >> j) & 1u) ? v : 0.f;
     }
 }
@@ -78,6 +94,7 @@ __device__ __forceinline__ void local_apply(const LocalGeom& g, const float (&p)
 // Conjugate gradients on A_i v = r (v starts at 0; r holds the right-hand
 // side on entry and the final residual on exit). Stops when ||r||^2 <= thresh
 // or after maxit iterations; returns the iteration count.
+template <bool FULL>
 __device__ __forceinline__ int local_cg(const LocalGeom& g, float (&v)[32], float (&r)[32], float thresh, int maxit) {
     float p[32], q[32];
     float rr = 0.f;
@@ -90,7 +107,7 @@ __device__ __forceinline__ int local_cg(const LocalGeom& g, float (&v)[32], floa
     rr = warp_sum_f(rr);
     int it = 0;
     while (rr > thresh && it < maxit) {
-        local_apply(g, p, q);
+        local_apply<FULL>(g, p, q);
         float pq = 0.f;
 #pragma unroll
         for (int j = 0; j < 32; ++j) pq += p[j] * q[j];
@@ -135,7 +152,7 @@ struct OrasArgs {
 // correction of the one subdomain whose core (the subdomain minus half the
 // overlap on each inner side) contains it, so every output pixel is written
 // by exactly one warp and the sweep needs no atomics.
-template <bool ZERO>
+template <bool ZERO, bool FULL>
 __global__ void __launch_bounds__(128) k_oras(OrasArgs a) {
     const int wid = blockIdx.x * 4 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -145,7 +162,7 @@ __global__ void __launch_bounds__(128) k_oras(OrasArgs a) {
     const int bi = wid - ch * nb;
     const int by = bi / a.nbx;
     const int bx = bi - by * a.nbx;
-    const int x0 = bx * a.stride, y0 = by * a.stride;
+    const int x0 = sub_origin(bx, a.W, a.stride), y0 = sub_origin(by, a.H, a.stride);
     const LocalGeom g = make_geom(x0, y0, a.H, a.W, a.m.ch(ch), a.theta);
     const int gx = x0 + lane;
     const bool act = lane < g.w;
@@ -187,13 +204,15 @@ __global__ void __launch_bounds__(128) k_oras(OrasArgs a) {
         }
     }
     const float thresh = (float)(a.rnorm2[ch] * a.thresh_scale);
-    const int it = local_cg(g, v, r, thresh, a.maxit);
+    const int it = local_cg<FULL>(g, v, r, thresh, a.maxit);
     if (a.iters && lane == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
 
-    const int ox0 = (bx == 0) ? 0 : a.ov / 2;
-    const int ox1 = (bx == a.nbx - 1) ? g.w : a.stride + a.ov / 2;
-    const int oy0 = (by == 0) ? 0 : a.ov / 2;
-    const int oy1 = (by == a.nby - 1) ? g.h : a.stride + a.ov / 2;
+    // owned core in absolute coordinates, then relative to the (possibly
+    // shifted) origin
+    const int ox0 = ((bx == 0) ? 0 : bx * a.stride + a.ov / 2) - x0;
+    const int ox1 = ((bx == a.nbx - 1) ? a.W : (bx + 1) * a.stride + a.ov / 2) - x0;
+    const int oy0 = ((by == 0) ? 0 : by * a.stride + a.ov / 2) - y0;
+    const int oy1 = ((by == a.nby - 1) ? a.H : (by + 1) * a.stride + a.ov / 2) - y0;
     if (lane >= ox0 && lane < ox1) {
         float* xo = a.xout + ch * a.cstride;
 #pragma unroll

@@ -21,7 +21,7 @@ struct Params {
     double tonal_echo_max_iter = 300;
     double hbm_budget_gb = 200.0;
     double trace = 0;
-    double tonal_oras_eta = 1e-2;   // local stop fraction inside the tonal inner solves
+    double tonal_oras_eta = 3e-2;   // local stop fraction inside the tonal inner solves
     double fine_pre = 1;            // ORAS pre-smoothing sweeps on the finest level
     double fine_post = 1;           // ORAS post-smoothing sweeps on the finest level
     double tonal_fine_pre = 2;      // fine_pre inside the tonal inner solves

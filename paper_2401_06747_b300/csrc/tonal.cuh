@@ -36,7 +36,7 @@ __global__ void k_tonal_count(MaskView m, int nbx, int nby, int stride, int* __r
     const int lane = threadIdx.x & 31;
     if (wid >= nbx * nby) return;
     const int by = wid / nbx, bx = wid - by * nbx;
-    const int x0 = bx * stride, y0 = by * stride;
+    const int x0 = sub_origin(bx, m.W, stride), y0 = sub_origin(by, m.H, stride);
     const int w = min(32, m.W - x0), h = min(32, m.H - y0);
     int c = 0;
     if (lane < h) c = __popc(m.window(x0, y0 + lane) & cols_valid(w));
@@ -52,7 +52,7 @@ __global__ void k_tonal_list(MaskView m, int nbx, int nby, int stride, const int
     const int lane = threadIdx.x & 31;
     if (wid >= nbx * nby) return;
     const int by = wid / nbx, bx = wid - by * nbx;
-    const int x0 = bx * stride, y0 = by * stride;
+    const int x0 = sub_origin(bx, m.W, stride), y0 = sub_origin(by, m.H, stride);
     const int w = min(32, m.W - x0), h = min(32, m.H - y0);
     uint32_t bits = (lane < h) ? (m.window(x0, y0 + lane) & cols_valid(w)) : 0u;
     int c = __popc(bits);
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(128) k_tonal_echo(EchoArgs a) {
     }
     const int i = lo;
     const int by = i / a.nbx, bx = i - by * a.nbx;
-    const int x0 = bx * a.stride, y0 = by * a.stride;
+    const int x0 = sub_origin(bx, a.m.W, a.stride), y0 = sub_origin(by, a.m.H, a.stride);
     const LocalGeom g = make_geom(x0, y0, a.m.H, a.m.W, a.m, 0.f);
     const int code = a.list[e];
     const int ky = code >> 5, kx = code & 31;
@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(128) k_tonal_echo(EchoArgs a) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) rr0 += r[j] * r[j];
     rr0 = warp_sum_f(rr0);
-    const int it = local_cg(g, v, r, a.rtol2 * rr0, a.maxit);
+    const int it = (g.w == 32 && g.h == 32) ? local_cg<true>(g, v, r, a.rtol2 * rr0, a.maxit)
+                                            : local_cg<false>(g, v, r, a.rtol2 * rr0, a.maxit);
     if (a.iters && lane == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
     float* out = a.echo + (size_t)e * 1024;
 #pragma unroll
@@ -247,11 +248,15 @@ struct LocalSolveArgs {
     float* out;      // full layout, accumulates D_i v_i (zeroed before the first colour)
 };
 
-// Number of subdomains covering coordinate x along an axis (1 or 2).
-__device__ __forceinline__ int cover_count(int x, int nb, int stride) {
-    const int hi = min(nb - 1, x / stride);
+// Number of subdomains covering coordinate x along an axis of n pixels
+// (1 or 2; the last subdomain sits at sub_origin(nb - 1, n, stride)).
+__device__ __forceinline__ int cover_count(int x, int nb, int stride, int n) {
+    if (nb == 1) return 1;
+    const int hi = min(nb - 2, x / stride);
     const int lo = max(0, (x - 31 + stride - 1) / stride);
-    return hi - lo + 1;
+    int c = (hi >= lo) ? hi - lo + 1 : 0;
+    if (x >= sub_origin(nb - 1, n, stride)) ++c;
+    return c;
 }
 
 // Local solves of one colour class ((bx & 1) | (by & 1) << 1 == color):
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(128) k_tonal_local(LocalSolveArgs a) {
     if (m == 0) return;
     const uint16_t* lst = a.list + a.off[i];
     const float* L = a.fac + a.goff[i];
-    const int x0 = bx * a.stride, y0 = by * a.stride;
+    const int x0 = sub_origin(bx, a.F.W, a.stride), y0 = sub_origin(by, a.F.H, a.stride);
     const float* r = a.r + ch * a.F.cs;
     float* v = sv[wl];
     for (int k = lane; k < m; k += 32) {
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(128) k_tonal_local(LocalSolveArgs a) {
     for (int k = lane; k < m; k += 32) {
         const int code = lst[k];
         const int px = x0 + (code & 31), py = y0 + (code >> 5);
-        const int mult = cover_count(px, a.nbx, a.stride) * cover_count(py, a.nby, a.stride);
+        const int mult = cover_count(px, a.nbx, a.stride, a.F.W) * cover_count(py, a.nby, a.stride, a.F.H);
         a.out[ch * a.F.cs + (size_t)py * a.F.pitch + px] += v[k] / (float)mult;
     }
 }
