@@ -259,23 +259,34 @@ __device__ __forceinline__ int cover_count(int x, int nb, int stride, int n) {
     return c;
 }
 
-// Local solves of one colour class ((bx & 1) | (by & 1) << 1 == color):
+// Colour classes along one axis: the last subdomain (which sits at the
+// border and may overlap the one two places earlier) is class 2, the others
+// alternate 0, 1. Two subdomains of one class never overlap.
+__host__ __device__ __forceinline__ int class_count(int c, int nb) {
+    const int inner = (nb >= 2) ? nb - 1 : nb;
+    if (c == 2) return (nb >= 2) ? 1 : 0;
+    return (inner - c + 1) / 2;
+}
+__host__ __device__ __forceinline__ int class_member(int c, int q, int nb) { return c == 2 ? nb - 1 : c + 2 * q; }
+
+// Local solves of one colour class (cx, cy), color = cy * 3 + cx:
 // v = (L L^T)^{-1} R_i r by forward and backward substitution, then
-// out += D_i v (out = P r after all four colours). Subdomains of one colour never overlap (stride 26 > 32/2), so
-// the updates need no atomics and their order is fixed. One warp per
-// (subdomain, channel).
+// out += D_i v (out = P r after all nine classes). Subdomains of one class
+// never overlap, so the updates need no atomics and their order is fixed.
+// One warp per (subdomain, channel).
 __global__ void __launch_bounds__(128) k_tonal_local(LocalSolveArgs a) {
     __shared__ float sv[4][kTonalMaxM];
     const int wl = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int hx = (a.nbx + 1 - (a.color & 1)) / 2;
-    const int hy = (a.nby + 1 - (a.color >> 1)) / 2;
+    const int cx = a.color % 3, cy = a.color / 3;
+    const int hx = class_count(cx, a.nbx);
+    const int hy = class_count(cy, a.nby);
     const long long wid = (long long)blockIdx.x * 4 + wl;
     if (wid >= (long long)hx * hy * a.nch) return;
     const int ch = (int)(wid / (hx * hy));
     const int q = (int)(wid - (long long)ch * hx * hy);
-    const int bx = 2 * (q % hx) + (a.color & 1);
-    const int by = 2 * (q / hx) + (a.color >> 1);
+    const int bx = class_member(cx, q % hx, a.nbx);
+    const int by = class_member(cy, q / hx, a.nby);
     const int i = by * a.nbx + bx;
     const int m = a.off[i + 1] - a.off[i];
     if (m == 0) return;
@@ -440,7 +451,7 @@ void Ctx::tonal_residual(DFc y, DFc w) {
 
 void Ctx::tonal_local(float* out) {
     const Level& L0 = lev[0];
-    for (int color = 0; color < 4; ++color) {
+    for (int color = 0; color < 9; ++color) {
         LocalSolveArgs a;
         a.F = arr(0);
         a.nbx = L0.nbx;
@@ -454,8 +465,8 @@ void Ctx::tonal_local(float* out) {
         a.fac = t_fac;
         a.r = tres;
         a.out = out;
-        const int hx = (L0.nbx + 1 - (color & 1)) / 2;
-        const int hy = (L0.nby + 1 - (color >> 1)) / 2;
+        const int hx = class_count(color % 3, L0.nbx);
+        const int hy = class_count(color / 3, L0.nby);
         const long long warps = (long long)hx * hy * nch;
         if (warps <= 0) continue;
         tstart(kT_Local);

@@ -53,3 +53,23 @@ def test_generated_data_is_recovered():
     fb = B_apply(g0, c)
     g, _ = run(fb, c, 1e-9)
     assert np.abs(g - g0).max() <= 1e-4
+
+
+def test_bitwise_determinism_across_contexts_and_history():
+    """Same input, different contexts and call histories: identical g. The
+    89 x 158 size makes the border subdomains overlap their same-parity
+    neighbours, which the local-phase colouring must keep race-free."""
+    need_gpu()
+    f = synth_rgb(89, 158, seeds=(7, 8, 9), dtype=np.float32)
+    c = random_mask(89, 158, 0.05, 10)
+    a = ctx()
+    g1 = torch.empty_like(dev(f))
+    a.tonal_opt(dev(f), dev(c), g1, tol=1e-6)
+    b = ctx()
+    other = dev(synth_rgb(37, 61, seeds=(1, 2, 3), dtype=np.float32))
+    b.tonal_opt(other, dev(random_mask(37, 61, 0.05, 3)), torch.empty_like(other), tol=1e-6)
+    g2 = torch.empty_like(g1)
+    b.tonal_opt(dev(f), dev(c), g2, tol=1e-6)
+    g3 = torch.empty_like(g1)
+    a.tonal_opt(dev(f), dev(c), g3, tol=1e-6)
+    assert torch.equal(g1, g2) and torch.equal(g1, g3)
