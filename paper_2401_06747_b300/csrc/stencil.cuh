@@ -239,7 +239,10 @@ __device__ __forceinline__ float prolong_at(const float* __restrict__ e, const L
     const int Yn = (py & 1) ? min(Y + 1, C.H - 1) : max(Y - 1, 0);
     const float* r0 = e + (size_t)Y * C.pitch;
     const float* r1 = e + (size_t)Yn * C.pitch;
-    return 0.5625f * r0[X] + 0.1875f * (r0[Xn] + r1[X]) + 0.0625f * r1[Xn];
+    // same operation order as prolong_row / the column-strip kernel
+    const float h0 = __fadd_rn(__fmul_rn(0.75f, r0[X]), __fmul_rn(0.25f, r0[Xn]));
+    const float h1 = __fadd_rn(__fmul_rn(0.75f, r1[X]), __fmul_rn(0.25f, r1[Xn]));
+    return __fadd_rn(__fmul_rn(0.75f, h0), __fmul_rn(0.25f, h1));
 }
 
 // Tiles of 32x8 pixels (used by the staging helpers' grids).
@@ -256,11 +259,30 @@ __device__ __forceinline__ float prolong_value(const float* __restrict__ xc, con
     return (MODE == 0 ? xc[idx] : 0.f) + prolong_at(ec, C, px, py);
 }
 
+// Horizontally interpolated coarse row R at this lane's fine column:
+// 3/4 e[R][X] + 1/4 e[R][Xn], X = x/2 and Xn the coarse neighbour on the side
+// of x. Lane pairs (2j, 2j+1) share X; the neighbour comes from the adjacent
+// lane by a shuffle, edge lanes load it.
+__device__ __forceinline__ float prolong_row(const float* __restrict__ ec, const LevelArr& C, int R, int x, int lane) {
+    const float* row = ec + (size_t)R * C.pitch;
+    const int X = min(x >> 1, C.W - 1);
+    const float own = row[X];
+    const bool odd = x & 1;
+    float nb = __shfl_sync(HDI_FULL, own, odd ? min(lane + 1, 31) : max(lane - 1, 0));
+    if ((lane == 0 && !odd) || (lane == 31 && odd)) {
+        const int Xn = odd ? min(X + 1, C.W - 1) : max(X - 1, 0);
+        nb = row[Xn];
+    }
+    return __fadd_rn(__fmul_rn(0.75f, own), __fmul_rn(0.25f, nb));
+}
+
 // MODE 0 (V-cycle): xout = xin + P e on unknown pixels, xin on known ones;
 // MODE 1 (FMG):     xout = b on known pixels, P e on unknown ones;
 // MODE 2 (start):   xout = b on known pixels, 0 on unknown ones (e unused).
 // Then ||b - A xout||^2 per channel (the next sweep's local stop rule).
-// Column strips: lane = column, three-row register window of xout values.
+// Column strips: lane = column, three-row register window of xout values;
+// the bilinear prolongation reads one coarse value per coarse row per lane
+// pair and takes the horizontal neighbour by a shuffle.
 template <int MODE>
 __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const float* __restrict__ xin,
                                                  const float* __restrict__ b, float* __restrict__ xout,
@@ -280,16 +302,31 @@ __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const 
     float sq = 0.f;
     if (x0 < F.W) {
         const uint32_t* mrow = fm.bits + (x0 >> 5);
+        // value of xout at (pxc, y) given the row's mask word
+        auto val = [&](int y, uint32_t w) -> float {
+            const size_t idx = (size_t)y * F.pitch + pxc;
+            const bool known = (w >> lane) & 1u;
+            float pe = 0.f;
+            if (MODE != 2) {
+                const int Y = y >> 1;
+                const int Yn = (y & 1) ? min(Y + 1, C.H - 1) : max(Y - 1, 0);
+                pe = __fadd_rn(__fmul_rn(0.75f, prolong_row(ec, C, Y, pxc, lane)),
+                               __fmul_rn(0.25f, prolong_row(ec, C, Yn, pxc, lane)));
+            }
+            if (known) return (MODE == 0) ? xc[idx] : bc[idx];
+            if (MODE == 2) return 0.f;
+            return (MODE == 0 ? xc[idx] : 0.f) + pe;
+        };
         float up = 0.f;
-        if (y0 > 0) up = prolong_value<MODE>(xc, bc, ec, F, C, fm.known(pxc, y0 - 1), pxc, y0 - 1);
+        if (y0 > 0) up = val(y0 - 1, mrow[(size_t)(y0 - 1) * fm.wpitch]);
         uint32_t wc = mrow[(size_t)y0 * fm.wpitch];
-        float cen = prolong_value<MODE>(xc, bc, ec, F, C, (wc >> lane) & 1u, pxc, y0);
+        float cen = val(y0, wc);
         for (int y = y0; y < y1; ++y) {
             uint32_t wn = 0;
             float dn = 0.f;
             if (y + 1 < F.H) {
                 wn = mrow[(size_t)(y + 1) * fm.wpitch];
-                dn = prolong_value<MODE>(xc, bc, ec, F, C, (wn >> lane) & 1u, pxc, y + 1);
+                dn = val(y + 1, wn);
             }
             float lf = __shfl_up_sync(HDI_FULL, cen, 1);
             float rt = __shfl_down_sync(HDI_FULL, cen, 1);
