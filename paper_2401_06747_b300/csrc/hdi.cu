@@ -43,6 +43,8 @@ const ParamDef kParams[] = {
     {"trace", &Params::trace, 0, 1},
     {"tonal_anderson", &Params::tonal_anderson, 0, 8},
     {"tonal_oras_eta", &Params::tonal_oras_eta, 1e-12, 1.0},
+    {"coarse_level_eta", &Params::coarse_level_eta, 0, 1.0},
+    {"coarse_level_max", &Params::coarse_level_max, 1, 1024},
     {"fine_pre", &Params::fine_pre, 0, 4},
     {"fine_post", &Params::fine_post, 0, 4},
     {"tonal_fine_pre", &Params::tonal_fine_pre, 0, 4},
@@ -272,8 +274,9 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     a.stride = 32 - kOv;
     a.ov = kOv;
     a.theta = (float)p.oras_theta;
-    a.maxit = coarsest ? (int)p.coarse_max_local : (int)p.oras_max_local;
-    a.thresh_scale = coarsest ? p.coarse_eta : p.oras_eta / (double)(L.nbx * L.nby);
+    const double eta = (l > 0 && p.coarse_level_eta > 0) ? p.coarse_level_eta : p.oras_eta;
+    a.maxit = coarsest ? (int)p.coarse_max_local : (l > 0 ? (int)p.coarse_level_max : (int)p.oras_max_local);
+    a.thresh_scale = coarsest ? p.coarse_eta : eta / (double)(L.nbx * L.nby);
     a.xin = xin;
     a.xout = xout;
     a.b = L.b;

@@ -22,6 +22,8 @@ struct Params {
     double hbm_budget_gb = 200.0;
     double trace = 0;
     double tonal_oras_eta = 3e-2;   // local stop fraction inside the tonal inner solves
+    double coarse_level_eta = 0;    // local stop fraction on levels >= 1 (0 = same as oras_eta)
+    double coarse_level_max = 48;   // local CG cap on levels >= 1 (below the coarsest)
     double fine_pre = 1;            // ORAS pre-smoothing sweeps on the finest level
     double fine_post = 1;           // ORAS post-smoothing sweeps on the finest level
     double tonal_fine_pre = 2;      // fine_pre inside the tonal inner solves

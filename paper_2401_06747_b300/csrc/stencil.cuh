@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
         float up = (y0 > 0) ? xc[(size_t)(y0 - 1) * F.pitch + pxc] : 0.f;
         float cen = xc[(size_t)y0 * F.pitch + pxc];
         float pair = 0.f;
+#pragma unroll 4
         for (int y = y0; y < y1; ++y) {
             const float dn = (y + 1 < F.H) ? xc[(size_t)(y + 1) * F.pitch + pxc] : 0.f;
             float lf = __shfl_up_sync(HDI_FULL, cen, 1);
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(128) k_level_residual_norm(LevelArr F, MaskVie
         const uint32_t* mrow = fm.bits + (x0 >> 5);
         float up = (y0 > 0) ? xc[(size_t)(y0 - 1) * F.pitch + pxc] : 0.f;
         float cen = xc[(size_t)y0 * F.pitch + pxc];
+#pragma unroll 4
         for (int y = y0; y < y1; ++y) {
             const float dn = (y + 1 < F.H) ? xc[(size_t)(y + 1) * F.pitch + pxc] : 0.f;
             float lf = __shfl_up_sync(HDI_FULL, cen, 1);
@@ -321,6 +323,7 @@ __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const 
         if (y0 > 0) up = val(y0 - 1, mrow[(size_t)(y0 - 1) * fm.wpitch]);
         uint32_t wc = mrow[(size_t)y0 * fm.wpitch];
         float cen = val(y0, wc);
+#pragma unroll 4
         for (int y = y0; y < y1; ++y) {
             uint32_t wn = 0;
             float dn = 0.f;
@@ -469,6 +472,7 @@ __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
         if (y0 > 0) res_value<RHS, INIT>(a, co, xc, y0 - 1, a.m.known(xc, y0 - 1), uh, ul);
         uint32_t wc = mrow[(size_t)y0 * a.m.wpitch];
         res_value<RHS, INIT>(a, co, xc, y0, (wc >> lane) & 1u, ch_, cl);
+#pragma unroll 4
         for (int y = y0; y < y1; ++y) {
             uint32_t wn = 0;
             if (y + 1 < a.F.H) {
