@@ -142,6 +142,15 @@ int Ctx::tflush() {
 
 static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+// Upper bound on the CTAs per channel of any reducing kernel on an H x W
+// level: column strips of 128 columns x at least 4 rows, and the 32x8 tiles
+// of the tonal residual.
+static inline int reduction_parts(int H, int W) {
+    const int strips = ((W + 127) / 128) * ((H + 3) / 4);
+    const int tiles = ((W + 31) / 32) * ((H + 7) / 8);
+    return std::max(strips, tiles);
+}
+
 // Plans the level sizes, reserves the workspace and carves the buffers.
 int Ctx::setup(int H_, int W_, int nch_, int nmask_) {
     if (H_ == H && W_ == W && nch_ == nch && nmask_ == nmask && ws.base) return HDI_OK;
@@ -164,8 +173,7 @@ int Ctx::setup(int H_, int W_, int nch_, int nmask_) {
         const int wp = (sizes[l].second + 31) / 32 + 1;
         acc((size_t)nmask_ * sizes[l].first * wp * 4);   // bits, one plane per mask
         for (int k = 0; k < 3; ++k) acc((size_t)nch_ * sizes[l].first * P * 4);   // xa, xb, b
-        const int parts = ((sizes[l].second + 31) / 32) * ((sizes[l].first + 7) / 8);
-        maxparts = std::max(maxparts, parts);
+        maxparts = std::max(maxparts, reduction_parts(sizes[l].first, sizes[l].second));
     }
     const int P0 = round_up(W_, 32);
     const size_t n32 = (size_t)nch_ * H_ * P0;
@@ -297,9 +305,9 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     if (l == 0) tstop();
 }
 
-// Grid of the column-strip kernels: 128 columns x CS_ROWS rows per CTA.
 static dim3 tiles_of(const Level& L, int nch) {
-    return dim3((L.W + 127) / 128, (L.H + CS_ROWS - 1) / CS_ROWS, nch);
+    const int r = strip_rows(L.H, L.W, nch);
+    return dim3((L.W + 127) / 128, (L.H + r - 1) / r, nch);
 }
 
 // One V-cycle (Sec. 3.2) on the correction equation A_l x = b_l, x from 0.
@@ -335,7 +343,7 @@ void Ctx::vcycle(int l) {
         dim3 blk(128), grd = tiles_of(L, nch);
         if (l == 0) tstart(kT_Restrict);
         k_restrict_residual<<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, arr(l + 1), mview(l + 1), C.b,
-                                                     reducer(l + 1, grd.x * grd.y));
+                                                     reducer(l + 1, grd.x * grd.y), strip_rows(L.H, L.W, nch));
         ++launches;
         if (l == 0) tstop();
     }
@@ -344,7 +352,7 @@ void Ctx::vcycle(int l) {
         dim3 grd = tiles_of(L, nch), blk(128);
         if (l == 0) tstart(kT_Prolong);
         k_prolong<0><<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, L.xb, arr(l + 1), C.xa,
-                                              reducer(l, grd.x * grd.y));
+                                              reducer(l, grd.x * grd.y), strip_rows(L.H, L.W, nch));
         ++launches;
         if (l == 0) tstop();
     }
@@ -366,7 +374,8 @@ void Ctx::vcycle(int l) {
 void Ctx::residual_norm_level(int l, const float* x, int slot) {
     const Level& L = lev[l];
     dim3 grd = tiles_of(L, nch), blk(128);
-    k_level_residual_norm<<<grd, blk, 0, stream>>>(arr(l), mview(l), x, L.b, reducer(slot, grd.x * grd.y));
+    k_level_residual_norm<<<grd, blk, 0, stream>>>(arr(l), mview(l), x, L.b, reducer(slot, grd.x * grd.y),
+                                                   strip_rows(L.H, L.W, nch));
     ++launches;
 }
 
@@ -388,14 +397,14 @@ void Ctx::fmg(DFc d) {
     {
         dim3 grd = tiles_of(lev[L], nch), blk(128);
         k_prolong<2><<<grd, blk, 0, stream>>>(arr(L), mview(L), nullptr, lev[L].b, lev[L].xb, arr(L), nullptr,
-                                              reducer(L, grd.x * grd.y));
+                                              reducer(L, grd.x * grd.y), strip_rows(lev[L].H, lev[L].W, nch));
         ++launches;
         oras(L, false, lev[L].xb, lev[L].xa, scal + L * kMaxCh, true, nullptr);
     }
     for (int l = L - 1; l >= 0; --l) {
         dim3 grd = tiles_of(lev[l], nch), blk(128);
         k_prolong<1><<<grd, blk, 0, stream>>>(arr(l), mview(l), nullptr, lev[l].b, lev[l].xb, arr(l + 1),
-                                              lev[l + 1].xa, reducer(l, grd.x * grd.y));
+                                              lev[l + 1].xa, reducer(l, grd.x * grd.y), strip_rows(lev[l].H, lev[l].W, nch));
         ++launches;
         oras(l, false, lev[l].xb, lev[l].xa, scal + l * kMaxCh, l == L, l == 0 ? counters + kCntLocal : nullptr);
     }
@@ -412,7 +421,8 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
     a.d = d;
     a.y = y;
     a.r32 = c.lev[0].b;
-    dim3 grd((c.W + 127) / 128, (c.H + CS_ROWS - 1) / CS_ROWS, c.nch), blk(128);
+    a.rows = strip_rows(c.H, c.W, c.nch);
+    dim3 grd((c.W + 127) / 128, (c.H + a.rows - 1) / a.rows, c.nch), blk(128);
     a.red_r = c.reducer(kSlotR64, grd.x * grd.y);
     a.red_b = c.reducer(kSlotB64, grd.x * grd.y);
     a.want_b = want_b ? 1 : 0;
@@ -964,8 +974,7 @@ size_t noalloc_layout(Ctx& c, char* base, size_t cap, int H_, int W_, int nch_) 
     };
     const bool carve = true;
     int maxparts = 1;
-    for (int l = 0; l < nl; ++l)
-        maxparts = std::max(maxparts, ((sizes[l][1] + 31) / 32) * ((sizes[l][0] + 7) / 8));
+    for (int l = 0; l < nl; ++l) maxparts = std::max(maxparts, reduction_parts(sizes[l][0], sizes[l][1]));
     // first pass: size only
     for (int pass = 0; pass < 2; ++pass) {
         off = 0;

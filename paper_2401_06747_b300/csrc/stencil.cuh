@@ -133,14 +133,26 @@ __device__ __forceinline__ float fine_residual(const float* __restrict__ x, cons
 // combined by a shuffle.
 #define CS_ROWS 64
 #define TILE_ROWS 16
+
+// Rows per CTA of the column-strip kernels: long strips on large levels (few
+// CTAs take part in each grid reduction), short ones on small levels, where
+// the serial walk down the rows would otherwise dominate. Always even (the
+// restriction pairs rows).
+static inline int strip_rows(int H, int W, int nch) {
+    const long long cols = (long long)((W + 127) / 128) * nch;
+    long long rows = (long long)H * cols / 2400;   // aim at >= ~2400 CTAs
+    rows = (rows < 4 ? 4LL : (rows > CS_ROWS ? (long long)CS_ROWS : rows));
+    return (int)(rows + (rows & 1));
+}
+
 __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                            const float* __restrict__ b, LevelArr C, MaskView cm,
-                                                           float* __restrict__ cb, GridReduce red) {
+                                                           float* __restrict__ cb, GridReduce red, int rows) {
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
     const int px = x0 + lane;
-    const int y0 = blockIdx.y * CS_ROWS;
-    const int y1 = min(y0 + CS_ROWS, F.H);
+    const int y0 = blockIdx.y * rows;
+    const int y1 = min(y0 + rows, F.H);
     const int ch = blockIdx.z;
     fm = fm.ch(ch);
     cm = cm.ch(ch);
@@ -154,7 +166,6 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
         float up = (y0 > 0) ? xc[(size_t)(y0 - 1) * F.pitch + pxc] : 0.f;
         float cen = xc[(size_t)y0 * F.pitch + pxc];
         float pair = 0.f;
-#pragma unroll 4
         for (int y = y0; y < y1; ++y) {
             const float dn = (y + 1 < F.H) ? xc[(size_t)(y + 1) * F.pitch + pxc] : 0.f;
             float lf = __shfl_up_sync(HDI_FULL, cen, 1);
@@ -192,12 +203,12 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
 
 // ||b - A x||^2 per channel on one level (column strips, FP32).
 __global__ void __launch_bounds__(128) k_level_residual_norm(LevelArr F, MaskView fm, const float* __restrict__ x,
-                                                             const float* __restrict__ b, GridReduce red) {
+                                                             const float* __restrict__ b, GridReduce red, int rows) {
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
     const int px = x0 + lane;
-    const int y0 = blockIdx.y * CS_ROWS;
-    const int y1 = min(y0 + CS_ROWS, F.H);
+    const int y0 = blockIdx.y * rows;
+    const int y1 = min(y0 + rows, F.H);
     const int ch = blockIdx.z;
     fm = fm.ch(ch);
     const bool act = px < F.W;
@@ -209,7 +220,6 @@ __global__ void __launch_bounds__(128) k_level_residual_norm(LevelArr F, MaskVie
         const uint32_t* mrow = fm.bits + (x0 >> 5);
         float up = (y0 > 0) ? xc[(size_t)(y0 - 1) * F.pitch + pxc] : 0.f;
         float cen = xc[(size_t)y0 * F.pitch + pxc];
-#pragma unroll 4
         for (int y = y0; y < y1; ++y) {
             const float dn = (y + 1 < F.H) ? xc[(size_t)(y + 1) * F.pitch + pxc] : 0.f;
             float lf = __shfl_up_sync(HDI_FULL, cen, 1);
@@ -288,12 +298,12 @@ __device__ __forceinline__ float prolong_row(const float* __restrict__ ec, const
 template <int MODE>
 __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const float* __restrict__ xin,
                                                  const float* __restrict__ b, float* __restrict__ xout,
-                                                 LevelArr C, const float* __restrict__ e, GridReduce red) {
+                                                 LevelArr C, const float* __restrict__ e, GridReduce red, int rows) {
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
     const int px = x0 + lane;
-    const int y0 = blockIdx.y * CS_ROWS;
-    const int y1 = min(y0 + CS_ROWS, F.H);
+    const int y0 = blockIdx.y * rows;
+    const int y1 = min(y0 + rows, F.H);
     const int ch = blockIdx.z;
     fm = fm.ch(ch);
     const bool act = px < F.W;
@@ -323,7 +333,6 @@ __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const 
         if (y0 > 0) up = val(y0 - 1, mrow[(size_t)(y0 - 1) * fm.wpitch]);
         uint32_t wc = mrow[(size_t)y0 * fm.wpitch];
         float cen = val(y0, wc);
-#pragma unroll 4
         for (int y = y0; y < y1; ++y) {
             uint32_t wn = 0;
             float dn = 0.f;
@@ -421,6 +430,7 @@ struct ResArgs {
     DFc d;                // data (RHS_DATA) or minuend (RHS_SOURCE)
     DFc y;                // subtrahend (RHS_SOURCE; hi == nullptr means 0)
     float* r32;           // out: residual rounded to FP32 (V-cycle right-hand side)
+    int rows;             // rows per CTA (even)
     GridReduce red_r;     // ||r||^2 per channel
     GridReduce red_b;     // ||b||^2 per channel (only if want_b)
     int want_b;
@@ -458,8 +468,8 @@ __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
     const int x = x0 + lane;
-    const int y0 = blockIdx.y * CS_ROWS;
-    const int y1 = min(y0 + CS_ROWS, a.F.H);
+    const int y0 = blockIdx.y * a.rows;
+    const int y1 = min(y0 + a.rows, a.F.H);
     const int ch = blockIdx.z;
     const long long co = ch * a.F.cs;
     const bool act = x < a.F.W;
@@ -472,7 +482,6 @@ __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
         if (y0 > 0) res_value<RHS, INIT>(a, co, xc, y0 - 1, a.m.known(xc, y0 - 1), uh, ul);
         uint32_t wc = mrow[(size_t)y0 * a.m.wpitch];
         res_value<RHS, INIT>(a, co, xc, y0, (wc >> lane) & 1u, ch_, cl);
-#pragma unroll 4
         for (int y = y0; y < y1; ++y) {
             uint32_t wn = 0;
             if (y + 1 < a.F.H) {

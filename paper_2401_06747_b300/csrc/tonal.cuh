@@ -206,29 +206,46 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
 // stored in FP32 for the local solves, and per channel ||r||^2 and
 // ||f - y||^2 (the tonal MSE numerator). y.hi == nullptr means y = 0 (B^T f).
 // The sums on mask pixels (a few percent of the image) are formed in FP64.
-__global__ void __launch_bounds__(256) k_tonal_residual(LevelArr F, MaskView m, DFc f, DFc y, DFc w,
-                                                        float* __restrict__ r, GridReduce red_r, GridReduce red_e) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_tonal_residual(LevelArr F, MaskView m, DFc f, DFc y, DFc w,
+                                                        float* __restrict__ r, GridReduce red_r, GridReduce red_e,
+                                                        int rows) {
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
+    const int px = x0 + lane;
+    const int y0 = blockIdx.y * rows;
+    const int y1 = min(y0 + rows, F.H);
     const int ch = blockIdx.z;
+    const bool act = px < F.W;
     float se = 0.f, sr = 0.f;
-    for (int band = 0; band < TILE_ROWS; ++band) {
-        const int yy = (blockIdx.y * TILE_ROWS + band) * blockDim.y + threadIdx.y;
-        if (x < F.W && yy < F.H) {
-            const size_t idx = ch * F.cs + (size_t)yy * F.pitch + x;
-            float sh, sl;
-            if (y.hi) df_add(f.hi[idx], f.lo[idx], -y.hi[idx], -y.lo[idx], sh, sl);
-            else { sh = f.hi[idx]; sl = f.lo[idx]; }
-            se += sh * sh;
-            if (m.known(x, yy)) {
-                double acc = (double)sh + (double)sl;
-                if (x > 0 && !m.known(x - 1, yy)) acc += (double)w.hi[idx - 1] + (double)w.lo[idx - 1];
-                if (x + 1 < F.W && !m.known(x + 1, yy)) acc += (double)w.hi[idx + 1] + (double)w.lo[idx + 1];
-                if (yy > 0 && !m.known(x, yy - 1)) acc += (double)w.hi[idx - F.pitch] + (double)w.lo[idx - F.pitch];
-                if (yy + 1 < F.H && !m.known(x, yy + 1))
-                    acc += (double)w.hi[idx + F.pitch] + (double)w.lo[idx + F.pitch];
-                r[idx] = (float)acc;
-                sr += (float)acc * (float)acc;
+    if (x0 < F.W) {
+        const uint32_t* mrow = m.bits + (x0 >> 5);
+        uint32_t wu = (y0 > 0) ? mrow[(size_t)(y0 - 1) * m.wpitch] : 0u;
+        uint32_t wc = mrow[(size_t)y0 * m.wpitch];
+        for (int yy = y0; yy < y1; ++yy) {
+            const uint32_t wd = (yy + 1 < F.H) ? mrow[(size_t)(yy + 1) * m.wpitch] : 0u;
+            if (act) {
+                const size_t idx = ch * F.cs + (size_t)yy * F.pitch + px;
+                float sh, sl;
+                if (y.hi) df_add(f.hi[idx], f.lo[idx], -y.hi[idx], -y.lo[idx], sh, sl);
+                else { sh = f.hi[idx]; sl = f.lo[idx]; }
+                se += sh * sh;
+                if ((wc >> lane) & 1u) {
+                    // B^T (f - y) on a mask pixel: s_K plus w on its unknown neighbours
+                    double acc = (double)sh + (double)sl;
+                    const bool kl = (lane > 0) ? ((wc >> (lane - 1)) & 1u) : (px > 0 && m.known(px - 1, yy));
+                    const bool kr = (lane < 31) ? ((wc >> (lane + 1)) & 1u) : (px + 1 < F.W && m.known(px + 1, yy));
+                    if (px > 0 && !kl) acc += (double)w.hi[idx - 1] + (double)w.lo[idx - 1];
+                    if (px + 1 < F.W && !kr) acc += (double)w.hi[idx + 1] + (double)w.lo[idx + 1];
+                    if (yy > 0 && !((wu >> lane) & 1u)) acc += (double)w.hi[idx - F.pitch] + (double)w.lo[idx - F.pitch];
+                    if (yy + 1 < F.H && !((wd >> lane) & 1u))
+                        acc += (double)w.hi[idx + F.pitch] + (double)w.lo[idx + F.pitch];
+                    const float rv = (float)acc;
+                    r[idx] = rv;
+                    sr += rv * rv;
+                }
             }
+            wu = wc;
+            wc = wd;
         }
     }
     const double tr = (double)block_sum_f(sr);
@@ -443,9 +460,11 @@ int Ctx::tonal_setup() {
 }
 
 void Ctx::tonal_residual(DFc y, DFc w) {
-    dim3 blk(32, 8), grd((W + 31) / 32, ((H + 7) / 8 + TILE_ROWS - 1) / TILE_ROWS, nch);
+    const int rows = strip_rows(H, W, nch);
+    dim3 blk(128), grd((W + 127) / 128, (H + rows - 1) / rows, nch);
     k_tonal_residual<<<grd, blk, 0, stream>>>(arr(0), mview(0), cview(dfv[kF]), y, w, tres,
-                                              reducer(kSlotTonalR, grd.x * grd.y), reducer(kSlotTonalE, grd.x * grd.y));
+                                              reducer(kSlotTonalR, grd.x * grd.y), reducer(kSlotTonalE, grd.x * grd.y),
+                                              rows);
     ++launches;
 }
 
