@@ -65,7 +65,7 @@ def load(path: str | None = None):
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB
+    path = path or os.environ.get("HDI_LIBRARY") or LIB
     if not os.path.exists(path):
         raise RuntimeError(f"libhdi.so not found at {path}; run paper_2401_06747_b300/build.py")
     lib = ctypes.CDLL(path)
