@@ -147,13 +147,16 @@ struct OrasArgs {
     unsigned long long* iters; // optional: total local CG iterations
 };
 
+// Launch bounds: 4 CTAs per SM caps the register file at 128 per thread
+// (16 warps per SM; the compiler spills a few values of the local CG to L1),
+// which measured faster than 255 registers at 8 warps per SM.
 // One ORAS iteration (Sec. 3.1): u <- u + sum_i R~_i^T v_i with
 // A_i v_i = R_i (b - A u). Restricted extension: each pixel takes the
 // correction of the one subdomain whose core (the subdomain minus half the
 // overlap on each inner side) contains it, so every output pixel is written
 // by exactly one warp and the sweep needs no atomics.
 template <bool ZERO, bool FULL>
-__global__ void __launch_bounds__(128) k_oras(OrasArgs a) {
+__global__ void __launch_bounds__(128, 4) k_oras(OrasArgs a) {
     const int wid = blockIdx.x * 4 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int nb = a.nbx * a.nby;

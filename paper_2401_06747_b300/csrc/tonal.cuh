@@ -83,7 +83,7 @@ struct EchoArgs {
 
 // One warp per (subdomain, mask pixel k): solve the Neumann subdomain problem
 // L_UU x = L_UK e_k by CG; x = S e_k is stored row-major over the 32x32 tile.
-__global__ void __launch_bounds__(128) k_tonal_echo(EchoArgs a) {
+__global__ void __launch_bounds__(128, 4) k_tonal_echo(EchoArgs a) {
     const long long e = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int total = a.off[a.nb];
