@@ -462,186 +462,78 @@ __device__ __forceinline__ void res_value(const ResArgs& a, long long co, int x,
     }
 }
 
-// Asynchronous global->shared copies of 16 bytes (cp.async, L2 only).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-#define RP_S 8   // raw rows in flight per CTA of the residual pipeline
-
-// The refinement residual, pipelined: a CTA covers 128 columns x `rows`
-// rows; the raw rows it reads (iterate hi/lo, correction, source terms) are
-// brought into a ring of RP_S shared-memory stages by cp.async, so that many
-// rows are in flight per CTA without holding registers. Each arriving row is
-// transformed once (INIT mode, Dirichlet values) into a three-row window with
-// halo columns, from which the error-free residual of the middle row is
-// formed. Rows are processed top to bottom; every output is written once.
 template <int RHS, int INIT>
 __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
-    constexpr bool NU = (INIT == INIT_KEEP || INIT == INIT_UPDATE);
-    constexpr bool NE = (INIT == INIT_UPDATE || INIT == INIT_FROM32);
-    constexpr bool NS = (RHS == RHS_SOURCE);
-    constexpr int NA = (NU ? 2 : 0) + (NE ? 1 : 0) + (NS ? 4 : 0);
-    constexpr int NAS = NA > 0 ? NA : 1;
-    __shared__ __align__(16) float raw[RP_S][NAS][128];
-    __shared__ float th[3][130], tl[3][130];     // transformed rows, halo columns at 0 and 129
-    __shared__ float tbh[3][128], tbl[3][128];   // RHS_SOURCE: b = d - y of the row
-    __shared__ unsigned char tk[3][128];         // known flags of the row
     a.m = a.m.ch(blockIdx.z);
-    const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * 128;
-    const int px = x0 + tid;
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
+    const int x = x0 + lane;
     const int y0 = blockIdx.y * a.rows;
     const int y1 = min(y0 + a.rows, a.F.H);
     const int ch = blockIdx.z;
     const long long co = ch * a.F.cs;
-    const int P = a.F.pitch;
-    const bool ynull = (a.y.hi == nullptr);
-
-    // source array k of the raw stage
-    auto src = [&](int k) -> const float* {
-        int j = 0;
-        if (NU) {
-            if (k == j) return a.uin.hi + co;
-            if (k == j + 1) return a.uin.lo + co;
-            j += 2;
-        }
-        if (NE) {
-            if (k == j) return a.x32 + co;
-            j += 1;
-        }
-        if (k == j) return a.d.hi + co;
-        if (k == j + 1) return a.d.lo + co;
-        if (k == j + 2) return ynull ? nullptr : a.y.hi + co;
-        return ynull ? nullptr : a.y.lo + co;
-    };
-    // issue the copies of raw row r (sequence number seq) into stage seq % RP_S
-    auto issue = [&](int seq) {
-        const int r = y0 - 1 + seq;
-        if (NA > 0 && r >= 0 && r < a.F.H && r <= y1) {
-#pragma unroll
-            for (int pc = tid; pc < NA * 32; pc += 128) {
-                const int k = pc >> 5, q = (pc & 31) * 4;
-                const float* g = src(k);
-                if (g && x0 + q < P) cp_async16(&raw[seq % RP_S][k][q], g + (size_t)r * P + x0 + q);
-            }
-        }
-        cp_async_commit();
-    };
-    // transform raw row r (sequence seq) into window slot r % 3
-    auto transform = [&](int seq) {
-        const int r = y0 - 1 + seq;
-        if (r < 0 || r >= a.F.H) return;
-        const int slot = r % 3;
-        const int st = seq % RP_S;
-        if (px < a.F.W) {
-            const bool known = a.m.known(px, r);
-            float h = 0.f, l = 0.f;
-            int j = 0;
-            float uh = 0.f, ul = 0.f, e = 0.f;
-            if (NU) { uh = raw[st][0][tid]; ul = raw[st][1][tid]; j = 2; }
-            if (NE) { e = raw[st][j][tid]; j += 1; }
-            if (known) {
-                if (RHS == RHS_DATA) {
-                    const size_t idx = co + (size_t)r * P + px;
-                    h = a.d.hi[idx];
-                    l = a.d.lo[idx];
-                }
-            } else if (INIT == INIT_KEEP) {
-                h = uh; l = ul;
-            } else if (INIT == INIT_UPDATE) {
-                df_add(uh, ul, e, 0.f, h, l);
-            } else if (INIT == INIT_FROM32) {
-                h = e;
-            }
-            th[slot][tid + 1] = h;
-            tl[slot][tid + 1] = l;
-            tk[slot][tid] = known;
-            if (NS) {
-                float bh = 0.f, bl = 0.f;
-                if (!known) {
-                    const float dh = raw[st][j][tid], dl = raw[st][j + 1][tid];
-                    const float yh = ynull ? 0.f : raw[st][j + 2][tid], yl = ynull ? 0.f : raw[st][j + 3][tid];
-                    df_add(dh, dl, -yh, -yl, bh, bl);
-                }
-                tbh[slot][tid] = bh;
-                tbl[slot][tid] = bl;
-            }
-        }
-        if (tid == 0 && x0 > 0) {
-            float h, l;
-            res_value<RHS, INIT>(a, co, x0 - 1, r, a.m.known(x0 - 1, r), h, l);
-            th[slot][0] = h;
-            tl[slot][0] = l;
-        }
-        if (tid == 127 && x0 + 128 < a.F.W) {
-            float h, l;
-            res_value<RHS, INIT>(a, co, x0 + 128, r, a.m.known(x0 + 128, r), h, l);
-            th[slot][129] = h;
-            tl[slot][129] = l;
-        }
-    };
-
+    const bool act = x < a.F.W;
+    const int xc = act ? x : a.F.W - 1;
+    const bool strip = x0 < a.F.W;
     float rr = 0.f, bb2 = 0.f;
-    for (int i = 0; i < RP_S; ++i) issue(i);
-    cp_async_wait<RP_S - 2>();
-    __syncthreads();
-    transform(0);
-    transform(1);
-    __syncthreads();
-    issue(RP_S);
-    issue(RP_S + 1);
-    for (int y = y0; y < y1; ++y) {
-        const int g = y - y0 + 2;   // sequence number of row y + 1
-        cp_async_wait<RP_S - 1>();
-        __syncthreads();
-        transform(g);
-        __syncthreads();
-        if (px < a.F.W) {
-            const int sc = y % 3, su = (y + 2) % 3, sd = (y + 1) % 3;
-            const size_t idx = co + (size_t)y * P + px;
-            const float ch_ = th[sc][tid + 1], cl = tl[sc][tid + 1];
-            a.uout.hi[idx] = ch_;
-            a.uout.lo[idx] = cl;
-            float r = 0.f;
-            if (tk[sc][tid]) {
-                if (RHS == RHS_DATA) { const float bh = ch_ + cl; bb2 += bh * bh; }
-            } else {
-                float sh = 0.f, sl = 0.f;
-                const float nh[4] = {th[sc][tid], th[sc][tid + 2], th[su][tid + 1], th[sd][tid + 1]};
-                const float nl[4] = {tl[sc][tid], tl[sc][tid + 2], tl[su][tid + 1], tl[sd][tid + 1]};
-                const bool ok[4] = {px > 0, px + 1 < a.F.W, y > 0, y + 1 < a.F.H};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (ok[k]) {
-                        float e1, e2, s2, t2;
-                        two_sum(ch_, -nh[k], e1, e2);
-                        e2 += cl - nl[k];
-                        two_sum(sh, e1, s2, t2);
-                        sh = s2;
-                        sl += t2 + e2;
-                    }
-                }
-                float bh = 0.f, bl = 0.f;
-                if (NS) {
-                    bh = tbh[sc][tid];
-                    bl = tbl[sc][tid];
-                    bb2 += bh * bh;
-                }
-                float rh2, rl2;
-                df_add(bh, bl, -sh, -sl, rh2, rl2);
-                r = rh2 + rl2;
+    if (strip) {
+        const uint32_t* mrow = a.m.bits + (x0 >> 5);
+        float uh = 0.f, ul = 0.f, ch_ = 0.f, cl = 0.f, dh = 0.f, dl = 0.f;
+        if (y0 > 0) res_value<RHS, INIT>(a, co, xc, y0 - 1, a.m.known(xc, y0 - 1), uh, ul);
+        uint32_t wc = mrow[(size_t)y0 * a.m.wpitch];
+        res_value<RHS, INIT>(a, co, xc, y0, (wc >> lane) & 1u, ch_, cl);
+        for (int y = y0; y < y1; ++y) {
+            uint32_t wn = 0;
+            if (y + 1 < a.F.H) {
+                wn = mrow[(size_t)(y + 1) * a.m.wpitch];
+                res_value<RHS, INIT>(a, co, xc, y + 1, (wn >> lane) & 1u, dh, dl);
             }
-            a.r32[idx] = r;
-            rr += r * r;
+            float lh = __shfl_up_sync(HDI_FULL, ch_, 1), ll = __shfl_up_sync(HDI_FULL, cl, 1);
+            float rh = __shfl_down_sync(HDI_FULL, ch_, 1), rl = __shfl_down_sync(HDI_FULL, cl, 1);
+            if (lane == 0 && x > 0) res_value<RHS, INIT>(a, co, x - 1, y, a.m.known(x - 1, y), lh, ll);
+            if (lane == 31 && x + 1 < a.F.W) res_value<RHS, INIT>(a, co, x + 1, y, a.m.known(x + 1, y), rh, rl);
+            const bool known = (wc >> lane) & 1u;
+            if (act) {
+                const size_t idx = co + (size_t)y * a.F.pitch + x;
+                a.uout.hi[idx] = ch_;
+                a.uout.lo[idx] = cl;
+                float r = 0.f;
+                if (known) {
+                    if (RHS == RHS_DATA) { const float bh = ch_ + cl; bb2 += bh * bh; }
+                } else {
+                    float sh = 0.f, sl = 0.f;
+                    const float nh[4] = {lh, rh, uh, dh};
+                    const float nl[4] = {ll, rl, ul, dl};
+                    const bool ok[4] = {x > 0, x + 1 < a.F.W, y > 0, y + 1 < a.F.H};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (ok[k]) {
+                            float e1, e2, s2, t2;
+                            two_sum(ch_, -nh[k], e1, e2);
+                            e2 += cl - nl[k];
+                            two_sum(sh, e1, s2, t2);
+                            sh = s2;
+                            sl += t2 + e2;
+                        }
+                    }
+                    float bh = 0.f, bl = 0.f;
+                    if (RHS == RHS_SOURCE) {
+                        const float yh = a.y.hi ? a.y.hi[idx] : 0.f, yl = a.y.hi ? a.y.lo[idx] : 0.f;
+                        df_add(a.d.hi[idx], a.d.lo[idx], -yh, -yl, bh, bl);
+                        bb2 += bh * bh;
+                    }
+                    float rh2, rl2;
+                    df_add(bh, bl, -sh, -sl, rh2, rl2);
+                    r = rh2 + rl2;
+                }
+                a.r32[idx] = r;
+                rr += r * r;
+            }
+            uh = ch_; ul = cl;
+            ch_ = dh; cl = dl;
+            wc = wn;
         }
-        issue(g + RP_S);
     }
-    cp_async_wait<0>();
     const double tot = (double)block_sum_f(rr);
     grid_reduce_commit(a.red_r, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
     if (a.want_b) {
