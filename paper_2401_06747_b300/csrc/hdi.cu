@@ -329,11 +329,9 @@ void Ctx::vcycle(int l) {
     if (npre > 0) {
         oras(l, true, nullptr, L.xa, pre_norm, false, it);
         have_x = true;
-        // further sweeps take the stop threshold from the norm of the
-        // right-hand side (the residual before the first sweep): a slightly
-        // stricter local stop, and no extra residual pass
         for (int i = 1; i < npre; ++i) {
-            oras(l, false, L.xa, L.xb, pre_norm, false, it);
+            residual_norm_level(l, L.xa, l);
+            oras(l, false, L.xa, L.xb, scal + l * kMaxCh, false, it);
             std::swap(L.xa, L.xb);
         }
     } else {
