@@ -1,9 +1,15 @@
 // oras.cuh -- warp-per-subdomain local solves (Sec. 3.1, Sec. 3.3).
 //
-// One warp owns one 32x32 subdomain: lane l holds column x0+l, and each
-// per-lane register array holds the 32 rows of that column. Vertical stencil
-// neighbours are register neighbours, horizontal ones come from warp
-// shuffles, and CG dot products are warp-shuffle reductions, so a local solve
+// One warp owns one 32x32 subdomain. Lane l holds the column pair
+// c = l & 15 (columns 2c and 2c+1) over the row half hh = l >> 4 (rows
+// 16hh .. 16hh+15); every per-lane array holds 16 float2 values, column 2c
+// in .x and 2c+1 in .y. The pair layout puts two pixels of one row in a
+// 64-bit register pair, so the vector updates and most of the stencil run as
+// packed FP32x2 operations (two results per instruction), and a lane needs
+// one shuffle per row and side for its horizontal neighbours (the inner
+// neighbours of the pair are its own registers). Vertical neighbours are
+// register neighbours, except across the two row halves (one xor-16 shuffle
+// per apply), and CG dot products are warp-shuffle reductions: a local solve
 // touches neither shared memory nor a block barrier.
 //
 // Local operator A_i (Sec. 3.1): the global A restricted to the subdomain,
@@ -20,74 +26,104 @@
 
 struct LocalGeom {
     int x0, y0, w, h;     // subdomain origin and extent (w, h <= 32)
-    uint32_t um;          // this lane's column: bit j set = row j is an unknown pixel
-    float dh;             // horizontal part of d_j for this lane
+    int c, hh;            // this lane's column pair and row half
+    uint32_t um;          // bit 2k+j: pixel (row 16hh+k, column 2c+j) is unknown and inside
+    // -1 where the neighbour lies in the subdomain, else 0: left of column
+    // 2c, right of column 2c+1, above row 0 / below row 15 of this half
+    float nwl, nwr, nwu, nwd;
+    float2 dh;            // horizontal part of d_j for the two columns
     float dtop, dbot;     // weight of the outside neighbour above row 0 / below row h-1
-    // full 32x32 subdomains: the diagonal of row 0, rows 1..30 and row 31,
-    // with lanes 0 and 31 compensated for the shuffle returning their own value
-    float d0, dmid, d31;
+    float2 dfirst, dmid, dlast;   // 32x32 subdomains: diagonal of rows k = 0, 1..14, 15
 };
 
-__device__ __forceinline__ float local_diag(const LocalGeom& g, int j) {
-    const float up = (j > 0) ? 1.f : g.dtop;
-    const float dn = (j < g.h - 1) ? 1.f : g.dbot;
-    return g.dh + up + dn;
-}
+// Per-warp shared-memory slab of the local CG: the 0/1 unknown-pixel mask of
+// the lane's 32 pixels as float2 (lane-private: each lane reads back only
+// what it wrote, so no synchronisation is needed). Multiplying by it inside
+// the packed stencil replaces a per-pixel bit test and select.
+constexpr int kLocalSlab = 16 * 32;   // float2 per warp
 
-__device__ __forceinline__ LocalGeom make_geom(int x0, int y0, int H, int W, const MaskView& m, float theta) {
+// Geometry of subdomain (x0, y0); writes the lane's mask floats to msk[k * 32]
+// (msk = warp slab + lane).
+__device__ __forceinline__ LocalGeom make_geom(int x0, int y0, int H, int W, const MaskView& m, float theta,
+                                               float2* msk) {
     const int lane = threadIdx.x & 31;
     LocalGeom g;
     g.x0 = x0;
     g.y0 = y0;
     g.w = min(32, W - x0);
     g.h = min(32, H - y0);
-    const int gx = x0 + lane;
-    const bool act = lane < g.w;
+    g.c = lane & 15;
+    g.hh = lane >> 4;
+    const int c0 = 2 * g.c, r0 = 16 * g.hh;
+    // lane l fetches the mask word of row l (rows past the subdomain read as known)
+    const uint32_t wrow = (lane < g.h) ? m.window(x0, y0 + lane) : ~0u;
     uint32_t um = 0;
-#pragma unroll 4
-    for (int j = 0; j < 32; ++j) {
-        if (j < g.h) {
-            const uint32_t word = m.window(x0, y0 + j);
-            const bool known = (word >> lane) & 1u;
-            if (act && !known) um |= 1u << j;
-        }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const uint32_t kn = __shfl_sync(HDI_FULL, wrow, r0 + k) >> c0;   // bit 0: column c0, bit 1: c0 + 1
+        const bool u0 = c0 < g.w && !(kn & 1u), u1 = c0 + 1 < g.w && !(kn & 2u);
+        um |= (u0 ? 1u : 0u) << (2 * k);
+        um |= (u1 ? 1u : 0u) << (2 * k + 1);
+        msk[k * 32] = make_float2(u0 ? 1.f : 0.f, u1 ? 1.f : 0.f);
     }
     g.um = um;
-    const float left = (lane > 0) ? 1.f : (gx > 0 ? theta : 0.f);
-    const float right = (lane < g.w - 1) ? 1.f : (gx < W - 1 ? theta : 0.f);
-    g.dh = left + right;
+    auto horiz = [&](int C) {
+        const int gx = x0 + C;
+        const float left = (C > 0) ? 1.f : (gx > 0 ? theta : 0.f);
+        const float right = (C < g.w - 1) ? 1.f : (gx < W - 1 ? theta : 0.f);
+        return left + right;
+    };
+    g.dh = make_float2(horiz(c0), horiz(c0 + 1));
     g.dtop = (y0 > 0) ? theta : 0.f;
     g.dbot = (y0 + g.h < H) ? theta : 0.f;
-    const float dhc = g.dh + ((lane == 0) ? 1.f : 0.f) + ((lane == 31) ? 1.f : 0.f);
-    g.d0 = dhc + 1.f + g.dtop;
-    g.dmid = dhc + 2.f;
-    g.d31 = dhc + 1.f + g.dbot;
+    g.nwl = (g.c > 0) ? -1.f : 0.f;
+    g.nwr = (g.c < 15) ? -1.f : 0.f;
+    g.nwu = g.hh ? -1.f : 0.f;
+    g.nwd = g.hh ? 0.f : -1.f;
+    const float vf = g.hh ? 2.f : 1.f + g.dtop;
+    const float vl = g.hh ? 1.f + g.dbot : 2.f;
+    g.dfirst = make_float2(g.dh.x + vf, g.dh.y + vf);
+    g.dmid = make_float2(g.dh.x + 2.f, g.dh.y + 2.f);
+    g.dlast = make_float2(g.dh.x + vl, g.dh.y + vl);
     return g;
 }
 
-// q = A_i p on the unknown pixels (p is zero on known / invalid pixels).
-// FULL: the subdomain is 32x32, so the row diagonal is known at compile time
-// and the edge lanes keep the value the shuffle returns (their own p, which
-// d0/dmid/d31 compensate) instead of selecting zero.
+// Diagonal of row k of this lane's half (both columns).
 template <bool FULL>
-__device__ __forceinline__ void local_apply(const LocalGeom& g, const float (&p)[32], float (&q)[32]) {
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ float2 local_diag(const LocalGeom& g, int k) {
+    if (FULL) return (k == 0) ? g.dfirst : ((k == 15) ? g.dlast : g.dmid);
+    const int R = 16 * g.hh + k;
+    const float v = ((R > 0) ? 1.f : g.dtop) + ((R < g.h - 1) ? 1.f : g.dbot);
+    return make_float2(g.dh.x + v, g.dh.y + v);
+}
+
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+    return make_float2(__shfl_xor_sync(HDI_FULL, v.x, m), __shfl_xor_sync(HDI_FULL, v.y, m));
+}
+
+// Q = A_i P on the unknown pixels (P is zero on known / outside pixels, so
+// shuffles that fetch such pixels contribute zero; neighbours outside the
+// subdomain carry weight 0). Q = d P + M (-neighbour sum) with M the 0/1
+// mask: on a known pixel P = 0 and M = 0, so Q = 0 there.
+template <bool FULL>
+__device__ __forceinline__ void local_apply(const LocalGeom& g, const float2* __restrict__ msk,
+                                            const float2 (&P)[16], float2 (&Q)[16]) {
+    const float2 U = shfl_xor2(P[15], 16);   // row 15 of the upper half (used by the lower half)
+    const float2 D = shfl_xor2(P[0], 16);    // row 16 of the lower half (used by the upper half)
+    const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        float pl = __shfl_up_sync(HDI_FULL, p[j], 1);
-        float pr = __shfl_down_sync(HDI_FULL, p[j], 1);
-        if (!FULL) {
-            if (lane == 0) pl = 0.f;
-            if (lane == 31) pr = 0.f;
-        }
-        float s = pl + pr;
-        if (j > 0) s += p[j - 1];
-        if (j < 31) s += p[j + 1];
-        float d;
-        if (FULL) d = (j == 0) ? g.d0 : ((j == 31) ? g.d31 : g.dmid);
-        else d = local_diag(g, j);
-        const float v = d * p[j] - s;
-        q[j] = ((g.um >> j) & 1u) ? v : 0.f;
+    for (int k = 0; k < 16; ++k) {
+        const float2 mk = msk[k * 32];
+        const float L = __shfl_up_sync(HDI_FULL, P[k].y, 1);     // column 2c-1
+        const float Rt = __shfl_down_sync(HDI_FULL, P[k].x, 1);  // column 2c+2
+        float2 ns;   // minus the neighbour sum
+        ns.x = fmaf(g.nwl, L, -P[k].y);
+        ns.y = fmaf(g.nwr, Rt, -P[k].x);
+        if (k > 0) ns = __ffma2_rn(m1, P[k - 1], ns);
+        else ns = __ffma2_rn(make_float2(g.nwu, g.nwu), U, ns);
+        if (k < 15) ns = __ffma2_rn(m1, P[k + 1], ns);
+        else ns = __ffma2_rn(make_float2(g.nwd, g.nwd), D, ns);
+        Q[k] = __ffma2_rn(mk, ns, __fmul2_rn(local_diag<FULL>(g, k), P[k]));
     }
 }
 
@@ -95,37 +131,47 @@ __device__ __forceinline__ void local_apply(const LocalGeom& g, const float (&p)
 // side on entry and the final residual on exit). Stops when ||r||^2 <= thresh
 // or after maxit iterations; returns the iteration count.
 template <bool FULL>
-__device__ __forceinline__ int local_cg(const LocalGeom& g, float (&v)[32], float (&r)[32], float thresh, int maxit) {
-    float p[32], q[32];
-    float rr = 0.f;
+__device__ __forceinline__ int local_cg(const LocalGeom& g, const float2* __restrict__ msk, float2 (&V)[16],
+                                        float2 (&R)[16], float thresh, int maxit) {
+    float2 P[16], Q[16];
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        v[j] = 0.f;
-        p[j] = r[j];
-        rr += r[j] * r[j];
+    for (int k = 0; k < 16; ++k) {
+        V[k] = make_float2(0.f, 0.f);
+        P[k] = R[k];
+        if (k & 1) a1 = __ffma2_rn(R[k], R[k], a1);
+        else a0 = __ffma2_rn(R[k], R[k], a0);
     }
-    rr = warp_sum_f(rr);
+    float rr = warp_sum_f((a0.x + a0.y) + (a1.x + a1.y));
     int it = 0;
     while (rr > thresh && it < maxit) {
-        local_apply<FULL>(g, p, q);
-        float pq = 0.f;
+        local_apply<FULL>(g, msk, P, Q);
+        a0 = make_float2(0.f, 0.f);
+        a1 = a0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) pq += p[j] * q[j];
-        pq = warp_sum_f(pq);
+        for (int k = 0; k < 16; ++k) {
+            if (k & 1) a1 = __ffma2_rn(P[k], Q[k], a1);
+            else a0 = __ffma2_rn(P[k], Q[k], a0);
+        }
+        const float pq = warp_sum_f((a0.x + a0.y) + (a1.x + a1.y));
         if (!(pq > 0.f)) break;
         const float alpha = rr / pq;
-        float rn = 0.f;
+        const float2 al = make_float2(alpha, alpha), nal = make_float2(-alpha, -alpha);
+        a0 = make_float2(0.f, 0.f);
+        a1 = a0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            v[j] += alpha * p[j];
-            r[j] -= alpha * q[j];
-            rn += r[j] * r[j];
+        for (int k = 0; k < 16; ++k) {
+            V[k] = __ffma2_rn(al, P[k], V[k]);
+            R[k] = __ffma2_rn(nal, Q[k], R[k]);
+            if (k & 1) a1 = __ffma2_rn(R[k], R[k], a1);
+            else a0 = __ffma2_rn(R[k], R[k], a0);
         }
-        rn = warp_sum_f(rn);
+        const float rn = warp_sum_f((a0.x + a0.y) + (a1.x + a1.y));
         const float beta = rn / rr;
         rr = rn;
+        const float2 be = make_float2(beta, beta);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) p[j] = r[j] + beta * p[j];
+        for (int k = 0; k < 16; ++k) P[k] = __ffma2_rn(be, P[k], R[k]);
         ++it;
     }
     return it;
@@ -147,18 +193,17 @@ struct OrasArgs {
     unsigned long long* iters; // optional: total local CG iterations
 };
 
-// Launch bounds: 4 CTAs per SM caps the register file at 128 per thread
-// (16 warps per SM; the compiler spills a few values of the local CG to L1),
-// which measured faster than 255 registers at 8 warps per SM.
+// Launch bounds: 3 CTAs of 4 warps per SM leave 168 registers per thread,
+// enough for the four 32-value vectors of the local CG without spills.
 // One ORAS iteration (Sec. 3.1): u <- u + sum_i R~_i^T v_i with
 // A_i v_i = R_i (b - A u). Restricted extension: each pixel takes the
 // correction of the one subdomain whose core (the subdomain minus half the
 // overlap on each inner side) contains it, so every output pixel is written
 // by exactly one warp and the sweep needs no atomics.
 template <bool ZERO, bool FULL>
-__global__ void __launch_bounds__(128, 4) k_oras(OrasArgs a) {
+__global__ void __launch_bounds__(128, 3) k_oras(OrasArgs a) {
+    __shared__ float2 slab[4 * kLocalSlab];
     const int wid = blockIdx.x * 4 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
     const int nb = a.nbx * a.nby;
     if (wid >= nb * a.nch) return;
     const int ch = wid / nb;
@@ -166,49 +211,73 @@ __global__ void __launch_bounds__(128, 4) k_oras(OrasArgs a) {
     const int by = bi / a.nbx;
     const int bx = bi - by * a.nbx;
     const int x0 = sub_origin(bx, a.W, a.stride), y0 = sub_origin(by, a.H, a.stride);
-    const LocalGeom g = make_geom(x0, y0, a.H, a.W, a.m.ch(ch), a.theta);
-    const int gx = x0 + lane;
-    const bool act = lane < g.w;
-    const int gxc = act ? gx : (a.W - 1);   // clamped column for safe loads
-    const float* xin = a.xin + ch * a.cstride;
-    const float* bb = a.b + ch * a.cstride;
+    const double rn2 = a.rnorm2[ch];
+    float2* msk = slab + (threadIdx.x >> 5) * kLocalSlab + (threadIdx.x & 31);
+    const LocalGeom g = make_geom(x0, y0, a.H, a.W, a.m.ch(ch), a.theta, msk);
+    const int c0 = 2 * g.c, r0 = 16 * g.hh;
+    const int gx = x0 + c0;                       // absolute column of .x
+    const int cx0 = min(gx, a.W - 1), cx1 = min(gx + 1, a.W - 1);
+    // 8-byte aligned pair inside the image: one float2 access per row
+    const bool vec = !(x0 & 1) && x0 + 32 <= a.W;
+    const float* __restrict__ xin = a.xin + ch * a.cstride;
+    const float* __restrict__ bb = a.b + ch * a.cstride;
+    auto ld2 = [&](const float* __restrict__ p, int y) {
+        const size_t row = (size_t)min(max(y, 0), a.H - 1) * a.pitch;
+        if (vec) return *reinterpret_cast<const float2*>(p + row + gx);
+        return make_float2(p[row + cx0], p[row + cx1]);
+    };
 
-    float r[32], v[32];
-    if (ZERO) {
+    float2 R[16], V[16];
+    {
+        float2 B[16];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int y = min(y0 + j, a.H - 1);
-            const float bv = bb[(size_t)y * a.pitch + gxc];
-            r[j] = ((g.um >> j) & 1u) ? bv : 0.f;
-        }
-    } else {
-        // R_i (b - A x) in difference form (sum of neighbour differences).
-        const bool has_l = (lane == 0) && (gx > 0);
-        const bool has_r = (lane == g.w - 1) && (gx + 1 < a.W);
-        float xu = xin[(size_t)max(y0 - 1, 0) * a.pitch + gxc];
-        float xc = xin[(size_t)y0 * a.pitch + gxc];
+        for (int k = 0; k < 16; ++k) B[k] = ld2(bb, y0 + r0 + k);
+        if (ZERO) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int y = min(y0 + j, a.H - 1);
-            const int yn = min(y + 1, a.H - 1);
-            const float xd = xin[(size_t)yn * a.pitch + gxc];
-            float xl = __shfl_up_sync(HDI_FULL, xc, 1);
-            float xr = __shfl_down_sync(HDI_FULL, xc, 1);
-            if (lane == 0) xl = has_l ? xin[(size_t)y * a.pitch + gx - 1] : xc;
-            if (has_r) xr = xin[(size_t)y * a.pitch + gx + 1];
-            else if (lane == g.w - 1) xr = xc;
-            const float bv = bb[(size_t)y * a.pitch + gxc];
-            const float up = (y > 0) ? xu : xc;
-            const float dn = (y + 1 < a.H) ? xd : xc;
-            const float lap = ((xc - xl) + (xc - xr)) + ((xc - up) + (xc - dn));
-            r[j] = ((g.um >> j) & 1u) ? (bv - lap) : 0.f;
-            xu = xc;
-            xc = xd;
+            for (int k = 0; k < 16; ++k) {
+                R[k].x = ((g.um >> (2 * k)) & 1u) ? B[k].x : 0.f;
+                R[k].y = ((g.um >> (2 * k + 1)) & 1u) ? B[k].y : 0.f;
+            }
+        } else {
+            // R_i (b - A x) in difference form (sum of neighbour differences);
+            // out-of-image neighbours take the centre value (zero difference).
+            // All loads are issued before the arithmetic.
+            const bool hl = (g.c == 0 && x0 > 0) || (g.c == 15 && x0 + 32 < a.W);
+            const int hcol = hl ? ((g.c == 0) ? x0 - 1 : x0 + 32) : cx0;
+            float2 X[18];
+            float HV[16];
+#pragma unroll
+            for (int t = 0; t < 18; ++t) X[t] = ld2(xin, y0 + r0 - 1 + t);
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                HV[k] = hl ? xin[(size_t)min(y0 + r0 + k, a.H - 1) * a.pitch + hcol] : 0.f;
+            const bool in1 = gx + 1 < a.W;        // column of .y inside the image
+            const bool in2 = gx + 2 < a.W;        // column right of the pair inside the image
+            const bool inl = gx > 0;              // column left of the pair inside the image
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int y = y0 + r0 + k;
+                const float2 up = X[k], xc = X[k + 1], dn = X[k + 2];
+                float L = __shfl_up_sync(HDI_FULL, xc.y, 1);
+                float Rt = __shfl_down_sync(HDI_FULL, xc.x, 1);
+                if (g.c == 0) L = hl ? HV[k] : xc.x;
+                if (g.c == 15) Rt = hl ? HV[k] : xc.y;
+                if (!inl) L = xc.x;
+                if (!in2) Rt = xc.y;
+                const float rx = in1 ? xc.y : xc.x;   // right neighbour of .x
+                const bool hu = y > 0, hd = y + 1 < a.H;
+                const float lapx =
+                    ((xc.x - L) + (xc.x - rx)) + ((xc.x - (hu ? up.x : xc.x)) + (xc.x - (hd ? dn.x : xc.x)));
+                const float lapy =
+                    ((xc.y - xc.x) + (xc.y - Rt)) + ((xc.y - (hu ? up.y : xc.y)) + (xc.y - (hd ? dn.y : xc.y)));
+                R[k].x = ((g.um >> (2 * k)) & 1u) ? (B[k].x - lapx) : 0.f;
+                R[k].y = ((g.um >> (2 * k + 1)) & 1u) ? (B[k].y - lapy) : 0.f;
+            }
         }
     }
-    const float thresh = (float)(a.rnorm2[ch] * a.thresh_scale);
-    const int it = local_cg<FULL>(g, v, r, thresh, a.maxit);
-    if (a.iters && lane == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
+    const float thresh = (float)(rn2 * a.thresh_scale);
+    const int it = local_cg<FULL>(g, msk, V, R, thresh, a.maxit);
+    if (a.iters && (threadIdx.x & 31) == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
 
     // owned core in absolute coordinates, then relative to the (possibly
     // shifted) origin
@@ -216,13 +285,28 @@ __global__ void __launch_bounds__(128, 4) k_oras(OrasArgs a) {
     const int ox1 = ((bx == a.nbx - 1) ? a.W : (bx + 1) * a.stride + a.ov / 2) - x0;
     const int oy0 = ((by == 0) ? 0 : by * a.stride + a.ov / 2) - y0;
     const int oy1 = ((by == a.nby - 1) ? a.H : (by + 1) * a.stride + a.ov / 2) - y0;
-    if (lane >= ox0 && lane < ox1) {
-        float* xo = a.xout + ch * a.cstride;
+    const bool w0 = c0 >= ox0 && c0 < ox1, w1 = c0 + 1 >= ox0 && c0 + 1 < ox1;
+    if (w0 || w1) {
+        float* __restrict__ xo = a.xout + ch * a.cstride;
+        if (!ZERO) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j >= oy0 && j < oy1) {
-                const size_t idx = (size_t)(y0 + j) * a.pitch + gx;
-                xo[idx] = ZERO ? v[j] : (xin[idx] + v[j]);
+            for (int k = 0; k < 16; ++k) {
+                const float2 xv = ld2(xin, y0 + r0 + k);
+                V[k].x += xv.x;
+                V[k].y += xv.y;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int R0 = r0 + k;
+            if (R0 >= oy0 && R0 < oy1) {
+                const size_t idx = (size_t)(y0 + R0) * a.pitch + gx;
+                if (w0 && w1 && vec) {
+                    *reinterpret_cast<float2*>(xo + idx) = V[k];
+                } else {
+                    if (w0) xo[idx] = V[k].x;
+                    if (w1) xo[idx + 1] = V[k].y;
+                }
             }
         }
     }

@@ -83,9 +83,9 @@ struct EchoArgs {
 
 // One warp per (subdomain, mask pixel k): solve the Neumann subdomain problem
 // L_UU x = L_UK e_k by CG; x = S e_k is stored row-major over the 32x32 tile.
-__global__ void __launch_bounds__(128, 4) k_tonal_echo(EchoArgs a) {
+__global__ void __launch_bounds__(128, 3) k_tonal_echo(EchoArgs a) {
+    __shared__ float2 slab[4 * kLocalSlab];
     const long long e = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
     const int total = a.off[a.nb];
     if (e >= total) return;
     // subdomain owning echo e: largest i with off[i] <= e
@@ -97,26 +97,31 @@ __global__ void __launch_bounds__(128, 4) k_tonal_echo(EchoArgs a) {
     const int i = lo;
     const int by = i / a.nbx, bx = i - by * a.nbx;
     const int x0 = sub_origin(bx, a.m.W, a.stride), y0 = sub_origin(by, a.m.H, a.stride);
-    const LocalGeom g = make_geom(x0, y0, a.m.H, a.m.W, a.m, 0.f);
+    float2* msk = slab + (threadIdx.x >> 5) * kLocalSlab + (threadIdx.x & 31);
+    const LocalGeom g = make_geom(x0, y0, a.m.H, a.m.W, a.m, 0.f, msk);
     const int code = a.list[e];
     const int ky = code >> 5, kx = code & 31;
+    const int c0 = 2 * g.c, r0 = 16 * g.hh;
     // right-hand side L_UK e_k: -1 at the unknown 4-neighbours of k inside the subdomain
-    float r[32], v[32];
+    float2 R[16], V[16];
+    float2 a0 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const bool nb = (lane == kx && (j == ky - 1 || j == ky + 1)) || (j == ky && (lane == kx - 1 || lane == kx + 1));
-        r[j] = (nb && ((g.um >> j) & 1u)) ? -1.f : 0.f;
+    for (int k = 0; k < 16; ++k) {
+        const int y = r0 + k;
+        const bool nx = (c0 == kx && (y == ky - 1 || y == ky + 1)) || (y == ky && (c0 == kx - 1 || c0 == kx + 1));
+        const bool ny =
+            (c0 + 1 == kx && (y == ky - 1 || y == ky + 1)) || (y == ky && (c0 + 1 == kx - 1 || c0 + 1 == kx + 1));
+        R[k].x = (nx && ((g.um >> (2 * k)) & 1u)) ? -1.f : 0.f;
+        R[k].y = (ny && ((g.um >> (2 * k + 1)) & 1u)) ? -1.f : 0.f;
+        a0 = __ffma2_rn(R[k], R[k], a0);
     }
-    float rr0 = 0.f;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) rr0 += r[j] * r[j];
-    rr0 = warp_sum_f(rr0);
-    const int it = (g.w == 32 && g.h == 32) ? local_cg<true>(g, v, r, a.rtol2 * rr0, a.maxit)
-                                            : local_cg<false>(g, v, r, a.rtol2 * rr0, a.maxit);
-    if (a.iters && lane == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
+    const float rr0 = warp_sum_f(a0.x + a0.y);
+    const int it = (g.w == 32 && g.h == 32) ? local_cg<true>(g, msk, V, R, a.rtol2 * rr0, a.maxit)
+                                            : local_cg<false>(g, msk, V, R, a.rtol2 * rr0, a.maxit);
+    if (a.iters && (threadIdx.x & 31) == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
     float* out = a.echo + (size_t)e * 1024;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) out[j * 32 + lane] = v[j];
+    for (int k = 0; k < 16; ++k) *reinterpret_cast<float2*>(out + (r0 + k) * 32 + c0) = V[k];
 }
 
 // G_i = I + S_i^T S_i and its Cholesky factor (packed lower, row-major) at
