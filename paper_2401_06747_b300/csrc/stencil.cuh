@@ -132,22 +132,46 @@ __device__ __forceinline__ float fine_residual(const float* __restrict__ x, cons
 // consecutive rows are summed in registers and lane pairs (2j, 2j+1) are
 // combined by a shuffle.
 #define CS_ROWS 64
-#define TILE_ROWS 16
+#define CS_CHUNK 8
 
 // Rows per CTA of the column-strip kernels: long strips on large levels (few
 // CTAs take part in each grid reduction), short ones on small levels, where
 // the serial walk down the rows would otherwise dominate. Always even (the
-// restriction pairs rows).
+// restriction pairs rows) and, from 8 rows on, a multiple of the load chunk.
 static inline int strip_rows(int H, int W, int nch) {
     const long long cols = (long long)((W + 127) / 128) * nch;
     long long rows = (long long)H * cols / 2400;   // aim at >= ~2400 CTAs
     rows = (rows < 4 ? 4LL : (rows > CS_ROWS ? (long long)CS_ROWS : rows));
+    if (rows >= CS_CHUNK) return (int)((rows + CS_CHUNK - 1) / CS_CHUNK * CS_CHUNK);
     return (int)(rows + (rows & 1));
 }
 
+// The column-strip kernels walk their rows in chunks of CS_CHUNK: every load
+// of a chunk (the rows below, the halo columns of lanes 0 and 31, mask words,
+// right-hand sides) is issued before any of its arithmetic, so a warp keeps
+// a chunk's worth of independent loads in flight instead of one row's.
+// Loads past the strip's last row are clamped into the image and unused.
+
+// Halo column of a strip's edge lanes: lane 0 reads column x0 - 1, lane 31
+// column x0 + 32 (the neighbouring strips' edge columns), when inside.
+struct StripHalo {
+    bool on;
+    int col;
+};
+__device__ __forceinline__ StripHalo strip_halo(int lane, int px, int pxc, int W) {
+    StripHalo h;
+    h.on = (lane == 0 && px > 0) || (lane == 31 && px + 1 < W);
+    h.col = h.on ? ((lane == 0) ? px - 1 : px + 1) : pxc;
+    return h;
+}
+
+// r = b - A x on level F with 2x2 sums into the coarse right-hand side
+// (restriction, Sec. 3.2), zero on coarse known pixels, and ||r_c||^2 per
+// channel.
 __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                            const float* __restrict__ b, LevelArr C, MaskView cm,
                                                            float* __restrict__ cb, GridReduce red, int rows) {
+    constexpr int CR = CS_CHUNK;
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
     const int px = x0 + lane;
@@ -163,38 +187,60 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
     float sq = 0.f;
     if (x0 < F.W) {
         const uint32_t* mrow = fm.bits + (x0 >> 5);
+        const StripHalo hl = strip_halo(lane, px, pxc, F.W);
+        const bool hasl = px > 0, hasr = px + 1 < F.W;
+        const int X = min(pxc >> 1, C.W - 1);
+        const uint32_t* cmw = cm.bits + (X >> 5);
         float up = (y0 > 0) ? xc[(size_t)(y0 - 1) * F.pitch + pxc] : 0.f;
         float cen = xc[(size_t)y0 * F.pitch + pxc];
         float pair = 0.f;
-        for (int y = y0; y < y1; ++y) {
-            const float dn = (y + 1 < F.H) ? xc[(size_t)(y + 1) * F.pitch + pxc] : 0.f;
-            float lf = __shfl_up_sync(HDI_FULL, cen, 1);
-            float rt = __shfl_down_sync(HDI_FULL, cen, 1);
-            if (lane == 0 && px > 0) lf = xc[(size_t)y * F.pitch + px - 1];
-            if (lane == 31 && px + 1 < F.W) rt = xc[(size_t)y * F.pitch + px + 1];
-            const bool known = (mrow[(size_t)y * fm.wpitch] >> lane) & 1u;
-            float r = 0.f;
-            if (act && !known) {
-                float lap = 0.f;
-                if (px > 0) lap += cen - lf;
-                if (px + 1 < F.W) lap += cen - rt;
-                if (y > 0) lap += cen - up;
-                if (y + 1 < F.H) lap += cen - dn;
-                r = bc[(size_t)y * F.pitch + px] - lap;
+        for (int yb = y0; yb < y1; yb += CR) {
+            float Xd[CR], Hv[CR], Bv[CR];
+            uint32_t Mw[CR], Cw[CR / 2];
+#pragma unroll
+            for (int k = 0; k < CR; ++k) {
+                const int y = min(yb + k, F.H - 1);
+                const size_t ry = (size_t)y * F.pitch;
+                Xd[k] = xc[(size_t)min(yb + k + 1, F.H - 1) * F.pitch + pxc];
+                Hv[k] = hl.on ? xc[ry + hl.col] : 0.f;
+                Bv[k] = bc[ry + pxc];
+                Mw[k] = mrow[(size_t)y * fm.wpitch];
             }
-            pair += r;
-            if ((y & 1) || y + 1 == F.H) {
-                const float s = pair + __shfl_down_sync(HDI_FULL, pair, 1);
-                const int X = px >> 1, Y = y >> 1;
-                if (!(lane & 1) && act) {
-                    const float v = cm.known(X, Y) ? 0.f : s;
-                    cb[ch * C.cs + (size_t)Y * C.pitch + X] = v;
-                    sq += v * v;
+#pragma unroll
+            for (int k = 0; k < CR / 2; ++k) Cw[k] = cmw[(size_t)min((yb >> 1) + k, C.H - 1) * cm.wpitch];
+#pragma unroll
+            for (int k = 0; k < CR; ++k) {
+                const int y = yb + k;
+                if (y >= y1) break;
+                const float dn = Xd[k];
+                float lf = __shfl_up_sync(HDI_FULL, cen, 1);
+                float rt = __shfl_down_sync(HDI_FULL, cen, 1);
+                if (lane == 0) lf = Hv[k];
+                if (lane == 31) rt = Hv[k];
+                const bool known = (Mw[k] >> lane) & 1u;
+                float r = 0.f;
+                if (act && !known) {
+                    float lap = 0.f;
+                    if (hasl) lap += cen - lf;
+                    if (hasr) lap += cen - rt;
+                    if (y > 0) lap += cen - up;
+                    if (y + 1 < F.H) lap += cen - dn;
+                    r = Bv[k] - lap;
                 }
-                pair = 0.f;
+                pair += r;
+                if ((y & 1) || y + 1 == F.H) {
+                    const float s = pair + __shfl_down_sync(HDI_FULL, pair, 1);
+                    const int Y = y >> 1;
+                    if (!(lane & 1) && act) {
+                        const float v = ((Cw[k >> 1] >> (X & 31)) & 1u) ? 0.f : s;
+                        cb[ch * C.cs + (size_t)Y * C.pitch + X] = v;
+                        sq += v * v;
+                    }
+                    pair = 0.f;
+                }
+                up = cen;
+                cen = dn;
             }
-            up = cen;
-            cen = dn;
         }
     }
     const double tot = (double)block_sum_f(sq);
@@ -204,6 +250,7 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
 // ||b - A x||^2 per channel on one level (column strips, FP32).
 __global__ void __launch_bounds__(128) k_level_residual_norm(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                              const float* __restrict__ b, GridReduce red, int rows) {
+    constexpr int CR = CS_CHUNK;
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
     const int px = x0 + lane;
@@ -218,87 +265,71 @@ __global__ void __launch_bounds__(128) k_level_residual_norm(LevelArr F, MaskVie
     float sq = 0.f;
     if (x0 < F.W) {
         const uint32_t* mrow = fm.bits + (x0 >> 5);
+        const StripHalo hl = strip_halo(lane, px, pxc, F.W);
+        const bool hasl = px > 0, hasr = px + 1 < F.W;
         float up = (y0 > 0) ? xc[(size_t)(y0 - 1) * F.pitch + pxc] : 0.f;
         float cen = xc[(size_t)y0 * F.pitch + pxc];
-        for (int y = y0; y < y1; ++y) {
-            const float dn = (y + 1 < F.H) ? xc[(size_t)(y + 1) * F.pitch + pxc] : 0.f;
-            float lf = __shfl_up_sync(HDI_FULL, cen, 1);
-            float rt = __shfl_down_sync(HDI_FULL, cen, 1);
-            if (lane == 0 && px > 0) lf = xc[(size_t)y * F.pitch + px - 1];
-            if (lane == 31 && px + 1 < F.W) rt = xc[(size_t)y * F.pitch + px + 1];
-            const bool known = (mrow[(size_t)y * fm.wpitch] >> lane) & 1u;
-            if (act && !known) {
-                float lap = 0.f;
-                if (px > 0) lap += cen - lf;
-                if (px + 1 < F.W) lap += cen - rt;
-                if (y > 0) lap += cen - up;
-                if (y + 1 < F.H) lap += cen - dn;
-                const float r = bc[(size_t)y * F.pitch + px] - lap;
-                sq += r * r;
+        for (int yb = y0; yb < y1; yb += CR) {
+            float Xd[CR], Hv[CR], Bv[CR];
+            uint32_t Mw[CR];
+#pragma unroll
+            for (int k = 0; k < CR; ++k) {
+                const int y = min(yb + k, F.H - 1);
+                const size_t ry = (size_t)y * F.pitch;
+                Xd[k] = xc[(size_t)min(yb + k + 1, F.H - 1) * F.pitch + pxc];
+                Hv[k] = hl.on ? xc[ry + hl.col] : 0.f;
+                Bv[k] = bc[ry + pxc];
+                Mw[k] = mrow[(size_t)y * fm.wpitch];
             }
-            up = cen;
-            cen = dn;
+#pragma unroll
+            for (int k = 0; k < CR; ++k) {
+                const int y = yb + k;
+                if (y >= y1) break;
+                const float dn = Xd[k];
+                float lf = __shfl_up_sync(HDI_FULL, cen, 1);
+                float rt = __shfl_down_sync(HDI_FULL, cen, 1);
+                if (lane == 0) lf = Hv[k];
+                if (lane == 31) rt = Hv[k];
+                const bool known = (Mw[k] >> lane) & 1u;
+                if (act && !known) {
+                    float lap = 0.f;
+                    if (hasl) lap += cen - lf;
+                    if (hasr) lap += cen - rt;
+                    if (y > 0) lap += cen - up;
+                    if (y + 1 < F.H) lap += cen - dn;
+                    const float r = Bv[k] - lap;
+                    sq += r * r;
+                }
+                up = cen;
+                cen = dn;
+            }
         }
     }
     const double tot = (double)block_sum_f(sq);
     grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
 }
 
-// Bilinear cell-centred prolongation of coarse e at fine pixel (px, py).
-__device__ __forceinline__ float prolong_at(const float* __restrict__ e, const LevelArr& C, int px, int py) {
-    const int X = px >> 1, Y = py >> 1;
-    const int Xn = (px & 1) ? min(X + 1, C.W - 1) : max(X - 1, 0);
-    const int Yn = (py & 1) ? min(Y + 1, C.H - 1) : max(Y - 1, 0);
-    const float* r0 = e + (size_t)Y * C.pitch;
-    const float* r1 = e + (size_t)Yn * C.pitch;
-    // same operation order as prolong_row / the column-strip kernel
-    const float h0 = __fadd_rn(__fmul_rn(0.75f, r0[X]), __fmul_rn(0.25f, r0[Xn]));
-    const float h1 = __fadd_rn(__fmul_rn(0.75f, r1[X]), __fmul_rn(0.25f, r1[Xn]));
-    return __fadd_rn(__fmul_rn(0.75f, h0), __fmul_rn(0.25f, h1));
-}
-
-// Tiles of 32x8 pixels (used by the staging helpers' grids).
-#define PT_W 32
-#define PT_H 8
-
-template <int MODE>
-__device__ __forceinline__ float prolong_value(const float* __restrict__ xc, const float* __restrict__ bc,
-                                               const float* __restrict__ ec, const LevelArr& F, const LevelArr& C,
-                                               bool known, int px, int py) {
-    const size_t idx = (size_t)py * F.pitch + px;
-    if (known) return (MODE == 0) ? xc[idx] : bc[idx];
-    if (MODE == 2) return 0.f;
-    return (MODE == 0 ? xc[idx] : 0.f) + prolong_at(ec, C, px, py);
-}
-
-// Horizontally interpolated coarse row R at this lane's fine column:
-// 3/4 e[R][X] + 1/4 e[R][Xn], X = x/2 and Xn the coarse neighbour on the side
-// of x. Lane pairs (2j, 2j+1) share X; the neighbour comes from the adjacent
-// lane by a shuffle, edge lanes load it.
-__device__ __forceinline__ float prolong_row(const float* __restrict__ ec, const LevelArr& C, int R, int x, int lane) {
-    const float* row = ec + (size_t)R * C.pitch;
-    const int X = min(x >> 1, C.W - 1);
-    const float own = row[X];
-    const bool odd = x & 1;
-    float nb = __shfl_sync(HDI_FULL, own, odd ? min(lane + 1, 31) : max(lane - 1, 0));
-    if ((lane == 0 && !odd) || (lane == 31 && odd)) {
-        const int Xn = odd ? min(X + 1, C.W - 1) : max(X - 1, 0);
-        nb = row[Xn];
-    }
-    return __fadd_rn(__fmul_rn(0.75f, own), __fmul_rn(0.25f, nb));
-}
-
 // MODE 0 (V-cycle): xout = xin + P e on unknown pixels, xin on known ones;
 // MODE 1 (FMG):     xout = b on known pixels, P e on unknown ones;
 // MODE 2 (start):   xout = b on known pixels, 0 on unknown ones (e unused).
+// P is bilinear cell-centred interpolation (Sec. 3.2): fine pixel (x, y) takes
+// 3/4 of its coarse cell (X, Y) = (x/2, y/2) and 1/4 of the neighbouring
+// coarse cell on its side in each direction, applied as a horizontal pass on
+// the coarse rows h(R) = 3/4 e[R][X] + 1/4 e[R][Xn] and a vertical one,
+// 3/4 h(Y) + 1/4 h(Yn) (clamped at the border).
 // Then ||b - A xout||^2 per channel (the next sweep's local stop rule).
-// Column strips: lane = column, three-row register window of xout values;
-// the bilinear prolongation reads one coarse value per coarse row per lane
-// pair and takes the horizontal neighbour by a shuffle.
+// Column strips: lane = column, three-row register window of xout values.
+// Each coarse row is interpolated once per chunk and reused by the fine rows
+// above and below it; lane pairs share a coarse cell, the horizontal
+// neighbour comes by a shuffle and the edge lanes load it. That neighbour is
+// also the halo column's own cell, so lanes 0 and 31 get the halo column's
+// interpolation (the mirror weights) without further coarse loads.
 template <int MODE>
 __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const float* __restrict__ xin,
                                                  const float* __restrict__ b, float* __restrict__ xout,
                                                  LevelArr C, const float* __restrict__ e, GridReduce red, int rows) {
+    constexpr int CR = CS_CHUNK;
+    constexpr int NS = CR / 2 + 2;   // coarse rows per chunk: (yb/2 - 1) .. (yb/2 + CR/2)
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
     const int px = x0 + lane;
@@ -311,55 +342,111 @@ __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const 
     const float* xc = (MODE == 0) ? xin + ch * F.cs : nullptr;
     const float* bc = b + ch * F.cs;
     const float* ec = (MODE == 2) ? nullptr : e + ch * C.cs;
+    float* xo = xout + ch * F.cs;
     float sq = 0.f;
     if (x0 < F.W) {
         const uint32_t* mrow = fm.bits + (x0 >> 5);
-        // value of xout at (pxc, y) given the row's mask word
-        auto val = [&](int y, uint32_t w) -> float {
-            const size_t idx = (size_t)y * F.pitch + pxc;
-            const bool known = (w >> lane) & 1u;
-            float pe = 0.f;
-            if (MODE != 2) {
-                const int Y = y >> 1;
-                const int Yn = (y & 1) ? min(Y + 1, C.H - 1) : max(Y - 1, 0);
-                pe = __fadd_rn(__fmul_rn(0.75f, prolong_row(ec, C, Y, pxc, lane)),
-                               __fmul_rn(0.25f, prolong_row(ec, C, Yn, pxc, lane)));
-            }
-            if (known) return (MODE == 0) ? xc[idx] : bc[idx];
-            if (MODE == 2) return 0.f;
-            return (MODE == 0 ? xc[idx] : 0.f) + pe;
+        const StripHalo hl = strip_halo(lane, px, pxc, F.W);
+        const uint32_t* hrow = fm.bits + (hl.col >> 5);
+        const int hbit = hl.col & 31;
+        const bool hasl = px > 0, hasr = px + 1 < F.W;
+        const bool odd = pxc & 1;
+        const int X = min(pxc >> 1, C.W - 1);
+        const int Xn = odd ? min(X + 1, C.W - 1) : max(X - 1, 0);
+        const int src = odd ? min(lane + 1, 31) : max(lane - 1, 0);
+        const bool edge = (lane == 0 && !odd) || (lane == 31 && odd);
+        // coarse slots: S[j] / SH[j] = horizontal interpolation of coarse row
+        // cb + j (clamped) at this lane's column / at the halo column
+        float S[NS], SH[NS];
+        auto coarse = [&](int R, float& ho, float& hh) {
+            if (MODE == 2) { ho = hh = 0.f; return; }
+            const float* row = ec + (size_t)min(max(R, 0), C.H - 1) * C.pitch;
+            const float own = row[X];
+            float nb = __shfl_sync(HDI_FULL, own, src);
+            if (edge) nb = row[Xn];
+            ho = __fadd_rn(__fmul_rn(0.75f, own), __fmul_rn(0.25f, nb));
+            hh = __fadd_rn(__fmul_rn(0.75f, nb), __fmul_rn(0.25f, own));
         };
-        float up = 0.f;
-        if (y0 > 0) up = val(y0 - 1, mrow[(size_t)(y0 - 1) * fm.wpitch]);
-        uint32_t wc = mrow[(size_t)y0 * fm.wpitch];
-        float cen = val(y0, wc);
-        for (int y = y0; y < y1; ++y) {
-            uint32_t wn = 0;
-            float dn = 0.f;
-            if (y + 1 < F.H) {
-                wn = mrow[(size_t)(y + 1) * fm.wpitch];
-                dn = val(y + 1, wn);
+        auto fval = [&](bool known, float xv, float bv, float hY, float hYn) -> float {
+            if (known) return (MODE == 0) ? xv : bv;
+            if (MODE == 2) return 0.f;
+            const float pe = __fadd_rn(__fmul_rn(0.75f, hY), __fmul_rn(0.25f, hYn));
+            return (MODE == 0 ? xv : 0.f) + pe;
+        };
+        // slots of fine row r relative to chunk row yb (r - yb = k, k in -1 .. CR)
+        // Y = r/2 -> slot (k >> 1) + 1 with floor division; Yn on the side of r
+        const int cb0 = (y0 >> 1) - 1;
+        coarse(cb0, S[0], SH[0]);
+        coarse(cb0 + 1, S[1], SH[1]);
+        // window: up = xout(y0 - 1) (slots: Y = cb0 -> 0, Yn = cb0 + 1 -> 1), cen = xout(y0) (Y -> 1, Yn -> 0)
+        float up = 0.f, cen;
+        {
+            const size_t r0 = (size_t)y0 * F.pitch + pxc;
+            const bool k0 = (mrow[(size_t)y0 * fm.wpitch] >> lane) & 1u;
+            cen = fval(k0, MODE == 0 ? xc[r0] : 0.f, bc[r0], S[1], S[0]);
+            if (y0 > 0) {
+                const size_t rm = (size_t)(y0 - 1) * F.pitch + pxc;
+                const bool km = (mrow[(size_t)(y0 - 1) * fm.wpitch] >> lane) & 1u;
+                up = fval(km, MODE == 0 ? xc[rm] : 0.f, bc[rm], S[0], S[1]);
             }
-            float lf = __shfl_up_sync(HDI_FULL, cen, 1);
-            float rt = __shfl_down_sync(HDI_FULL, cen, 1);
-            if (lane == 0 && px > 0) lf = prolong_value<MODE>(xc, bc, ec, F, C, fm.known(px - 1, y), px - 1, y);
-            if (lane == 31 && px + 1 < F.W)
-                rt = prolong_value<MODE>(xc, bc, ec, F, C, fm.known(px + 1, y), px + 1, y);
-            if (act) {
-                xout[ch * F.cs + (size_t)y * F.pitch + px] = cen;
-                if (!((wc >> lane) & 1u)) {
-                    float lap = 0.f;
-                    if (px > 0) lap += cen - lf;
-                    if (px + 1 < F.W) lap += cen - rt;
-                    if (y > 0) lap += cen - up;
-                    if (y + 1 < F.H) lap += cen - dn;
-                    const float r = bc[(size_t)y * F.pitch + px] - lap;
-                    sq += r * r;
+        }
+        for (int yb = y0; yb < y1; yb += CR) {
+            const int cb = (yb >> 1) - 1;
+            float Xd[CR], Bd[CR + 1], Hx[CR], Hb[CR];
+            uint32_t Mw[CR + 1], Hm[CR];
+#pragma unroll
+            for (int j = 2; j < NS; ++j) coarse(cb + j, S[j], SH[j]);
+#pragma unroll
+            for (int k = 0; k <= CR; ++k) {
+                const int y = min(yb + k, F.H - 1);
+                Bd[k] = bc[(size_t)y * F.pitch + pxc];
+                Mw[k] = mrow[(size_t)y * fm.wpitch];
+            }
+#pragma unroll
+            for (int k = 0; k < CR; ++k) {
+                const int y = min(yb + k, F.H - 1);
+                const size_t ry = (size_t)y * F.pitch;
+                Xd[k] = (MODE == 0) ? xc[(size_t)min(yb + k + 1, F.H - 1) * F.pitch + pxc] : 0.f;
+                Hx[k] = (MODE == 0 && hl.on) ? xc[ry + hl.col] : 0.f;
+                Hb[k] = hl.on ? bc[ry + hl.col] : 0.f;
+                Hm[k] = hl.on ? hrow[(size_t)y * fm.wpitch] : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < CR; ++k) {
+                const int y = yb + k;
+                if (y >= y1) break;
+                // row y + 1 (k + 1 relative): Y slot ((k+1) >> 1) + 1, Yn on its side
+                const int kd = k + 1;
+                const int sY = (kd >> 1) + 1, sYn = (kd & 1) ? sY + 1 : sY - 1;
+                float dn = 0.f;
+                if (y + 1 < F.H) dn = fval((Mw[k + 1] >> lane) & 1u, Xd[k], Bd[k + 1], S[sY], S[sYn]);
+                float lf = __shfl_up_sync(HDI_FULL, cen, 1);
+                float rt = __shfl_down_sync(HDI_FULL, cen, 1);
+                if (hl.on) {
+                    const int hY = (k >> 1) + 1, hYn = (k & 1) ? hY + 1 : hY - 1;
+                    const float hv = fval((Hm[k] >> hbit) & 1u, Hx[k], Hb[k], SH[hY], SH[hYn]);
+                    if (lane == 0) lf = hv;
+                    else rt = hv;
                 }
+                if (act) {
+                    xo[(size_t)y * F.pitch + px] = cen;
+                    if (!((Mw[k] >> lane) & 1u)) {
+                        float lap = 0.f;
+                        if (hasl) lap += cen - lf;
+                        if (hasr) lap += cen - rt;
+                        if (y > 0) lap += cen - up;
+                        if (y + 1 < F.H) lap += cen - dn;
+                        const float r = Bd[k] - lap;
+                        sq += r * r;
+                    }
+                }
+                up = cen;
+                cen = dn;
             }
-            up = cen;
-            cen = dn;
-            wc = wn;
+            S[0] = S[NS - 2];
+            S[1] = S[NS - 1];
+            SH[0] = SH[NS - 2];
+            SH[1] = SH[NS - 1];
         }
     }
     const double tot = (double)block_sum_f(sq);
