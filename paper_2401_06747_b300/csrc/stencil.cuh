@@ -133,6 +133,9 @@ __device__ __forceinline__ float fine_residual(const float* __restrict__ x, cons
 // combined by a shuffle.
 #define CS_ROWS 64
 #define CS_CHUNK 8
+#ifndef RES_CHUNK
+#define RES_CHUNK 4
+#endif
 
 // Rows per CTA of the column-strip kernels: long strips on large levels (few
 // CTAs take part in each grid reduction), short ones on small levels, where
@@ -529,28 +532,17 @@ struct ResArgs {
 // neighbours by warp shuffles (lanes 0 and 31 read the neighbouring strip
 // from L1/L2), and reads the mask as one broadcast word per row.
 
-// Iterate value at (x, y) after the INIT transform (and the Dirichlet value on
-// known pixels), as a double-float pair.
-template <int RHS, int INIT>
-__device__ __forceinline__ void res_value(const ResArgs& a, long long co, int x, int y, bool known, float& h,
-                                          float& l) {
-    const size_t idx = co + (size_t)y * a.F.pitch + x;
-    if (known) {
-        if (RHS == RHS_DATA) { h = a.d.hi[idx]; l = a.d.lo[idx]; }
-        else { h = 0.f; l = 0.f; }
-    } else if (INIT == INIT_KEEP) {
-        h = a.uin.hi[idx]; l = a.uin.lo[idx];
-    } else if (INIT == INIT_UPDATE) {
-        df_add(a.uin.hi[idx], a.uin.lo[idx], a.x32[idx], 0.f, h, l);
-    } else if (INIT == INIT_FROM32) {
-        h = a.x32[idx]; l = 0.f;
-    } else {
-        h = 0.f; l = 0.f;
-    }
-}
-
+// Chunked like the FP32 strip kernels. Known pixels take their Dirichlet
+// value (d for RHS_DATA, 0 for RHS_SOURCE). With INIT_UPDATE the input
+// iterate already holds it there (every refinement step writes it, and the
+// V-cycle correction is zero on known pixels), so d is read only by the
+// other INIT modes, after the chunk's mask words have arrived.
 template <int RHS, int INIT>
 __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
+    constexpr int RC = RES_CHUNK;
+    constexpr bool LOAD_D = (RHS == RHS_DATA) && (INIT != INIT_UPDATE);
+    constexpr bool HAS_U = (INIT == INIT_KEEP || INIT == INIT_UPDATE);
+    constexpr bool HAS_E = (INIT == INIT_UPDATE || INIT == INIT_FROM32);
     a.m = a.m.ch(blockIdx.z);
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
@@ -558,67 +550,144 @@ __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
     const int y0 = blockIdx.y * a.rows;
     const int y1 = min(y0 + a.rows, a.F.H);
     const int ch = blockIdx.z;
+    const int H = a.F.H, W = a.F.W;
     const long long co = ch * a.F.cs;
-    const bool act = x < a.F.W;
-    const int xc = act ? x : a.F.W - 1;
-    const bool strip = x0 < a.F.W;
+    const bool act = x < W;
+    const int xc = act ? x : W - 1;
     float rr = 0.f, bb2 = 0.f;
-    if (strip) {
+    if (x0 < W) {
         const uint32_t* mrow = a.m.bits + (x0 >> 5);
-        float uh = 0.f, ul = 0.f, ch_ = 0.f, cl = 0.f, dh = 0.f, dl = 0.f;
-        if (y0 > 0) res_value<RHS, INIT>(a, co, xc, y0 - 1, a.m.known(xc, y0 - 1), uh, ul);
-        uint32_t wc = mrow[(size_t)y0 * a.m.wpitch];
-        res_value<RHS, INIT>(a, co, xc, y0, (wc >> lane) & 1u, ch_, cl);
-        for (int y = y0; y < y1; ++y) {
-            uint32_t wn = 0;
-            if (y + 1 < a.F.H) {
-                wn = mrow[(size_t)(y + 1) * a.m.wpitch];
-                res_value<RHS, INIT>(a, co, xc, y + 1, (wn >> lane) & 1u, dh, dl);
-            }
-            float lh = __shfl_up_sync(HDI_FULL, ch_, 1), ll = __shfl_up_sync(HDI_FULL, cl, 1);
-            float rh = __shfl_down_sync(HDI_FULL, ch_, 1), rl = __shfl_down_sync(HDI_FULL, cl, 1);
-            if (lane == 0 && x > 0) res_value<RHS, INIT>(a, co, x - 1, y, a.m.known(x - 1, y), lh, ll);
-            if (lane == 31 && x + 1 < a.F.W) res_value<RHS, INIT>(a, co, x + 1, y, a.m.known(x + 1, y), rh, rl);
-            const bool known = (wc >> lane) & 1u;
-            if (act) {
-                const size_t idx = co + (size_t)y * a.F.pitch + x;
-                a.uout.hi[idx] = ch_;
-                a.uout.lo[idx] = cl;
-                float r = 0.f;
-                if (known) {
-                    if (RHS == RHS_DATA) { const float bh = ch_ + cl; bb2 += bh * bh; }
+        const StripHalo hl = strip_halo(lane, x, xc, W);
+        const uint32_t* hrow = a.m.bits + (hl.col >> 5);
+        const int hbit = hl.col & 31;
+        const bool hasl = x > 0, hasr = x + 1 < W;
+        auto at = [&](int y, int col) { return co + (size_t)min(y, H - 1) * a.F.pitch + col; };
+        // iterate value after the INIT transform, from the loaded sources
+        auto value = [&](bool known, float uh, float ul, float e, float dh, float dl, float& h, float& l) {
+            if (known) {
+                if (RHS == RHS_DATA) {
+                    if (INIT == INIT_UPDATE) { h = uh; l = ul; }
+                    else { h = dh; l = dl; }
                 } else {
-                    float sh = 0.f, sl = 0.f;
-                    const float nh[4] = {lh, rh, uh, dh};
-                    const float nl[4] = {ll, rl, ul, dl};
-                    const bool ok[4] = {x > 0, x + 1 < a.F.W, y > 0, y + 1 < a.F.H};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (ok[k]) {
-                            float e1, e2, s2, t2;
-                            two_sum(ch_, -nh[k], e1, e2);
-                            e2 += cl - nl[k];
-                            two_sum(sh, e1, s2, t2);
-                            sh = s2;
-                            sl += t2 + e2;
-                        }
-                    }
-                    float bh = 0.f, bl = 0.f;
-                    if (RHS == RHS_SOURCE) {
-                        const float yh = a.y.hi ? a.y.hi[idx] : 0.f, yl = a.y.hi ? a.y.lo[idx] : 0.f;
-                        df_add(a.d.hi[idx], a.d.lo[idx], -yh, -yl, bh, bl);
-                        bb2 += bh * bh;
-                    }
-                    float rh2, rl2;
-                    df_add(bh, bl, -sh, -sl, rh2, rl2);
-                    r = rh2 + rl2;
+                    h = 0.f; l = 0.f;
                 }
-                a.r32[idx] = r;
-                rr += r * r;
+            } else if (INIT == INIT_KEEP) {
+                h = uh; l = ul;
+            } else if (INIT == INIT_UPDATE) {
+                df_add(uh, ul, e, 0.f, h, l);
+            } else if (INIT == INIT_FROM32) {
+                h = e; l = 0.f;
+            } else {
+                h = 0.f; l = 0.f;
             }
-            uh = ch_; ul = cl;
-            ch_ = dh; cl = dl;
-            wc = wn;
+        };
+        auto full_value = [&](int y, int col, uint32_t word, int bit, float& h, float& l) {
+            const size_t idx = at(y, col);
+            const bool known = (word >> bit) & 1u;
+            const float uh = HAS_U ? a.uin.hi[idx] : 0.f, ul = HAS_U ? a.uin.lo[idx] : 0.f;
+            const float e = HAS_E ? a.x32[idx] : 0.f;
+            float dh = 0.f, dl = 0.f;
+            if (LOAD_D && known) { dh = a.d.hi[idx]; dl = a.d.lo[idx]; }
+            value(known, uh, ul, e, dh, dl, h, l);
+        };
+        // window: (uh_, ul_) = u(y0 - 1), (ch_, cl) = u(y0)
+        float uh_ = 0.f, ul_ = 0.f, ch_, cl;
+        full_value(y0, xc, mrow[(size_t)y0 * a.m.wpitch], lane, ch_, cl);
+        if (y0 > 0) full_value(y0 - 1, xc, mrow[(size_t)(y0 - 1) * a.m.wpitch], lane, uh_, ul_);
+        for (int yb = y0; yb < y1; yb += RC) {
+            uint32_t Mw[RC + 1], Hm[RC];
+            float Uh[RC], Ul[RC], E[RC];       // rows yb+1 .. yb+RC, own column
+            float HUh[RC], HUl[RC], HE[RC];    // rows yb .. yb+RC-1, halo column
+            float Dh[RC], Dl[RC], Yh[RC], Yl[RC];   // RHS_SOURCE: d and y, rows yb .. yb+RC-1
+#pragma unroll
+            for (int k = 0; k <= RC; ++k) Mw[k] = mrow[(size_t)min(yb + k, H - 1) * a.m.wpitch];
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                const size_t id = at(yb + k + 1, xc), ih = at(yb + k, hl.col), ic = at(yb + k, xc);
+                Uh[k] = HAS_U ? a.uin.hi[id] : 0.f;
+                Ul[k] = HAS_U ? a.uin.lo[id] : 0.f;
+                E[k] = HAS_E ? a.x32[id] : 0.f;
+                Hm[k] = hl.on ? hrow[(size_t)min(yb + k, H - 1) * a.m.wpitch] : 0u;
+                HUh[k] = (HAS_U && hl.on) ? a.uin.hi[ih] : 0.f;
+                HUl[k] = (HAS_U && hl.on) ? a.uin.lo[ih] : 0.f;
+                HE[k] = (HAS_E && hl.on) ? a.x32[ih] : 0.f;
+                if (RHS == RHS_SOURCE) {
+                    Dh[k] = a.d.hi[ic];
+                    Dl[k] = a.d.lo[ic];
+                    Yh[k] = a.y.hi ? a.y.hi[ic] : 0.f;
+                    Yl[k] = a.y.hi ? a.y.lo[ic] : 0.f;
+                }
+            }
+            float KDh[RC], KDl[RC], HDh[RC], HDl[RC];   // data on known pixels (after the mask words)
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                KDh[k] = KDl[k] = HDh[k] = HDl[k] = 0.f;
+                if (LOAD_D) {
+                    if ((Mw[k + 1] >> lane) & 1u) {
+                        const size_t id = at(yb + k + 1, xc);
+                        KDh[k] = a.d.hi[id];
+                        KDl[k] = a.d.lo[id];
+                    }
+                    if (hl.on && ((Hm[k] >> hbit) & 1u)) {
+                        const size_t ih = at(yb + k, hl.col);
+                        HDh[k] = a.d.hi[ih];
+                        HDl[k] = a.d.lo[ih];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                const int y = yb + k;
+                if (y >= y1) break;
+                float dh = 0.f, dl = 0.f;
+                if (y + 1 < H) value((Mw[k + 1] >> lane) & 1u, Uh[k], Ul[k], E[k], KDh[k], KDl[k], dh, dl);
+                float lh = __shfl_up_sync(HDI_FULL, ch_, 1), ll = __shfl_up_sync(HDI_FULL, cl, 1);
+                float rh = __shfl_down_sync(HDI_FULL, ch_, 1), rl = __shfl_down_sync(HDI_FULL, cl, 1);
+                if (hl.on) {
+                    float hh, hlo;
+                    value((Hm[k] >> hbit) & 1u, HUh[k], HUl[k], HE[k], HDh[k], HDl[k], hh, hlo);
+                    if (lane == 0) { lh = hh; ll = hlo; }
+                    else { rh = hh; rl = hlo; }
+                }
+                const bool known = (Mw[k] >> lane) & 1u;
+                if (act) {
+                    const size_t idx = co + (size_t)y * a.F.pitch + x;
+                    a.uout.hi[idx] = ch_;
+                    a.uout.lo[idx] = cl;
+                    float r = 0.f;
+                    if (known) {
+                        if (RHS == RHS_DATA) { const float bh = ch_ + cl; bb2 += bh * bh; }
+                    } else {
+                        float sh = 0.f, sl = 0.f;
+                        const float nh[4] = {lh, rh, uh_, dh};
+                        const float nl[4] = {ll, rl, ul_, dl};
+                        const bool ok[4] = {hasl, hasr, y > 0, y + 1 < H};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (ok[q]) {
+                                float e1, e2, s2, t2;
+                                two_sum(ch_, -nh[q], e1, e2);
+                                e2 += cl - nl[q];
+                                two_sum(sh, e1, s2, t2);
+                                sh = s2;
+                                sl += t2 + e2;
+                            }
+                        }
+                        float bh = 0.f, bl = 0.f;
+                        if (RHS == RHS_SOURCE) {
+                            df_add(Dh[k], Dl[k], -Yh[k], -Yl[k], bh, bl);
+                            bb2 += bh * bh;
+                        }
+                        float rh2, rl2;
+                        df_add(bh, bl, -sh, -sl, rh2, rl2);
+                        r = rh2 + rl2;
+                    }
+                    a.r32[idx] = r;
+                    rr += r * r;
+                }
+                uh_ = ch_; ul_ = cl;
+                ch_ = dh; cl = dl;
+            }
         }
     }
     const double tot = (double)block_sum_f(rr);
