@@ -81,9 +81,18 @@ __global__ void __launch_bounds__(256) k_aa_gather(AAArgs a, int new_slot) {
     const int ch = blockIdx.y;
     const int part = blockIdx.x;
     constexpr int ND = K * (K + 1) / 2 + K;
-    double acc[ND > 0 ? ND : 1];
+    constexpr int NA = ND > 0 ? ND : 1;
+    // per-thread dot products as compensated FP32 sums (TwoSum on every term:
+    // value as + ae, about twice the FP32 precision)
+    float as[NA], ae[NA];
 #pragma unroll
-    for (int q = 0; q < (ND > 0 ? ND : 1); ++q) acc[q] = 0.0;
+    for (int q = 0; q < NA; ++q) as[q] = ae[q] = 0.f;
+    auto acc = [&](int q, float x) {
+        const float t = as[q] + x;
+        const float bp = t - as[q];
+        ae[q] += (as[q] - (t - bp)) + (x - bp);
+        as[q] = t;
+    };
     const size_t co = (size_t)ch * a.M;
     const size_t vs = (size_t)a.nch * a.M;   // stride between window slots
     for (int i = part * 256 + threadIdx.x; i < a.M; i += a.nparts * 256) {
@@ -104,20 +113,31 @@ __global__ void __launch_bounds__(256) k_aa_gather(AAArgs a, int new_slot) {
 #pragma unroll
             for (int r = 0; r < K; ++r)
 #pragma unroll
-                for (int c = r; c < K; ++c) acc[q++] += (double)(d[r] * d[c]);
+                for (int c = r; c < K; ++c) acc(q++, d[r] * d[c]);
 #pragma unroll
-            for (int r = 0; r < K; ++r) acc[q++] += (double)(d[r] * f);
+            for (int r = 0; r < K; ++r) acc(q++, d[r] * f);
         }
     }
     if (K == 0) return;
-    // block reduce each dot, deposit partials; last CTA per launch sums
+    // block reduce all dots at once: warp sums in FP64, one shared-memory
+    // exchange, then thread q adds the warps' values of dot q
+    __shared__ double wsum[8][NA];
+#pragma unroll
     for (int q = 0; q < ND; ++q) {
-        const double t = block_sum_d(acc[q]);
-        if (threadIdx.x == 0) a.partials[((size_t)ch * ND + q) * a.nparts + part] = t;
+        const double t = warp_sum_d((double)as[q] + (double)ae[q]);
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5][q] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < ND) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += wsum[w][threadIdx.x];
+        a.partials[((size_t)ch * ND + threadIdx.x) * a.nparts + part] = t;
+        __threadfence();   // each writer publishes its partial before the ticket
     }
     __shared__ bool last;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         const unsigned t = atomicAdd(a.ticket, 1u);
         last = (t == (unsigned)(a.nparts * a.nch - 1));
     }

@@ -210,47 +210,86 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
 // r_K = (f - y)_K + sum of w over the unknown 4-neighbours (B^T (f - y)),
 // stored in FP32 for the local solves, and per channel ||r||^2 and
 // ||f - y||^2 (the tonal MSE numerator). y.hi == nullptr means y = 0 (B^T f).
-// The sums on mask pixels (a few percent of the image) are formed in FP64.
+// The sums on mask pixels (a few percent of the image) are formed in
+// double-float arithmetic (the FP64 rate of the target is a small fraction of
+// its FP32 rate).
 __global__ void __launch_bounds__(128) k_tonal_residual(LevelArr F, MaskView m, DFc f, DFc y, DFc w,
                                                         float* __restrict__ r, GridReduce red_r, GridReduce red_e,
                                                         int rows) {
+    constexpr int RC = 4;   // rows per load chunk (see the column-strip kernels)
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
     const int px = x0 + lane;
     const int y0 = blockIdx.y * rows;
     const int y1 = min(y0 + rows, F.H);
     const int ch = blockIdx.z;
+    const int H = F.H;
     const bool act = px < F.W;
+    const int pxc = act ? px : F.W - 1;
     float se = 0.f, sr = 0.f;
     if (x0 < F.W) {
         const uint32_t* mrow = m.bits + (x0 >> 5);
+        const StripHalo hl = strip_halo(lane, px, pxc, F.W);
+        const uint32_t* hrow = m.bits + (hl.col >> 5);
+        const int hbit = hl.col & 31;
+        const bool hasl = px > 0, hasr = px + 1 < F.W;
+        const size_t co = ch * F.cs;
         uint32_t wu = (y0 > 0) ? mrow[(size_t)(y0 - 1) * m.wpitch] : 0u;
-        uint32_t wc = mrow[(size_t)y0 * m.wpitch];
-        for (int yy = y0; yy < y1; ++yy) {
-            const uint32_t wd = (yy + 1 < F.H) ? mrow[(size_t)(yy + 1) * m.wpitch] : 0u;
-            if (act) {
-                const size_t idx = ch * F.cs + (size_t)yy * F.pitch + px;
-                float sh, sl;
-                if (y.hi) df_add(f.hi[idx], f.lo[idx], -y.hi[idx], -y.lo[idx], sh, sl);
-                else { sh = f.hi[idx]; sl = f.lo[idx]; }
-                se += sh * sh;
-                if ((wc >> lane) & 1u) {
-                    // B^T (f - y) on a mask pixel: s_K plus w on its unknown neighbours
-                    double acc = (double)sh + (double)sl;
-                    const bool kl = (lane > 0) ? ((wc >> (lane - 1)) & 1u) : (px > 0 && m.known(px - 1, yy));
-                    const bool kr = (lane < 31) ? ((wc >> (lane + 1)) & 1u) : (px + 1 < F.W && m.known(px + 1, yy));
-                    if (px > 0 && !kl) acc += (double)w.hi[idx - 1] + (double)w.lo[idx - 1];
-                    if (px + 1 < F.W && !kr) acc += (double)w.hi[idx + 1] + (double)w.lo[idx + 1];
-                    if (yy > 0 && !((wu >> lane) & 1u)) acc += (double)w.hi[idx - F.pitch] + (double)w.lo[idx - F.pitch];
-                    if (yy + 1 < F.H && !((wd >> lane) & 1u))
-                        acc += (double)w.hi[idx + F.pitch] + (double)w.lo[idx + F.pitch];
-                    const float rv = (float)acc;
-                    r[idx] = rv;
-                    sr += rv * rv;
+        for (int yb = y0; yb < y1; yb += RC) {
+            uint32_t Mw[RC + 1], Hm[RC];
+            float Fh[RC], Fl[RC], Yh[RC], Yl[RC];
+#pragma unroll
+            for (int k = 0; k <= RC; ++k) Mw[k] = (yb + k < H) ? mrow[(size_t)(yb + k) * m.wpitch] : 0u;
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                const size_t idx = co + (size_t)min(yb + k, H - 1) * F.pitch + pxc;
+                Hm[k] = hl.on ? hrow[(size_t)min(yb + k, H - 1) * m.wpitch] : 0u;
+                Fh[k] = f.hi[idx];
+                Fl[k] = f.lo[idx];
+                Yh[k] = y.hi ? y.hi[idx] : 0.f;
+                Yl[k] = y.hi ? y.lo[idx] : 0.f;
+            }
+            // mask pixels: w on the unknown 4-neighbours, read once the mask words are in
+            float Wh[RC][4], Wl[RC][4];
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                const int yy = min(yb + k, H - 1);
+                const uint32_t wc = Mw[k], wup = (k == 0) ? wu : Mw[k - 1], wdn = Mw[k + 1];
+                const bool mk = act && ((wc >> lane) & 1u);
+                const bool kl = (lane > 0) ? ((wc >> (lane - 1)) & 1u) : ((Hm[k] >> hbit) & 1u);
+                const bool kr = (lane < 31) ? ((wc >> (lane + 1)) & 1u) : ((Hm[k] >> hbit) & 1u);
+                const bool nb[4] = {mk && hasl && !kl, mk && hasr && !kr, mk && yy > 0 && !((wup >> lane) & 1u),
+                                    mk && yy + 1 < H && !((wdn >> lane) & 1u)};
+                const size_t idx = co + (size_t)yy * F.pitch + pxc;
+                const size_t nidx[4] = {idx - 1, idx + 1, idx - F.pitch, idx + F.pitch};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    Wh[k][q] = nb[q] ? w.hi[nidx[q]] : 0.f;
+                    Wl[k][q] = nb[q] ? w.lo[nidx[q]] : 0.f;
                 }
             }
-            wu = wc;
-            wc = wd;
+#pragma unroll
+            for (int k = 0; k < RC; ++k) {
+                const int yy = yb + k;
+                if (yy >= y1) break;
+                if (act) {
+                    float sh, sl;
+                    if (y.hi) df_add(Fh[k], Fl[k], -Yh[k], -Yl[k], sh, sl);
+                    else { sh = Fh[k]; sl = Fl[k]; }
+                    se += sh * sh;
+                    if ((Mw[k] >> lane) & 1u) {
+                        // B^T (f - y) on a mask pixel: s_K plus w on its unknown neighbours,
+                        // summed in double-float (terms of absent neighbours are zero)
+                        float ah = sh, al = sl;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) df_add(ah, al, Wh[k][q], Wl[k][q], ah, al);
+                        const float rv = ah + al;
+                        r[co + (size_t)yy * F.pitch + px] = rv;
+                        sr += rv * rv;
+                    }
+                }
+            }
+            wu = Mw[RC - 1];
         }
     }
     const double tr = (double)block_sum_f(sr);
