@@ -124,84 +124,132 @@ __global__ void __launch_bounds__(128, 3) k_tonal_echo(EchoArgs a) {
     for (int k = 0; k < 16; ++k) *reinterpret_cast<float2*>(out + (r0 + k) * 32 + c0) = V[k];
 }
 
+// Shared-memory floats of k_tonal_gram for subdomains of up to m mask pixels.
+__host__ __device__ inline int gram_round4(int m) { return (m + 3) & ~3; }
+__host__ __device__ inline size_t gram_smem_floats(int m) {
+    const int m4 = gram_round4(m);
+    return (size_t)m * (m | 1) + 4 + (size_t)32 * (m4 + 4) + 256 * 16;
+}
+
 // G_i = I + S_i^T S_i and its Cholesky factor (packed lower, row-major) at
-// fac + goff[i]. One CTA of 256 threads per subdomain; G lives in dynamic
-// shared memory (m_i <= kTonalMaxM).
+// fac + goff[i]. One CTA of 256 threads per subdomain.
+// Products: each thread accumulates one 4x4 block of the lower triangle of G
+// (m rounded up to a multiple of 4); with few blocks the 1024 pixels are
+// split into ks interleaved slices whose partial blocks are added in a fixed
+// order. Pixels are staged 32 at a time in shared memory, transposed, so a
+// thread reads four echoes' values of one pixel with one 16-byte load.
+// Cholesky (right-looking): thread r owns row r, two barriers per column.
 __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off, const long long* __restrict__ goff,
                                                     const float* __restrict__ echo, float* __restrict__ fac,
                                                     unsigned* bad) {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     const int i = blockIdx.x;
     const int m = off[i + 1] - off[i];
     if (m == 0) return;
     const int tid = threadIdx.x;
-    float* G = sm;                       // m x m, row stride m
-    float* tA = sm + m * m;              // [32 pixels][64] tile of echoes (rows ti)
-    float* tB = tA + 32 * 64;            // [32 pixels][64] (rows tj)
+    const int m4 = gram_round4(m);
+    const int nb = m4 / 4;
+    const int nblk = nb * (nb + 1) / 2;
+    const int ks = (nblk >= 256) ? 1 : min(8, 256 / nblk);
+    const int gs = m | 1;                          // row stride of G
+    const int es = m4 + 4;                         // row stride of the staged pixels
+    float* G = sm;                                 // m x gs
+    float* Es = sm + (((size_t)m * gs + 3) & ~(size_t)3);   // [32][es], 16-byte aligned rows
+    float* part = Es + 32 * es;                    // [ks][nblk][16] (ks > 1)
     const float* E = echo + (size_t)off[i] * 1024;
-    const int nt = (m + 63) / 64;
-    const int tr = tid / 16, tc = tid % 16;   // 16x16 threads, 4x4 outputs each
-    for (int ti = 0; ti < nt; ++ti) {
-        for (int tj = 0; tj <= ti; ++tj) {
-            float acc[4][4];
+    for (int b0 = 0; b0 < nblk; b0 += 256) {       // rounds of up to 256 blocks (ks == 1 when > 1 round)
+        const int slot = tid % (ks > 1 ? nblk : 256);
+        const int sl = tid / (ks > 1 ? nblk : 256);
+        const int bidx = b0 + slot;
+        const bool on = sl < ks && bidx < nblk && (ks == 1 || slot < nblk);
+        int br = 0, bc = 0;
+        if (on) {
+            br = (int)((sqrtf(8.f * (float)bidx + 1.f) - 1.f) * 0.5f);
+            while (br * (br + 1) / 2 > bidx) --br;
+            while ((br + 1) * (br + 2) / 2 <= bidx) ++br;
+            bc = bidx - br * (br + 1) / 2;
+        }
+        float acc[4][4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-            for (int p0 = 0; p0 < 1024; p0 += 32) {
-                __syncthreads();
-                for (int q = tid; q < 32 * 64; q += 256) {
-                    const int kk = q >> 5, pp = q & 31;   // consecutive threads read consecutive pixels
-                    const int ka = ti * 64 + kk, kb = tj * 64 + kk;
-                    tA[pp * 64 + kk] = (ka < m) ? E[(size_t)ka * 1024 + p0 + pp] : 0.f;
-                    tB[pp * 64 + kk] = (kb < m) ? E[(size_t)kb * 1024 + p0 + pp] : 0.f;
-                }
-                __syncthreads();
-#pragma unroll 8
-                for (int pp = 0; pp < 32; ++pp) {
-                    float av[4], bv[4];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) av[a] = tA[pp * 64 + tr * 4 + a];
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) bv[b] = tB[pp * 64 + tc * 4 + b];
+            for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        for (int p0 = 0; p0 < 1024; p0 += 32) {
+            __syncthreads();
+            for (int q = tid; q < m4 * 32; q += 256) {
+                const int k = q >> 5, pp = q & 31;
+                Es[pp * es + k] = (k < m) ? E[(size_t)k * 1024 + p0 + pp] : 0.f;
+            }
+            __syncthreads();
+            if (on) {
+                for (int pp = sl; pp < 32; pp += ks) {
+                    const float4 av = *reinterpret_cast<const float4*>(Es + pp * es + 4 * br);
+                    const float4 bv = *reinterpret_cast<const float4*>(Es + pp * es + 4 * bc);
+                    const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(a4[a], b4[b], acc[a][b]);
                 }
+            }
+        }
+        if (ks > 1) {
+            if (on) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) part[((size_t)sl * nblk + slot) * 16 + a * 4 + b] = acc[a][b];
+            }
+            __syncthreads();
+            if (tid < nblk) {
+                for (int e = 0; e < 16; ++e) {
+                    float t = part[(size_t)tid * 16 + e];
+                    for (int q = 1; q < ks; ++q) t += part[((size_t)q * nblk + tid) * 16 + e];
+                    acc[e >> 2][e & 3] = t;
+                }
+            }
+        }
+        const bool own = (ks > 1) ? (tid < nblk) : on;
+        if (own) {
+            if (ks > 1) {   // the summing thread tid holds block tid
+                br = (int)((sqrtf(8.f * (float)tid + 1.f) - 1.f) * 0.5f);
+                while (br * (br + 1) / 2 > tid) --br;
+                while ((br + 1) * (br + 2) / 2 <= tid) ++br;
+                bc = tid - br * (br + 1) / 2;
             }
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    const int r = ti * 64 + tr * 4 + a, c = tj * 64 + tc * 4 + b;
-                    if (r < m && c < m && c <= r) G[r * m + c] = acc[a][b] + (r == c ? 1.f : 0.f);
+                    const int r = 4 * br + a, c = 4 * bc + b;
+                    if (r < m && c <= r) G[r * gs + c] = acc[a][b] + (r == c ? 1.f : 0.f);
                 }
         }
     }
     __syncthreads();
-    // right-looking Cholesky on the lower triangle
+    // right-looking Cholesky on the lower triangle; thread r updates row r
+    const int r = tid;
     for (int j = 0; j < m; ++j) {
-        const float d = sqrtf(G[j * m + j]);
-        __syncthreads();
-        if (tid == 0) {
+        if (r == j) {
+            const float d = sqrtf(G[j * gs + j]);
             if (!(d > 0.f)) atomicOr(bad, 1u);
-            G[j * m + j] = d;
-        }
-        const float inv = 1.f / d;
-        for (int r = j + 1 + tid; r < m; r += 256) G[r * m + j] *= inv;
-        __syncthreads();
-        const int n = m - j - 1;   // trailing block (j+1..m-1)^2, lower part
-        for (int q = tid; q < n * n; q += 256) {
-            const int r = j + 1 + q / n, c = j + 1 + q % n;
-            if (c <= r) G[r * m + c] -= G[r * m + j] * G[c * m + j];
+            G[j * gs + j] = d;
         }
         __syncthreads();
+        float lrj = 0.f;
+        if (r > j && r < m) {
+            lrj = G[r * gs + j] / G[j * gs + j];
+            G[r * gs + j] = lrj;
+        }
+        __syncthreads();
+        if (r > j && r < m)
+            for (int c = j + 1; c <= r; ++c) G[r * gs + c] = fmaf(-lrj, G[c * gs + j], G[r * gs + c]);
     }
+    __syncthreads();
     float* L = fac + goff[i];
     for (int q = tid; q < m * m; q += 256) {
-        const int r = q / m, c = q % m;
-        if (c <= r) L[r * (r + 1) / 2 + c] = G[r * m + c];
+        const int rr = q / m, c = q % m;
+        if (c <= rr) L[rr * (rr + 1) / 2 + c] = G[rr * gs + c];
     }
 }
 
@@ -487,7 +535,7 @@ int Ctx::tonal_setup() {
         k_tonal_echo<<<(unsigned)((total + 3) / 4), 128, 0, stream>>>(ea);
         ++launches;
         tstop();
-        const size_t shm = ((size_t)maxm * maxm + 2 * 32 * 64) * 4;
+        const size_t shm = gram_smem_floats(maxm) * 4;
         cudaFuncSetAttribute(k_tonal_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         cudaMemsetAsync(flags, 0, 4, stream);
         tstart(kT_Gram);
