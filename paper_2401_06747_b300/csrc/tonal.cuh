@@ -128,10 +128,10 @@ __global__ void __launch_bounds__(128, 3) k_tonal_echo(EchoArgs a) {
 __host__ __device__ inline int gram_round4(int m) { return (m + 3) & ~3; }
 __host__ __device__ inline size_t gram_smem_floats(int m) {
     const int m4 = gram_round4(m);
-    return (size_t)m * (m | 1) + 4 + (size_t)32 * (m4 + 4) + 256 * 16;
+    return (size_t)m * (m | 1) + 4 + (size_t)32 * (m4 + 4) + 256 * 16 + m4;
 }
 
-// G_i = I + S_i^T S_i and its Cholesky factor (packed lower, row-major) at
+// G_i = I + S_i^T S_i and its inverse (full m x m, row-major) at
 // fac + goff[i]. One CTA of 256 threads per subdomain.
 // Products: each thread accumulates one 4x4 block of the lower triangle of G
 // (m rounded up to a multiple of 4); with few blocks the 1024 pixels are
@@ -139,6 +139,10 @@ __host__ __device__ inline size_t gram_smem_floats(int m) {
 // order. Pixels are staged 32 at a time in shared memory, transposed, so a
 // thread reads four echoes' values of one pixel with one 16-byte load.
 // Cholesky (right-looking): thread r owns row r, two barriers per column.
+// Inverse: W = L^{-1} column by column (thread j forward-substitutes e_j;
+// W^T is kept in the free upper triangle of G's buffer), then
+// G^{-1} = W^T W, written in full so the local solves are one dense
+// symmetric matrix-vector product.
 __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off, const long long* __restrict__ goff,
                                                     const float* __restrict__ echo, float* __restrict__ fac,
                                                     unsigned* bad) {
@@ -246,10 +250,37 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
             for (int c = j + 1; c <= r; ++c) G[r * gs + c] = fmaf(-lrj, G[c * gs + j], G[r * gs + c]);
     }
     __syncthreads();
-    float* L = fac + goff[i];
-    for (int q = tid; q < m * m; q += 256) {
-        const int rr = q / m, c = q % m;
-        if (c <= rr) L[rr * (rr + 1) / 2 + c] = G[rr * gs + c];
+    // W = L^{-1}; thread j owns column j of W, stored as row j of W^T:
+    // Wt[j][k] = W[k][j] at G[j * gs + k] for k > j, the diagonal in dinv.
+    float* dinv = part + 256 * 16;
+    if (r < m) {
+        const float dj = 1.f / G[r * gs + r];
+        dinv[r] = dj;
+        for (int ii = r + 1; ii < m; ++ii) {
+            float s0 = G[ii * gs + r] * dj, s1 = 0.f;   // k = r term, then k = r+1 .. ii-1
+            int k = r + 1;
+            for (; k + 1 < ii; k += 2) {
+                s0 = fmaf(G[ii * gs + k], G[r * gs + k], s0);
+                s1 = fmaf(G[ii * gs + k + 1], G[r * gs + k + 1], s1);
+            }
+            if (k < ii) s0 = fmaf(G[ii * gs + k], G[r * gs + k], s0);
+            G[r * gs + ii] = -(s0 + s1) / G[ii * gs + ii];
+        }
+    }
+    __syncthreads();
+    // G^{-1}[a][b] = sum_{k >= max(a, b)} W[k][a] W[k][b], entries a >= b
+    float* Gi = fac + goff[i];
+    const int ne = m * (m + 1) / 2;
+    for (int e = tid; e < ne; e += 256) {
+        int ra = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+        while (ra * (ra + 1) / 2 > e) --ra;
+        while ((ra + 1) * (ra + 2) / 2 <= e) ++ra;
+        const int cb = e - ra * (ra + 1) / 2;
+        // k = ra term: W[ra][ra] W[ra][cb] (W[ra][cb] = Wt[cb][ra], or dinv when cb == ra)
+        float acc = dinv[ra] * ((cb == ra) ? dinv[ra] : G[cb * gs + ra]);
+        for (int k = ra + 1; k < m; ++k) acc = fmaf(G[ra * gs + k], G[cb * gs + k], acc);
+        Gi[(size_t)ra * m + cb] = acc;
+        Gi[(size_t)cb * m + ra] = acc;
     }
 }
 
@@ -379,60 +410,79 @@ __host__ __device__ __forceinline__ int class_count(int c, int nb) {
 __host__ __device__ __forceinline__ int class_member(int c, int q, int nb) { return c == 2 ? nb - 1 : c + 2 * q; }
 
 // Local solves of one colour class (cx, cy), color = cy * 3 + cx:
-// v = (L L^T)^{-1} R_i r by forward and backward substitution, then
+// v = G_i^{-1} R_i r with the dense inverse from the setup, then
 // out += D_i v (out = P r after all nine classes). Subdomains of one class
 // never overlap, so the updates need no atomics and their order is fixed.
-// One warp per (subdomain, channel).
-__global__ void __launch_bounds__(128) k_tonal_local(LocalSolveArgs a) {
-    __shared__ float sv[4][kTonalMaxM];
-    const int wl = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
+// One warp (a CTA of 32 threads) per subdomain solves all channels; lane l
+// forms entries l, l + 32, ... of v, reading row c of the symmetric inverse
+// (coalesced) for every mask pixel c, so there is no serial substitution.
+__global__ void __launch_bounds__(32) k_tonal_local(LocalSolveArgs a) {
+    constexpr int NT = (kTonalMaxM + 31) / 32;
+    __shared__ float xs[4 * kTonalMaxM];
+    const int lane = threadIdx.x;
     const int cx = a.color % 3, cy = a.color / 3;
     const int hx = class_count(cx, a.nbx);
     const int hy = class_count(cy, a.nby);
-    const long long wid = (long long)blockIdx.x * 4 + wl;
-    if (wid >= (long long)hx * hy * a.nch) return;
-    const int ch = (int)(wid / (hx * hy));
-    const int q = (int)(wid - (long long)ch * hx * hy);
+    const int q = blockIdx.x;
+    if (q >= hx * hy) return;
     const int bx = class_member(cx, q % hx, a.nbx);
     const int by = class_member(cy, q / hx, a.nby);
     const int i = by * a.nbx + bx;
     const int m = a.off[i + 1] - a.off[i];
     if (m == 0) return;
+    const int nch = a.nch;   // 1..4 (image channels)
     const uint16_t* lst = a.list + a.off[i];
-    const float* L = a.fac + a.goff[i];
+    const float* __restrict__ Gi = a.fac + a.goff[i];
     const int x0 = sub_origin(bx, a.F.W, a.stride), y0 = sub_origin(by, a.F.H, a.stride);
-    const float* r = a.r + ch * a.F.cs;
-    float* v = sv[wl];
-    for (int k = lane; k < m; k += 32) {
-        const int code = lst[k];
-        v[k] = r[(size_t)(y0 + (code >> 5)) * a.F.pitch + x0 + (code & 31)];
+    size_t pix[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int k = lane + 32 * t;
+        pix[t] = 0;
+        if (k < m) {
+            const int code = lst[k];
+            pix[t] = (size_t)(y0 + (code >> 5)) * a.F.pitch + x0 + (code & 31);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < nch) xs[c * m + k] = a.r[c * a.F.cs + pix[t]];
+        }
     }
     __syncwarp();
-    // forward: L y = r (column-oriented)
+    float y[4][NT];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int t = 0; t < NT; ++t) y[c][t] = 0.f;
+#pragma unroll 4
     for (int j = 0; j < m; ++j) {
-        const float yj = v[j] / L[j * (j + 1) / 2 + j];
-        __syncwarp();
-        if (lane == 0) v[j] = yj;
-        for (int k = j + 1 + lane; k < m; k += 32) v[k] -= L[k * (k + 1) / 2 + j] * yj;
-        __syncwarp();
+        const float* row = Gi + (size_t)j * m;
+        float xj[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) xj[c] = (c < nch) ? xs[c * m + j] : 0.f;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int k = lane + 32 * t;
+            if (k < m) {
+                const float g = row[k];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) y[c][t] = fmaf(g, xj[c], y[c][t]);
+            }
+        }
     }
-    // backward: L^T x = y (row j of L holds column j of L^T)
-    for (int j = m - 1; j >= 0; --j) {
-        const float xj = v[j] / L[j * (j + 1) / 2 + j];
-        __syncwarp();
-        if (lane == 0) v[j] = xj;
-        const float* Lj = L + j * (j + 1) / 2;
-        for (int k = lane; k < j; k += 32) v[k] -= Lj[k] * xj;
-        __syncwarp();
-    }
-    for (int k = lane; k < m; k += 32) {
-        const int code = lst[k];
-        const int px = x0 + (code & 31), py = y0 + (code >> 5);
-        const int mult = cover_count(px, a.nbx, a.stride, a.F.W) * cover_count(py, a.nby, a.stride, a.F.H);
-        a.out[ch * a.F.cs + (size_t)py * a.F.pitch + px] += v[k] / (float)mult;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int k = lane + 32 * t;
+        if (k < m) {
+            const int code = lst[k];
+            const int px = x0 + (code & 31), py = y0 + (code >> 5);
+            const int mult = cover_count(px, a.nbx, a.stride, a.F.W) * cover_count(py, a.nby, a.stride, a.F.H);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < nch) a.out[c * a.F.cs + pix[t]] += y[c][t] / (float)mult;
+        }
     }
 }
+
 
 // ------------------------------------------------------------ the driver ---
 
@@ -457,7 +507,7 @@ int Ctx::tonal_setup() {
     int maxm = 0;
     for (int i = 0; i < nb; ++i) {
         off[i + 1] = off[i] + cnt[i];
-        goff[i + 1] = goff[i] + (long long)cnt[i] * (cnt[i] + 1) / 2;
+        goff[i + 1] = goff[i] + (long long)cnt[i] * cnt[i];
         maxm = std::max(maxm, cnt[i]);
     }
     if (maxm > kTonalMaxM)
@@ -578,10 +628,10 @@ void Ctx::tonal_local(float* out) {
         a.out = out;
         const int hx = class_count(color % 3, L0.nbx);
         const int hy = class_count(color / 3, L0.nby);
-        const long long warps = (long long)hx * hy * nch;
-        if (warps <= 0) continue;
+        const long long blocks = (long long)hx * hy;
+        if (blocks <= 0) continue;
         tstart(kT_Local);
-        k_tonal_local<<<(unsigned)((warps + 3) / 4), 128, 0, stream>>>(a);
+        k_tonal_local<<<(unsigned)blocks, 32, 0, stream>>>(a);
         ++launches;
         tstop();
     }
