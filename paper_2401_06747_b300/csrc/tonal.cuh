@@ -413,13 +413,16 @@ __host__ __device__ __forceinline__ int class_member(int c, int q, int nb) { ret
 // v = G_i^{-1} R_i r with the dense inverse from the setup, then
 // out += D_i v (out = P r after all nine classes). Subdomains of one class
 // never overlap, so the updates need no atomics and their order is fixed.
-// One warp (a CTA of 32 threads) per subdomain solves all channels; lane l
-// forms entries l, l + 32, ... of v, reading row c of the symmetric inverse
-// (coalesced) for every mask pixel c, so there is no serial substitution.
-__global__ void __launch_bounds__(32) k_tonal_local(LocalSolveArgs a) {
+// One CTA of kLocalWarps warps per subdomain solves all channels: warp w
+// takes the rows j = w, w + kLocalWarps, ... of the symmetric inverse (each
+// read coalesced), lane l accumulates entries l, l + 32, ... of v, and the
+// warps' partial sums are added in a fixed order.
+constexpr int kLocalWarps = 4;
+__global__ void __launch_bounds__(32 * kLocalWarps) k_tonal_local(LocalSolveArgs a) {
     constexpr int NT = (kTonalMaxM + 31) / 32;
     __shared__ float xs[4 * kTonalMaxM];
-    const int lane = threadIdx.x;
+    __shared__ float ps[kLocalWarps][4][NT * 32];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int cx = a.color % 3, cy = a.color / 3;
     const int hx = class_count(cx, a.nbx);
     const int hy = class_count(cy, a.nby);
@@ -434,27 +437,24 @@ __global__ void __launch_bounds__(32) k_tonal_local(LocalSolveArgs a) {
     const uint16_t* lst = a.list + a.off[i];
     const float* __restrict__ Gi = a.fac + a.goff[i];
     const int x0 = sub_origin(bx, a.F.W, a.stride), y0 = sub_origin(by, a.F.H, a.stride);
-    size_t pix[NT];
+    auto pixel = [&](int k) {
+        const int code = lst[k];
+        return (size_t)(y0 + (code >> 5)) * a.F.pitch + x0 + (code & 31);
+    };
+    for (int k = threadIdx.x; k < m; k += 32 * kLocalWarps) {
+        const size_t p = pixel(k);
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        const int k = lane + 32 * t;
-        pix[t] = 0;
-        if (k < m) {
-            const int code = lst[k];
-            pix[t] = (size_t)(y0 + (code >> 5)) * a.F.pitch + x0 + (code & 31);
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (c < nch) xs[c * m + k] = a.r[c * a.F.cs + pix[t]];
-        }
+        for (int c = 0; c < 4; ++c)
+            if (c < nch) xs[c * m + k] = a.r[c * a.F.cs + p];
     }
-    __syncwarp();
+    __syncthreads();
     float y[4][NT];
 #pragma unroll
     for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int t = 0; t < NT; ++t) y[c][t] = 0.f;
 #pragma unroll 4
-    for (int j = 0; j < m; ++j) {
+    for (int j = wl; j < m; j += kLocalWarps) {
         const float* row = Gi + (size_t)j * m;
         float xj[4];
 #pragma unroll
@@ -470,15 +470,23 @@ __global__ void __launch_bounds__(32) k_tonal_local(LocalSolveArgs a) {
         }
     }
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        const int k = lane + 32 * t;
-        if (k < m) {
-            const int code = lst[k];
-            const int px = x0 + (code & 31), py = y0 + (code >> 5);
-            const int mult = cover_count(px, a.nbx, a.stride, a.F.W) * cover_count(py, a.nby, a.stride, a.F.H);
+    for (int c = 0; c < 4; ++c)
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (c < nch) a.out[c * a.F.cs + pix[t]] += y[c][t] / (float)mult;
+        for (int t = 0; t < NT; ++t) ps[wl][c][t * 32 + lane] = y[c][t];
+    __syncthreads();
+    for (int k = threadIdx.x; k < m; k += 32 * kLocalWarps) {
+        const int code = lst[k];
+        const int px = x0 + (code & 31), py = y0 + (code >> 5);
+        const int mult = cover_count(px, a.nbx, a.stride, a.F.W) * cover_count(py, a.nby, a.stride, a.F.H);
+        const size_t p = (size_t)py * a.F.pitch + px;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (c < nch) {
+                float v = ps[0][c][k];
+#pragma unroll
+                for (int w = 1; w < kLocalWarps; ++w) v += ps[w][c][k];
+                a.out[c * a.F.cs + p] += v / (float)mult;
+            }
         }
     }
 }
@@ -631,7 +639,7 @@ void Ctx::tonal_local(float* out) {
         const long long blocks = (long long)hx * hy;
         if (blocks <= 0) continue;
         tstart(kT_Local);
-        k_tonal_local<<<(unsigned)blocks, 32, 0, stream>>>(a);
+        k_tonal_local<<<(unsigned)blocks, 32 * kLocalWarps, 0, stream>>>(a);
         ++launches;
         tstop();
     }
