@@ -658,29 +658,32 @@ __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
                     if (known) {
                         if (RHS == RHS_DATA) { const float bh = ch_ + cl; bb2 += bh * bh; }
                     } else {
-                        float sh = 0.f, sl = 0.f;
-                        const float nh[4] = {lh, rh, uh_, dh};
-                        const float nl[4] = {ll, rl, ul_, dl};
-                        const bool ok[4] = {hasl, hasr, y > 0, y + 1 < H};
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            if (ok[q]) {
-                                float e1, e2, s2, t2;
-                                two_sum(ch_, -nh[q], e1, e2);
-                                e2 += cl - nl[q];
-                                two_sum(sh, e1, s2, t2);
-                                sh = s2;
-                                sl += t2 + e2;
-                            }
-                        }
-                        float bh = 0.f, bl = 0.f;
+                        // A u = 4 u_c - (sum of the 4 neighbours), an absent
+                        // neighbour replaced by u_c (zero difference): the
+                        // neighbour sum and the difference by TwoSum, the low
+                        // parts added in FP32
+                        const float n0h = hasl ? lh : ch_, n0l = hasl ? ll : cl;
+                        const float n1h = hasr ? rh : ch_, n1l = hasr ? rl : cl;
+                        const float n2h = (y > 0) ? uh_ : ch_, n2l = (y > 0) ? ul_ : cl;
+                        const float n3h = (y + 1 < H) ? dh : ch_, n3l = (y + 1 < H) ? dl : cl;
+                        float sa, ea, sb, eb, sh, eh;
+                        two_sum(n0h, n1h, sa, ea);
+                        two_sum(n2h, n3h, sb, eb);
+                        two_sum(sa, sb, sh, eh);
+                        const float sl = ((n0l + n1l) + (n2l + n3l)) + ((ea + eb) + eh);
+                        float ah, ae;
+                        two_sum(4.f * ch_, -sh, ah, ae);
+                        const float al = ae + (4.f * cl - sl);   // A u = ah + al
                         if (RHS == RHS_SOURCE) {
+                            float bh, bl;
                             df_add(Dh[k], Dl[k], -Yh[k], -Yl[k], bh, bl);
                             bb2 += bh * bh;
+                            float rh2, rl2;
+                            df_add(bh, bl, -ah, -al, rh2, rl2);
+                            r = rh2 + rl2;
+                        } else {
+                            r = -(ah + al);   // b = 0 on unknown pixels
                         }
-                        float rh2, rl2;
-                        df_add(bh, bl, -sh, -sl, rh2, rl2);
-                        r = rh2 + rl2;
                     }
                     a.r32[idx] = r;
                     rr += r * r;
