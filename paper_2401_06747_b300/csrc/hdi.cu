@@ -290,16 +290,15 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     a.b = L.b;
     a.rnorm2 = rnorm2;
     a.iters = iters;
-    const int warps = L.nbx * L.nby * nch;
-    const int blocks = (warps + 3) / 4;
+    const int blocks = L.nbx * L.nby * nch;   // one CTA per (subdomain, channel)
     if (l == 0) tstart(kT_Oras);
     const bool full = L.W >= 32 && L.H >= 32;
     if (zero) {
-        if (full) k_oras<true, true><<<blocks, 128, 0, stream>>>(a);
-        else k_oras<true, false><<<blocks, 128, 0, stream>>>(a);
+        if (full) k_oras<true, true><<<blocks, kLocalThreads, 0, stream>>>(a);
+        else k_oras<true, false><<<blocks, kLocalThreads, 0, stream>>>(a);
     } else {
-        if (full) k_oras<false, true><<<blocks, 128, 0, stream>>>(a);
-        else k_oras<false, false><<<blocks, 128, 0, stream>>>(a);
+        if (full) k_oras<false, true><<<blocks, kLocalThreads, 0, stream>>>(a);
+        else k_oras<false, false><<<blocks, kLocalThreads, 0, stream>>>(a);
     }
     ++launches;
     if (l == 0) tstop();

@@ -1,16 +1,18 @@
-// oras.cuh -- warp-per-subdomain local solves (Sec. 3.1, Sec. 3.3).
+// oras.cuh -- subdomain local solves (Sec. 3.1, Sec. 3.3).
 //
-// One warp owns one 32x32 subdomain. Lane l holds the column pair
-// c = l & 15 (columns 2c and 2c+1) over the row half hh = l >> 4 (rows
-// 16hh .. 16hh+15); every per-lane array holds 16 float2 values, column 2c
-// in .x and 2c+1 in .y. The pair layout puts two pixels of one row in a
-// 64-bit register pair, so the vector updates and most of the stencil run as
-// packed FP32x2 operations (two results per instruction), and a lane needs
-// one shuffle per row and side for its horizontal neighbours (the inner
-// neighbours of the pair are its own registers). Vertical neighbours are
-// register neighbours, except across the two row halves (one xor-16 shuffle
-// per apply), and CG dot products are warp-shuffle reductions: a local solve
-// touches neither shared memory nor a block barrier.
+// One CTA of two warps owns one 32x32 subdomain. Thread t = 32 w + l holds
+// the column pair c = l & 15 (columns 2c, 2c+1) over the eight rows
+// r0 .. r0+7, r0 = 16 w + 8 (l >> 4): per-thread arrays hold 8 float2
+// values, column 2c in .x and 2c+1 in .y. The pair layout puts two pixels of
+// a row in a 64-bit register pair, so the vector updates and most of the
+// stencil run as packed FP32x2 operations; horizontal neighbours outside the
+// pair come by one shuffle per row and side, vertical ones are register
+// neighbours, the row octets of a warp meet by an xor-16 shuffle, and the two
+// warps meet at rows 15/16 through shared memory. CG dot products are warp
+// reductions plus one shared-memory exchange, and each iteration has two CTA
+// barriers: the boundary rows for the next stencil travel with the second
+// reduction (the neighbour warp's residual and old search direction, from
+// which each thread forms the new direction itself).
 //
 // Local operator A_i (Sec. 3.1): the global A restricted to the subdomain,
 // acting on corrections that vanish on known pixels. For an unknown pixel j
@@ -24,47 +26,50 @@
 #pragma once
 #include "common.cuh"
 
+constexpr int kLocalThreads = 64;   // threads per subdomain (two warps)
+
 struct LocalGeom {
     int x0, y0, w, h;     // subdomain origin and extent (w, h <= 32)
-    int c, hh;            // this lane's column pair and row half
-    uint32_t um;          // bit 2k+j: pixel (row 16hh+k, column 2c+j) is unknown and inside
+    int c, r0;            // this thread's column pair and first row
+    uint32_t um;          // bit 2k+j: pixel (row r0+k, column 2c+j) is unknown and inside
     // -1 where the neighbour lies in the subdomain, else 0: left of column
-    // 2c, right of column 2c+1, above row 0 / below row 15 of this half
+    // 2c, right of column 2c+1, above row r0 / below row r0+7
     float nwl, nwr, nwu, nwd;
     float2 dh;            // horizontal part of d_j for the two columns
     float dtop, dbot;     // weight of the outside neighbour above row 0 / below row h-1
-    float2 dfirst, dmid, dlast;   // 32x32 subdomains: diagonal of rows k = 0, 1..14, 15
+    float2 dfirst, dmid, dlast;   // 32x32 subdomains: diagonal of rows k = 0, 1..6, 7
 };
 
-// Per-warp shared-memory slab of the local CG: the 0/1 unknown-pixel mask of
-// the lane's 32 pixels as float2 (lane-private: each lane reads back only
-// what it wrote, so no synchronisation is needed). Multiplying by it inside
-// the packed stencil replaces a per-pixel bit test and select.
-constexpr int kLocalSlab = 16 * 32;   // float2 per warp
+// Shared memory of one subdomain's local CG.
+struct LocalShared {
+    float2 msk[8][kLocalThreads];  // 0/1 unknown-pixel mask per thread and row (thread-private)
+    float2 seam[2][2][2][16];      // [parity][side: 0 = row 15, 1 = row 16][R, P_old][column pair]
+    float red[5][2];               // warp partial sums: pq / rn by parity, initial rr
+};
 
-// Geometry of subdomain (x0, y0); writes the lane's mask floats to msk[k * 32]
-// (msk = warp slab + lane).
+// Geometry of subdomain (x0, y0); writes the thread's mask floats.
 __device__ __forceinline__ LocalGeom make_geom(int x0, int y0, int H, int W, const MaskView& m, float theta,
-                                               float2* msk) {
-    const int lane = threadIdx.x & 31;
+                                               LocalShared& sh) {
+    const int t = threadIdx.x;
+    const int lane = t & 31;
     LocalGeom g;
     g.x0 = x0;
     g.y0 = y0;
     g.w = min(32, W - x0);
     g.h = min(32, H - y0);
     g.c = lane & 15;
-    g.hh = lane >> 4;
-    const int c0 = 2 * g.c, r0 = 16 * g.hh;
-    // lane l fetches the mask word of row l (rows past the subdomain read as known)
+    g.r0 = 16 * (t >> 5) + 8 * (lane >> 4);
+    const int c0 = 2 * g.c;
+    // lane l of each warp fetches the mask word of row l (rows past the subdomain read as known)
     const uint32_t wrow = (lane < g.h) ? m.window(x0, y0 + lane) : ~0u;
     uint32_t um = 0;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const uint32_t kn = __shfl_sync(HDI_FULL, wrow, r0 + k) >> c0;   // bit 0: column c0, bit 1: c0 + 1
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t kn = __shfl_sync(HDI_FULL, wrow, g.r0 + k) >> c0;   // bit 0: column c0, bit 1: c0 + 1
         const bool u0 = c0 < g.w && !(kn & 1u), u1 = c0 + 1 < g.w && !(kn & 2u);
         um |= (u0 ? 1u : 0u) << (2 * k);
         um |= (u1 ? 1u : 0u) << (2 * k + 1);
-        msk[k * 32] = make_float2(u0 ? 1.f : 0.f, u1 ? 1.f : 0.f);
+        sh.msk[k][t] = make_float2(u0 ? 1.f : 0.f, u1 ? 1.f : 0.f);
     }
     g.um = um;
     auto horiz = [&](int C) {
@@ -78,21 +83,21 @@ __device__ __forceinline__ LocalGeom make_geom(int x0, int y0, int H, int W, con
     g.dbot = (y0 + g.h < H) ? theta : 0.f;
     g.nwl = (g.c > 0) ? -1.f : 0.f;
     g.nwr = (g.c < 15) ? -1.f : 0.f;
-    g.nwu = g.hh ? -1.f : 0.f;
-    g.nwd = g.hh ? 0.f : -1.f;
-    const float vf = g.hh ? 2.f : 1.f + g.dtop;
-    const float vl = g.hh ? 1.f + g.dbot : 2.f;
+    g.nwu = (g.r0 > 0) ? -1.f : 0.f;
+    g.nwd = (g.r0 + 8 < 32) ? -1.f : 0.f;
+    const float vf = (g.r0 == 0) ? 1.f + g.dtop : 2.f;
+    const float vl = (g.r0 + 7 == 31) ? 1.f + g.dbot : 2.f;
     g.dfirst = make_float2(g.dh.x + vf, g.dh.y + vf);
     g.dmid = make_float2(g.dh.x + 2.f, g.dh.y + 2.f);
     g.dlast = make_float2(g.dh.x + vl, g.dh.y + vl);
     return g;
 }
 
-// Diagonal of row k of this lane's half (both columns).
+// Diagonal of row r0 + k (both columns).
 template <bool FULL>
 __device__ __forceinline__ float2 local_diag(const LocalGeom& g, int k) {
-    if (FULL) return (k == 0) ? g.dfirst : ((k == 15) ? g.dlast : g.dmid);
-    const int R = 16 * g.hh + k;
+    if (FULL) return (k == 0) ? g.dfirst : ((k == 7) ? g.dlast : g.dmid);
+    const int R = g.r0 + k;
     const float v = ((R > 0) ? 1.f : g.dtop) + ((R < g.h - 1) ? 1.f : g.dbot);
     return make_float2(g.dh.x + v, g.dh.y + v);
 }
@@ -101,77 +106,106 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
     return make_float2(__shfl_xor_sync(HDI_FULL, v.x, m), __shfl_xor_sync(HDI_FULL, v.y, m));
 }
 
+// Sum over the CTA of one value per thread: warp sums, exchanged through
+// red[slot] across one barrier, added in a fixed order (every thread gets the
+// same result).
+__device__ __forceinline__ float cta_sum2(float v, LocalShared& sh, int slot) {
+    v = warp_sum_f(v);
+    if ((threadIdx.x & 31) == 0) sh.red[slot][threadIdx.x >> 5] = v;
+    __syncthreads();
+    return sh.red[slot][0] + sh.red[slot][1];
+}
+
 // Q = A_i P on the unknown pixels (P is zero on known / outside pixels, so
-// shuffles that fetch such pixels contribute zero; neighbours outside the
+// fetched neighbours of that kind contribute zero; neighbours outside the
 // subdomain carry weight 0). Q = d P + M (-neighbour sum) with M the 0/1
-// mask: on a known pixel P = 0 and M = 0, so Q = 0 there.
+// mask: on a known pixel P = 0 and M = 0, so Q = 0 there. Nb = rows r0-1
+// and r0+8 of P as seen by this thread (from the other octet or warp).
 template <bool FULL>
-__device__ __forceinline__ void local_apply(const LocalGeom& g, const float2* __restrict__ msk,
-                                            const float2 (&P)[16], float2 (&Q)[16]) {
-    const float2 U = shfl_xor2(P[15], 16);   // row 15 of the upper half (used by the lower half)
-    const float2 D = shfl_xor2(P[0], 16);    // row 16 of the lower half (used by the upper half)
+__device__ __forceinline__ void local_apply(const LocalGeom& g, const LocalShared& sh, const float2 (&P)[8],
+                                            float2 up, float2 dn, float2 (&Q)[8]) {
     const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const float2 mk = msk[k * 32];
+    for (int k = 0; k < 8; ++k) {
+        const float2 mk = sh.msk[k][threadIdx.x];
         const float L = __shfl_up_sync(HDI_FULL, P[k].y, 1);     // column 2c-1
         const float Rt = __shfl_down_sync(HDI_FULL, P[k].x, 1);  // column 2c+2
         float2 ns;   // minus the neighbour sum
         ns.x = fmaf(g.nwl, L, -P[k].y);
         ns.y = fmaf(g.nwr, Rt, -P[k].x);
         if (k > 0) ns = __ffma2_rn(m1, P[k - 1], ns);
-        else ns = __ffma2_rn(make_float2(g.nwu, g.nwu), U, ns);
-        if (k < 15) ns = __ffma2_rn(m1, P[k + 1], ns);
-        else ns = __ffma2_rn(make_float2(g.nwd, g.nwd), D, ns);
+        else ns = __ffma2_rn(make_float2(g.nwu, g.nwu), up, ns);
+        if (k < 7) ns = __ffma2_rn(m1, P[k + 1], ns);
+        else ns = __ffma2_rn(make_float2(g.nwd, g.nwd), dn, ns);
         Q[k] = __ffma2_rn(mk, ns, __fmul2_rn(local_diag<FULL>(g, k), P[k]));
     }
 }
 
 // Conjugate gradients on A_i v = r (v starts at 0; r holds the right-hand
 // side on entry and the final residual on exit). Stops when ||r||^2 <= thresh
-// or after maxit iterations; returns the iteration count.
+// or after maxit iterations; returns the iteration count. Called by all 64
+// threads of the CTA (the loop control is uniform: every thread holds the
+// same reduced values).
 template <bool FULL>
-__device__ __forceinline__ int local_cg(const LocalGeom& g, const float2* __restrict__ msk, float2 (&V)[16],
-                                        float2 (&R)[16], float thresh, int maxit) {
-    float2 P[16], Q[16];
+__device__ __forceinline__ int local_cg(const LocalGeom& g, LocalShared& sh, float2 (&V)[8], float2 (&R)[8],
+                                        float thresh, int maxit) {
+    const int t = threadIdx.x, lane = t & 31, wv = t >> 5, oct = lane >> 4;
+    // boundary rows exchanged between the warps: octet 1 of warp 0 owns
+    // row 15 (k = 7), octet 0 of warp 1 owns row 16 (k = 0)
+    const bool w15 = (wv == 0 && oct == 1), w16 = (wv == 1 && oct == 0);
+    float2 P[8], Q[8];
     float2 a0 = make_float2(0.f, 0.f), a1 = a0;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < 8; ++k) {
         V[k] = make_float2(0.f, 0.f);
         P[k] = R[k];
         if (k & 1) a1 = __ffma2_rn(R[k], R[k], a1);
         else a0 = __ffma2_rn(R[k], R[k], a0);
     }
-    float rr = warp_sum_f((a0.x + a0.y) + (a1.x + a1.y));
+    const float2 z2 = make_float2(0.f, 0.f);
+    if (w15) { sh.seam[0][0][0][g.c] = R[7]; sh.seam[0][0][1][g.c] = z2; }
+    if (w16) { sh.seam[0][1][0][g.c] = R[0]; sh.seam[0][1][1][g.c] = z2; }
+    float rr = cta_sum2((a0.x + a0.y) + (a1.x + a1.y), sh, 4);
+    float beta = 0.f;   // P = R + beta * P_old for the rows in the seam buffer
     int it = 0;
     while (rr > thresh && it < maxit) {
-        local_apply<FULL>(g, msk, P, Q);
+        const int par = it & 1;
+        // rows r0-1 / r0+8: the other octet of the warp, or the other warp
+        const float2 xu = shfl_xor2(P[7], 16), xd = shfl_xor2(P[0], 16);
+        const float2 b2 = make_float2(beta, beta);
+        float2 up = xu, dn = xd;
+        if (oct == 0) up = __ffma2_rn(b2, sh.seam[par][0][1][g.c], sh.seam[par][0][0][g.c]);
+        if (oct == 1) dn = __ffma2_rn(b2, sh.seam[par][1][1][g.c], sh.seam[par][1][0][g.c]);
+        local_apply<FULL>(g, sh, P, up, dn, Q);
         a0 = make_float2(0.f, 0.f);
         a1 = a0;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 8; ++k) {
             if (k & 1) a1 = __ffma2_rn(P[k], Q[k], a1);
             else a0 = __ffma2_rn(P[k], Q[k], a0);
         }
-        const float pq = warp_sum_f((a0.x + a0.y) + (a1.x + a1.y));
+        const float pq = cta_sum2((a0.x + a0.y) + (a1.x + a1.y), sh, par * 2);
         if (!(pq > 0.f)) break;
         const float alpha = rr / pq;
         const float2 al = make_float2(alpha, alpha), nal = make_float2(-alpha, -alpha);
         a0 = make_float2(0.f, 0.f);
         a1 = a0;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 8; ++k) {
             V[k] = __ffma2_rn(al, P[k], V[k]);
             R[k] = __ffma2_rn(nal, Q[k], R[k]);
             if (k & 1) a1 = __ffma2_rn(R[k], R[k], a1);
             else a0 = __ffma2_rn(R[k], R[k], a0);
         }
-        const float rn = warp_sum_f((a0.x + a0.y) + (a1.x + a1.y));
-        const float beta = rn / rr;
+        const int npar = par ^ 1;
+        if (w15) { sh.seam[npar][0][0][g.c] = R[7]; sh.seam[npar][0][1][g.c] = P[7]; }
+        if (w16) { sh.seam[npar][1][0][g.c] = R[0]; sh.seam[npar][1][1][g.c] = P[0]; }
+        const float rn = cta_sum2((a0.x + a0.y) + (a1.x + a1.y), sh, par * 2 + 1);
+        beta = rn / rr;
         rr = rn;
         const float2 be = make_float2(beta, beta);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) P[k] = __ffma2_rn(be, P[k], R[k]);
+        for (int k = 0; k < 8; ++k) P[k] = __ffma2_rn(be, P[k], R[k]);
         ++it;
     }
     return it;
@@ -193,28 +227,25 @@ struct OrasArgs {
     unsigned long long* iters; // optional: total local CG iterations
 };
 
-// Launch bounds: 3 CTAs of 4 warps per SM leave 168 registers per thread,
-// enough for the four 32-value vectors of the local CG without spills.
 // One ORAS iteration (Sec. 3.1): u <- u + sum_i R~_i^T v_i with
 // A_i v_i = R_i (b - A u). Restricted extension: each pixel takes the
 // correction of the one subdomain whose core (the subdomain minus half the
 // overlap on each inner side) contains it, so every output pixel is written
-// by exactly one warp and the sweep needs no atomics.
+// by exactly one thread and the sweep needs no atomics.
+// One CTA per (subdomain, channel); 10 CTAs per SM leave 102 registers per
+// thread, enough for the four 16-value vectors of the local CG.
 template <bool ZERO, bool FULL>
-__global__ void __launch_bounds__(128, 3) k_oras(OrasArgs a) {
-    __shared__ float2 slab[4 * kLocalSlab];
-    const int wid = blockIdx.x * 4 + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(kLocalThreads, 10) k_oras(OrasArgs a) {
+    __shared__ LocalShared sh;
     const int nb = a.nbx * a.nby;
-    if (wid >= nb * a.nch) return;
-    const int ch = wid / nb;
-    const int bi = wid - ch * nb;
+    const int ch = blockIdx.x / nb;
+    const int bi = blockIdx.x - ch * nb;
     const int by = bi / a.nbx;
     const int bx = bi - by * a.nbx;
     const int x0 = sub_origin(bx, a.W, a.stride), y0 = sub_origin(by, a.H, a.stride);
     const double rn2 = a.rnorm2[ch];
-    float2* msk = slab + (threadIdx.x >> 5) * kLocalSlab + (threadIdx.x & 31);
-    const LocalGeom g = make_geom(x0, y0, a.H, a.W, a.m.ch(ch), a.theta, msk);
-    const int c0 = 2 * g.c, r0 = 16 * g.hh;
+    const LocalGeom g = make_geom(x0, y0, a.H, a.W, a.m.ch(ch), a.theta, sh);
+    const int c0 = 2 * g.c, r0 = g.r0;
     const int gx = x0 + c0;                       // absolute column of .x
     const int cx0 = min(gx, a.W - 1), cx1 = min(gx + 1, a.W - 1);
     // 8-byte aligned pair inside the image: one float2 access per row
@@ -227,14 +258,14 @@ __global__ void __launch_bounds__(128, 3) k_oras(OrasArgs a) {
         return make_float2(p[row + cx0], p[row + cx1]);
     };
 
-    float2 R[16], V[16];
+    float2 R[8], V[8];
     {
-        float2 B[16];
+        float2 B[8];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) B[k] = ld2(bb, y0 + r0 + k);
+        for (int k = 0; k < 8; ++k) B[k] = ld2(bb, y0 + r0 + k);
         if (ZERO) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
+            for (int k = 0; k < 8; ++k) {
                 R[k].x = ((g.um >> (2 * k)) & 1u) ? B[k].x : 0.f;
                 R[k].y = ((g.um >> (2 * k + 1)) & 1u) ? B[k].y : 0.f;
             }
@@ -244,18 +275,18 @@ __global__ void __launch_bounds__(128, 3) k_oras(OrasArgs a) {
             // All loads are issued before the arithmetic.
             const bool hl = (g.c == 0 && x0 > 0) || (g.c == 15 && x0 + 32 < a.W);
             const int hcol = hl ? ((g.c == 0) ? x0 - 1 : x0 + 32) : cx0;
-            float2 X[18];
-            float HV[16];
+            float2 X[10];
+            float HV[8];
 #pragma unroll
-            for (int t = 0; t < 18; ++t) X[t] = ld2(xin, y0 + r0 - 1 + t);
+            for (int t = 0; t < 10; ++t) X[t] = ld2(xin, y0 + r0 - 1 + t);
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
+            for (int k = 0; k < 8; ++k)
                 HV[k] = hl ? xin[(size_t)min(y0 + r0 + k, a.H - 1) * a.pitch + hcol] : 0.f;
             const bool in1 = gx + 1 < a.W;        // column of .y inside the image
             const bool in2 = gx + 2 < a.W;        // column right of the pair inside the image
             const bool inl = gx > 0;              // column left of the pair inside the image
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
+            for (int k = 0; k < 8; ++k) {
                 const int y = y0 + r0 + k;
                 const float2 up = X[k], xc = X[k + 1], dn = X[k + 2];
                 float L = __shfl_up_sync(HDI_FULL, xc.y, 1);
@@ -276,8 +307,8 @@ __global__ void __launch_bounds__(128, 3) k_oras(OrasArgs a) {
         }
     }
     const float thresh = (float)(rn2 * a.thresh_scale);
-    const int it = local_cg<FULL>(g, msk, V, R, thresh, a.maxit);
-    if (a.iters && (threadIdx.x & 31) == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
+    const int it = local_cg<FULL>(g, sh, V, R, thresh, a.maxit);
+    if (a.iters && threadIdx.x == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
 
     // owned core in absolute coordinates, then relative to the (possibly
     // shifted) origin
@@ -290,14 +321,14 @@ __global__ void __launch_bounds__(128, 3) k_oras(OrasArgs a) {
         float* __restrict__ xo = a.xout + ch * a.cstride;
         if (!ZERO) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
+            for (int k = 0; k < 8; ++k) {
                 const float2 xv = ld2(xin, y0 + r0 + k);
                 V[k].x += xv.x;
                 V[k].y += xv.y;
             }
         }
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 8; ++k) {
             const int R0 = r0 + k;
             if (R0 >= oy0 && R0 < oy1) {
                 const size_t idx = (size_t)(y0 + R0) * a.pitch + gx;

@@ -81,11 +81,12 @@ struct EchoArgs {
     unsigned long long* iters;
 };
 
-// One warp per (subdomain, mask pixel k): solve the Neumann subdomain problem
-// L_UU x = L_UK e_k by CG; x = S e_k is stored row-major over the 32x32 tile.
-__global__ void __launch_bounds__(128, 3) k_tonal_echo(EchoArgs a) {
-    __shared__ float2 slab[4 * kLocalSlab];
-    const long long e = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+// One CTA (two warps) per (subdomain, mask pixel k): solve the Neumann
+// subdomain problem L_UU x = L_UK e_k by CG; x = S e_k is stored row-major
+// over the 32x32 tile.
+__global__ void __launch_bounds__(kLocalThreads, 8) k_tonal_echo(EchoArgs a) {
+    __shared__ LocalShared sh;
+    const long long e = blockIdx.x;
     const int total = a.off[a.nb];
     if (e >= total) return;
     // subdomain owning echo e: largest i with off[i] <= e
@@ -97,16 +98,15 @@ __global__ void __launch_bounds__(128, 3) k_tonal_echo(EchoArgs a) {
     const int i = lo;
     const int by = i / a.nbx, bx = i - by * a.nbx;
     const int x0 = sub_origin(bx, a.m.W, a.stride), y0 = sub_origin(by, a.m.H, a.stride);
-    float2* msk = slab + (threadIdx.x >> 5) * kLocalSlab + (threadIdx.x & 31);
-    const LocalGeom g = make_geom(x0, y0, a.m.H, a.m.W, a.m, 0.f, msk);
+    const LocalGeom g = make_geom(x0, y0, a.m.H, a.m.W, a.m, 0.f, sh);
     const int code = a.list[e];
     const int ky = code >> 5, kx = code & 31;
-    const int c0 = 2 * g.c, r0 = 16 * g.hh;
+    const int c0 = 2 * g.c, r0 = g.r0;
     // right-hand side L_UK e_k: -1 at the unknown 4-neighbours of k inside the subdomain
-    float2 R[16], V[16];
+    float2 R[8], V[8];
     float2 a0 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < 8; ++k) {
         const int y = r0 + k;
         const bool nx = (c0 == kx && (y == ky - 1 || y == ky + 1)) || (y == ky && (c0 == kx - 1 || c0 == kx + 1));
         const bool ny =
@@ -115,14 +115,15 @@ __global__ void __launch_bounds__(128, 3) k_tonal_echo(EchoArgs a) {
         R[k].y = (ny && ((g.um >> (2 * k + 1)) & 1u)) ? -1.f : 0.f;
         a0 = __ffma2_rn(R[k], R[k], a0);
     }
-    const float rr0 = warp_sum_f(a0.x + a0.y);
-    const int it = (g.w == 32 && g.h == 32) ? local_cg<true>(g, msk, V, R, a.rtol2 * rr0, a.maxit)
-                                            : local_cg<false>(g, msk, V, R, a.rtol2 * rr0, a.maxit);
-    if (a.iters && (threadIdx.x & 31) == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
+    const float rr0 = cta_sum2(a0.x + a0.y, sh, 4);
+    const int it = (g.w == 32 && g.h == 32) ? local_cg<true>(g, sh, V, R, a.rtol2 * rr0, a.maxit)
+                                            : local_cg<false>(g, sh, V, R, a.rtol2 * rr0, a.maxit);
+    if (a.iters && threadIdx.x == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
     float* out = a.echo + (size_t)e * 1024;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) *reinterpret_cast<float2*>(out + (r0 + k) * 32 + c0) = V[k];
+    for (int k = 0; k < 8; ++k) *reinterpret_cast<float2*>(out + (r0 + k) * 32 + c0) = V[k];
 }
+
 
 // Shared-memory floats of k_tonal_gram for subdomains of up to m mask pixels.
 __host__ __device__ inline int gram_round4(int m) { return (m + 3) & ~3; }
@@ -590,7 +591,7 @@ int Ctx::tonal_setup() {
         ea.maxit = (int)p.tonal_echo_max_iter;
         ea.iters = counters + kCntEcho;
         tstart(kT_Echo);
-        k_tonal_echo<<<(unsigned)((total + 3) / 4), 128, 0, stream>>>(ea);
+        k_tonal_echo<<<(unsigned)total, kLocalThreads, 0, stream>>>(ea);
         ++launches;
         tstop();
         const size_t shm = gram_smem_floats(maxm) * 4;
