@@ -132,7 +132,7 @@ __device__ __forceinline__ float fine_residual(const float* __restrict__ x, cons
 // consecutive rows are summed in registers and lane pairs (2j, 2j+1) are
 // combined by a shuffle.
 #define CS_ROWS 64
-#define CS_CHUNK 8
+#define CS_CHUNK 4
 #ifndef RES_CHUNK
 #define RES_CHUNK 4
 #endif
