@@ -140,7 +140,7 @@ __device__ __forceinline__ float fine_residual(const float* __restrict__ x, cons
 // Rows per CTA of the column-strip kernels: long strips on large levels (few
 // CTAs take part in each grid reduction), short ones on small levels, where
 // the serial walk down the rows would otherwise dominate. Always even (the
-// restriction pairs rows) and, from 8 rows on, a multiple of the load chunk.
+// restriction pairs rows) and, from CS_CHUNK rows on, a multiple of it.
 static inline int strip_rows(int H, int W, int nch) {
     const long long cols = (long long)((W + 127) / 128) * nch;
     long long rows = (long long)H * cols / 2400;   // aim at >= ~2400 CTAs
