@@ -177,6 +177,18 @@ def all_max(x: float, world: int) -> float:
 #   restrict_fine : read x, b, mask; write b_H/4                   9.125
 ALGO_BYTES_PER_VALUE = {"oras_fine": 12.125, "residual_fine": 24.125, "prolong_fine": 13.125,
                         "restrict_fine": 9.125}
+# The level-0 ORAS sweep is bound by FP32 arithmetic, not by HBM: its local CG
+# runs about ten iterations in registers per subdomain, some 20 flops per byte
+# moved. Algorithmic flops per unknown subdomain pixel: 16 per local CG
+# iteration (A p: four adds and one FMA = 6; p.q and r.r: 2 each; the updates
+# of v, r and p: 2 each) and 9 per sweep (the initial residual b - A x: four
+# differences, three adds and a subtraction; the output add).
+ORAS_FLOPS_PER_ITER = 16
+ORAS_FLOPS_PER_SWEEP = 9
+# FP32 peak from the unit counts and the maximum SM clock: 148 SMs x 128 FP32
+# lanes x 2 flops per FMA x 2032 MHz.
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2032e6 / 1e12
+SUB, OV = 32, 6   # ORAS subdomain size and overlap
 
 
 def run_hdi(args, rank, world):
@@ -237,10 +249,8 @@ def run_hdi(args, rank, world):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    peak = float(peaks.get("hbm_gbs", 6400.0))
-    bytes_per_launch = ALGO_BYTES_PER_VALUE[name] * H4K * W4K * CH
-    avg_s = (ms / max(n, 1)) / 1e3
-    achieved = bytes_per_launch / avg_s / 1e9 if n else 0.0
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6400 GB/s"
     share = ms / max(t_max, 1e-9)
     traffic = None
     tpath = os.path.join(ROOT, "profiles", f"{name}_4k_rgb.md")
@@ -248,12 +258,35 @@ def run_hdi(args, rank, world):
         for line in open(tpath):
             if line.startswith("traffic_bytes_per_launch:"):
                 traffic = int(line.split(":")[1])
-    roofline = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_launch": bytes_per_launch, "launches": n, "avg_ms": round(ms / max(n, 1), 4),
-                "share_of_step_time": round(share, 3),
-                "classes_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kt.items()}}
+    values = H4K * W4K * CH
+
+    def hbm_entry(k):
+        kms, kn = kt[k]
+        b = ALGO_BYTES_PER_VALUE[k] * values
+        gbs = b / ((kms / max(kn, 1)) / 1e3) / 1e9 if kn else 0.0
+        return {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+                "algorithmic_bytes_per_launch": b, "launches": kn, "avg_ms": round(kms / max(kn, 1), 4)}
+
+    if name == "oras_fine":
+        nsub = -(-(W4K - OV) // (SUB - OV)) * -(-(H4K - OV) // (SUB - OV)) * CH
+        unknown = SUB * SUB * (1.0 - DENSITY)
+        iters = sum(s1["local_iters"] + s2["local_iters"] for s1, s2 in stats)
+        flops = unknown * (ORAS_FLOPS_PER_ITER * iters + ORAS_FLOPS_PER_SWEEP * nsub * n)
+        achieved = flops / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+        roofline = {"bound": "alu", "kernel": name, "achieved": round(achieved, 2), "peak": round(FP32_PEAK_TFLOPS, 2),
+                    "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": traffic,
+                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2032 MHz",
+                    "algorithmic_flops_per_launch": round(flops / max(n, 1)), "local_cg_iterations_per_launch":
+                    round(iters / max(n, 1)), "launches": n, "avg_ms": round(ms / max(n, 1), 4),
+                    "share_of_step_time": round(share, 3)}
+    else:
+        roofline = dict(hbm_entry(name), bound="hbm", kernel=name, traffic=traffic, peak_source=hbm_src,
+                        share_of_step_time=round(share, 3))
+    roofline["classes_ms_per_step"] = {k: round(v[0] / args.steps, 3) for k, v in kt.items()}
+    # the streaming stencil kernels against the HBM roofline
+    roofline["stencil_hbm"] = {k: hbm_entry(k) for k in ("residual_fine", "prolong_fine", "restrict_fine")
+                               if kt.get(k, (0, 0))[1]}
+    roofline["stencil_hbm_peak_source"] = hbm_src
 
     # end to end through the public API with host buffers
     fh = torch.from_numpy(f).pin_memory()
