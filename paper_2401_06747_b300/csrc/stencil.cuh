@@ -197,30 +197,34 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
         float up = (y0 > 0) ? xc[(size_t)(y0 - 1) * F.pitch + pxc] : 0.f;
         float cen = xc[(size_t)y0 * F.pitch + pxc];
         float pair = 0.f;
-        for (int yb = y0; yb < y1; yb += CR) {
+        struct Chunk {
             float Xd[CR], Hv[CR], Bv[CR];
             uint32_t Mw[CR], Cw[CR / 2];
+        };
+        auto load = [&](Chunk& c, int yb) {
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
                 const int y = min(yb + k, F.H - 1);
                 const size_t ry = (size_t)y * F.pitch;
-                Xd[k] = xc[(size_t)min(yb + k + 1, F.H - 1) * F.pitch + pxc];
-                Hv[k] = hl.on ? xc[ry + hl.col] : 0.f;
-                Bv[k] = bc[ry + pxc];
-                Mw[k] = mrow[(size_t)y * fm.wpitch];
+                c.Xd[k] = xc[(size_t)min(yb + k + 1, F.H - 1) * F.pitch + pxc];
+                c.Hv[k] = hl.on ? xc[ry + hl.col] : 0.f;
+                c.Bv[k] = bc[ry + pxc];
+                c.Mw[k] = mrow[(size_t)y * fm.wpitch];
             }
 #pragma unroll
-            for (int k = 0; k < CR / 2; ++k) Cw[k] = cmw[(size_t)min((yb >> 1) + k, C.H - 1) * cm.wpitch];
+            for (int k = 0; k < CR / 2; ++k) c.Cw[k] = cmw[(size_t)min((yb >> 1) + k, C.H - 1) * cm.wpitch];
+        };
+        auto compute = [&](const Chunk& c, int yb) {
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
                 const int y = yb + k;
                 if (y >= y1) break;
-                const float dn = Xd[k];
+                const float dn = c.Xd[k];
                 float lf = __shfl_up_sync(HDI_FULL, cen, 1);
                 float rt = __shfl_down_sync(HDI_FULL, cen, 1);
-                if (lane == 0) lf = Hv[k];
-                if (lane == 31) rt = Hv[k];
-                const bool known = (Mw[k] >> lane) & 1u;
+                if (lane == 0) lf = c.Hv[k];
+                if (lane == 31) rt = c.Hv[k];
+                const bool known = (c.Mw[k] >> lane) & 1u;
                 float r = 0.f;
                 if (act && !known) {
                     float lap = 0.f;
@@ -228,14 +232,14 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
                     if (hasr) lap += cen - rt;
                     if (y > 0) lap += cen - up;
                     if (y + 1 < F.H) lap += cen - dn;
-                    r = Bv[k] - lap;
+                    r = c.Bv[k] - lap;
                 }
                 pair += r;
                 if ((y & 1) || y + 1 == F.H) {
                     const float s = pair + __shfl_down_sync(HDI_FULL, pair, 1);
                     const int Y = y >> 1;
                     if (!(lane & 1) && act) {
-                        const float v = ((Cw[k >> 1] >> (X & 31)) & 1u) ? 0.f : s;
+                        const float v = ((c.Cw[k >> 1] >> (X & 31)) & 1u) ? 0.f : s;
                         cb[ch * C.cs + (size_t)Y * C.pitch + X] = v;
                         sq += v * v;
                     }
@@ -244,6 +248,17 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
                 up = cen;
                 cen = dn;
             }
+        };
+        // two chunk buffers: the loads of the next chunk are in flight while
+        // the current one is computed
+        Chunk A, B;
+        load(A, y0);
+        for (int yb = y0; yb < y1; yb += 2 * CR) {
+            if (yb + CR < y1) load(B, yb + CR);
+            compute(A, yb);
+            if (yb + CR >= y1) break;
+            if (yb + 2 * CR < y1) load(A, yb + 2 * CR);
+            compute(B, yb + CR);
         }
     }
     const double tot = (double)block_sum_f(sq);
