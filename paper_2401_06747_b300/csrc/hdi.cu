@@ -339,10 +339,11 @@ void Ctx::vcycle(int l) {
     (void)have_x;
     Level& C = lev[l + 1];
     {
-        dim3 blk(128), grd = tiles_of(L, nch);
+        const int qr = quad_rows(L.H, L.W, nch);
+        dim3 blk(128), grd = quad_grid(L.H, L.W, nch, qr);
         if (l == 0) tstart(kT_Restrict);
         k_restrict_residual<<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, arr(l + 1), mview(l + 1), C.b,
-                                                     reducer(l + 1, grd.x * grd.y), strip_rows(L.H, L.W, nch));
+                                                     reducer(l + 1, grd.x * grd.y), qr);
         ++launches;
         if (l == 0) tstop();
     }
@@ -372,9 +373,9 @@ void Ctx::vcycle(int l) {
 // coarse level's zero-filled scratch is avoided: a plain residual pass).
 void Ctx::residual_norm_level(int l, const float* x, int slot) {
     const Level& L = lev[l];
-    dim3 grd = tiles_of(L, nch), blk(128);
-    k_level_residual_norm<<<grd, blk, 0, stream>>>(arr(l), mview(l), x, L.b, reducer(slot, grd.x * grd.y),
-                                                   strip_rows(L.H, L.W, nch));
+    const int qr = quad_rows(L.H, L.W, nch);
+    dim3 grd = quad_grid(L.H, L.W, nch, qr), blk(128);
+    k_level_residual_norm<<<grd, blk, 0, stream>>>(arr(l), mview(l), x, L.b, reducer(slot, grd.x * grd.y), qr);
     ++launches;
 }
 

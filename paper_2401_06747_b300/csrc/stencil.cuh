@@ -168,89 +168,156 @@ __device__ __forceinline__ StripHalo strip_halo(int lane, int px, int pxc, int W
     return h;
 }
 
+// ---- quad strips ----
+// A warp covers 128 columns of `rows` rows: lane l holds columns x0 + 4l ..
+// x0 + 4l + 3 as one float4 (16-byte loads: rows are 128-byte aligned and x0
+// is a multiple of 128), so one load instruction moves 512 bytes. A CTA
+// stacks four warps on consecutive row blocks of one strip. Lanes 0 and 31
+// read the neighbouring strips' edge columns; lanes past the image still
+// take part in the shuffles with clamped loads. Rows are walked in chunks of
+// QS_CHUNK with two chunk buffers: the next chunk's loads are in flight
+// while the current one is computed.
+#define QS_COLS 128
+#define QS_CHUNK 2
+
+// Rows per warp: the same number of warps as column strips of
+// strip_rows(H, W, nch) rows would give, at least one chunk, even.
+static inline int quad_rows(int H, int W, int nch) {
+    int r = strip_rows(H, W, nch) / 4;
+    r = (r + QS_CHUNK - 1) / QS_CHUNK * QS_CHUNK;
+    return r < QS_CHUNK ? QS_CHUNK : r;
+}
+static inline dim3 quad_grid(int H, int W, int nch, int rows) {
+    return dim3((W + QS_COLS - 1) / QS_COLS, (H + 4 * rows - 1) / (4 * rows), nch);
+}
+
+struct QuadLane {
+    int lane, x0, c0, cq;    // strip origin, first column of the lane, clamped load column
+    bool act[4];             // column c0 + j inside the image
+    bool lin[4], rin[4];     // left / right neighbour of column c0 + j inside the image
+    bool hon;                // lane 0 / 31 reads a halo column
+    int hcol;                // that column (clamped when unused)
+    int shift;               // bit of column c0 in its mask word
+    int mword;               // index of that word within a mask row
+};
+__device__ __forceinline__ QuadLane quad_lane(int x0, const LevelArr& F, const MaskView& m) {
+    QuadLane q;
+    q.lane = threadIdx.x & 31;
+    q.x0 = x0;
+    q.c0 = x0 + 4 * q.lane;
+    q.cq = min(q.c0, F.pitch - 4);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        q.act[j] = q.c0 + j < F.W;
+        q.lin[j] = q.c0 + j > 0;
+        q.rin[j] = q.c0 + j + 1 < F.W;
+    }
+    q.hon = (q.lane == 0 && x0 > 0) || (q.lane == 31 && x0 + QS_COLS < F.W);
+    q.hcol = q.hon ? ((q.lane == 0) ? x0 - 1 : x0 + QS_COLS) : min(q.c0, F.W - 1);
+    q.shift = q.c0 & 31;
+    q.mword = min(q.c0 >> 5, m.wpitch - 1);
+    return q;
+}
+__device__ __forceinline__ void f4_to(const float4 v, float (&a)[4]) {
+    a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+}
+// b - A x at the lane's four columns of one row (difference form; absent
+// neighbours contribute nothing), given the rows above / below and the halo.
+__device__ __forceinline__ void quad_residual(const QuadLane& q, const float (&c)[4], const float (&u)[4],
+                                             const float (&d)[4], const float (&bv)[4], float hv, bool hasu,
+                                             bool hasd, float (&r)[4]) {
+    float lw = __shfl_up_sync(HDI_FULL, c[3], 1);
+    float rw = __shfl_down_sync(HDI_FULL, c[0], 1);
+    if (q.lane == 0) lw = hv;
+    if (q.lane == 31) rw = hv;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float l = (j == 0) ? lw : c[j - 1];
+        const float rr = (j == 3) ? rw : c[j + 1];
+        float lap = 0.f;
+        if (q.lin[j]) lap += c[j] - l;
+        if (q.rin[j]) lap += c[j] - rr;
+        if (hasu) lap += c[j] - u[j];
+        if (hasd) lap += c[j] - d[j];
+        r[j] = bv[j] - lap;
+    }
+}
+
 // r = b - A x on level F with 2x2 sums into the coarse right-hand side
 // (restriction, Sec. 3.2), zero on coarse known pixels, and ||r_c||^2 per
-// channel.
+// channel. Quad strips: the lane's four columns feed two coarse columns.
 __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                            const float* __restrict__ b, LevelArr C, MaskView cm,
                                                            float* __restrict__ cb, GridReduce red, int rows) {
-    constexpr int CR = CS_CHUNK;
-    const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
-    const int px = x0 + lane;
-    const int y0 = blockIdx.y * rows;
-    const int y1 = min(y0 + rows, F.H);
+    constexpr int CR = QS_CHUNK;
+    static_assert(CR == 2, "one coarse row per chunk");
     const int ch = blockIdx.z;
     fm = fm.ch(ch);
     cm = cm.ch(ch);
-    const bool act = px < F.W;
-    const int pxc = act ? px : F.W - 1;
+    const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * rows;
+    const int y1 = min(y0 + rows, F.H);
+    const QuadLane q = quad_lane(blockIdx.x * QS_COLS, F, fm);
     const float* xc = x + ch * F.cs;
     const float* bc = b + ch * F.cs;
     float sq = 0.f;
-    if (x0 < F.W) {
-        const uint32_t* mrow = fm.bits + (x0 >> 5);
-        const StripHalo hl = strip_halo(lane, px, pxc, F.W);
-        const bool hasl = px > 0, hasr = px + 1 < F.W;
-        const int X = min(pxc >> 1, C.W - 1);
-        const uint32_t* cmw = cm.bits + (X >> 5);
-        float up = (y0 > 0) ? xc[(size_t)(y0 - 1) * F.pitch + pxc] : 0.f;
-        float cen = xc[(size_t)y0 * F.pitch + pxc];
-        float pair = 0.f;
+    if (y0 < F.H) {
+        const uint32_t* mrow = fm.bits + q.mword;
+        const int X = q.c0 >> 1;                  // first of the lane's two coarse columns
+        const uint32_t* cmw = cm.bits + min(X >> 5, cm.wpitch - 1);
+        float up[4] = {0.f, 0.f, 0.f, 0.f}, cen[4];
+        if (y0 > 0) f4_to(*reinterpret_cast<const float4*>(xc + (size_t)(y0 - 1) * F.pitch + q.cq), up);
+        f4_to(*reinterpret_cast<const float4*>(xc + (size_t)y0 * F.pitch + q.cq), cen);
+        float pair[2] = {0.f, 0.f};
         struct Chunk {
-            float Xd[CR], Hv[CR], Bv[CR];
-            uint32_t Mw[CR], Cw[CR / 2];
+            float4 Xd[CR], Bv[CR];
+            float Hv[CR];
+            uint32_t Mw[CR], Cw;
         };
         auto load = [&](Chunk& c, int yb) {
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
-                const int y = min(yb + k, F.H - 1);
-                const size_t ry = (size_t)y * F.pitch;
-                c.Xd[k] = xc[(size_t)min(yb + k + 1, F.H - 1) * F.pitch + pxc];
-                c.Hv[k] = hl.on ? xc[ry + hl.col] : 0.f;
-                c.Bv[k] = bc[ry + pxc];
-                c.Mw[k] = mrow[(size_t)y * fm.wpitch];
+                const size_t ry = (size_t)min(yb + k, F.H - 1) * F.pitch;
+                c.Xd[k] = *reinterpret_cast<const float4*>(xc + (size_t)min(yb + k + 1, F.H - 1) * F.pitch + q.cq);
+                c.Bv[k] = *reinterpret_cast<const float4*>(bc + ry + q.cq);
+                c.Hv[k] = q.hon ? xc[ry + q.hcol] : 0.f;
+                c.Mw[k] = mrow[(size_t)min(yb + k, F.H - 1) * fm.wpitch];
             }
-#pragma unroll
-            for (int k = 0; k < CR / 2; ++k) c.Cw[k] = cmw[(size_t)min((yb >> 1) + k, C.H - 1) * cm.wpitch];
+            c.Cw = cmw[(size_t)min(yb >> 1, C.H - 1) * cm.wpitch];   // CR == 2: one coarse row
         };
         auto compute = [&](const Chunk& c, int yb) {
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
                 const int y = yb + k;
                 if (y >= y1) break;
-                const float dn = c.Xd[k];
-                float lf = __shfl_up_sync(HDI_FULL, cen, 1);
-                float rt = __shfl_down_sync(HDI_FULL, cen, 1);
-                if (lane == 0) lf = c.Hv[k];
-                if (lane == 31) rt = c.Hv[k];
-                const bool known = (c.Mw[k] >> lane) & 1u;
-                float r = 0.f;
-                if (act && !known) {
-                    float lap = 0.f;
-                    if (hasl) lap += cen - lf;
-                    if (hasr) lap += cen - rt;
-                    if (y > 0) lap += cen - up;
-                    if (y + 1 < F.H) lap += cen - dn;
-                    r = c.Bv[k] - lap;
+                float dn[4], bv[4], r[4];
+                f4_to(c.Xd[k], dn);
+                f4_to(c.Bv[k], bv);
+                quad_residual(q, cen, up, dn, bv, c.Hv[k], y > 0, y + 1 < F.H, r);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool unk = q.act[j] && !((c.Mw[k] >> (q.shift + j)) & 1u);
+                    pair[j >> 1] += unk ? r[j] : 0.f;
                 }
-                pair += r;
                 if ((y & 1) || y + 1 == F.H) {
-                    const float s = pair + __shfl_down_sync(HDI_FULL, pair, 1);
                     const int Y = y >> 1;
-                    if (!(lane & 1) && act) {
-                        const float v = ((c.Cw[k >> 1] >> (X & 31)) & 1u) ? 0.f : s;
-                        cb[ch * C.cs + (size_t)Y * C.pitch + X] = v;
-                        sq += v * v;
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const bool ok = q.act[2 * t] && X + t < C.W;
+                        const float v = ((c.Cw >> ((X & 31) + t)) & 1u) ? 0.f : pair[t];
+                        if (ok) {
+                            cb[ch * C.cs + (size_t)Y * C.pitch + X + t] = v;
+                            sq += v * v;
+                        }
+                        pair[t] = 0.f;
                     }
-                    pair = 0.f;
                 }
-                up = cen;
-                cen = dn;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    up[j] = cen[j];
+                    cen[j] = dn[j];
+                }
             }
         };
-        // two chunk buffers: the loads of the next chunk are in flight while
-        // the current one is computed
         Chunk A, B;
         load(A, y0);
         for (int yb = y0; yb < y1; yb += 2 * CR) {
@@ -265,62 +332,64 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
     grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
 }
 
-// ||b - A x||^2 per channel on one level (column strips, FP32).
+// ||b - A x||^2 per channel on one level (quad strips, FP32).
 __global__ void __launch_bounds__(128) k_level_residual_norm(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                              const float* __restrict__ b, GridReduce red, int rows) {
-    constexpr int CR = CS_CHUNK;
-    const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
-    const int px = x0 + lane;
-    const int y0 = blockIdx.y * rows;
-    const int y1 = min(y0 + rows, F.H);
+    constexpr int CR = QS_CHUNK;
     const int ch = blockIdx.z;
     fm = fm.ch(ch);
-    const bool act = px < F.W;
-    const int pxc = act ? px : F.W - 1;
+    const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * rows;
+    const int y1 = min(y0 + rows, F.H);
+    const QuadLane q = quad_lane(blockIdx.x * QS_COLS, F, fm);
     const float* xc = x + ch * F.cs;
     const float* bc = b + ch * F.cs;
     float sq = 0.f;
-    if (x0 < F.W) {
-        const uint32_t* mrow = fm.bits + (x0 >> 5);
-        const StripHalo hl = strip_halo(lane, px, pxc, F.W);
-        const bool hasl = px > 0, hasr = px + 1 < F.W;
-        float up = (y0 > 0) ? xc[(size_t)(y0 - 1) * F.pitch + pxc] : 0.f;
-        float cen = xc[(size_t)y0 * F.pitch + pxc];
-        for (int yb = y0; yb < y1; yb += CR) {
-            float Xd[CR], Hv[CR], Bv[CR];
+    if (y0 < F.H) {
+        const uint32_t* mrow = fm.bits + q.mword;
+        float up[4] = {0.f, 0.f, 0.f, 0.f}, cen[4];
+        if (y0 > 0) f4_to(*reinterpret_cast<const float4*>(xc + (size_t)(y0 - 1) * F.pitch + q.cq), up);
+        f4_to(*reinterpret_cast<const float4*>(xc + (size_t)y0 * F.pitch + q.cq), cen);
+        struct Chunk {
+            float4 Xd[CR], Bv[CR];
+            float Hv[CR];
             uint32_t Mw[CR];
+        };
+        auto load = [&](Chunk& c, int yb) {
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
-                const int y = min(yb + k, F.H - 1);
-                const size_t ry = (size_t)y * F.pitch;
-                Xd[k] = xc[(size_t)min(yb + k + 1, F.H - 1) * F.pitch + pxc];
-                Hv[k] = hl.on ? xc[ry + hl.col] : 0.f;
-                Bv[k] = bc[ry + pxc];
-                Mw[k] = mrow[(size_t)y * fm.wpitch];
+                const size_t ry = (size_t)min(yb + k, F.H - 1) * F.pitch;
+                c.Xd[k] = *reinterpret_cast<const float4*>(xc + (size_t)min(yb + k + 1, F.H - 1) * F.pitch + q.cq);
+                c.Bv[k] = *reinterpret_cast<const float4*>(bc + ry + q.cq);
+                c.Hv[k] = q.hon ? xc[ry + q.hcol] : 0.f;
+                c.Mw[k] = mrow[(size_t)min(yb + k, F.H - 1) * fm.wpitch];
             }
+        };
+        auto compute = [&](const Chunk& c, int yb) {
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
                 const int y = yb + k;
                 if (y >= y1) break;
-                const float dn = Xd[k];
-                float lf = __shfl_up_sync(HDI_FULL, cen, 1);
-                float rt = __shfl_down_sync(HDI_FULL, cen, 1);
-                if (lane == 0) lf = Hv[k];
-                if (lane == 31) rt = Hv[k];
-                const bool known = (Mw[k] >> lane) & 1u;
-                if (act && !known) {
-                    float lap = 0.f;
-                    if (hasl) lap += cen - lf;
-                    if (hasr) lap += cen - rt;
-                    if (y > 0) lap += cen - up;
-                    if (y + 1 < F.H) lap += cen - dn;
-                    const float r = Bv[k] - lap;
-                    sq += r * r;
+                float dn[4], bv[4], r[4];
+                f4_to(c.Xd[k], dn);
+                f4_to(c.Bv[k], bv);
+                quad_residual(q, cen, up, dn, bv, c.Hv[k], y > 0, y + 1 < F.H, r);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool unk = q.act[j] && !((c.Mw[k] >> (q.shift + j)) & 1u);
+                    if (unk) sq += r[j] * r[j];
+                    up[j] = cen[j];
+                    cen[j] = dn[j];
                 }
-                up = cen;
-                cen = dn;
             }
+        };
+        Chunk A, B;
+        load(A, y0);
+        for (int yb = y0; yb < y1; yb += 2 * CR) {
+            if (yb + CR < y1) load(B, yb + CR);
+            compute(A, yb);
+            if (yb + CR >= y1) break;
+            if (yb + 2 * CR < y1) load(A, yb + 2 * CR);
+            compute(B, yb + CR);
         }
     }
     const double tot = (double)block_sum_f(sq);
