@@ -304,10 +304,6 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     if (l == 0) tstop();
 }
 
-static dim3 tiles_of(const Level& L, int nch) {
-    const int r = strip_rows(L.H, L.W, nch);
-    return dim3((L.W + 127) / 128, (L.H + r - 1) / r, nch);
-}
 
 // One V-cycle (Sec. 3.2) on the correction equation A_l x = b_l, x from 0.
 // Result in lev[l].xa. Level 0 uses fine_pre / fine_post ORAS sweeps
@@ -349,10 +345,11 @@ void Ctx::vcycle(int l) {
     }
     vcycle(l + 1);
     {
-        dim3 grd = tiles_of(L, nch), blk(128);
+        const int qr = quad_rows(L.H, L.W, nch);
+        dim3 grd = quad_grid(L.H, L.W, nch, qr), blk(128);
         if (l == 0) tstart(kT_Prolong);
         k_prolong<0><<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, L.xb, arr(l + 1), C.xa,
-                                              reducer(l, grd.x * grd.y), strip_rows(L.H, L.W, nch));
+                                              reducer(l, grd.x * grd.y), qr);
         ++launches;
         if (l == 0) tstop();
     }
@@ -395,16 +392,18 @@ void Ctx::fmg(DFc d) {
     }
     const int L = nlev - 1;
     {
-        dim3 grd = tiles_of(lev[L], nch), blk(128);
+        const int qr = quad_rows(lev[L].H, lev[L].W, nch);
+        dim3 grd = quad_grid(lev[L].H, lev[L].W, nch, qr), blk(128);
         k_prolong<2><<<grd, blk, 0, stream>>>(arr(L), mview(L), nullptr, lev[L].b, lev[L].xb, arr(L), nullptr,
-                                              reducer(L, grd.x * grd.y), strip_rows(lev[L].H, lev[L].W, nch));
+                                              reducer(L, grd.x * grd.y), qr);
         ++launches;
         oras(L, false, lev[L].xb, lev[L].xa, scal + L * kMaxCh, true, nullptr);
     }
     for (int l = L - 1; l >= 0; --l) {
-        dim3 grd = tiles_of(lev[l], nch), blk(128);
+        const int qr = quad_rows(lev[l].H, lev[l].W, nch);
+        dim3 grd = quad_grid(lev[l].H, lev[l].W, nch, qr), blk(128);
         k_prolong<1><<<grd, blk, 0, stream>>>(arr(l), mview(l), nullptr, lev[l].b, lev[l].xb, arr(l + 1),
-                                              lev[l + 1].xa, reducer(l, grd.x * grd.y), strip_rows(lev[l].H, lev[l].W, nch));
+                                              lev[l + 1].xa, reducer(l, grd.x * grd.y), qr);
         ++launches;
         oras(l, false, lev[l].xb, lev[l].xa, scal + l * kMaxCh, l == L, l == 0 ? counters + kCntLocal : nullptr);
     }

@@ -405,54 +405,61 @@ __global__ void __launch_bounds__(128) k_level_residual_norm(LevelArr F, MaskVie
 // the coarse rows h(R) = 3/4 e[R][X] + 1/4 e[R][Xn] and a vertical one,
 // 3/4 h(Y) + 1/4 h(Yn) (clamped at the border).
 // Then ||b - A xout||^2 per channel (the next sweep's local stop rule).
-// Column strips: lane = column, three-row register window of xout values.
-// Each coarse row is interpolated once per chunk and reused by the fine rows
-// above and below it; lane pairs share a coarse cell, the horizontal
-// neighbour comes by a shuffle and the edge lanes load it. That neighbour is
-// also the halo column's own cell, so lanes 0 and 31 get the halo column's
-// interpolation (the mirror weights) without further coarse loads.
+// Quad strips: the lane's four fine columns lie over two coarse cells
+// (X0, X0 + 1), read as one float2; the outer neighbours X0 - 1 and X0 + 2
+// come from the adjacent lanes by shuffles (edge lanes load them), and they
+// are also the halo columns' cells, so lanes 0 and 31 interpolate the halo
+// column without further coarse loads. Each coarse row is interpolated once
+// and reused by the fine rows above and below it.
 template <int MODE>
 __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const float* __restrict__ xin,
                                                  const float* __restrict__ b, float* __restrict__ xout,
                                                  LevelArr C, const float* __restrict__ e, GridReduce red, int rows) {
-    constexpr int CR = CS_CHUNK;
+    constexpr int CR = QS_CHUNK;
     constexpr int NS = CR / 2 + 2;   // coarse rows per chunk: (yb/2 - 1) .. (yb/2 + CR/2)
-    const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
-    const int px = x0 + lane;
-    const int y0 = blockIdx.y * rows;
-    const int y1 = min(y0 + rows, F.H);
     const int ch = blockIdx.z;
     fm = fm.ch(ch);
-    const bool act = px < F.W;
-    const int pxc = act ? px : F.W - 1;
+    const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * rows;
+    const int y1 = min(y0 + rows, F.H);
+    const QuadLane q = quad_lane(blockIdx.x * QS_COLS, F, fm);
+    const int lane = q.lane;
     const float* xc = (MODE == 0) ? xin + ch * F.cs : nullptr;
     const float* bc = b + ch * F.cs;
     const float* ec = (MODE == 2) ? nullptr : e + ch * C.cs;
     float* xo = xout + ch * F.cs;
     float sq = 0.f;
-    if (x0 < F.W) {
-        const uint32_t* mrow = fm.bits + (x0 >> 5);
-        const StripHalo hl = strip_halo(lane, px, pxc, F.W);
-        const uint32_t* hrow = fm.bits + (hl.col >> 5);
-        const int hbit = hl.col & 31;
-        const bool hasl = px > 0, hasr = px + 1 < F.W;
-        const bool odd = pxc & 1;
-        const int X = min(pxc >> 1, C.W - 1);
-        const int Xn = odd ? min(X + 1, C.W - 1) : max(X - 1, 0);
-        const int src = odd ? min(lane + 1, 31) : max(lane - 1, 0);
-        const bool edge = (lane == 0 && !odd) || (lane == 31 && odd);
-        // coarse slots: S[j] / SH[j] = horizontal interpolation of coarse row
-        // cb + j (clamped) at this lane's column / at the halo column
-        float S[NS], SH[NS];
-        auto coarse = [&](int R, float& ho, float& hh) {
-            if (MODE == 2) { ho = hh = 0.f; return; }
+    if (y0 < F.H) {
+        const uint32_t* mrow = fm.bits + q.mword;
+        const uint32_t* hrow = fm.bits + (q.hcol >> 5);
+        const int hbit = q.hcol & 31;
+        const int X0 = q.c0 >> 1;
+        const int Xq = min(X0, C.pitch - 2);          // float2 load column (clamped for idle lanes)
+        const bool in1 = X0 + 1 < C.W, in2 = X0 + 2 < C.W, inm = X0 > 0;
+        // the neighbour cells of the edge lanes: X0 - 1 (lane 0), X0 + 2 (lane 31)
+        const int Xe = (lane == 0) ? max(X0 - 1, 0) : min(X0 + 2, C.W - 1);
+        // horizontal interpolation of coarse row R at the lane's four columns
+        // (h[0..3]) and at its halo column (hh, lanes 0 / 31)
+        auto hinterp = [&](float2 ev, float ee, float (&h)[4], float& hh) {
+            const float e0 = ev.x;
+            const float e1 = in1 ? ev.y : ev.x;
+            float em = __shfl_up_sync(HDI_FULL, e1, 1);
+            float e2 = __shfl_down_sync(HDI_FULL, e0, 1);
+            if (lane == 0) em = ee;
+            if (lane == 31) e2 = ee;
+            if (!inm) em = e0;
+            if (!in2) e2 = e1;
+            h[0] = __fadd_rn(__fmul_rn(0.75f, e0), __fmul_rn(0.25f, em));
+            h[1] = __fadd_rn(__fmul_rn(0.75f, e0), __fmul_rn(0.25f, e1));
+            h[2] = __fadd_rn(__fmul_rn(0.75f, e1), __fmul_rn(0.25f, e0));
+            h[3] = __fadd_rn(__fmul_rn(0.75f, e1), __fmul_rn(0.25f, e2));
+            hh = (lane == 0) ? __fadd_rn(__fmul_rn(0.75f, em), __fmul_rn(0.25f, e0))
+                             : __fadd_rn(__fmul_rn(0.75f, e2), __fmul_rn(0.25f, e1));
+        };
+        auto cload = [&](int R, float2& ev, float& ee) {
+            if (MODE == 2) { ev = make_float2(0.f, 0.f); ee = 0.f; return; }
             const float* row = ec + (size_t)min(max(R, 0), C.H - 1) * C.pitch;
-            const float own = row[X];
-            float nb = __shfl_sync(HDI_FULL, own, src);
-            if (edge) nb = row[Xn];
-            ho = __fadd_rn(__fmul_rn(0.75f, own), __fmul_rn(0.25f, nb));
-            hh = __fadd_rn(__fmul_rn(0.75f, nb), __fmul_rn(0.25f, own));
+            ev = *reinterpret_cast<const float2*>(row + Xq);
+            ee = (lane == 0 || lane == 31) ? row[Xe] : 0.f;
         };
         auto fval = [&](bool known, float xv, float bv, float hY, float hYn) -> float {
             if (known) return (MODE == 0) ? xv : bv;
@@ -460,44 +467,69 @@ __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const 
             const float pe = __fadd_rn(__fmul_rn(0.75f, hY), __fmul_rn(0.25f, hYn));
             return (MODE == 0 ? xv : 0.f) + pe;
         };
-        // slots of fine row r relative to chunk row yb (r - yb = k, k in -1 .. CR)
-        // Y = r/2 -> slot (k >> 1) + 1 with floor division; Yn on the side of r
-        const int cb0 = (y0 >> 1) - 1;
-        coarse(cb0, S[0], SH[0]);
-        coarse(cb0 + 1, S[1], SH[1]);
-        // window: up = xout(y0 - 1) (slots: Y = cb0 -> 0, Yn = cb0 + 1 -> 1), cen = xout(y0) (Y -> 1, Yn -> 0)
-        float up = 0.f, cen;
+        // coarse slots: S[j] / SH[j] = interpolated coarse row cb + j (clamped)
+        float S[NS][4], SH[NS];
         {
-            const size_t r0 = (size_t)y0 * F.pitch + pxc;
-            const bool k0 = (mrow[(size_t)y0 * fm.wpitch] >> lane) & 1u;
-            cen = fval(k0, MODE == 0 ? xc[r0] : 0.f, bc[r0], S[1], S[0]);
+            const int cb0 = (y0 >> 1) - 1;
+            float2 ev;
+            float ee;
+            cload(cb0, ev, ee);
+            hinterp(ev, ee, S[0], SH[0]);
+            cload(cb0 + 1, ev, ee);
+            hinterp(ev, ee, S[1], SH[1]);
+        }
+        // window: up = xout(y0 - 1) (Y slot 0, Yn slot 1), cen = xout(y0) (Y slot 1, Yn slot 0)
+        float up[4] = {0.f, 0.f, 0.f, 0.f}, cen[4];
+        {
+            float xv[4] = {0.f, 0.f, 0.f, 0.f}, bv[4];
+            const size_t r0 = (size_t)y0 * F.pitch + q.cq;
+            if (MODE == 0) f4_to(*reinterpret_cast<const float4*>(xc + r0), xv);
+            f4_to(*reinterpret_cast<const float4*>(bc + r0), bv);
+            const uint32_t w0 = mrow[(size_t)y0 * fm.wpitch];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cen[j] = fval((w0 >> (q.shift + j)) & 1u, xv[j], bv[j], S[1][j], S[0][j]);
             if (y0 > 0) {
-                const size_t rm = (size_t)(y0 - 1) * F.pitch + pxc;
-                const bool km = (mrow[(size_t)(y0 - 1) * fm.wpitch] >> lane) & 1u;
-                up = fval(km, MODE == 0 ? xc[rm] : 0.f, bc[rm], S[0], S[1]);
+                const size_t rm = (size_t)(y0 - 1) * F.pitch + q.cq;
+                if (MODE == 0) f4_to(*reinterpret_cast<const float4*>(xc + rm), xv);
+                f4_to(*reinterpret_cast<const float4*>(bc + rm), bv);
+                const uint32_t wm = mrow[(size_t)(y0 - 1) * fm.wpitch];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) up[j] = fval((wm >> (q.shift + j)) & 1u, xv[j], bv[j], S[0][j], S[1][j]);
             }
         }
-        for (int yb = y0; yb < y1; yb += CR) {
-            const int cb = (yb >> 1) - 1;
-            float Xd[CR], Bd[CR + 1], Hx[CR], Hb[CR];
+        struct Chunk {
+            float4 Xd[CR], Bd[CR + 1];
             uint32_t Mw[CR + 1], Hm[CR];
+            float Hx[CR], Hb[CR];
+            float2 Ev[NS - 2];
+            float Ee[NS - 2];
+        };
+        auto load = [&](Chunk& c, int yb) {
+            const int cb = (yb >> 1) - 1;
 #pragma unroll
-            for (int j = 2; j < NS; ++j) coarse(cb + j, S[j], SH[j]);
+            for (int j = 0; j < NS - 2; ++j) cload(cb + 2 + j, c.Ev[j], c.Ee[j]);
 #pragma unroll
             for (int k = 0; k <= CR; ++k) {
                 const int y = min(yb + k, F.H - 1);
-                Bd[k] = bc[(size_t)y * F.pitch + pxc];
-                Mw[k] = mrow[(size_t)y * fm.wpitch];
+                c.Bd[k] = *reinterpret_cast<const float4*>(bc + (size_t)y * F.pitch + q.cq);
+                c.Mw[k] = mrow[(size_t)y * fm.wpitch];
             }
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
                 const int y = min(yb + k, F.H - 1);
                 const size_t ry = (size_t)y * F.pitch;
-                Xd[k] = (MODE == 0) ? xc[(size_t)min(yb + k + 1, F.H - 1) * F.pitch + pxc] : 0.f;
-                Hx[k] = (MODE == 0 && hl.on) ? xc[ry + hl.col] : 0.f;
-                Hb[k] = hl.on ? bc[ry + hl.col] : 0.f;
-                Hm[k] = hl.on ? hrow[(size_t)y * fm.wpitch] : 0u;
+                if (MODE == 0)
+                    c.Xd[k] = *reinterpret_cast<const float4*>(xc + (size_t)min(yb + k + 1, F.H - 1) * F.pitch + q.cq);
+                else
+                    c.Xd[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                c.Hx[k] = (MODE == 0 && q.hon) ? xc[ry + q.hcol] : 0.f;
+                c.Hb[k] = q.hon ? bc[ry + q.hcol] : 0.f;
+                c.Hm[k] = q.hon ? hrow[(size_t)y * fm.wpitch] : 0u;
             }
+        };
+        auto compute = [&](const Chunk& c, int yb) {
+#pragma unroll
+            for (int j = 0; j < NS - 2; ++j) hinterp(c.Ev[j], c.Ee[j], S[2 + j], SH[2 + j]);
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
                 const int y = yb + k;
@@ -505,35 +537,51 @@ __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const 
                 // row y + 1 (k + 1 relative): Y slot ((k+1) >> 1) + 1, Yn on its side
                 const int kd = k + 1;
                 const int sY = (kd >> 1) + 1, sYn = (kd & 1) ? sY + 1 : sY - 1;
-                float dn = 0.f;
-                if (y + 1 < F.H) dn = fval((Mw[k + 1] >> lane) & 1u, Xd[k], Bd[k + 1], S[sY], S[sYn]);
-                float lf = __shfl_up_sync(HDI_FULL, cen, 1);
-                float rt = __shfl_down_sync(HDI_FULL, cen, 1);
-                if (hl.on) {
-                    const int hY = (k >> 1) + 1, hYn = (k & 1) ? hY + 1 : hY - 1;
-                    const float hv = fval((Hm[k] >> hbit) & 1u, Hx[k], Hb[k], SH[hY], SH[hYn]);
-                    if (lane == 0) lf = hv;
-                    else rt = hv;
+                float dn[4] = {0.f, 0.f, 0.f, 0.f};
+                if (y + 1 < F.H) {
+                    float xv[4], bv[4];
+                    f4_to(c.Xd[k], xv);
+                    f4_to(c.Bd[k + 1], bv);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        dn[j] = fval((c.Mw[k + 1] >> (q.shift + j)) & 1u, xv[j], bv[j], S[sY][j], S[sYn][j]);
                 }
-                if (act) {
-                    xo[(size_t)y * F.pitch + px] = cen;
-                    if (!((Mw[k] >> lane) & 1u)) {
-                        float lap = 0.f;
-                        if (hasl) lap += cen - lf;
-                        if (hasr) lap += cen - rt;
-                        if (y > 0) lap += cen - up;
-                        if (y + 1 < F.H) lap += cen - dn;
-                        const float r = Bd[k] - lap;
-                        sq += r * r;
-                    }
+                const int hY = (k >> 1) + 1, hYn = (k & 1) ? hY + 1 : hY - 1;
+                const float hv = fval((c.Hm[k] >> hbit) & 1u, c.Hx[k], c.Hb[k], SH[hY], SH[hYn]);
+                float bv[4], r[4];
+                f4_to(c.Bd[k], bv);
+                quad_residual(q, cen, up, dn, bv, hv, y > 0, y + 1 < F.H, r);
+                float* orow = xo + (size_t)y * F.pitch + q.c0;
+                if (q.act[3]) {
+                    *reinterpret_cast<float4*>(orow) = make_float4(cen[0], cen[1], cen[2], cen[3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (q.act[j]) orow[j] = cen[j];
                 }
-                up = cen;
-                cen = dn;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool unk = q.act[j] && !((c.Mw[k] >> (q.shift + j)) & 1u);
+                    if (unk) sq += r[j] * r[j];
+                    up[j] = cen[j];
+                    cen[j] = dn[j];
+                }
             }
-            S[0] = S[NS - 2];
-            S[1] = S[NS - 1];
-            SH[0] = SH[NS - 2];
-            SH[1] = SH[NS - 1];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) S[j][t] = S[NS - 2 + j][t];
+                SH[j] = SH[NS - 2 + j];
+            }
+        };
+        Chunk A, B;
+        load(A, y0);
+        for (int yb = y0; yb < y1; yb += 2 * CR) {
+            if (yb + CR < y1) load(B, yb + CR);
+            compute(A, yb);
+            if (yb + CR >= y1) break;
+            if (yb + 2 * CR < y1) load(A, yb + 2 * CR);
+            compute(B, yb + CR);
         }
     }
     const double tot = (double)block_sum_f(sq);
