@@ -420,8 +420,8 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
     a.d = d;
     a.y = y;
     a.r32 = c.lev[0].b;
-    a.rows = strip_rows(c.H, c.W, c.nch);
-    dim3 grd((c.W + 127) / 128, (c.H + a.rows - 1) / a.rows, c.nch), blk(128);
+    a.rows = quad_rows(c.H, c.W, c.nch);
+    dim3 grd = quad_grid(c.H, c.W, c.nch, a.rows), blk(128);
     a.red_r = c.reducer(kSlotR64, grd.x * grd.y);
     a.red_b = c.reducer(kSlotB64, grd.x * grd.y);
     a.want_b = want_b ? 1 : 0;

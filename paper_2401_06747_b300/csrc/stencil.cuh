@@ -134,7 +134,7 @@ __device__ __forceinline__ float fine_residual(const float* __restrict__ x, cons
 #define CS_ROWS 64
 #define CS_CHUNK 4
 #ifndef RES_CHUNK
-#define RES_CHUNK 4
+#define RES_CHUNK 1
 #endif
 
 // Rows per CTA of the column-strip kernels: long strips on large levels (few
@@ -658,42 +658,33 @@ struct ResArgs {
     int want_b;
 };
 
-// Column-strip layout of the streaming kernels: a CTA of four warps covers
-// 128 columns x CS_ROWS rows; lane l of warp w owns one column and walks
-// down the rows with a three-row register window, takes its left and right
-// neighbours by warp shuffles (lanes 0 and 31 read the neighbouring strip
-// from L1/L2), and reads the mask as one broadcast word per row.
-
-// Chunked like the FP32 strip kernels. Known pixels take their Dirichlet
-// value (d for RHS_DATA, 0 for RHS_SOURCE). With INIT_UPDATE the input
-// iterate already holds it there (every refinement step writes it, and the
-// V-cycle correction is zero on known pixels), so d is read only by the
-// other INIT modes, after the chunk's mask words have arrived.
+// Quad strips like the FP32 kernels (lane = four columns, float4 loads of
+// the hi and lo words). Known pixels take their Dirichlet value (d for
+// RHS_DATA, 0 for RHS_SOURCE). With INIT_UPDATE the input iterate already
+// holds it there (every refinement step writes it, and the V-cycle
+// correction is zero on known pixels), so d is read only by the other INIT
+// modes, once the row's mask word has arrived.
 template <int RHS, int INIT>
 __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
     constexpr int RC = RES_CHUNK;
     constexpr bool LOAD_D = (RHS == RHS_DATA) && (INIT != INIT_UPDATE);
     constexpr bool HAS_U = (INIT == INIT_KEEP || INIT == INIT_UPDATE);
     constexpr bool HAS_E = (INIT == INIT_UPDATE || INIT == INIT_FROM32);
-    a.m = a.m.ch(blockIdx.z);
-    const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
-    const int x = x0 + lane;
-    const int y0 = blockIdx.y * a.rows;
-    const int y1 = min(y0 + a.rows, a.F.H);
     const int ch = blockIdx.z;
+    const MaskView m = a.m.ch(ch);
     const int H = a.F.H, W = a.F.W;
+    const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * a.rows;
+    const int y1 = min(y0 + a.rows, H);
+    const QuadLane q = quad_lane(blockIdx.x * QS_COLS, a.F, m);
+    const int lane = q.lane;
     const long long co = ch * a.F.cs;
-    const bool act = x < W;
-    const int xc = act ? x : W - 1;
     float rr = 0.f, bb2 = 0.f;
-    if (x0 < W) {
-        const uint32_t* mrow = a.m.bits + (x0 >> 5);
-        const StripHalo hl = strip_halo(lane, x, xc, W);
-        const uint32_t* hrow = a.m.bits + (hl.col >> 5);
-        const int hbit = hl.col & 31;
-        const bool hasl = x > 0, hasr = x + 1 < W;
+    if (y0 < H) {
+        const uint32_t* mrow = m.bits + q.mword;
+        const uint32_t* hrow = m.bits + (q.hcol >> 5);
+        const int hbit = q.hcol & 31;
         auto at = [&](int y, int col) { return co + (size_t)min(y, H - 1) * a.F.pitch + col; };
+        auto ld4 = [&](const float* p, size_t i) { return *reinterpret_cast<const float4*>(p + i); };
         // iterate value after the INIT transform, from the loaded sources
         auto value = [&](bool known, float uh, float ul, float e, float dh, float dl, float& h, float& l) {
             if (known) {
@@ -713,103 +704,129 @@ __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
                 h = 0.f; l = 0.f;
             }
         };
-        auto full_value = [&](int y, int col, uint32_t word, int bit, float& h, float& l) {
-            const size_t idx = at(y, col);
-            const bool known = (word >> bit) & 1u;
-            const float uh = HAS_U ? a.uin.hi[idx] : 0.f, ul = HAS_U ? a.uin.lo[idx] : 0.f;
-            const float e = HAS_E ? a.x32[idx] : 0.f;
-            float dh = 0.f, dl = 0.f;
-            if (LOAD_D && known) { dh = a.d.hi[idx]; dl = a.d.lo[idx]; }
-            value(known, uh, ul, e, dh, dl, h, l);
+        // the lane's four values of row y (all loads inside)
+        auto row_value = [&](int y, float (&h)[4], float (&l)[4]) {
+            const size_t i = at(y, q.cq);
+            const uint32_t w = mrow[(size_t)min(y, H - 1) * m.wpitch];
+            float uh[4] = {0.f, 0.f, 0.f, 0.f}, ul[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+            float dh[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
+            if (HAS_U) { f4_to(ld4(a.uin.hi, i), uh); f4_to(ld4(a.uin.lo, i), ul); }
+            if (HAS_E) f4_to(ld4(a.x32, i), e);
+            if (LOAD_D) { f4_to(ld4(a.d.hi, i), dh); f4_to(ld4(a.d.lo, i), dl); }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) value((w >> (q.shift + j)) & 1u, uh[j], ul[j], e[j], dh[j], dl[j], h[j], l[j]);
         };
-        // window: (uh_, ul_) = u(y0 - 1), (ch_, cl) = u(y0)
-        float uh_ = 0.f, ul_ = 0.f, ch_, cl;
-        full_value(y0, xc, mrow[(size_t)y0 * a.m.wpitch], lane, ch_, cl);
-        if (y0 > 0) full_value(y0 - 1, xc, mrow[(size_t)(y0 - 1) * a.m.wpitch], lane, uh_, ul_);
-        for (int yb = y0; yb < y1; yb += RC) {
+        float uph[4] = {0.f, 0.f, 0.f, 0.f}, upl[4] = {0.f, 0.f, 0.f, 0.f}, ch_[4], cl[4];
+        row_value(y0, ch_, cl);
+        if (y0 > 0) row_value(y0 - 1, uph, upl);
+        struct Chunk {
+            float4 Uh[RC], Ul[RC], E[RC];          // rows yb+1 .. yb+RC
+            float4 Dh[RC], Dl[RC], Yh[RC], Yl[RC];   // RHS_SOURCE: d and y of rows yb .. yb+RC-1
+            float4 KDh[RC], KDl[RC];               // LOAD_D: data of rows yb+1 .. (known pixels)
             uint32_t Mw[RC + 1], Hm[RC];
-            float Uh[RC], Ul[RC], E[RC];       // rows yb+1 .. yb+RC, own column
-            float HUh[RC], HUl[RC], HE[RC];    // rows yb .. yb+RC-1, halo column
-            float Dh[RC], Dl[RC], Yh[RC], Yl[RC];   // RHS_SOURCE: d and y, rows yb .. yb+RC-1
+            float HUh[RC], HUl[RC], HE[RC], HDh[RC], HDl[RC];   // halo column, rows yb ..
+        };
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto load = [&](Chunk& c, int yb) {
 #pragma unroll
-            for (int k = 0; k <= RC; ++k) Mw[k] = mrow[(size_t)min(yb + k, H - 1) * a.m.wpitch];
+            for (int k = 0; k <= RC; ++k) c.Mw[k] = mrow[(size_t)min(yb + k, H - 1) * m.wpitch];
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
-                const size_t id = at(yb + k + 1, xc), ih = at(yb + k, hl.col), ic = at(yb + k, xc);
-                Uh[k] = HAS_U ? a.uin.hi[id] : 0.f;
-                Ul[k] = HAS_U ? a.uin.lo[id] : 0.f;
-                E[k] = HAS_E ? a.x32[id] : 0.f;
-                Hm[k] = hl.on ? hrow[(size_t)min(yb + k, H - 1) * a.m.wpitch] : 0u;
-                HUh[k] = (HAS_U && hl.on) ? a.uin.hi[ih] : 0.f;
-                HUl[k] = (HAS_U && hl.on) ? a.uin.lo[ih] : 0.f;
-                HE[k] = (HAS_E && hl.on) ? a.x32[ih] : 0.f;
+                const size_t id = at(yb + k + 1, q.cq), ih = at(yb + k, q.hcol), ic = at(yb + k, q.cq);
+                c.Uh[k] = HAS_U ? ld4(a.uin.hi, id) : z4;
+                c.Ul[k] = HAS_U ? ld4(a.uin.lo, id) : z4;
+                c.E[k] = HAS_E ? ld4(a.x32, id) : z4;
+                c.Hm[k] = q.hon ? hrow[(size_t)min(yb + k, H - 1) * m.wpitch] : 0u;
+                c.HUh[k] = (HAS_U && q.hon) ? a.uin.hi[ih] : 0.f;
+                c.HUl[k] = (HAS_U && q.hon) ? a.uin.lo[ih] : 0.f;
+                c.HE[k] = (HAS_E && q.hon) ? a.x32[ih] : 0.f;
                 if (RHS == RHS_SOURCE) {
-                    Dh[k] = a.d.hi[ic];
-                    Dl[k] = a.d.lo[ic];
-                    Yh[k] = a.y.hi ? a.y.hi[ic] : 0.f;
-                    Yl[k] = a.y.hi ? a.y.lo[ic] : 0.f;
+                    c.Dh[k] = ld4(a.d.hi, ic);
+                    c.Dl[k] = ld4(a.d.lo, ic);
+                    c.Yh[k] = a.y.hi ? ld4(a.y.hi, ic) : z4;
+                    c.Yl[k] = a.y.hi ? ld4(a.y.lo, ic) : z4;
                 }
             }
-            float KDh[RC], KDl[RC], HDh[RC], HDl[RC];   // data on known pixels (after the mask words)
+            if (LOAD_D) {   // data only where the mask word says known
 #pragma unroll
-            for (int k = 0; k < RC; ++k) {
-                KDh[k] = KDl[k] = HDh[k] = HDl[k] = 0.f;
-                if (LOAD_D) {
-                    if ((Mw[k + 1] >> lane) & 1u) {
-                        const size_t id = at(yb + k + 1, xc);
-                        KDh[k] = a.d.hi[id];
-                        KDl[k] = a.d.lo[id];
-                    }
-                    if (hl.on && ((Hm[k] >> hbit) & 1u)) {
-                        const size_t ih = at(yb + k, hl.col);
-                        HDh[k] = a.d.hi[ih];
-                        HDl[k] = a.d.lo[ih];
-                    }
+                for (int k = 0; k < RC; ++k) {
+                    const uint32_t kb = (c.Mw[k + 1] >> q.shift) & 15u;
+                    const size_t id = at(yb + k + 1, q.cq), ih = at(yb + k, q.hcol);
+                    c.KDh[k] = kb ? ld4(a.d.hi, id) : z4;
+                    c.KDl[k] = kb ? ld4(a.d.lo, id) : z4;
+                    const bool kh = q.hon && ((c.Hm[k] >> hbit) & 1u);
+                    c.HDh[k] = kh ? a.d.hi[ih] : 0.f;
+                    c.HDl[k] = kh ? a.d.lo[ih] : 0.f;
                 }
             }
+        };
+        auto compute = [&](const Chunk& c, int yb) {
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 const int y = yb + k;
                 if (y >= y1) break;
-                float dh = 0.f, dl = 0.f;
-                if (y + 1 < H) value((Mw[k + 1] >> lane) & 1u, Uh[k], Ul[k], E[k], KDh[k], KDl[k], dh, dl);
-                float lh = __shfl_up_sync(HDI_FULL, ch_, 1), ll = __shfl_up_sync(HDI_FULL, cl, 1);
-                float rh = __shfl_down_sync(HDI_FULL, ch_, 1), rl = __shfl_down_sync(HDI_FULL, cl, 1);
-                if (hl.on) {
-                    float hh, hlo;
-                    value((Hm[k] >> hbit) & 1u, HUh[k], HUl[k], HE[k], HDh[k], HDl[k], hh, hlo);
-                    if (lane == 0) { lh = hh; ll = hlo; }
-                    else { rh = hh; rl = hlo; }
+                float dnh[4] = {0.f, 0.f, 0.f, 0.f}, dnl[4] = {0.f, 0.f, 0.f, 0.f};
+                if (y + 1 < H) {
+                    float uh[4], ul[4], e[4], dh[4], dl[4];
+                    f4_to(c.Uh[k], uh);
+                    f4_to(c.Ul[k], ul);
+                    f4_to(c.E[k], e);
+                    f4_to(LOAD_D ? c.KDh[k] : z4, dh);
+                    f4_to(LOAD_D ? c.KDl[k] : z4, dl);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        value((c.Mw[k + 1] >> (q.shift + j)) & 1u, uh[j], ul[j], e[j], dh[j], dl[j], dnh[j], dnl[j]);
                 }
-                const bool known = (Mw[k] >> lane) & 1u;
-                if (act) {
-                    const size_t idx = co + (size_t)y * a.F.pitch + x;
-                    a.uout.hi[idx] = ch_;
-                    a.uout.lo[idx] = cl;
+                // horizontal neighbours outside the lane: shuffles, halo at the strip edges
+                float lwh = __shfl_up_sync(HDI_FULL, ch_[3], 1), lwl = __shfl_up_sync(HDI_FULL, cl[3], 1);
+                float rwh = __shfl_down_sync(HDI_FULL, ch_[0], 1), rwl = __shfl_down_sync(HDI_FULL, cl[0], 1);
+                if (q.hon) {
+                    float hh, hlo;
+                    value((c.Hm[k] >> hbit) & 1u, c.HUh[k], c.HUl[k], c.HE[k], LOAD_D ? c.HDh[k] : 0.f,
+                          LOAD_D ? c.HDl[k] : 0.f, hh, hlo);
+                    if (lane == 0) { lwh = hh; lwl = hlo; }
+                    else { rwh = hh; rwl = hlo; }
+                }
+                float sdh[4], sdl[4], syh[4], syl[4];
+                if (RHS == RHS_SOURCE) {
+                    f4_to(c.Dh[k], sdh);
+                    f4_to(c.Dl[k], sdl);
+                    f4_to(c.Yh[k], syh);
+                    f4_to(c.Yl[k], syl);
+                }
+                float oh[4], ol[4], orr[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float cjh = ch_[j], cjl = cl[j];
+                    oh[j] = cjh;
+                    ol[j] = cjl;
+                    const bool known = (c.Mw[k] >> (q.shift + j)) & 1u;
                     float r = 0.f;
                     if (known) {
-                        if (RHS == RHS_DATA) { const float bh = ch_ + cl; bb2 += bh * bh; }
+                        if (RHS == RHS_DATA && q.act[j]) { const float bh = cjh + cjl; bb2 += bh * bh; }
                     } else {
                         // A u = 4 u_c - (sum of the 4 neighbours), an absent
                         // neighbour replaced by u_c (zero difference): the
                         // neighbour sum and the difference by TwoSum, the low
                         // parts added in FP32
-                        const float n0h = hasl ? lh : ch_, n0l = hasl ? ll : cl;
-                        const float n1h = hasr ? rh : ch_, n1l = hasr ? rl : cl;
-                        const float n2h = (y > 0) ? uh_ : ch_, n2l = (y > 0) ? ul_ : cl;
-                        const float n3h = (y + 1 < H) ? dh : ch_, n3l = (y + 1 < H) ? dl : cl;
+                        const float lh = (j == 0) ? lwh : ch_[j - 1], ll = (j == 0) ? lwl : cl[j - 1];
+                        const float rh = (j == 3) ? rwh : ch_[j + 1], rl = (j == 3) ? rwl : cl[j + 1];
+                        const float n0h = q.lin[j] ? lh : cjh, n0l = q.lin[j] ? ll : cjl;
+                        const float n1h = q.rin[j] ? rh : cjh, n1l = q.rin[j] ? rl : cjl;
+                        const float n2h = (y > 0) ? uph[j] : cjh, n2l = (y > 0) ? upl[j] : cjl;
+                        const float n3h = (y + 1 < H) ? dnh[j] : cjh, n3l = (y + 1 < H) ? dnl[j] : cjl;
                         float sa, ea, sb, eb, sh, eh;
                         two_sum(n0h, n1h, sa, ea);
                         two_sum(n2h, n3h, sb, eb);
                         two_sum(sa, sb, sh, eh);
                         const float sl = ((n0l + n1l) + (n2l + n3l)) + ((ea + eb) + eh);
                         float ah, ae;
-                        two_sum(4.f * ch_, -sh, ah, ae);
-                        const float al = ae + (4.f * cl - sl);   // A u = ah + al
+                        two_sum(4.f * cjh, -sh, ah, ae);
+                        const float al = ae + (4.f * cjl - sl);   // A u = ah + al
                         if (RHS == RHS_SOURCE) {
                             float bh, bl;
-                            df_add(Dh[k], Dl[k], -Yh[k], -Yl[k], bh, bl);
-                            bb2 += bh * bh;
+                            df_add(sdh[j], sdl[j], -syh[j], -syl[j], bh, bl);
+                            if (q.act[j]) bb2 += bh * bh;
                             float rh2, rl2;
                             df_add(bh, bl, -ah, -al, rh2, rl2);
                             r = rh2 + rl2;
@@ -817,12 +834,38 @@ __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
                             r = -(ah + al);   // b = 0 on unknown pixels
                         }
                     }
-                    a.r32[idx] = r;
-                    rr += r * r;
+                    orr[j] = r;
+                    if (q.act[j]) rr += r * r;
                 }
-                uh_ = ch_; ul_ = cl;
-                ch_ = dh; cl = dl;
+                const size_t idx = co + (size_t)y * a.F.pitch + q.c0;
+                if (q.act[3]) {
+                    *reinterpret_cast<float4*>(a.uout.hi + idx) = make_float4(oh[0], oh[1], oh[2], oh[3]);
+                    *reinterpret_cast<float4*>(a.uout.lo + idx) = make_float4(ol[0], ol[1], ol[2], ol[3]);
+                    *reinterpret_cast<float4*>(a.r32 + idx) = make_float4(orr[0], orr[1], orr[2], orr[3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (q.act[j]) {
+                            a.uout.hi[idx + j] = oh[j];
+                            a.uout.lo[idx + j] = ol[j];
+                            a.r32[idx + j] = orr[j];
+                        }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    uph[j] = ch_[j]; upl[j] = cl[j];
+                    ch_[j] = dnh[j]; cl[j] = dnl[j];
+                }
             }
+        };
+        Chunk A, B;
+        load(A, y0);
+        for (int yb = y0; yb < y1; yb += 2 * RC) {
+            if (yb + RC < y1) load(B, yb + RC);
+            compute(A, yb);
+            if (yb + RC >= y1) break;
+            if (yb + 2 * RC < y1) load(A, yb + 2 * RC);
+            compute(B, yb + RC);
         }
     }
     const double tot = (double)block_sum_f(rr);
