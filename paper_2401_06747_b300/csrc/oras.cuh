@@ -45,6 +45,7 @@ struct LocalShared {
     float2 msk[8][kLocalThreads];  // 0/1 unknown-pixel mask per thread and row (thread-private)
     float2 seam[2][2][2][16];      // [parity][side: 0 = row 15, 1 = row 16][R, P_old][column pair]
     float red[5][2];               // warp partial sums: pq / rn by parity, initial rr
+    float2 xkeep[8][kLocalThreads]; // iterate at the thread's pixels (interior sweeps: reused by the output)
 };
 
 // Geometry of subdomain (x0, y0); writes the thread's mask floats.
@@ -258,8 +259,47 @@ __global__ void __launch_bounds__(kLocalThreads, 10) k_oras(OrasArgs a) {
         return make_float2(p[row + cx0], p[row + cx1]);
     };
 
+    // Interior subdomains (all neighbours and the halo inside the image; x0 is
+    // then a multiple of the stride, so even) take a path without clamping or
+    // boundary selects; the others the general one.
+    const bool interior = x0 > 0 && x0 + 32 < a.W && y0 > 0 && y0 + 32 < a.H;
     float2 R[8], V[8];
-    {
+    if (interior) {
+        const float* __restrict__ xr = xin + (size_t)(y0 + r0 - 1) * a.pitch + gx;   // window row r0 - 1
+        const float* __restrict__ br = bb + (size_t)(y0 + r0) * a.pitch + gx;
+        float2 B[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) B[k] = *reinterpret_cast<const float2*>(br + (size_t)k * a.pitch);
+        if (ZERO) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                R[k].x = ((g.um >> (2 * k)) & 1u) ? B[k].x : 0.f;
+                R[k].y = ((g.um >> (2 * k + 1)) & 1u) ? B[k].y : 0.f;
+            }
+        } else {
+            const bool hl = g.c == 0 || g.c == 15;
+            const int hoff = (g.c == 0) ? -1 : 2;
+            float2 X[10];
+            float HV[8];
+#pragma unroll
+            for (int t = 0; t < 10; ++t) X[t] = *reinterpret_cast<const float2*>(xr + (size_t)t * a.pitch);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) HV[k] = hl ? xr[(size_t)(k + 1) * a.pitch + hoff] : 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float2 up = X[k], xc = X[k + 1], dn = X[k + 2];
+                sh.xkeep[k][threadIdx.x] = xc;
+                float L = __shfl_up_sync(HDI_FULL, xc.y, 1);
+                float Rt = __shfl_down_sync(HDI_FULL, xc.x, 1);
+                if (g.c == 0) L = HV[k];
+                if (g.c == 15) Rt = HV[k];
+                const float lapx = ((xc.x - L) + (xc.x - xc.y)) + ((xc.x - up.x) + (xc.x - dn.x));
+                const float lapy = ((xc.y - xc.x) + (xc.y - Rt)) + ((xc.y - up.y) + (xc.y - dn.y));
+                R[k].x = ((g.um >> (2 * k)) & 1u) ? (B[k].x - lapx) : 0.f;
+                R[k].y = ((g.um >> (2 * k + 1)) & 1u) ? (B[k].y - lapy) : 0.f;
+            }
+        }
+    } else {
         float2 B[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) B[k] = ld2(bb, y0 + r0 + k);
@@ -310,6 +350,33 @@ __global__ void __launch_bounds__(kLocalThreads, 10) k_oras(OrasArgs a) {
     const int it = local_cg<FULL>(g, sh, V, R, thresh, a.maxit);
     if (a.iters && threadIdx.x == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
 
+    if (interior) {
+        // owned core [3, 29) x [3, 29) (half the overlap off every side)
+        constexpr int lo = 3, hi = 29;
+        const bool w0 = c0 >= lo && c0 < hi, w1 = c0 + 1 >= lo && c0 + 1 < hi;
+        if (w0 || w1) {
+            float* __restrict__ xo = a.xout + ch * a.cstride + (size_t)(y0 + r0) * a.pitch + gx;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (r0 + k >= lo && r0 + k < hi) {
+                    float2 o = V[k];
+                    if (!ZERO) {
+                        const float2 xv = sh.xkeep[k][threadIdx.x];
+                        o.x += xv.x;
+                        o.y += xv.y;
+                    }
+                    float* dst = xo + (size_t)k * a.pitch;
+                    if (w0 && w1) {
+                        *reinterpret_cast<float2*>(dst) = o;
+                    } else {
+                        if (w0) dst[0] = o.x;
+                        if (w1) dst[1] = o.y;
+                    }
+                }
+            }
+        }
+        return;
+    }
     // owned core in absolute coordinates, then relative to the (possibly
     // shifted) origin
     const int ox0 = ((bx == 0) ? 0 : bx * a.stride + a.ov / 2) - x0;
