@@ -187,7 +187,7 @@ __device__ __forceinline__ int local_cg(const LocalGeom& g, LocalShared& sh, flo
         }
         const float pq = cta_sum2((a0.x + a0.y) + (a1.x + a1.y), sh, par * 2);
         if (!(pq > 0.f)) break;
-        const float alpha = rr / pq;
+        const float alpha = __fdividef(rr, pq);   // CG step lengths need no IEEE rounding
         const float2 al = make_float2(alpha, alpha), nal = make_float2(-alpha, -alpha);
         a0 = make_float2(0.f, 0.f);
         a1 = a0;
@@ -202,7 +202,7 @@ __device__ __forceinline__ int local_cg(const LocalGeom& g, LocalShared& sh, flo
         if (w15) { sh.seam[npar][0][0][g.c] = R[7]; sh.seam[npar][0][1][g.c] = P[7]; }
         if (w16) { sh.seam[npar][1][0][g.c] = R[0]; sh.seam[npar][1][1][g.c] = P[0]; }
         const float rn = cta_sum2((a0.x + a0.y) + (a1.x + a1.y), sh, par * 2 + 1);
-        beta = rn / rr;
+        beta = __fdividef(rn, rr);
         rr = rn;
         const float2 be = make_float2(beta, beta);
 #pragma unroll
