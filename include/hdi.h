@@ -207,7 +207,11 @@ const char* hdi_version(void);
  *   tonal_oras_eta    [3e-2]  oras_eta used inside the tonal inner solves
  *   fine_pre, fine_post [1, 1] ORAS sweeps before / after the coarse correction on the finest level
  *   tonal_fine_pre, tonal_fine_post [2, 1] the same inside the tonal inner solves
- *   tonal_echo_rtol   [1e-3]  relative CG tolerance of the local echo solves
+ *   tonal_echo_rtol   [3e-3]  relative CG tolerance of the local echo solves
+ *   tonal_echo_max_iter [300] CG iteration cap of an echo solve
+ *   coarse_level_eta  [0.3]   oras_eta on the levels between the finest and the coarsest (0 = oras_eta)
+ *   coarse_level_max  [48]    local CG iteration cap on those levels
+ *   coarse_max_local  [600]   CG iteration cap of the coarsest solve
  *   trace             [0]     1 = one line per RAS iteration on stderr
  *   hbm_budget_gb     [200]   workspace cap for this context
  */

@@ -17,12 +17,12 @@ struct Params {
     double max_vcycles = 60;
     double tonal_max_iter = 400;
     double tonal_inner_ratio = 0.1;
-    double tonal_echo_rtol = 1e-3;
+    double tonal_echo_rtol = 3e-3;
     double tonal_echo_max_iter = 300;
     double hbm_budget_gb = 200.0;
     double trace = 0;
     double tonal_oras_eta = 3e-2;   // local stop fraction inside the tonal inner solves
-    double coarse_level_eta = 0;    // local stop fraction on levels >= 1 (0 = same as oras_eta)
+    double coarse_level_eta = 0.3;  // local stop fraction on levels >= 1 (0 = same as oras_eta)
     double coarse_level_max = 48;   // local CG cap on levels >= 1 (below the coarsest)
     double fine_pre = 1;            // ORAS pre-smoothing sweeps on the finest level
     double fine_post = 1;           // ORAS post-smoothing sweeps on the finest level
