@@ -290,7 +290,7 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     a.b = L.b;
     a.rnorm2 = rnorm2;
     a.iters = iters;
-    const int blocks = L.nbx * L.nby * nch;   // one CTA per (subdomain, channel)
+    const dim3 blocks(L.nbx, L.nby, nch);   // one CTA per (subdomain, channel)
     if (l == 0) tstart(kT_Oras);
     const bool full = L.W >= 32 && L.H >= 32;
     if (zero) {

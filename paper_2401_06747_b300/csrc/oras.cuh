@@ -238,11 +238,7 @@ struct OrasArgs {
 template <bool ZERO, bool FULL>
 __global__ void __launch_bounds__(kLocalThreads, 10) k_oras(OrasArgs a) {
     __shared__ LocalShared sh;
-    const int nb = a.nbx * a.nby;
-    const int ch = blockIdx.x / nb;
-    const int bi = blockIdx.x - ch * nb;
-    const int by = bi / a.nbx;
-    const int bx = bi - by * a.nbx;
+    const int bx = blockIdx.x, by = blockIdx.y, ch = blockIdx.z;   // grid (nbx, nby, nch)
     const int x0 = sub_origin(bx, a.W, a.stride), y0 = sub_origin(by, a.H, a.stride);
     const double rn2 = a.rnorm2[ch];
     const LocalGeom g = make_geom(x0, y0, a.H, a.W, a.m.ch(ch), a.theta, sh);

@@ -47,7 +47,7 @@ __global__ void k_tonal_count(MaskView m, int nbx, int nby, int stride, int* __r
 // Local pixel codes (ly * 32 + lx) of the mask pixels of each subdomain, in
 // raster order, at list + off[i].
 __global__ void k_tonal_list(MaskView m, int nbx, int nby, int stride, const int* __restrict__ off,
-                             uint16_t* __restrict__ list) {
+                             uint16_t* __restrict__ list, int* __restrict__ owner) {
     const int wid = blockIdx.x * 4 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (wid >= nbx * nby) return;
@@ -66,6 +66,7 @@ __global__ void k_tonal_list(MaskView m, int nbx, int nby, int stride, const int
     while (bits) {
         const int lx = __ffs(bits) - 1;
         bits &= bits - 1;
+        owner[pos] = wid;
         list[pos++] = (uint16_t)(lane * 32 + lx);
     }
 }
@@ -75,6 +76,7 @@ struct EchoArgs {
     int nbx, nby, stride, nb;
     const int* off;          // [nb + 1] exclusive prefix of m_i
     const uint16_t* list;
+    const int* owner;        // [sum m_i] subdomain of each echo
     float* echo;             // [sum m_i][32 rows][32 lanes]
     float rtol2;
     int maxit;
@@ -89,13 +91,7 @@ __global__ void __launch_bounds__(kLocalThreads, 8) k_tonal_echo(EchoArgs a) {
     const long long e = blockIdx.x;
     const int total = a.off[a.nb];
     if (e >= total) return;
-    // subdomain owning echo e: largest i with off[i] <= e
-    int lo = 0, hi = a.nb - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.off[mid] <= e) lo = mid; else hi = mid - 1;
-    }
-    const int i = lo;
+    const int i = a.owner[e];
     const int by = i / a.nbx, bx = i - by * a.nbx;
     const int x0 = sub_origin(bx, a.m.W, a.stride), y0 = sub_origin(by, a.m.H, a.stride);
     const LocalGeom g = make_geom(x0, y0, a.m.H, a.m.W, a.m, 0.f, sh);
@@ -549,12 +545,14 @@ int Ctx::tonal_setup() {
     acc((size_t)(nb + 1) * 4);
     acc((size_t)(nb + 1) * 8);
     acc((size_t)total * 2);
+    acc((size_t)total * 4);
     acc((size_t)total * 1024 * 4);
     acc((size_t)goff[nb] * 4);
     if ((rc = tws.reserve(*this, bytes, "tonal local factors"))) return rc;
     t_off = (int*)tws.take((size_t)(nb + 1) * 4);
     t_goff = (long long*)tws.take((size_t)(nb + 1) * 8);
     t_list = (uint16_t*)tws.take((size_t)total * 2);
+    int* t_owner = (int*)tws.take((size_t)total * 4);
     t_echo = (float*)tws.take((size_t)total * 1024 * 4);
     t_fac = (float*)tws.take((size_t)goff[nb] * 4);
     int* drowoff = (int*)tws.take((size_t)(H + 1) * 4);
@@ -575,7 +573,7 @@ int Ctx::tonal_setup() {
     ++launches;
     cudaMemcpyAsync(t_off, off.data(), (size_t)(nb + 1) * 4, cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(t_goff, goff.data(), (size_t)(nb + 1) * 8, cudaMemcpyHostToDevice, stream);
-    k_tonal_list<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), L0.nbx, L0.nby, stride, t_off, t_list);
+    k_tonal_list<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), L0.nbx, L0.nby, stride, t_off, t_list, t_owner);
     ++launches;
     if (total > 0) {
         EchoArgs ea;
@@ -586,6 +584,7 @@ int Ctx::tonal_setup() {
         ea.nb = nb;
         ea.off = t_off;
         ea.list = t_list;
+        ea.owner = t_owner;
         ea.echo = t_echo;
         ea.rtol2 = (float)(p.tonal_echo_rtol * p.tonal_echo_rtol);
         ea.maxit = (int)p.tonal_echo_max_iter;
