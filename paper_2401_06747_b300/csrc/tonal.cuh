@@ -832,7 +832,7 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     const int max_it = (int)p.tonal_max_iter;
     double mse_last = 0.0;
     for (;; ++it) {
-        const double tin = std::max(1e-13, std::min(1e-3, ratio * rel_prev));
+        const double tin = std::max(1e-13, std::min(p.tonal_inner_max, ratio * rel_prev));
         sy.tol = tin;
         rc = solve(sy);
         if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED)
