@@ -402,6 +402,97 @@ def run_batch(args, rank, world):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------- scaling sweep and C4 loop ---
+
+def _timed(fn, stream, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, r
+
+
+def run_sweep(args, rank, world):
+    """Scaling on synthetic data (the shapes of the paper's resolution and
+    density experiments): cold inpainting and tonal optimisation of RGB images
+    from 480x270 to 3840x2160 at 4% density, and of the 4K image at densities
+    0.5% .. 15%; time per solve and per pixel (a slope-1 check in resolution)."""
+    import numpy as np
+    import torch
+    import paper_2401_06747_b300 as hdi
+    from synthdata import synth_rgb, random_mask
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = hdi.Context(local, stream=stream)
+    rows = []
+    cases = [(h, w, DENSITY) for (h, w) in ((270, 480), (540, 960), (1080, 1920), (2160, 3840))]
+    cases += [(H4K, W4K, d) for d in (0.005, 0.01, 0.02, 0.08, 0.15)]
+    for (h, w, d) in cases:
+        f = torch.from_numpy(synth_rgb(h, w, seeds=IMAGE_SEEDS, dtype=np.float32)).cuda()
+        c = torch.from_numpy(random_mask(h, w, d, MASK_SEED)).cuda()
+        out = torch.empty_like(f)
+        ti, si = _timed(lambda: ctx.inpaint(f, c, out, tol=TOL), stream, max(args.steps // 2, 1))
+        tt, st = _timed(lambda: ctx.tonal_opt(f, c, out, tol=TOL, allow_not_converged=True), stream, 1)
+        rows.append({"height": h, "width": w, "density": d, "inpaint_ms": round(ti, 3),
+                     "inpaint_ns_per_pixel": round(ti * 1e6 / (h * w * 3), 4), "inpaint_vcycles": si["vcycles"],
+                     "tonal_ms": round(tt, 3), "tonal_iterations": st["iterations"], "tonal_vcycles": st["vcycles"],
+                     "tonal_rel_res": st["rel_res"]})
+    res4k = [r for r in rows if r["height"] == H4K and r["density"] == DENSITY][0]
+    out = {"metric": "scaling sweep: 4K RGB inpaint solves/s (4% mask) with resolution and density series",
+           "value": round(1e3 / res4k["inpaint_ms"], 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": 1, "ms_per_step": res4k["inpaint_ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "RGB 480x270..3840x2160 at 4%, 4K at 0.5..15%; cold solves to 1e-6",
+                      "rows": rows}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_densify(args, rank, world):
+    """The C4 loop: the 4K RGB image from an empty mask, eight densification
+    steps of 0.5% (Alg. 1 with t = 1), each followed by a warm-started
+    re-inpainting, then tonal optimisation on the final 4% mask."""
+    import numpy as np
+    import torch
+    import paper_2401_06747_b300 as hdi
+    from synthdata import synth_rgb
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = hdi.Context(local, stream=stream)
+    f = torch.from_numpy(synth_rgb(H4K, W4K, seeds=IMAGE_SEEDS, dtype=np.float32)).cuda()
+    step_px = int(round(0.005 * H4K * W4K))
+
+    def loop():
+        m = torch.zeros((H4K, W4K), dtype=torch.uint8, device="cuda")
+        u = torch.empty_like(f)
+        g = torch.empty_like(f)
+        for s in range(8):
+            ctx.densify_step(f, m, None if s == 0 else u, step_px, 300)
+            ctx.inpaint(f, m, u, u0=None if s == 0 else u, tol=TOL)
+        st = ctx.tonal_opt(f, m, g, tol=TOL)
+        return int(m.sum().item()), st
+
+    for _ in range(args.warmup):
+        loop()
+    ms_, (ones, st) = _timed(loop, stream, args.steps)
+    out = {"metric": "C4 densify loop: 4K RGB, 8 x 0.5% steps + warm re-inpaint + tonal, loops/s",
+           "value": round(1e3 / ms_, 4), "unit": "loops/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "3840x2160 RGB (seeds 1/2/3), empty mask, densify seed 300", "mask_pixels": ones,
+                      "tonal": {k: st[k] for k in ("iterations", "vcycles", "rel_res", "mse")}}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------ serving (C5) ---
 
 def run_serve(args, rank, world):
@@ -449,7 +540,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hdi", "reference"], default="hdi")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["4k", "batch", "serve"], default="4k")
+    ap.add_argument("--workload", choices=["4k", "batch", "serve", "sweep", "densify"], default="4k")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=120.0)
@@ -463,6 +554,10 @@ def main():
         run_batch(args, rank, world)
     elif args.workload == "serve":
         run_serve(args, rank, world)
+    elif args.workload == "sweep":
+        run_sweep(args, rank, world)
+    elif args.workload == "densify":
+        run_densify(args, rank, world)
     else:
         run_hdi(args, rank, world)
     if world > 1:
