@@ -23,7 +23,8 @@
 #include "oras.cuh"
 #include "anderson.cuh"
 
-constexpr int kTonalMaxM = 192;   // mask pixels per 32x32 subdomain handled by the dense local solve
+constexpr int kTonalMaxM = 1024;  // mask pixels per 32x32 subdomain (all of them)
+constexpr int kGramSmem = 208;    // subdomains with more mask pixels factor G_i in global memory
 
 // ----------------------------------------------------------- setup kernels ---
 
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
     extern __shared__ __align__(16) float sm[];
     const int i = blockIdx.x;
     const int m = off[i + 1] - off[i];
-    if (m == 0) return;
+    if (m == 0 || m > kGramSmem) return;   // dense subdomains: k_tonal_gram_big
     const int tid = threadIdx.x;
     const int m4 = gram_round4(m);
     const int nb = m4 / 4;
@@ -279,6 +280,134 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
         Gi[(size_t)ra * m + cb] = acc;
         Gi[(size_t)cb * m + ra] = acc;
     }
+}
+
+// Dense subdomains (m_i > kGramSmem mask pixels): the same G_i and inverse,
+// with G_i in its global output block instead of shared memory. The Gram
+// product uses the same register blocks (pixels staged in shared memory); the
+// Cholesky factor and W = L^{-1} (as W^T in the upper triangle) are formed
+// in place, G_i^{-1} = W^T W is written to the subdomain's echo block, which
+// the product no longer needs (m_i x 1024 >= m_i x m_i floats), and copied
+// back. Threads own rows r = tid, tid + 256, ...
+__global__ void __launch_bounds__(256) k_tonal_gram_big(const int* __restrict__ off,
+                                                        const long long* __restrict__ goff,
+                                                        float* __restrict__ echo, float* __restrict__ fac,
+                                                        unsigned* bad) {
+    extern __shared__ __align__(16) float sm[];
+    const int i = blockIdx.x;
+    const int m = off[i + 1] - off[i];
+    if (m <= kGramSmem) return;
+    const int tid = threadIdx.x;
+    const int m4 = gram_round4(m);
+    const int nb = m4 / 4;
+    const long long nblk = (long long)nb * (nb + 1) / 2;
+    const int es = m4 + 4;
+    float* Es = sm;                        // [32][es]
+    float* dinv = sm + 32 * es;            // [m]
+    float* col = dinv + m4;                // [m]: the current column of L
+    float* sd = col + m4;                  // [1]: the current diagonal
+    float* G = fac + goff[i];              // m x m
+    float* E = echo + (size_t)off[i] * 1024;
+    // G = I + S^T S, lower triangle, 4x4 blocks
+    for (long long b0 = 0; b0 < nblk; b0 += 256) {
+        const long long bidx = b0 + tid;
+        const bool on = bidx < nblk;
+        int br = 0, bc = 0;
+        if (on) {
+            br = (int)((sqrtf(8.f * (float)bidx + 1.f) - 1.f) * 0.5f);
+            while ((long long)br * (br + 1) / 2 > bidx) --br;
+            while ((long long)(br + 1) * (br + 2) / 2 <= bidx) ++br;
+            bc = (int)(bidx - (long long)br * (br + 1) / 2);
+        }
+        float acc[4][4];
+#pragma unroll
+        for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) acc[aa][bb] = 0.f;
+        for (int p0 = 0; p0 < 1024; p0 += 32) {
+            __syncthreads();
+            for (int q = tid; q < m4 * 32; q += 256) {
+                const int k = q >> 5, pp = q & 31;
+                Es[pp * es + k] = (k < m) ? E[(size_t)k * 1024 + p0 + pp] : 0.f;
+            }
+            __syncthreads();
+            if (on) {
+                for (int pp = 0; pp < 32; ++pp) {
+                    const float4 av = *reinterpret_cast<const float4*>(Es + pp * es + 4 * br);
+                    const float4 bv = *reinterpret_cast<const float4*>(Es + pp * es + 4 * bc);
+                    const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                    for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+                        for (int bb = 0; bb < 4; ++bb) acc[aa][bb] = fmaf(a4[aa], b4[bb], acc[aa][bb]);
+                }
+            }
+        }
+        if (on) {
+#pragma unroll
+            for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    const int r = 4 * br + aa, c = 4 * bc + bb;
+                    if (r < m && c <= r) G[(size_t)r * m + c] = acc[aa][bb] + (r == c ? 1.f : 0.f);
+                }
+        }
+    }
+    __syncthreads();
+    // right-looking Cholesky in place (lower triangle)
+    for (int j = 0; j < m; ++j) {
+        if (tid == (j & 255)) {
+            const float d = sqrtf(G[(size_t)j * m + j]);
+            if (!(d > 0.f)) atomicOr(bad, 1u);
+            G[(size_t)j * m + j] = d;
+            sd[0] = d;
+        }
+        __syncthreads();
+        const float dj = sd[0];
+        for (int r = j + 1 + ((tid - j - 1) & 255); r < m; r += 256) {
+            const float l = G[(size_t)r * m + j] / dj;
+            G[(size_t)r * m + j] = l;
+            col[r] = l;   // column j of L, read by every row's update
+        }
+        __syncthreads();
+        for (int r = j + 1 + ((tid - j - 1) & 255); r < m; r += 256) {
+            const float l = col[r];
+            float* __restrict__ gr = G + (size_t)r * m;
+            for (int c = j + 1; c <= r; ++c) gr[c] = fmaf(-l, col[c], gr[c]);
+        }
+        __syncthreads();
+    }
+    // W = L^{-1}: thread owns columns j; W^T row j in the upper triangle
+    for (int r = tid; r < m; r += 256) {
+        const float dj = 1.f / G[(size_t)r * m + r];
+        dinv[r] = dj;
+        for (int ii = r + 1; ii < m; ++ii) {
+            const float* li = G + (size_t)ii * m;
+            float s0 = li[r] * dj, s1 = 0.f;
+            int k = r + 1;
+            for (; k + 1 < ii; k += 2) {
+                s0 = fmaf(li[k], G[(size_t)r * m + k], s0);
+                s1 = fmaf(li[k + 1], G[(size_t)r * m + k + 1], s1);
+            }
+            if (k < ii) s0 = fmaf(li[k], G[(size_t)r * m + k], s0);
+            G[(size_t)r * m + ii] = -(s0 + s1) / li[ii];
+        }
+    }
+    __syncthreads();
+    // G^{-1} = W^T W into the echo block, then back
+    const long long ne = (long long)m * (m + 1) / 2;
+    for (long long e = tid; e < ne; e += 256) {
+        int ra = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+        while ((long long)ra * (ra + 1) / 2 > e) --ra;
+        while ((long long)(ra + 1) * (ra + 2) / 2 <= e) ++ra;
+        const int cb = (int)(e - (long long)ra * (ra + 1) / 2);
+        float acc = dinv[ra] * ((cb == ra) ? dinv[ra] : G[(size_t)cb * m + ra]);
+        for (int k = ra + 1; k < m; ++k) acc = fmaf(G[(size_t)ra * m + k], G[(size_t)cb * m + k], acc);
+        E[(size_t)ra * m + cb] = acc;
+        E[(size_t)cb * m + ra] = acc;
+    }
+    __syncthreads();
+    for (long long e = tid; e < (long long)m * m; e += 256) G[e] = E[e];
 }
 
 // ------------------------------------------------------- outer iteration ---
@@ -416,7 +545,7 @@ __host__ __device__ __forceinline__ int class_member(int c, int q, int nb) { ret
 // warps' partial sums are added in a fixed order.
 constexpr int kLocalWarps = 4;
 __global__ void __launch_bounds__(32 * kLocalWarps) k_tonal_local(LocalSolveArgs a) {
-    constexpr int NT = (kTonalMaxM + 31) / 32;
+    constexpr int NT = 4;                 // rows of v per lane and pass: 128 per pass
     __shared__ float xs[4 * kTonalMaxM];
     __shared__ float ps[kLocalWarps][4][NT * 32];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -445,44 +574,48 @@ __global__ void __launch_bounds__(32 * kLocalWarps) k_tonal_local(LocalSolveArgs
             if (c < nch) xs[c * m + k] = a.r[c * a.F.cs + p];
     }
     __syncthreads();
-    float y[4][NT];
+    // passes over 128 rows of v (one pass unless the subdomain is dense)
+    for (int base = 0; base < m; base += NT * 32) {
+        float y[4][NT];
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int t = 0; t < NT; ++t) y[c][t] = 0.f;
+            for (int t = 0; t < NT; ++t) y[c][t] = 0.f;
 #pragma unroll 4
-    for (int j = wl; j < m; j += kLocalWarps) {
-        const float* row = Gi + (size_t)j * m;
-        float xj[4];
+        for (int j = wl; j < m; j += kLocalWarps) {
+            const float* row = Gi + (size_t)j * m + base;
+            float xj[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) xj[c] = (c < nch) ? xs[c * m + j] : 0.f;
+            for (int c = 0; c < 4; ++c) xj[c] = (c < nch) ? xs[c * m + j] : 0.f;
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const int k = lane + 32 * t;
-            if (k < m) {
-                const float g = row[k];
+            for (int t = 0; t < NT; ++t) {
+                const int k = lane + 32 * t;
+                if (base + k < m) {
+                    const float g = row[k];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) y[c][t] = fmaf(g, xj[c], y[c][t]);
+                    for (int c = 0; c < 4; ++c) y[c][t] = fmaf(g, xj[c], y[c][t]);
+                }
             }
         }
-    }
+        if (base > 0) __syncthreads();   // the previous pass has read ps
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int t = 0; t < NT; ++t) ps[wl][c][t * 32 + lane] = y[c][t];
-    __syncthreads();
-    for (int k = threadIdx.x; k < m; k += 32 * kLocalWarps) {
-        const int code = lst[k];
-        const int px = x0 + (code & 31), py = y0 + (code >> 5);
-        const int mult = cover_count(px, a.nbx, a.stride, a.F.W) * cover_count(py, a.nby, a.stride, a.F.H);
-        const size_t p = (size_t)py * a.F.pitch + px;
+            for (int t = 0; t < NT; ++t) ps[wl][c][t * 32 + lane] = y[c][t];
+        __syncthreads();
+        for (int k = threadIdx.x; k < NT * 32 && base + k < m; k += 32 * kLocalWarps) {
+            const int code = lst[base + k];
+            const int px = x0 + (code & 31), py = y0 + (code >> 5);
+            const int mult = cover_count(px, a.nbx, a.stride, a.F.W) * cover_count(py, a.nby, a.stride, a.F.H);
+            const size_t p = (size_t)py * a.F.pitch + px;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            if (c < nch) {
-                float v = ps[0][c][k];
+            for (int c = 0; c < 4; ++c) {
+                if (c < nch) {
+                    float v = ps[0][c][k];
 #pragma unroll
-                for (int w = 1; w < kLocalWarps; ++w) v += ps[w][c][k];
-                a.out[c * a.F.cs + p] += v / (float)mult;
+                    for (int w = 1; w < kLocalWarps; ++w) v += ps[w][c][k];
+                    a.out[c * a.F.cs + p] += v / (float)mult;
+                }
             }
         }
     }
@@ -515,8 +648,6 @@ int Ctx::tonal_setup() {
         goff[i + 1] = goff[i] + (long long)cnt[i] * cnt[i];
         maxm = std::max(maxm, cnt[i]);
     }
-    if (maxm > kTonalMaxM)
-        return fail(HDI_ERR_UNSUPPORTED, "tonal: a 32x32 subdomain holds %d mask pixels (limit %d)", maxm, kTonalMaxM);
     const long long total = off[nb];
     // compact list of mask pixels (row counts on the device, scan on the host)
     std::vector<int> rc_h(H), rowoff(H + 1);
@@ -593,12 +724,18 @@ int Ctx::tonal_setup() {
         k_tonal_echo<<<(unsigned)total, kLocalThreads, 0, stream>>>(ea);
         ++launches;
         tstop();
-        const size_t shm = gram_smem_floats(maxm) * 4;
+        const size_t shm = gram_smem_floats(std::min(maxm, kGramSmem)) * 4;
         cudaFuncSetAttribute(k_tonal_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         cudaMemsetAsync(flags, 0, 4, stream);
         tstart(kT_Gram);
         k_tonal_gram<<<nb, 256, shm, stream>>>(t_off, t_goff, t_echo, t_fac, flags);
         ++launches;
+        if (maxm > kGramSmem) {
+            const size_t shb = ((size_t)32 * (gram_round4(maxm) + 4) + 2 * gram_round4(maxm) + 4) * 4;
+            cudaFuncSetAttribute(k_tonal_gram_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
+            k_tonal_gram_big<<<nb, 256, shb, stream>>>(t_off, t_goff, t_echo, t_fac, flags);
+            ++launches;
+        }
         tstop();
         unsigned bad = 0;
         cudaMemcpyAsync(&bad, flags, 4, cudaMemcpyDeviceToHost, stream);

@@ -73,3 +73,21 @@ def test_bitwise_determinism_across_contexts_and_history():
     g3 = torch.empty_like(g1)
     a.tonal_opt(dev(f), dev(c), g3, tol=1e-6)
     assert torch.equal(g1, g2) and torch.equal(g1, g3)
+
+
+@pytest.mark.parametrize("H,W,d,block", [(96, 128, 0.15, 0), (90, 110, 0.05, 40)])
+def test_dense_subdomains(H, W, d, block):
+    """Subdomains above 128 mask pixels take the global-memory factorisation:
+    15% density (the top of the paper's range), and a fully known 40 x 40
+    block (subdomains with up to all 1024 pixels on the mask)."""
+    f = synth_rgb(H, W, seeds=(31, 32, 33), dtype=np.float32)
+    c = random_mask(H, W, d, 77)
+    if block:
+        c[20:20 + block, 30:30 + block] = 1
+    g, st = run(f, c, 1e-6)
+    f64 = f.astype(np.float64)
+    ref = tonal_ref(f64, c)
+    assert st["rel_res"] <= 1e-6
+    assert normal_residual(f64, c, g.astype(np.float64)).max() <= 2e-6
+    assert np.abs(g - ref).max() <= 0.05
+    assert np.all(g[:, c == 0] == 0)
