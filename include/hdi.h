@@ -204,6 +204,7 @@ const char* hdi_version(void);
  *   tonal_max_iter    [400]   RAS iterations per tonal solve
  *   tonal_inner_ratio [0.1]   inner solves target: ratio * current outer relative residual
  *   tonal_inner_max   [3e-2]  ... but at most this (the early outer iterations)
+ *   tonal_anderson_beta [1.0] Anderson mixing parameter beta (step = beta f - sum gamma (dX + beta dF))
  *   tonal_anderson    [8]     Anderson window on the RAS iteration (0 = plain Alg. 2)
  *   tonal_oras_eta    [3e-2]  oras_eta used inside the tonal inner solves
  *   fine_pre, fine_post [1, 1] ORAS sweeps before / after the coarse correction on the finest level

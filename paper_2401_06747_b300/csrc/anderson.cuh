@@ -59,6 +59,7 @@ struct AAArgs {
     int M;              // known pixels per channel
     long long cs;       // channel stride of the full-layout arrays
     int nch, k, slot, mwin;
+    float beta;         // mixing: step = beta f_n - sum_j gamma_j (dX_j + beta dF_j)
     const int* idx;     // [M]
     const float* fvfull;// P r in full layout (valid on known pixels)
     float* fv;          // [nch][M] current f_n
@@ -154,17 +155,17 @@ __global__ void __launch_bounds__(256) k_aa_gather(AAArgs a, int new_slot) {
     if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
-// step = f_n - sum_j gamma_j (dX_j + dF_j);  g += step;  dX[write_slot] = step.
+// step = beta f_n - sum_j gamma_j (dX_j + beta dF_j);  g += step;  dX[write_slot] = step.
 __global__ void __launch_bounds__(256) k_aa_update(AAArgs a, int write_slot) {
     const int ch = blockIdx.y;
     const size_t co = (size_t)ch * a.M;
     const size_t vs = (size_t)a.nch * a.M;
     for (int i = blockIdx.x * 256 + threadIdx.x; i < a.M; i += gridDim.x * 256) {
-        float s = a.fv[co + i];
+        float s = a.beta * a.fv[co + i];
         for (int j = 0; j < a.k; ++j) {
             const int sl = (a.slot - j + a.mwin * 4) % a.mwin;
             const float gj = (float)a.gamma[ch * kAAMax + j];
-            s -= gj * (a.dX[(size_t)sl * vs + co + i] + a.dF[(size_t)sl * vs + co + i]);
+            s -= gj * fmaf(a.beta, a.dF[(size_t)sl * vs + co + i], a.dX[(size_t)sl * vs + co + i]);
         }
         const size_t p = ch * a.cs + a.idx[i];
         float h, l;

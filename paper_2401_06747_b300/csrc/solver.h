@@ -17,6 +17,7 @@ struct Params {
     double max_vcycles = 60;
     double tonal_max_iter = 400;
     double tonal_inner_ratio = 0.1;
+    double tonal_anderson_beta = 1.0;  // Anderson mixing parameter
     double tonal_inner_max = 3e-2;   // loosest inner solve tolerance (early outer iterations)
     double tonal_echo_rtol = 3e-3;
     double tonal_echo_max_iter = 300;

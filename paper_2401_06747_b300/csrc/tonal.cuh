@@ -844,6 +844,7 @@ int Ctx::tonal_aa_step(int n, const float* fvfull, DF G) {
     a.k = k;
     a.slot = n >= 1 ? (n - 1) % ring : 0;
     a.mwin = ring;
+    a.beta = (float)p.tonal_anderson_beta;
     a.idx = aa_idx;
     a.fvfull = fvfull;
     a.fv = aa_fv;
