@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kLocalThreads, 8) k_tonal_echo(EchoArgs a) {
         R[k].y = (ny && ((g.um >> (2 * k + 1)) & 1u)) ? -1.f : 0.f;
         a0 = __ffma2_rn(R[k], R[k], a0);
     }
-    const float rr0 = cta_sum2(a0.x + a0.y, sh, 4);
+    const float rr0 = cta_sum2(a0.x + a0.y, sh, 3);   // slot 4 is reused right away by the CG set-up
     const int it = (g.w == 32 && g.h == 32) ? local_cg<true>(g, sh, V, R, a.rtol2 * rr0, a.maxit)
                                             : local_cg<false>(g, sh, V, R, a.rtol2 * rr0, a.maxit);
     if (a.iters && threadIdx.x == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
