@@ -10,7 +10,8 @@ Modules
   laplace   -- the discrete model of Sec. 2.1: L, A = C + (I-C)L, b = Cf,
                the inpainting solve and its general-right-hand-side variant.
   tonal     -- tonal optimisation (Sec. 5): B = A^{-1}C, B^T via the
-               symmetrised system, CG on the normal equations, and an
+               symmetrised system, CG on the normal equations, CGNR with the
+               MSE-gain stopping rule, and an
                independent projection formulation used as a cross-check.
   ras       -- restricted additive Schwarz for tonal optimisation (Alg. 2)
                with exact local solves, and the overlapping decomposition.
@@ -37,4 +38,6 @@ from .tonal import (  # noqa: F401
     tonal_projection,
     normal_residual,
     mse,
+    tonal_cgnr,
+    mse_gain_stop,
 )

@@ -22,7 +22,7 @@ struct Params {
     double tonal_echo_rtol = 3e-3;
     double tonal_echo_max_iter = 300;
     double hbm_budget_gb = 200.0;
-    double trace = 0;
+    double trace = 0;               // 1: one line per outer iteration on stderr
     double tonal_oras_eta = 3e-2;   // local stop fraction inside the tonal inner solves
     double coarse_level_eta = 0.3;  // local stop fraction on levels >= 1 (0 = same as oras_eta)
     double coarse_level_max = 48;   // local CG cap on levels >= 1 (below the coarsest)
@@ -30,7 +30,7 @@ struct Params {
     double fine_post = 1;           // ORAS post-smoothing sweeps on the finest level
     double tonal_fine_pre = 2;      // fine_pre inside the tonal inner solves
     double tonal_fine_post = 1;     // fine_post inside the tonal inner solves
-    double tonal_anderson = 8;      // Anderson window on the RAS iteration (0 = plain Alg. 2)               // 1: one line per outer iteration on stderr
+    double tonal_anderson = 8;      // Anderson window on the RAS iteration (0 = plain Alg. 2)
 };
 
 struct Level {
@@ -103,8 +103,8 @@ struct Ctx {
     int* d_chmask = nullptr;   // [kMaxCh] mask plane of each channel (batched solves)
     Level lev[kMaxLevels];
     DF dfv[kNumDF] = {};
-    float* tres = nullptr;
-    float* flo2 = nullptr;     // bits of f below its double-float pair (FP64 input)     // tonal residual B^T (f - B g) on mask pixels, FP32
+    float* tres = nullptr;     // tonal residual B^T (f - B g) on mask pixels, FP32
+    float* flo2 = nullptr;     // bits of f below its double-float pair (FP64 input)
     double* partials = nullptr;
     double* scal = nullptr;
     unsigned* tickets = nullptr;

@@ -4,7 +4,7 @@ the paper and by the mathematics."""
 import numpy as np
 import pytest
 
-from oracle import (B_apply, Bt_apply, tonal, tonal_projection, normal_residual,
+from oracle import (B_apply, Bt_apply, tonal, tonal_projection, normal_residual, tonal_cgnr, mse_gain_stop,
                     inpaint, mse, laplacian)
 from synthdata import synth_image, random_mask
 
@@ -116,3 +116,65 @@ def test_normal_residual_of_unoptimised_values_is_large():
     f = synth_image(H, W, 14)
     c = random_mask(H, W, 0.04, 15)
     assert normal_residual(f, c, f * c)[0] > 1e-3
+
+
+# ---- CGNR (Sec. 5.1, "Improvements") and the MSE-gain stopping rule ----------
+
+def _tiny_case(H=9, W=11, d=0.12, seed=21):
+    f = np.stack([synth_image(H, W, seed), synth_image(H, W, seed + 1)])
+    c = random_mask(H, W, d, seed + 2)
+    return f, c
+
+
+def test_cgnr_finite_termination():
+    """CG on the m x m normal equations reaches the exact minimiser within m
+    steps; compared with the independent projection formulation."""
+    f, c = _tiny_case()
+    m = int(c.sum())
+    g, hist = tonal_cgnr(f, c, max_iter=m, rtol=0.0)
+    gp = tonal_projection(f, c)
+    assert np.abs(g - gp).max() <= 1e-7 * np.abs(gp).max()
+    assert hist["rel"][-1] < 1e-7
+
+
+def test_cgnr_first_step_is_exact_line_search():
+    """The first CGNR step minimises ||f - B(g0 + t z0)|| over t: the
+    minimiser of the quadratic through three samples t = 0, 1, 2."""
+    f, c = _tiny_case(seed=31)
+    f = f[0]
+    g0 = f * c
+    z0 = Bt_apply(f - B_apply(g0, c), c)
+    q = [float(np.sum((f - B_apply(g0 + t * z0, c)) ** 2)) for t in (0.0, 1.0, 2.0)]
+    a2 = (q[2] - 2 * q[1] + q[0]) / 2.0
+    b1 = q[1] - q[0] - a2
+    t_star = -b1 / (2 * a2)
+    g1, _ = tonal_cgnr(f, c, max_iter=1, rtol=0.0)
+    np.testing.assert_allclose(g1, g0 + t_star * z0, atol=1e-9 * np.abs(g0).max())
+
+
+def test_cgnr_residual_never_increases():
+    """CGNR minimises ||f - B g|| over a growing Krylov space: the MSE
+    history is non-increasing and ends at the optimum."""
+    f = synth_image(24, 20, 41)
+    c = random_mask(24, 20, 0.06, 42)
+    g, hist = tonal_cgnr(f, c, max_iter=200, rtol=1e-12)
+    m = np.asarray(hist["mse"])
+    assert np.all(np.diff(m) <= 1e-12 * m[0])
+    e_opt = mse(B_apply(tonal(f, c), c), f)
+    assert abs(m[-1] - e_opt) <= 1e-9 * e_opt
+    np.testing.assert_allclose(g, tonal(f, c), atol=1e-7 * np.abs(f).max())
+
+
+def test_cgnr_mse_gain_stop():
+    """With the 0.1% rule the run stops at the first iteration whose MSE gain
+    is below 0.1%, and not before."""
+    f = np.stack([synth_image(32, 30, 51), synth_image(32, 30, 52)])
+    c = random_mask(32, 30, 0.04, 53)
+    _, full = tonal_cgnr(f, c, max_iter=300, rtol=1e-13)
+    _, hist = tonal_cgnr(f, c, max_iter=300, rtol=1e-13, mse_gain=1e-3)
+    m = full["mse"]
+    k = len(hist["mse"]) - 1
+    assert 1 <= k < len(m) - 1
+    assert mse_gain_stop(m[k - 1], m[k], 1e-3)
+    assert not any(mse_gain_stop(m[j - 1], m[j], 1e-3) for j in range(1, k))
+    np.testing.assert_allclose(hist["mse"], m[:k + 1], rtol=1e-12)
