@@ -205,6 +205,10 @@ const char* hdi_version(void);
  *   tonal_inner_ratio [0.1]   inner solves target: ratio * current outer relative residual
  *   tonal_inner_max   [3e-2]  ... but at most this (the early outer iterations)
  *   tonal_anderson_beta [1.0] Anderson mixing parameter beta (step = beta f - sum gamma (dX + beta dF))
+ *   tonal_method      [0]     0: RAS (Alg. 2); 1: CGNR, conjugate gradients on the normal equations
+ *                             with multigrid inner solves (Sec. 5.1, "Improvements")
+ *   tonal_mse_gain    [0]     > 0: hdi_tonal_opt also stops (successfully) once an outer iteration
+ *                             improves the MSE by less than this relative amount (Sec. 6: 1e-3)
  *   tonal_anderson    [8]     Anderson window on the RAS iteration (0 = plain Alg. 2)
  *   tonal_oras_eta    [3e-2]  oras_eta used inside the tonal inner solves
  *   fine_pre, fine_post [1, 1] ORAS sweeps before / after the coarse correction on the finest level

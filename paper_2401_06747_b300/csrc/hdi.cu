@@ -39,6 +39,8 @@ const ParamDef kParams[] = {
     {"tonal_inner_ratio", &Params::tonal_inner_ratio, 1e-6, 1.0},
     {"tonal_inner_max", &Params::tonal_inner_max, 1e-12, 0.5},
     {"tonal_anderson_beta", &Params::tonal_anderson_beta, 1e-3, 2.0},
+    {"tonal_method", &Params::tonal_method, 0, 1},
+    {"tonal_mse_gain", &Params::tonal_mse_gain, 0, 0.5},
     {"tonal_echo_rtol", &Params::tonal_echo_rtol, 1e-12, 1.0},
     {"tonal_echo_max_iter", &Params::tonal_echo_max_iter, 1, 4096},
     {"hbm_budget_gb", &Params::hbm_budget_gb, 0.001, 1e6},

@@ -31,6 +31,8 @@ struct Params {
     double tonal_fine_pre = 2;      // fine_pre inside the tonal inner solves
     double tonal_fine_post = 1;     // fine_post inside the tonal inner solves
     double tonal_anderson = 8;      // Anderson window on the RAS iteration (0 = plain Alg. 2)
+    double tonal_method = 0;        // 0: RAS (Alg. 2), 1: CGNR (Sec. 5.1)
+    double tonal_mse_gain = 0;      // > 0: also stop once an iteration improves the MSE by less (relative)
 };
 
 struct Level {
@@ -81,13 +83,16 @@ constexpr int kSlotR64 = 16;      // ||r||^2 of the FP64 residual
 constexpr int kSlotB64 = 17;      // ||b||^2 of the FP64 residual
 constexpr int kSlotTonalR = 18;   // ||B^T(f - Bg)||^2
 constexpr int kSlotTonalE = 19;   // ||f - Bg||^2
+constexpr int kSlotCgW = 20;      // CGNR: ||B p||^2
+constexpr int kSlotCgZ = 21;      // CGNR: ||z||^2 of the previous iteration
+constexpr int kSlotCgZP = 22;     // CGNR: <z, p>
 constexpr int kCntOnes = 0;
 constexpr int kCntLocal = 1;
 constexpr int kCntEcho = 2;
 constexpr int kMaxTimed = 2048;   // timed launches buffered between flushes
 enum { kT_Oras = 0, kT_Residual, kT_Prolong, kT_Restrict, kT_Echo, kT_Gram, kT_Local, kT_Anderson };
 // double-float vectors of level-0 size
-enum { kF = 0, kU0, kU1, kG, kY0, kY1, kW0, kW1, kNumDF };
+enum { kF = 0, kU0, kU1, kG, kY0, kY1, kW0, kW1, kP, kNumDF };
 
 struct Ctx {
     int device = 0;
@@ -171,6 +176,8 @@ struct Ctx {
     void tonal_residual(DFc y, DFc w);
     void tonal_local(float* out);
     int tonal_aa_step(int n, const float* fvfull, DF G);
+    int tonal_cgnr(SolveSpec& sw, const double* btf2, double tol, int& it, double& rel_max, double& mse_last,
+                   bool& by_gain);
     int inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,
                 hdi_stats* st);
     int tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hdi_image* g, double tol,

@@ -22,6 +22,7 @@
 #pragma once
 #include "oras.cuh"
 #include "anderson.cuh"
+#include "cgnr.cuh"
 
 constexpr int kTonalMaxM = 1024;  // mask pixels per 32x32 subdomain (all of them)
 constexpr int kGramSmem = 208;    // subdomains with more mask pixels factor G_i in global memory
@@ -921,7 +922,8 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     }
     vcycles_run = 0;
     cudaMemsetAsync(counters + kCntLocal, 0, 16, stream);
-    if ((rc = tonal_setup())) return rc;
+    const bool cgnr = p.tonal_method >= 0.5;
+    if (!cgnr && (rc = tonal_setup())) return rc;
 
     // the inner solves use their own local stop fraction (restored on exit)
     struct EtaSwap {
@@ -953,55 +955,64 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     rc = solve(sw);
     if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return fail(rc, "tonal: B^T f solve: %s", err.c_str());
     tonal_residual(DFc{nullptr, nullptr}, cview(sw.u[sw.cur]));
-    double btf2[4], r2[4], e2[4];
+    double btf2[kMaxCh], r2[kMaxCh], e2[kMaxCh];
     if ((rc = read_slot(kSlotTonalR, btf2))) return rc;
-
-    SolveSpec sy;
-    sy.u[0] = dfv[kY0];
-    sy.u[1] = dfv[kY1];
-    sy.cur = 0;
-    sy.rhs = RHS_DATA;
-    sy.d = cview(G);
-    sy.start = START_FMG;
-    sy.max_iter = (int)p.max_vcycles;
-    sw.start = START_WARM;
-    double rel_prev = 1.0, rel_max = 1.0;
     int it = 0;
-    const int max_it = (int)p.tonal_max_iter;
-    double mse_last = 0.0;
-    for (;; ++it) {
-        const double tin = std::max(1e-13, std::min(p.tonal_inner_max, ratio * rel_prev));
-        sy.tol = tin;
-        rc = solve(sy);
-        if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED)
-            return fail(rc, "tonal: B g solve, iteration %d: %s", it, err.c_str());
-        sy.start = START_WARM;
-        sw.tol = tin;
-        sw.y = cview(sy.u[sy.cur]);
-        rc = solve(sw);
-        if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED)
-            return fail(rc, "tonal: adjoint solve, iteration %d: %s", it, err.c_str());
-        tonal_residual(cview(sy.u[sy.cur]), cview(sw.u[sw.cur]));
-        if ((rc = read_slot(kSlotTonalR, r2))) return rc;
-        if ((rc = read_slot(kSlotTonalE, e2))) return rc;
-        rel_max = 0.0;
-        double esum = 0.0;
-        for (int c = 0; c < nch; ++c) {
-            if (!std::isfinite(r2[c])) return fail(HDI_ERR_NONFINITE, "tonal: non-finite residual");
-            const double rel = btf2[c] > 0 ? std::sqrt(r2[c] / btf2[c]) : 0.0;
-            rel_max = std::max(rel_max, rel);
-            esum += e2[c];
+    double rel_max = 1.0, mse_last = 0.0;
+    bool by_gain = false;
+    if (cgnr) {
+        if ((rc = tonal_cgnr(sw, btf2, tol, it, rel_max, mse_last, by_gain))) return rc;
+    } else {
+        SolveSpec sy;
+        sy.u[0] = dfv[kY0];
+        sy.u[1] = dfv[kY1];
+        sy.cur = 0;
+        sy.rhs = RHS_DATA;
+        sy.d = cview(G);
+        sy.start = START_FMG;
+        sy.max_iter = (int)p.max_vcycles;
+        sw.start = START_WARM;
+        double rel_prev = 1.0, mse_prev = 0.0;
+        const int max_it = (int)p.tonal_max_iter;
+        for (;; ++it) {
+            const double tin = std::max(1e-13, std::min(p.tonal_inner_max, ratio * rel_prev));
+            sy.tol = tin;
+            rc = solve(sy);
+            if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED)
+                return fail(rc, "tonal: B g solve, iteration %d: %s", it, err.c_str());
+            sy.start = START_WARM;
+            sw.tol = tin;
+            sw.y = cview(sy.u[sy.cur]);
+            rc = solve(sw);
+            if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED)
+                return fail(rc, "tonal: adjoint solve, iteration %d: %s", it, err.c_str());
+            tonal_residual(cview(sy.u[sy.cur]), cview(sw.u[sw.cur]));
+            if ((rc = read_slot(kSlotTonalR, r2))) return rc;
+            if ((rc = read_slot(kSlotTonalE, e2))) return rc;
+            rel_max = 0.0;
+            double esum = 0.0;
+            for (int c = 0; c < nch; ++c) {
+                if (!std::isfinite(r2[c])) return fail(HDI_ERR_NONFINITE, "tonal: non-finite residual");
+                const double rel = btf2[c] > 0 ? std::sqrt(r2[c] / btf2[c]) : 0.0;
+                rel_max = std::max(rel_max, rel);
+                esum += e2[c];
+            }
+            mse_last = esum / ((double)nch * H * W);
+            if (p.trace > 0)
+                fprintf(stderr, "[hdi tonal] it %d rel %.3e mse %.6f inner tol %.2e y: %d vc rel %.2e  w: %d vc rel %.2e\n",
+                        it, rel_max, mse_last, tin, sy.iterations, sy.rel_max, sw.iterations, sw.rel_max);
+            if (rel_max <= tol || it >= max_it) break;
+            if (p.tonal_mse_gain > 0 && it > 0 && mse_prev - mse_last < p.tonal_mse_gain * mse_prev) {
+                by_gain = true;
+                break;
+            }
+            rel_prev = rel_max;
+            mse_prev = mse_last;
+            float* fvfull = lev[0].xb;   // free between solves
+            cudaMemsetAsync(fvfull, 0, (size_t)nch * lev[0].cs * 4, stream);
+            tonal_local(fvfull);
+            if ((rc = tonal_aa_step(it, fvfull, G))) return rc;
         }
-        mse_last = esum / ((double)nch * H * W);
-        if (p.trace > 0)
-            fprintf(stderr, "[hdi tonal] it %d rel %.3e mse %.6f inner tol %.2e y: %d vc rel %.2e  w: %d vc rel %.2e\n",
-                    it, rel_max, mse_last, tin, sy.iterations, sy.rel_max, sw.iterations, sw.rel_max);
-        if (rel_max <= tol || it >= max_it) break;
-        rel_prev = rel_max;
-        float* fvfull = lev[0].xb;   // free between solves
-        cudaMemsetAsync(fvfull, 0, (size_t)nch * lev[0].cs * 4, stream);
-        tonal_local(fvfull);
-        if ((rc = tonal_aa_step(it, fvfull, G))) return rc;
     }
     if ((rc = store_image(cview(G), g, true))) return rc;
     if (st) {
@@ -1014,7 +1025,105 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
         st->mse = mse_last;
     }
     if ((rc = tflush())) return rc;
-    if (rel_max > tol)
-        return fail(HDI_ERR_NOT_CONVERGED, "tonal: relative residual %.3e after %d RAS iterations", rel_max, it);
+    if (rel_max > tol && !by_gain)
+        return fail(HDI_ERR_NOT_CONVERGED, "tonal: relative residual %.3e after %d %s iterations", rel_max, it,
+                    cgnr ? "CGNR" : "RAS");
     return HDI_OK;
+}
+
+// CGNR outer loop (Sec. 5.1, "Improvements"; kernels in cgnr.cuh). On entry
+// G holds g0 and sw the warm adjoint solve of B^T f. Per iteration: w = B p
+// (inpainting of p from full multigrid), the alpha step on y and g, then
+// y = B g re-solved warm from the updated y (so that inexact inner solves do
+// not accumulate in the residual), z = B^T (f - y) and the new direction.
+// Inner tolerances follow the RAS driver: ratio * current relative residual,
+// at most tonal_inner_max.
+int Ctx::tonal_cgnr(SolveSpec& sw, const double* btf2, double tol, int& it, double& rel_max, double& mse_last,
+                    bool& by_gain) {
+    int rc;
+    const DF G = dfv[kG];
+    const DF P = dfv[kP];
+    const double ratio = p.tonal_inner_ratio;
+    const int max_it = (int)p.tonal_max_iter;
+    const int parts = std::min(maxparts_, 4 * 148);
+    const dim3 vgrid(parts, nch);
+    const MaskView m0 = mview(0);
+    SolveSpec sy;   // y = B g
+    sy.u[0] = dfv[kY0];
+    sy.u[1] = dfv[kY1];
+    sy.cur = 0;
+    sy.rhs = RHS_DATA;
+    sy.d = cview(G);
+    sy.start = START_FMG;
+    sy.max_iter = (int)p.max_vcycles;
+    SolveSpec spw;  // w = B p
+    spw.u[0] = dfv[kU0];
+    spw.u[1] = dfv[kU1];
+    spw.rhs = RHS_DATA;
+    spw.d = cview(P);
+    spw.max_iter = (int)p.max_vcycles;
+    double r2[kMaxCh], e2[kMaxCh];
+    double rel_prev = 1.0, mse_prev = 0.0;
+    sw.start = START_WARM;
+    // z = B^T (f - y) and the figures of the current iterate
+    auto evaluate = [&](double tin) -> int {
+        int r;
+        sy.tol = tin;
+        r = solve(sy);
+        if (r != HDI_OK && r != HDI_ERR_NOT_CONVERGED) return fail(r, "CGNR: B g solve: %s", err.c_str());
+        sy.start = START_WARM;
+        sw.tol = tin;
+        sw.y = cview(sy.u[sy.cur]);
+        r = solve(sw);
+        if (r != HDI_OK && r != HDI_ERR_NOT_CONVERGED) return fail(r, "CGNR: adjoint solve: %s", err.c_str());
+        tonal_residual(cview(sy.u[sy.cur]), cview(sw.u[sw.cur]));
+        if ((r = read_slot(kSlotTonalR, r2))) return r;
+        if ((r = read_slot(kSlotTonalE, e2))) return r;
+        rel_max = 0.0;
+        double esum = 0.0;
+        for (int c = 0; c < nch; ++c) {
+            if (!std::isfinite(r2[c])) return fail(HDI_ERR_NONFINITE, "CGNR: non-finite residual");
+            rel_max = std::max(rel_max, btf2[c] > 0 ? std::sqrt(r2[c] / btf2[c]) : 0.0);
+            esum += e2[c];
+        }
+        mse_last = esum / ((double)nch * H * W);
+        return HDI_OK;
+    };
+    if ((rc = evaluate(std::max(1e-13, std::min(p.tonal_inner_max, ratio))))) return rc;
+    k_cgnr_direction<<<vgrid, kCgnrThreads, 0, stream>>>(arr(0), m0, tres, P, scal + kSlotTonalR * kMaxCh,
+                                                           scal + kSlotCgZ * kMaxCh, 1);
+    ++launches;
+    for (it = 0;; ++it) {
+        if (p.trace > 0)
+            fprintf(stderr, "[hdi cgnr] it %d rel %.3e mse %.6f  y: %d vc  w: %d vc\n", it, rel_max, mse_last,
+                    sy.iterations, sw.iterations);
+        if (rel_max <= tol || it >= max_it) break;
+        if (p.tonal_mse_gain > 0 && it > 0 && mse_prev - mse_last < p.tonal_mse_gain * mse_prev) {
+            by_gain = true;
+            break;
+        }
+        const double tin = std::max(1e-13, std::min(p.tonal_inner_max, ratio * rel_max));
+        rel_prev = rel_max;
+        mse_prev = mse_last;
+        // w = B p
+        spw.cur = 0;
+        spw.start = START_FMG;
+        spw.tol = tin;
+        rc = solve(spw);
+        if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return fail(rc, "CGNR: B p solve: %s", err.c_str());
+        const DF w = spw.u[spw.cur];
+        k_cgnr_dots<<<vgrid, kCgnrThreads, 0, stream>>>(arr(0), m0, cview(w), tres, cview(P), reducer(kSlotCgW, parts),
+                                                         reducer(kSlotCgZP, parts));
+        // y += alpha w (the warm start of the next B g solve), g += alpha p
+        k_cgnr_step<<<vgrid, kCgnrThreads, 0, stream>>>(arr(0), m0, sy.u[sy.cur], cview(w), G, cview(P),
+                                                         scal + kSlotTonalR * kMaxCh, scal + kSlotCgZP * kMaxCh,
+                                                         scal + kSlotCgW * kMaxCh, scal + kSlotCgZ * kMaxCh);
+        launches += 2;
+        if ((rc = evaluate(tin))) return rc;
+        k_cgnr_direction<<<vgrid, kCgnrThreads, 0, stream>>>(arr(0), m0, tres, P, scal + kSlotTonalR * kMaxCh,
+                                                               scal + kSlotCgZ * kMaxCh, 0);
+        ++launches;
+    }
+    (void)rel_prev;
+    return cuda_check(cudaGetLastError(), "CGNR");
 }
