@@ -15,6 +15,9 @@ Modules
                independent projection formulation used as a cross-check.
   ras       -- restricted additive Schwarz for tonal optimisation (Alg. 2)
                with exact local solves, and the overlapping decomposition.
+  vi        -- Voronoi initialisation of tonal optimisation (Sec. 5.3):
+               influence-zone weights, the average-interpolation Richardson
+               iteration with its stop-on-rise rule.
   densify   -- one Delaunay densification step (Sec. 4, Alg. 1) with exact
                integer geometry, and the random-dithering initial mask.
   splitmix  -- SplitMix64 counter-based generator (Steele, Lea, Flood 2014).
