@@ -45,11 +45,11 @@ class Mask(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("vcycles", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("local_iters", ctypes.c_int64), ("rel_res", ctypes.c_double),
+                ("init_steps", ctypes.c_int32), ("local_iters", ctypes.c_int64), ("rel_res", ctypes.c_double),
                 ("mse", ctypes.c_double), ("seconds", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 SYMBOLS = ["hdi_create", "hdi_destroy", "hdi_set_param", "hdi_get_param", "hdi_inpaint",

@@ -17,6 +17,7 @@
 #include "solver.h"
 #include "tonal.cuh"
 #include "densify.cuh"
+#include "vi.cuh"
 
 // ----------------------------------------------------------------- params ---
 
@@ -35,12 +36,17 @@ const ParamDef kParams[] = {
     {"coarse_eta", &Params::coarse_eta, 1e-16, 1.0},
     {"coarse_max_local", &Params::coarse_max_local, 1, 4096},
     {"max_vcycles", &Params::max_vcycles, 1, 10000},
-    {"tonal_max_iter", &Params::tonal_max_iter, 1, 100000},
+    {"tonal_max_iter", &Params::tonal_max_iter, 0, 100000},
     {"tonal_inner_ratio", &Params::tonal_inner_ratio, 1e-6, 1.0},
     {"tonal_inner_max", &Params::tonal_inner_max, 1e-12, 0.5},
     {"tonal_anderson_beta", &Params::tonal_anderson_beta, 1e-3, 2.0},
     {"tonal_method", &Params::tonal_method, 0, 1},
     {"tonal_mse_gain", &Params::tonal_mse_gain, 0, 0.5},
+    {"tonal_init", &Params::tonal_init, 0, 1},
+    {"vi_max_iter", &Params::vi_max_iter, 0, 1000},
+    {"vi_tau", &Params::vi_tau, 1e-3, 2.0},
+    {"vi_weight", &Params::vi_weight, 0, 2},
+    {"vi_inner_tol", &Params::vi_inner_tol, 1e-12, 0.5},
     {"tonal_echo_rtol", &Params::tonal_echo_rtol, 1e-12, 1.0},
     {"tonal_echo_max_iter", &Params::tonal_echo_max_iter, 1, 4096},
     {"hbm_budget_gb", &Params::hbm_budget_gb, 0.001, 1e6},
@@ -113,7 +119,7 @@ void* Arena::take(size_t bytes) {
     return (char*)base + off;
 }
 
-size_t Ctx::other_bytes() const { return ws.cap + tws.cap + dws.cap + stage.cap; }
+size_t Ctx::other_bytes() const { return ws.cap + tws.cap + dws.cap + vws.cap + stage.cap; }
 
 // Device-time bookkeeping per kernel class (CUDA events on the context's
 // stream around each timed launch; resolved after the stream drains).
@@ -676,6 +682,7 @@ int hdi_destroy(hdi_ctx* h) {
     c->ws.release();
     c->tws.release();
     c->dws.release();
+    c->vws.release();
     c->stage.release();
     if (c->flags) cudaFree(c->flags);
     if (c->tev) {

@@ -33,6 +33,11 @@ struct Params {
     double tonal_anderson = 8;      // Anderson window on the RAS iteration (0 = plain Alg. 2)
     double tonal_method = 0;        // 0: RAS (Alg. 2), 1: CGNR (Sec. 5.1)
     double tonal_mse_gain = 0;      // > 0: also stop once an iteration improves the MSE by less (relative)
+    double tonal_init = 0;          // 0: g0 (or f on the mask); 1: Voronoi initialisation (Sec. 5.3) first
+    double vi_max_iter = 20;        // Richardson steps of the Voronoi initialisation
+    double vi_tau = 1.0;            // its step size
+    double vi_weight = 0;           // 0: Voronoi cell, inverse-log distance; 1: Voronoi cell, constant; 2: 3x3
+    double vi_inner_tol = 1e-3;     // relative residual of its inpaintings
 };
 
 struct Level {
@@ -86,6 +91,7 @@ constexpr int kSlotTonalE = 19;   // ||f - Bg||^2
 constexpr int kSlotCgW = 20;      // CGNR: ||B p||^2
 constexpr int kSlotCgZ = 21;      // CGNR: ||z||^2 of the previous iteration
 constexpr int kSlotCgZP = 22;     // CGNR: <z, p>
+constexpr int kSlotViE = 23;      // Voronoi initialisation: ||f - u||^2
 constexpr int kCntOnes = 0;
 constexpr int kCntLocal = 1;
 constexpr int kCntEcho = 2;
@@ -102,6 +108,7 @@ struct Ctx {
     Arena ws;      // multigrid + FP64 vectors
     Arena tws;     // tonal local factors
     Arena dws;     // densification
+    Arena vws;     // Voronoi initialisation
     Arena stage;   // host staging
     int H = 0, W = 0, nch = 0, nlev = 0;
     int nmask = 1;             // mask planes (1 = shared by all channels)
@@ -178,6 +185,8 @@ struct Ctx {
     int tonal_aa_step(int n, const float* fvfull, DF G);
     int tonal_cgnr(SolveSpec& sw, const double* btf2, double tol, int& it, double& rel_max, double& mse_last,
                    bool& by_gain);
+    int tonal_vi(int& steps, double& mse_best, DF* u_kept);
+    bool y_warm = false;       // tonal: Y0 holds B g of the initial g (from the Voronoi initialisation)
     int inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,
                 hdi_stats* st);
     int tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hdi_image* g, double tol,

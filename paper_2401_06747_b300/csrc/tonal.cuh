@@ -923,7 +923,8 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     vcycles_run = 0;
     cudaMemsetAsync(counters + kCntLocal, 0, 16, stream);
     const bool cgnr = p.tonal_method >= 0.5;
-    if (!cgnr && (rc = tonal_setup())) return rc;
+    const bool outer = p.tonal_max_iter >= 1;   // 0: only the initial values (e.g. the Voronoi initialisation)
+    if (!cgnr && outer && (rc = tonal_setup())) return rc;
 
     // the inner solves use their own local stop fraction (restored on exit)
     struct EtaSwap {
@@ -940,6 +941,17 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
             p.fine_post = kpost;
         }
     } eta_swap(p);
+    int vi_steps = 0;
+    double vi_mse = 0.0;
+    y_warm = false;
+    if (p.tonal_init >= 0.5) {
+        DF uk;
+        if ((rc = tonal_vi(vi_steps, vi_mse, &uk))) return rc;
+        if (uk.hi) {   // its inpainting warm-starts the first B g solve
+            cudaMemcpyAsync(dfv[kY0].hi, uk.hi, (size_t)nch * lev[0].cs * 8, cudaMemcpyDeviceToDevice, stream);
+            y_warm = true;
+        }
+    }
     const double ratio = p.tonal_inner_ratio;
     // ||B^T f||: w_f solves A w = (I - C) f.
     SolveSpec sw;
@@ -969,11 +981,14 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
         sy.cur = 0;
         sy.rhs = RHS_DATA;
         sy.d = cview(G);
-        sy.start = START_FMG;
+        sy.start = y_warm ? START_WARM : START_FMG;
         sy.max_iter = (int)p.max_vcycles;
         sw.start = START_WARM;
         double rel_prev = 1.0, mse_prev = 0.0;
         const int max_it = (int)p.tonal_max_iter;
+        // the MSE rule returns the best iterate seen (RAS is not monotone in the MSE)
+        const DF Gbest = dfv[kU0];
+        double mse_best = INFINITY, rel_best = 1.0;
         for (;; ++it) {
             const double tin = std::max(1e-13, std::min(p.tonal_inner_max, ratio * rel_prev));
             sy.tol = tin;
@@ -1004,7 +1019,17 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
             if (rel_max <= tol || it >= max_it) break;
             if (p.tonal_mse_gain > 0 && it > 0 && mse_prev - mse_last < p.tonal_mse_gain * mse_prev) {
                 by_gain = true;
+                if (mse_best < mse_last) {
+                    cudaMemcpyAsync(G.hi, Gbest.hi, (size_t)nch * lev[0].cs * 8, cudaMemcpyDeviceToDevice, stream);
+                    mse_last = mse_best;
+                    rel_max = rel_best;
+                }
                 break;
+            }
+            if (p.tonal_mse_gain > 0 && mse_last < mse_best) {
+                cudaMemcpyAsync(Gbest.hi, G.hi, (size_t)nch * lev[0].cs * 8, cudaMemcpyDeviceToDevice, stream);
+                mse_best = mse_last;
+                rel_best = rel_max;
             }
             rel_prev = rel_max;
             mse_prev = mse_last;
@@ -1022,10 +1047,13 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
         st->vcycles = vcycles_run;
         st->local_iters = (int64_t)li[0];
         st->rel_res = rel_max;
-        st->mse = mse_last;
+        // without outer iterations the initialisation's own MSE (inpaintings
+        // at vi_inner_tol) is the better figure than the first evaluation's
+        st->mse = (!outer && p.tonal_init >= 0.5) ? vi_mse : mse_last;
+        st->init_steps = vi_steps;
     }
     if ((rc = tflush())) return rc;
-    if (rel_max > tol && !by_gain)
+    if (rel_max > tol && !by_gain && outer)
         return fail(HDI_ERR_NOT_CONVERGED, "tonal: relative residual %.3e after %d %s iterations", rel_max, it,
                     cgnr ? "CGNR" : "RAS");
     return HDI_OK;
@@ -1054,7 +1082,7 @@ int Ctx::tonal_cgnr(SolveSpec& sw, const double* btf2, double tol, int& it, doub
     sy.cur = 0;
     sy.rhs = RHS_DATA;
     sy.d = cview(G);
-    sy.start = START_FMG;
+    sy.start = y_warm ? START_WARM : START_FMG;
     sy.max_iter = (int)p.max_vcycles;
     SolveSpec spw;  // w = B p
     spw.u[0] = dfv[kU0];
