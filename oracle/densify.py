@@ -98,6 +98,83 @@ def voronoi_labels(c: np.ndarray) -> np.ndarray:
     return out.reshape(H, W)
 
 
+def jfa_labels(c: np.ndarray, first_step: int | None = None) -> np.ndarray:
+    """Approximate Voronoi labels by jump flooding (Rong and Tan 2006; the
+    paper's speed mode, Sec. 4.2): every seed starts with its own label, and
+    for step k = first_step, first_step / 2, ..., 1 every pixel takes, among
+    its own label and the labels of the 8 pixels at offsets (+-k or 0,
+    +-k or 0), the site of least (d^2, linear index); each pass reads the
+    labels of the previous one. first_step defaults to half the smallest
+    power of two >= max(H, W) (the full schedule); a smaller first step
+    (a power of two at least the largest pixel-to-site distance) saves passes
+    once the mask is dense."""
+    cb = np.asarray(c, dtype=bool)
+    H, W = cb.shape
+    if not cb.any():
+        raise ValueError("empty mask has no Voronoi diagram")
+    N = H * W
+    idx = np.arange(N, dtype=np.int64)
+    lab = np.where(cb.ravel(), idx, -1)
+    py, px = np.divmod(idx, W)
+    if first_step is None:
+        n2 = 1
+        while n2 < max(H, W):
+            n2 *= 2
+        first_step = max(n2 // 2, 1)
+    k = int(first_step)
+    while k >= 1:
+        best_d2 = np.full(N, np.iinfo(np.int64).max)
+        best_s = np.full(N, -1, dtype=np.int64)
+        for dy in (-k, 0, k):
+            for dx in (-k, 0, k):
+                ny, nx = py + dy, px + dx
+                inside = (ny >= 0) & (ny < H) & (nx >= 0) & (nx < W)
+                s = np.full(N, -1, dtype=np.int64)
+                s[inside] = lab[ny[inside] * W + nx[inside]]
+                ok = s >= 0
+                sy, sx = np.divmod(np.where(ok, s, 0), W)
+                d2 = (px - sx) ** 2 + (py - sy) ** 2
+                better = ok & ((d2 < best_d2) | ((d2 == best_d2) & (s < best_s)))
+                best_d2 = np.where(better, d2, best_d2)
+                best_s = np.where(better, s, best_s)
+        lab = best_s
+        k //= 2
+    return lab.reshape(H, W)
+
+
+def label_max_dist2(V: np.ndarray) -> int:
+    """Largest squared distance from a pixel to the site of its label."""
+    H, W = V.shape
+    py, px = np.divmod(np.arange(H * W, dtype=np.int64), W)
+    sy, sx = np.divmod(V.ravel().astype(np.int64), W)
+    return int(((px - sx) ** 2 + (py - sy) ** 2).max())
+
+
+def jfa_first_step(max_dist2: int) -> int:
+    """Smallest power of two >= the distance bound sqrt(max_dist2) (>= 1)."""
+    k = 1
+    while k * k < max_dist2:
+        k *= 2
+    return k
+
+
+def densify_counts(total: int, n: int, t: float) -> list:
+    """Pixels to have after each of the n densification iterations (Sec. 4.2,
+    "Number of New Pixels per Iteration"): the count added in iteration i is
+    t times that of iteration i - 1, and the first count is chosen so that
+    the n iterations add `total` pixels. Cumulative targets are rounded
+    (floor(x + 0.5)) so that the last one is exactly `total`."""
+    out = []
+    for i in range(1, n + 1):
+        if t == 1.0:
+            frac = i / n
+        else:
+            frac = (t ** i - 1.0) / (t ** n - 1.0)
+        out.append(int(np.floor(total * frac + 0.5)))
+    out[-1] = int(total)
+    return out
+
+
 def _orient(ax, ay, bx, by, cx, cy):
     return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax)
 
@@ -215,8 +292,12 @@ def initial_mask(f: np.ndarray, k: int, seed: int) -> np.ndarray:
     return take.reshape(H, W).astype(np.uint8)
 
 
-def densify_step(f: np.ndarray, c: np.ndarray, u: np.ndarray | None, k: int, seed: int = 0):
-    """Returns (new mask uint8, number of pixels added)."""
+def densify_step(f: np.ndarray, c: np.ndarray, u: np.ndarray | None, k: int, seed: int = 0,
+                 voronoi: str = "exact", first_step: int | None = None, info: dict | None = None):
+    """Returns (new mask uint8, number of pixels added). voronoi = "jfa" uses
+    jump-flooding labels (first pass step `first_step`) instead of the exact
+    ones; `info`, if given, receives the labels' largest squared
+    pixel-to-site distance ("max_dist2")."""
     cb = np.asarray(c, dtype=bool)
     H, W = cb.shape
     if k < 0:
@@ -226,7 +307,9 @@ def densify_step(f: np.ndarray, c: np.ndarray, u: np.ndarray | None, k: int, see
         return m, int(m.sum())
     e = error_map(u, f)
     eq = quantise_error(e).ravel()
-    V = voronoi_labels(cb)
+    V = voronoi_labels(cb) if voronoi == "exact" else jfa_labels(cb, first_step)
+    if info is not None:
+        info["max_dist2"] = label_max_dist2(V)
     T, I = triangles(V)
     own = ownership(cb, V, T, I).ravel()
     free = own >= 0
@@ -245,3 +328,37 @@ def densify_step(f: np.ndarray, c: np.ndarray, u: np.ndarray | None, k: int, see
     new = cb.ravel().copy()
     new[best[rank]] = True
     return new.reshape(H, W).astype(np.uint8), int(rank.size)
+
+
+def densify(f: np.ndarray, n: int, t: float, density: float, seed: int, voronoi: str = "exact", solve=None):
+    """Delaunay densification from an empty mask (Sec. 4, Alg. 1 with the
+    image-adaptive initial mask and the growth factor t of Sec. 4.2): n
+    iterations, each a densification step to the cumulative target of
+    densify_counts(floor(density * N + 0.5), n, t) followed by an inpainting.
+    The first iteration draws the initial mask. With voronoi = "jfa" every
+    step after the first uses jump flooding whose first step comes from the
+    previous labels' largest distance (the mask only grows, so that bound
+    holds for the next mask); the first JFA step runs the full schedule.
+    `solve(f, c)` computes the inpainting (default: the exact one).
+    Returns (mask, u, history) with the mask size after every iteration."""
+    from .laplace import inpaint
+    solve = solve or inpaint
+    f3 = _as3(f)
+    H, W = f3.shape[1:]
+    total = int(np.floor(density * H * W + 0.5))
+    targets = densify_counts(total, n, t)
+    c = np.zeros((H, W), np.uint8)
+    u = None
+    first = None
+    sizes = []
+    for i in range(n):
+        k = max(targets[i] - int(c.sum()), 0)
+        info = {}
+        c, _ = densify_step(f3, c, u, k, seed, voronoi, first, info)
+        if voronoi == "jfa" and "max_dist2" in info:
+            first = jfa_first_step(info["max_dist2"])
+        u = solve(f3, c)
+        sizes.append(int(c.sum()))
+    if np.ndim(f) == 2:
+        u = u[0] if np.ndim(u) == 3 else u
+    return c, u, {"sizes": sizes, "targets": targets}

@@ -183,3 +183,77 @@ def test_laplace_weight_is_abs_of_laplacian():
     L = laplacian(17, 23)
     w = sum(np.abs(L @ f[ch].ravel()) for ch in range(3)).reshape(17, 23)
     np.testing.assert_allclose(laplace_weight(f), w, rtol=0, atol=1e-9)
+
+
+# ---- jump flooding, the growth schedule and the full loop (Sec. 4.2) -------
+
+from oracle.densify import jfa_labels, label_max_dist2, jfa_first_step, densify_counts, densify
+
+
+def _brute_labels(c):
+    H, W = c.shape
+    sy, sx = np.nonzero(c)
+    sites = sy * W + sx
+    py, px = np.divmod(np.arange(H * W), W)
+    d2 = (px[:, None] - sx[None]) ** 2 + (py[:, None] - sy[None]) ** 2
+    m = d2.min(axis=1)
+    lab = np.where(d2 == m[:, None], sites[None], 10 ** 9).min(axis=1)
+    return lab.reshape(H, W), m.reshape(H, W)
+
+
+def test_jfa_single_seed_is_exact():
+    c = np.zeros((37, 53), np.uint8)
+    c[20, 7] = 1
+    assert np.all(jfa_labels(c) == 20 * 53 + 7)
+
+
+@pytest.mark.parametrize("H,W,d,seed", [(48, 64, 0.01, 1), (61, 47, 0.04, 2), (33, 90, 0.1, 3)])
+def test_jfa_close_to_exact_and_never_closer(H, W, d, seed):
+    """JFA labels are seeds, are never nearer than the true nearest seed, and
+    agree with the exact diagram on nearly every pixel; the same holds with
+    the first step cut down to the distance bound."""
+    c = random_mask(H, W, d, seed)
+    lab_b, m = _brute_labels(c)
+    for first in (None, jfa_first_step(int(m.max()))):
+        V = jfa_labels(c, first)
+        assert np.all(c.ravel()[V.ravel()] == 1)
+        py, px = np.divmod(np.arange(H * W), W)
+        sy, sx = np.divmod(V.ravel(), W)
+        dj = ((px - sx) ** 2 + (py - sy) ** 2).reshape(H, W)
+        assert np.all(dj >= m)
+        assert (V == lab_b).mean() >= 0.99
+        assert label_max_dist2(V) >= m.max()
+
+
+def test_jfa_distance_bound_from_an_earlier_mask():
+    """The bound taken from a sparser mask's labels still covers a denser
+    superset: every pixel gets a label."""
+    c1 = random_mask(70, 90, 0.01, 4)
+    bound = jfa_first_step(label_max_dist2(jfa_labels(c1)))
+    c2 = np.maximum(c1, random_mask(70, 90, 0.02, 5))
+    V = jfa_labels(c2, bound)
+    assert V.min() >= 0
+    assert (V == voronoi_labels(c2)).mean() >= 0.99
+
+
+@pytest.mark.parametrize("total,n,t", [(1000, 8, 1.0), (41472 * 8, 8, 1.0), (5000, 20, 1.03), (777, 5, 0.9)])
+def test_densify_counts(total, n, t):
+    """Cumulative targets end at the total; the increments grow by t
+    (equal for t = 1) up to the rounding of the targets."""
+    c = densify_counts(total, n, t)
+    assert c[-1] == total and len(c) == n
+    k = np.diff([0] + c)
+    assert np.all(k >= 0)
+    k1 = total * (t - 1) / (t ** n - 1) if t != 1.0 else total / n
+    want = k1 * t ** np.arange(n)
+    assert np.all(np.abs(k - want) <= 1.0 + 1e-9)
+
+
+def test_densify_loop_reaches_the_density():
+    f = synth_rgb(40, 52, seeds=(1, 2, 3))
+    for vor in ("exact", "jfa"):
+        c, u, hist = densify(f, n=6, t=1.03, density=0.05, seed=7, voronoi=vor)
+        total = int(np.floor(0.05 * 40 * 52 + 0.5))
+        assert hist["sizes"][-1] == total == int(c.sum())
+        assert all(b >= a for a, b in zip(hist["sizes"], hist["sizes"][1:]))
+        np.testing.assert_allclose(u[:, c == 1], f[:, c == 1], atol=1e-9)
