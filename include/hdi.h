@@ -138,6 +138,26 @@ int hdi_tonal_opt(hdi_ctx* ctx, const hdi_image* f, const hdi_mask* mask,
 int hdi_densify_step(hdi_ctx* ctx, const hdi_image* f, hdi_mask* mask,
                      const hdi_image* u, int64_t k, uint64_t seed, int64_t* added);
 
+/* Densification from the given mask (normally empty) to `density` in n
+ * iterations (Sec. 4, Alg. 1 with the image-adaptive initial mask and the
+ * growth factor of Sec. 4.2): iteration i runs hdi_densify_step to the
+ * cumulative target floor(total * (t^i - 1) / (t^n - 1) + 0.5) (i / n for
+ * t = 1; total = floor(density * H * W + 0.5)) and then inpaints to
+ * densify_tol, warm-started from the previous inpainting. The paper's
+ * experiments use n = 20, t = 1, density 0.05. With densify_voronoi = 1 the
+ * Voronoi labels come from jump flooding whose first step after the first
+ * labelled mask is the power of two covering the previous labels' largest
+ * pixel-to-site distance (the mask only grows, so the bound holds).
+ *   f        : image (as hdi_inpaint)
+ *   mask     : in/out, the final mask
+ *   u   in/out: in: the inpainting of the given mask when it is not empty;
+ *                out: the inpainting of the final mask (same shape/dtype as f)
+ *   sizes out: may be NULL; n entries, the mask size after each iteration
+ * Errors: as hdi_densify_step and hdi_inpaint; NOT_CONVERGED inpaintings are
+ * accepted inside the loop. */
+int hdi_densify(hdi_ctx* ctx, const hdi_image* f, hdi_mask* mask, hdi_image* u, int32_t n, double t,
+                double density, uint64_t seed, int64_t* sizes);
+
 /* Number of kernels this context has launched since it was created. */
 int64_t hdi_launch_count(const hdi_ctx* ctx);
 
@@ -219,6 +239,11 @@ const char* hdi_version(void);
  *   vi_inner_tol      [1e-3]  relative residual of its inpaintings (1e-5 gives the same steps and
  *                             PSNR to 4 decimals at 4K, 1.5x slower)
  *   tonal_max_iter = 0 returns the initial values (with their residual and MSE) as a success.
+ *   densify_voronoi   [0]     hdi_densify_step / hdi_densify: 0 exact Voronoi labels, 1 jump flooding
+ *                             (Sec. 4.2; approximate, so masks differ from the exact mode)
+ *   jfa_first_step    [0]     first jump-flooding step of hdi_densify_step (0: half the padded side;
+ *                             a shortened schedule that misses pixels falls back to the full one)
+ *   densify_tol       [1e-6]  relative residual of the inpaintings inside hdi_densify
  *   tonal_anderson    [8]     Anderson window on the RAS iteration (0 = plain Alg. 2)
  *   tonal_oras_eta    [3e-2]  oras_eta used inside the tonal inner solves
  *   fine_pre, fine_post [1, 1] ORAS sweeps before / after the coarse correction on the finest level

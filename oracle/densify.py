@@ -307,7 +307,12 @@ def densify_step(f: np.ndarray, c: np.ndarray, u: np.ndarray | None, k: int, see
         return m, int(m.sum())
     e = error_map(u, f)
     eq = quantise_error(e).ravel()
-    V = voronoi_labels(cb) if voronoi == "exact" else jfa_labels(cb, first_step)
+    if voronoi == "exact":
+        V = voronoi_labels(cb)
+    else:
+        V = jfa_labels(cb, first_step)
+        if V.min() < 0:   # a shortened schedule that missed pixels: the full one
+            V = jfa_labels(cb, None)
     if info is not None:
         info["max_dist2"] = label_max_dist2(V)
     T, I = triangles(V)

@@ -53,7 +53,7 @@ class Stats(ctypes.Structure):
 
 
 SYMBOLS = ["hdi_create", "hdi_destroy", "hdi_set_param", "hdi_get_param", "hdi_inpaint",
-           "hdi_tonal_opt", "hdi_densify_step", "hdi_last_error", "hdi_version", "hdi_launch_count",
+           "hdi_tonal_opt", "hdi_densify_step", "hdi_densify", "hdi_last_error", "hdi_version", "hdi_launch_count",
            "hdi_timing", "hdi_timing_name", "hdi_inpaint_noalloc", "hdi_inpaint_batch"]
 TIMING_CLASSES = 8
 
@@ -78,6 +78,8 @@ def load(path: str | None = None):
     lib.hdi_tonal_opt.argtypes = [ctypes.c_void_p, P(Image), P(Mask), P(Image), P(Image), ctypes.c_double, P(Stats)]
     lib.hdi_densify_step.argtypes = [ctypes.c_void_p, P(Image), P(Mask), P(Image), ctypes.c_int64,
                                      ctypes.c_uint64, P(ctypes.c_int64)]
+    lib.hdi_densify.argtypes = [ctypes.c_void_p, P(Image), P(Mask), P(Image), ctypes.c_int32, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_uint64, P(ctypes.c_int64)]
     lib.hdi_last_error.argtypes = [ctypes.c_void_p]
     lib.hdi_last_error.restype = ctypes.c_char_p
     lib.hdi_version.restype = ctypes.c_char_p
@@ -214,6 +216,16 @@ class Context:
                                        ctypes.c_uint64(seed), ctypes.byref(added))
         self._check(rc)
         return added.value
+
+    def densify(self, f, mask, u, n: int = 20, t: float = 1.0, density: float = 0.05, seed: int = 0) -> list:
+        """Densification loop into `mask` (in/out) and its inpainting into `u`;
+        returns the mask size after every iteration."""
+        fi, mi, ui = image_of(f), mask_of(mask), image_of(u)
+        sizes = (ctypes.c_int64 * n)()
+        rc = self.lib.hdi_densify(self.h, ctypes.byref(fi), ctypes.byref(mi), ctypes.byref(ui), int(n), float(t),
+                                  float(density), ctypes.c_uint64(seed), sizes)
+        self._check(rc)
+        return list(sizes)
 
 
     def launch_count(self) -> int:

@@ -156,6 +156,64 @@ __global__ void k_vor_rows(const int* __restrict__ ys, int H, int W, int* __rest
     V[(size_t)y * W + x] = (int)bs;
 }
 
+// Jump flooding (Rong and Tan 2006), the paper's approximate Voronoi diagram
+// (Sec. 4.2): seeds label themselves; each pass with step k gives every pixel
+// the site of least (d^2, linear index) among its own label and those of the
+// 8 pixels at offsets (+-k or 0, +-k or 0) in the previous pass.
+__global__ void k_jfa_init(MaskView m, int* __restrict__ lab) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= m.W) return;
+    const size_t p = (size_t)y * m.W + x;
+    lab[p] = m.known(x, y) ? (int)p : -1;
+}
+
+__global__ void k_jfa_pass(const int* __restrict__ in, int* __restrict__ out, int H, int W, int k) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W) return;
+    long long bd = LLONG_MAX;
+    int bs = -1;
+    for (int dy = -k; dy <= k; dy += k) {
+        const int ny = y + dy;
+        if (ny < 0 || ny >= H) continue;
+        for (int dx = -k; dx <= k; dx += k) {
+            const int nx = x + dx;
+            if (nx < 0 || nx >= W) continue;
+            const int s = in[(size_t)ny * W + nx];
+            if (s < 0) continue;
+            const int sy = s / W, sx = s - sy * W;
+            const long long d2 = (long long)(x - sx) * (x - sx) + (long long)(y - sy) * (y - sy);
+            if (d2 < bd || (d2 == bd && s < bs)) { bd = d2; bs = s; }
+        }
+    }
+    out[(size_t)y * W + x] = bs;
+}
+
+// Largest squared pixel-to-site distance of a label map (the bound that lets
+// the next, denser mask start jump flooding with a smaller step); all ones if
+// a pixel has no label.
+__global__ void k_label_maxd2(const int* __restrict__ V, int H, int W, unsigned long long* maxd2) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    unsigned long long d2 = 0;
+    if (x < W) {
+        const int s = V[(size_t)y * W + x];
+        if (s < 0) {
+            d2 = ~0ull;   // unlabelled pixel
+        } else {
+            const int sy = s / W, sx = s - sy * W;
+            d2 = (unsigned long long)((long long)(x - sx) * (x - sx) + (long long)(y - sy) * (y - sy));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(HDI_FULL, d2, o);
+        d2 = v > d2 ? v : d2;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(maxd2, d2);
+}
+
 // ------------------------------------------------------------ triangles ---
 
 struct Tri {
@@ -407,7 +465,7 @@ int Ctx::densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t
     img.W = W;
     img.nch = nch;
     dim3 grow((W + 127) / 128, H);
-    unsigned long long hcnt[4] = {0, 0, 0, 0};
+    unsigned long long hcnt[5] = {0, 0, 0, 0, 0};
     if (ones == 0) {
         long long* wq = eq;   // reuse
         k_dens_lapw<<<grow, 128, 0, stream>>>(img, wq, cnt + 1);
@@ -417,15 +475,54 @@ int Ctx::densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t
         if ((rc = dens_load(u, Uu, hst))) return rc;
         const MaskView mv = mview(0);
         k_dens_error<<<grow, 128, 0, stream>>>(img, e, eq);
-        k_vor_columns<<<(W + 127) / 128, 128, 0, stream>>>(mv, ys);
-        k_vor_rows<<<grow, 128, 0, stream>>>(ys, H, W, V);
+        if (p.densify_voronoi >= 0.5) {
+            // jump flooding from the first step, ping-pong between ys and V so
+            // that the last pass lands in V
+            int full = 1;
+            while (full < std::max(H, W)) full *= 2;
+            full = std::max(full / 2, 1);
+            int first = (int)p.jfa_first_step;
+            if (first < 1 || first > full) first = full;
+            for (;;) {
+                int passes = 0;
+                for (int k2 = first; k2 >= 1; k2 /= 2) ++passes;
+                int* a0 = (passes & 1) ? ys : V;
+                int* a1 = (passes & 1) ? V : ys;
+                k_jfa_init<<<grow, 128, 0, stream>>>(mv, a0);
+                ++launches;
+                for (int k2 = first; k2 >= 1; k2 /= 2) {
+                    k_jfa_pass<<<grow, 128, 0, stream>>>(a0, a1, H, W, k2);
+                    ++launches;
+                    std::swap(a0, a1);
+                }
+                if (first == full) break;
+                // a shortened schedule must still reach every pixel; if it
+                // did not, run the full one
+                cudaMemsetAsync(cnt + 4, 0, 8, stream);
+                k_label_maxd2<<<grow, 128, 0, stream>>>(V, H, W, cnt + 4);
+                ++launches;
+                unsigned long long md = 0;
+                cudaMemcpyAsync(&md, cnt + 4, 8, cudaMemcpyDeviceToHost, stream);
+                if ((rc = sync("jump flooding"))) return rc;
+                if (md != ~0ull) break;
+                first = full;
+            }
+        } else {
+            k_vor_columns<<<(W + 127) / 128, 128, 0, stream>>>(mv, ys);
+            k_vor_rows<<<grow, 128, 0, stream>>>(ys, H, W, V);
+            launches += 2;
+        }
+        cudaMemsetAsync(cnt + 4, 0, 8, stream);
+        k_label_maxd2<<<grow, 128, 0, stream>>>(V, H, W, cnt + 4);
+        ++launches;
         unsigned* tcount = (unsigned*)(cnt + 2);
         unsigned* ncand = (unsigned*)(cnt + 3);
         k_dens_quads<<<dim3((W + 127) / 128, H), 128, 0, stream>>>(V, H, W, tris, tcount, (unsigned)tcap);
         cudaMemsetAsync(owner, 0x7F, N * 4, stream);
-        launches += 4;
-        cudaMemcpyAsync(hcnt, cnt, 32, cudaMemcpyDeviceToHost, stream);
+        launches += 2;   // k_dens_error, k_dens_quads
+        cudaMemcpyAsync(hcnt, cnt, 40, cudaMemcpyDeviceToHost, stream);
         if ((rc = sync("densification triangles"))) return rc;
+        last_label_maxd2 = (long long)hcnt[4];
         const unsigned ntri = (unsigned)(hcnt[2] & 0xffffffffull);
         if (ntri > tcap) return fail(HDI_ERR_CUDA, "internal: triangle list overflow");
         if (ntri) {

@@ -47,6 +47,9 @@ const ParamDef kParams[] = {
     {"vi_tau", &Params::vi_tau, 1e-3, 2.0},
     {"vi_weight", &Params::vi_weight, 0, 2},
     {"vi_inner_tol", &Params::vi_inner_tol, 1e-12, 0.5},
+    {"densify_voronoi", &Params::densify_voronoi, 0, 1},
+    {"jfa_first_step", &Params::jfa_first_step, 0, 1 << 30},
+    {"densify_tol", &Params::densify_tol, 1e-12, 0.5},
     {"tonal_echo_rtol", &Params::tonal_echo_rtol, 1e-12, 1.0},
     {"tonal_echo_max_iter", &Params::tonal_echo_max_iter, 1, 4096},
     {"hbm_budget_gb", &Params::hbm_budget_gb, 0.001, 1e6},
@@ -793,7 +796,74 @@ int hdi_densify_step(hdi_ctx* h, const hdi_image* f, hdi_mask* mask, const hdi_i
     return c->densify(f, mask, u, k, seed, added);
 }
 
+int hdi_densify(hdi_ctx* h, const hdi_image* f, hdi_mask* mask, hdi_image* u, int32_t n, double t, double density,
+                uint64_t seed, int64_t* sizes) {
+    if (!h) return HDI_ERR_INVALID_ARG;
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    c->err.clear();
+    return c->densify_run(f, mask, u, n, t, density, seed, sizes);
+}
+
 }  // extern "C"
+
+// ------------------------------------------------------- densification ---
+
+// Cumulative mask sizes after each of n iterations whose additions grow by the
+// factor t and sum to `total` (Sec. 4.2): floor(total * (t^i - 1) / (t^n - 1)
+// + 0.5), i / n for t = 1; the last target is total itself.
+static void densify_targets(long long total, int n, double t, std::vector<long long>& out) {
+    out.resize(n);
+    for (int i = 1; i <= n; ++i) {
+        const double frac = (t == 1.0) ? (double)i / n : (std::pow(t, i) - 1.0) / (std::pow(t, n) - 1.0);
+        out[i - 1] = (long long)std::floor((double)total * frac + 0.5);
+    }
+    out[n - 1] = total;
+}
+
+// The densification loop (Sec. 4, Alg. 1 with the initial mask and growth
+// factor of Sec. 4.2): n iterations, each a densification step to the next
+// cumulative target followed by an inpainting warm-started from the previous
+// one. With jump flooding, every step after the first starts at the power of
+// two covering the previous labels' largest pixel-to-site distance.
+int Ctx::densify_run(const hdi_image* f, hdi_mask* mask, hdi_image* u, int n, double t, double density,
+                     uint64_t seed, int64_t* sizes) {
+    int rc;
+    if (!f || !mask || !u) return fail(HDI_ERR_INVALID_ARG, "densify: f, mask and u are required");
+    if (n < 1) return fail(HDI_ERR_INVALID_ARG, "densify: n must be >= 1");
+    if (!(t > 0.0) || !std::isfinite(t)) return fail(HDI_ERR_INVALID_ARG, "densify: t must be positive");
+    if (!(density > 0.0 && density <= 1.0)) return fail(HDI_ERR_INVALID_ARG, "densify: density must lie in (0, 1]");
+    if ((rc = check_image(f, "f", -1, 0, 0))) return rc;
+    if ((rc = check_image(u, "u", f->height, f->width, f->channels))) return rc;
+    const long long total = (long long)std::floor(density * (double)f->height * f->width + 0.5);
+    std::vector<long long> target;
+    densify_targets(total, n, t, target);
+    if ((rc = setup(f->height, f->width, f->channels))) return rc;
+    long long ones = 0;
+    if ((rc = load_mask(mask, &ones))) return rc;
+    const bool jfa = p.densify_voronoi >= 0.5;
+    const double keep_first = p.jfa_first_step;
+    int first = 0;   // full schedule until a label map has given a bound
+    for (int i = 0; i < n; ++i) {
+        const long long k = std::max(target[i] - ones, 0LL);
+        int64_t added = 0;
+        if (jfa) p.jfa_first_step = first;
+        rc = densify(f, mask, ones > 0 ? u : nullptr, k, seed, &added);
+        p.jfa_first_step = keep_first;
+        if (rc) return rc;
+        if (jfa && ones > 0) {
+            int b = 1;
+            while ((long long)b * b < last_label_maxd2) b *= 2;
+            first = b;
+        }
+        ones += added;
+        if (ones == 0) return fail(HDI_ERR_EMPTY_MASK, "densify: the initial mask came out empty");
+        hdi_stats st;
+        rc = inpaint(f, mask, ones > added ? u : nullptr, u, p.densify_tol, &st);
+        if (rc != HDI_OK && rc != HDI_ERR_NOT_CONVERGED) return rc;
+        if (sizes) sizes[i] = ones;
+    }
+    return HDI_OK;
+}
 
 // ------------------------------------------------------------ batch ---
 

@@ -38,6 +38,9 @@ struct Params {
     double vi_tau = 1.0;            // its step size
     double vi_weight = 0;           // 0: Voronoi cell, inverse-log distance; 1: Voronoi cell, constant; 2: 3x3
     double vi_inner_tol = 1e-3;     // relative residual of its inpaintings
+    double densify_voronoi = 0;     // 0: exact Voronoi labels; 1: jump flooding (Sec. 4.2)
+    double jfa_first_step = 0;      // first jump-flooding step (0: half the padded image side)
+    double densify_tol = 1e-6;      // relative residual of the inpaintings of hdi_densify
 };
 
 struct Level {
@@ -186,11 +189,14 @@ struct Ctx {
     int tonal_cgnr(SolveSpec& sw, const double* btf2, double tol, int& it, double& rel_max, double& mse_last,
                    bool& by_gain);
     int tonal_vi(int& steps, double& mse_best, DF* u_kept);
-    bool y_warm = false;       // tonal: Y0 holds B g of the initial g (from the Voronoi initialisation)
+    bool y_warm = false;
+    long long last_label_maxd2 = 0;   // densification: largest squared pixel-to-site distance of the last labels       // tonal: Y0 holds B g of the initial g (from the Voronoi initialisation)
     int inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,
                 hdi_stats* st);
     int tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hdi_image* g, double tol,
               hdi_stats* st);
     int dens_load(const hdi_image* im, double* dst, void* hstage);
     int densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t k, uint64_t seed, int64_t* added);
+    int densify_run(const hdi_image* f, hdi_mask* mask, hdi_image* u, int n, double t, double density, uint64_t seed,
+                    int64_t* sizes);
 };

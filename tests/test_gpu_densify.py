@@ -97,3 +97,64 @@ def test_densify_loop_matches_oracle_loop():
         np.testing.assert_array_equal(cg.cpu().numpy(), co, err_msg=f"step {s}")
         kx.inpaint(fd, cg, ug, tol=1e-12)
         uo = inpaint_ref(f, co)
+
+
+# ---- jump flooding and the full densification loop (Sec. 4.2) -------------
+
+from oracle.densify import densify as densify_loop_ref, densify_counts, jfa_first_step, label_max_dist2, jfa_labels
+
+
+@pytest.mark.parametrize("H,W,d,k", [(77, 131, 0.02, 40), (150, 200, 0.05, 300), (64, 33, 0.1, 20)])
+def test_jfa_step_bit_exact(H, W, d, k):
+    """A densification step on jump-flooding labels (full schedule, and the
+    schedule shortened to the bound of a sparser mask's labels)."""
+    need_gpu()
+    f = synth_rgb(H, W, seeds=(4, 5, 6)).astype(np.float64)
+    c = random_mask(H, W, d, 7)
+    u = inpaint_ref(f, c)
+    sparse = random_mask(H, W, d / 2, 7) & c
+    sparse[0, 0] = 1
+    bound = jfa_first_step(label_max_dist2(jfa_labels(sparse)))
+    for first in (0, bound):
+        want, added_ref = densify_ref(f, c, u, k, 0, voronoi="jfa", first_step=first or None)
+        kx = ctx(densify_voronoi=1, jfa_first_step=first)
+        md = dev(c.copy())
+        added = kx.densify_step(dev(f), md, dev(u), k, 0)
+        assert added == added_ref
+        np.testing.assert_array_equal(md.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("voronoi", [0, 1])
+def test_densify_loop_bit_exact(voronoi):
+    """hdi_densify against the oracle loop (each side inpaints with its own
+    solver, tight tolerance): the same mask after the same schedule."""
+    need_gpu()
+    H, W = 120, 160
+    f = synth_rgb(H, W, seeds=(8, 9, 10)).astype(np.float64)
+    n, t, d = 6, 1.03, 0.05
+    want, _, hist = densify_loop_ref(f, n, t, d, 300, "jfa" if voronoi else "exact")
+    kx = ctx(densify_voronoi=voronoi, densify_tol=1e-12)
+    m = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
+    u = torch.empty_like(dev(f))
+    sizes = kx.densify(dev(f), m, u, n, t, d, 300)
+    assert sizes == hist["sizes"]
+    assert sizes[-1] == densify_counts(int(np.floor(d * H * W + 0.5)), n, t)[-1]
+    np.testing.assert_array_equal(m.cpu().numpy(), want)
+    np.testing.assert_allclose(u.cpu().numpy(), inpaint_ref(f, want), atol=1e-6)
+
+
+def test_jfa_loop_quality_matches_exact():
+    """The paper's setting (20 iterations to 5%, t = 1): jump flooding costs
+    at most a few hundredths of a dB against exact labels."""
+    need_gpu()
+    H, W = 240, 320
+    f = synth_rgb(H, W, seeds=(11, 12, 13), dtype=np.float32)
+    psnr = {}
+    for vor in (0, 1):
+        kx = ctx(densify_voronoi=vor)
+        m = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
+        u = torch.empty_like(dev(f))
+        kx.densify(dev(f), m, u, 20, 1.0, 0.05, 300)
+        err = float(((u.cpu().numpy().astype(np.float64) - f) ** 2).mean())
+        psnr[vor] = 10 * np.log10(255.0 ** 2 / err)
+    assert abs(psnr[1] - psnr[0]) <= 0.05
