@@ -122,7 +122,7 @@ void* Arena::take(size_t bytes) {
     return (char*)base + off;
 }
 
-size_t Ctx::other_bytes() const { return ws.cap + tws.cap + dws.cap + vws.cap + stage.cap; }
+size_t Ctx::other_bytes() const { return ws.cap + tws.cap + dws.cap + vws.cap + lws.cap + stage.cap; }
 
 // Device-time bookkeeping per kernel class (CUDA events on the context's
 // stream around each timed launch; resolved after the stream drains).
@@ -686,6 +686,7 @@ int hdi_destroy(hdi_ctx* h) {
     c->tws.release();
     c->dws.release();
     c->vws.release();
+    c->lws.release();
     c->stage.release();
     if (c->flags) cudaFree(c->flags);
     if (c->tev) {

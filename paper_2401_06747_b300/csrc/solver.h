@@ -112,6 +112,7 @@ struct Ctx {
     Arena tws;     // tonal local factors
     Arena dws;     // densification
     Arena vws;     // Voronoi initialisation
+    Arena lws;     // list of mask pixels (tonal optimisation)
     Arena stage;   // host staging
     int H = 0, W = 0, nch = 0, nlev = 0;
     int nmask = 1;             // mask planes (1 = shared by all channels)
@@ -189,6 +190,9 @@ struct Ctx {
     int tonal_cgnr(SolveSpec& sw, const double* btf2, double tol, int& it, double& rel_max, double& mse_last,
                    bool& by_gain);
     int tonal_vi(int& steps, double& mse_best, DF* u_kept);
+    int mask_list();
+    int* mlist = nullptr;      // level-0 mask pixels, raster order (offsets y * pitch + x)
+    int mlist_n = 0;
     bool y_warm = false;
     long long last_label_maxd2 = 0;   // densification: largest squared pixel-to-site distance of the last labels       // tonal: Y0 holds B g of the initial g (from the Voronoi initialisation)
     int inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, hdi_image* u, double tol,

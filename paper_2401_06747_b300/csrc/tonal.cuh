@@ -413,95 +413,41 @@ __global__ void __launch_bounds__(256) k_tonal_gram_big(const int* __restrict__ 
 
 // ------------------------------------------------------- outer iteration ---
 
-// r_K = (f - y)_K + sum of w over the unknown 4-neighbours (B^T (f - y)),
-// stored in FP32 for the local solves, and per channel ||r||^2 and
-// ||f - y||^2 (the tonal MSE numerator). y.hi == nullptr means y = 0 (B^T f).
-// The sums on mask pixels (a few percent of the image) are formed in
-// double-float arithmetic (the FP64 rate of the target is a small fraction of
-// its FP32 rate).
-__global__ void __launch_bounds__(128) k_tonal_residual(LevelArr F, MaskView m, DFc f, DFc y, DFc w,
-                                                        float* __restrict__ r, GridReduce red_r, GridReduce red_e,
-                                                        int rows) {
-    constexpr int RC = 4;   // rows per load chunk (see the column-strip kernels)
-    const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
-    const int px = x0 + lane;
-    const int y0 = blockIdx.y * rows;
-    const int y1 = min(y0 + rows, F.H);
-    const int ch = blockIdx.z;
-    const int H = F.H;
-    const bool act = px < F.W;
-    const int pxc = act ? px : F.W - 1;
+// B^T (f - y) on the mask pixels, from the list of mask pixels (raster order,
+// level-0 offsets y * pitch + x): r_K = (f - y)_K + sum of w over the unknown
+// in-image 4-neighbours (Sec. 5.1), in double-float, written to r at the
+// pixel; per channel ||r_K||^2 into red_r and ||(f - y)_K||^2 into red_e (the
+// unknown pixels' part of ||f - y||^2 is the right-hand-side norm of the
+// adjoint solve). y == nullptr means y = 0. One pass over the list per
+// channel (grid y), a thread per mask pixel.
+__global__ void __launch_bounds__(256) k_tonal_residual(LevelArr F, MaskView m, DFc f, DFc y, DFc w,
+                                                        const int* __restrict__ list, int M, float* __restrict__ r,
+                                                        GridReduce red_r, GridReduce red_e) {
+    const int ch = blockIdx.y;
+    const size_t co = (size_t)ch * F.cs;
     float se = 0.f, sr = 0.f;
-    if (x0 < F.W) {
-        const uint32_t* mrow = m.bits + (x0 >> 5);
-        const StripHalo hl = strip_halo(lane, px, pxc, F.W);
-        const uint32_t* hrow = m.bits + (hl.col >> 5);
-        const int hbit = hl.col & 31;
-        const bool hasl = px > 0, hasr = px + 1 < F.W;
-        const size_t co = ch * F.cs;
-        uint32_t wu = (y0 > 0) ? mrow[(size_t)(y0 - 1) * m.wpitch] : 0u;
-        for (int yb = y0; yb < y1; yb += RC) {
-            uint32_t Mw[RC + 1], Hm[RC];
-            float Fh[RC], Fl[RC], Yh[RC], Yl[RC];
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < M; i += gridDim.x * 256) {
+        const int p = list[i];
+        const int py = p / F.pitch, px = p - py * F.pitch;
+        const size_t at = co + p;
+        float sh = f.hi[at], sl = f.lo[at];
+        if (y.hi) df_add(sh, sl, -y.hi[at], -y.lo[at], sh, sl);
+        se += (sh + sl) * (sh + sl);
+        float ah = sh, al = sl;
+        const bool nb[4] = {px > 0 && !m.known(px - 1, py), px + 1 < F.W && !m.known(px + 1, py),
+                            py > 0 && !m.known(px, py - 1), py + 1 < F.H && !m.known(px, py + 1)};
+        const long long off[4] = {-1, 1, -(long long)F.pitch, (long long)F.pitch};
 #pragma unroll
-            for (int k = 0; k <= RC; ++k) Mw[k] = (yb + k < H) ? mrow[(size_t)(yb + k) * m.wpitch] : 0u;
-#pragma unroll
-            for (int k = 0; k < RC; ++k) {
-                const size_t idx = co + (size_t)min(yb + k, H - 1) * F.pitch + pxc;
-                Hm[k] = hl.on ? hrow[(size_t)min(yb + k, H - 1) * m.wpitch] : 0u;
-                Fh[k] = f.hi[idx];
-                Fl[k] = f.lo[idx];
-                Yh[k] = y.hi ? y.hi[idx] : 0.f;
-                Yl[k] = y.hi ? y.lo[idx] : 0.f;
-            }
-            // mask pixels: w on the unknown 4-neighbours, read once the mask words are in
-            float Wh[RC][4], Wl[RC][4];
-#pragma unroll
-            for (int k = 0; k < RC; ++k) {
-                const int yy = min(yb + k, H - 1);
-                const uint32_t wc = Mw[k], wup = (k == 0) ? wu : Mw[k - 1], wdn = Mw[k + 1];
-                const bool mk = act && ((wc >> lane) & 1u);
-                const bool kl = (lane > 0) ? ((wc >> (lane - 1)) & 1u) : ((Hm[k] >> hbit) & 1u);
-                const bool kr = (lane < 31) ? ((wc >> (lane + 1)) & 1u) : ((Hm[k] >> hbit) & 1u);
-                const bool nb[4] = {mk && hasl && !kl, mk && hasr && !kr, mk && yy > 0 && !((wup >> lane) & 1u),
-                                    mk && yy + 1 < H && !((wdn >> lane) & 1u)};
-                const size_t idx = co + (size_t)yy * F.pitch + pxc;
-                const size_t nidx[4] = {idx - 1, idx + 1, idx - F.pitch, idx + F.pitch};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    Wh[k][q] = nb[q] ? w.hi[nidx[q]] : 0.f;
-                    Wl[k][q] = nb[q] ? w.lo[nidx[q]] : 0.f;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < RC; ++k) {
-                const int yy = yb + k;
-                if (yy >= y1) break;
-                if (act) {
-                    float sh, sl;
-                    if (y.hi) df_add(Fh[k], Fl[k], -Yh[k], -Yl[k], sh, sl);
-                    else { sh = Fh[k]; sl = Fl[k]; }
-                    se += sh * sh;
-                    if ((Mw[k] >> lane) & 1u) {
-                        // B^T (f - y) on a mask pixel: s_K plus w on its unknown neighbours,
-                        // summed in double-float (terms of absent neighbours are zero)
-                        float ah = sh, al = sl;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) df_add(ah, al, Wh[k][q], Wl[k][q], ah, al);
-                        const float rv = ah + al;
-                        r[co + (size_t)yy * F.pitch + px] = rv;
-                        sr += rv * rv;
-                    }
-                }
-            }
-            wu = Mw[RC - 1];
-        }
+        for (int q = 0; q < 4; ++q)
+            if (nb[q]) df_add(ah, al, w.hi[at + off[q]], w.lo[at + off[q]], ah, al);
+        const float rv = ah + al;
+        r[at] = rv;
+        sr += rv * rv;
     }
     const double tr = (double)block_sum_f(sr);
-    grid_reduce_commit(red_r, ch, blockIdx.y * gridDim.x + blockIdx.x, tr);
+    grid_reduce_commit(red_r, ch, blockIdx.x, tr);
     const double te = (double)block_sum_f(se);
-    grid_reduce_commit(red_e, ch, blockIdx.y * gridDim.x + blockIdx.x, te);
+    grid_reduce_commit(red_e, ch, blockIdx.x, te);
 }
 
 struct LocalSolveArgs {
@@ -650,22 +596,11 @@ int Ctx::tonal_setup() {
         maxm = std::max(maxm, cnt[i]);
     }
     const long long total = off[nb];
-    // compact list of mask pixels (row counts on the device, scan on the host)
-    std::vector<int> rc_h(H), rowoff(H + 1);
-    int* drc = dcnt;
-    k_row_counts<<<(H + 3) / 4, 128, 0, stream>>>(mview(0), drc);
-    ++launches;
-    cudaMemcpyAsync(rc_h.data(), drc, (size_t)H * 4, cudaMemcpyDeviceToHost, stream);
-    if ((rc = sync("mask row counts"))) return rc;
-    rowoff[0] = 0;
-    for (int y = 0; y < H; ++y) rowoff[y + 1] = rowoff[y] + rc_h[y];
-    const int M = rowoff[H];
+    const int M = mlist_n;   // the mask list (built by the caller)
     const int mwin = (int)p.tonal_anderson;
     // layout
     size_t bytes = 0;
     auto acc = [&](size_t b) { bytes += (b + 255) & ~(size_t)255; };
-    acc((size_t)(H + 1) * 4);
-    acc((size_t)M * 4);
     acc((size_t)nch * M * 4);
     acc((size_t)nch * M * 4);
     acc((size_t)std::max(mwin, 1) * nch * M * 4);
@@ -687,8 +622,7 @@ int Ctx::tonal_setup() {
     int* t_owner = (int*)tws.take((size_t)total * 4);
     t_echo = (float*)tws.take((size_t)total * 1024 * 4);
     t_fac = (float*)tws.take((size_t)goff[nb] * 4);
-    int* drowoff = (int*)tws.take((size_t)(H + 1) * 4);
-    aa_idx = (int*)tws.take((size_t)M * 4);
+    aa_idx = mlist;
     aa_fv = (float*)tws.take((size_t)nch * M * 4);
     aa_fvprev = (float*)tws.take((size_t)nch * M * 4);
     aa_dF = (float*)tws.take((size_t)std::max(mwin, 1) * nch * M * 4);
@@ -700,9 +634,6 @@ int Ctx::tonal_setup() {
     if (tws.used > tws.cap) return fail(HDI_ERR_CUDA, "internal: tonal workspace carving exceeds its reservation");
     cudaMemsetAsync(aa_ticket, 0, 256, stream);
     aa_M = M;
-    cudaMemcpyAsync(drowoff, rowoff.data(), (size_t)(H + 1) * 4, cudaMemcpyHostToDevice, stream);
-    k_compact_fill<<<(H + 3) / 4, 128, 0, stream>>>(mview(0), lev[0].P, drowoff, aa_idx);
-    ++launches;
     cudaMemcpyAsync(t_off, off.data(), (size_t)(nb + 1) * 4, cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(t_goff, goff.data(), (size_t)(nb + 1) * 8, cudaMemcpyHostToDevice, stream);
     k_tonal_list<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), L0.nbx, L0.nby, stride, t_off, t_list, t_owner);
@@ -748,12 +679,36 @@ int Ctx::tonal_setup() {
 }
 
 void Ctx::tonal_residual(DFc y, DFc w) {
-    const int rows = strip_rows(H, W, nch);
-    dim3 blk(128), grd((W + 127) / 128, (H + rows - 1) / rows, nch);
-    k_tonal_residual<<<grd, blk, 0, stream>>>(arr(0), mview(0), cview(dfv[kF]), y, w, tres,
-                                              reducer(kSlotTonalR, grd.x * grd.y), reducer(kSlotTonalE, grd.x * grd.y),
-                                              rows);
+    const int parts = std::max(1, std::min(maxparts_, (mlist_n + 255) / 256));
+    k_tonal_residual<<<dim3(parts, nch), 256, 0, stream>>>(arr(0), mview(0), cview(dfv[kF]), y, w, mlist, mlist_n,
+                                                          tres, reducer(kSlotTonalR, parts),
+                                                          reducer(kSlotTonalE, parts));
     ++launches;
+}
+
+// Raster-order list of the level-0 mask pixels (offsets y * pitch + x): the
+// index set of the tonal residual, the Anderson vectors and the mask values.
+int Ctx::mask_list() {
+    int rc;
+    std::vector<int> rc_h(H), rowoff(H + 1);
+    if ((rc = lws.reserve(*this, std::max(lws.cap, (size_t)(H + 1) * 8 + 512), "mask list counts"))) return rc;
+    int* drc = (int*)lws.take((size_t)(H + 1) * 4);
+    k_row_counts<<<(H + 3) / 4, 128, 0, stream>>>(mview(0), drc);
+    ++launches;
+    cudaMemcpyAsync(rc_h.data(), drc, (size_t)H * 4, cudaMemcpyDeviceToHost, stream);
+    if ((rc = sync("mask row counts"))) return rc;
+    rowoff[0] = 0;
+    for (int yy = 0; yy < H; ++yy) rowoff[yy + 1] = rowoff[yy] + rc_h[yy];
+    const int M = rowoff[H];
+    const size_t bytes = ((size_t)(H + 1) * 4 + 255) / 256 * 256 + ((size_t)std::max(M, 1) * 4 + 255) / 256 * 256;
+    if ((rc = lws.reserve(*this, std::max(lws.cap, bytes), "mask list"))) return rc;
+    int* drowoff = (int*)lws.take((size_t)(H + 1) * 4);
+    mlist = (int*)lws.take((size_t)std::max(M, 1) * 4);
+    mlist_n = M;
+    cudaMemcpyAsync(drowoff, rowoff.data(), (size_t)(H + 1) * 4, cudaMemcpyHostToDevice, stream);
+    k_compact_fill<<<(H + 3) / 4, 128, 0, stream>>>(mview(0), lev[0].P, drowoff, mlist);
+    ++launches;
+    return cuda_check(cudaGetLastError(), "mask list");
 }
 
 void Ctx::tonal_local(float* out) {
@@ -924,6 +879,7 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     cudaMemsetAsync(counters + kCntLocal, 0, 16, stream);
     const bool cgnr = p.tonal_method >= 0.5;
     const bool outer = p.tonal_max_iter >= 1;   // 0: only the initial values (e.g. the Voronoi initialisation)
+    if ((rc = mask_list())) return rc;
     if (!cgnr && outer && (rc = tonal_setup())) return rc;
 
     // the inner solves use their own local stop fraction (restored on exit)
@@ -1010,7 +966,7 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
                 if (!std::isfinite(r2[c])) return fail(HDI_ERR_NONFINITE, "tonal: non-finite residual");
                 const double rel = btf2[c] > 0 ? std::sqrt(r2[c] / btf2[c]) : 0.0;
                 rel_max = std::max(rel_max, rel);
-                esum += e2[c];
+                esum += e2[c] + sw.bnorm2[c];   // mask pixels + the rest (the adjoint right-hand side)
             }
             mse_last = esum / ((double)nch * H * W);
             if (p.trace > 0)
@@ -1112,7 +1068,7 @@ int Ctx::tonal_cgnr(SolveSpec& sw, const double* btf2, double tol, int& it, doub
         for (int c = 0; c < nch; ++c) {
             if (!std::isfinite(r2[c])) return fail(HDI_ERR_NONFINITE, "CGNR: non-finite residual");
             rel_max = std::max(rel_max, btf2[c] > 0 ? std::sqrt(r2[c] / btf2[c]) : 0.0);
-            esum += e2[c];
+            esum += e2[c] + sw.bnorm2[c];   // mask pixels + the rest (the adjoint right-hand side)
         }
         mse_last = esum / ((double)nch * H * W);
         return HDI_OK;
