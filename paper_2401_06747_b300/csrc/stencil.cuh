@@ -175,8 +175,11 @@ __device__ __forceinline__ StripHalo strip_halo(int lane, int px, int pxc, int W
 // stacks four warps on consecutive row blocks of one strip. Lanes 0 and 31
 // read the neighbouring strips' edge columns; lanes past the image still
 // take part in the shuffles with clamped loads. Rows are walked in chunks of
-// QS_CHUNK with two chunk buffers: the next chunk's loads are in flight
-// while the current one is computed.
+// QS_CHUNK, every load of a chunk issued before its arithmetic. The
+// prolongation keeps two chunk buffers (the next chunk's loads in flight
+// while the current one is computed); the residual and restriction kernels
+// keep one and run at 64-72 registers instead, so that more resident warps
+// hide the load latency (measured faster on the 4K RGB workload).
 #define QS_COLS 128
 #define QS_CHUNK 2
 
@@ -246,7 +249,7 @@ __device__ __forceinline__ void quad_residual(const QuadLane& q, const float (&c
 // r = b - A x on level F with 2x2 sums into the coarse right-hand side
 // (restriction, Sec. 3.2), zero on coarse known pixels, and ||r_c||^2 per
 // channel. Quad strips: the lane's four columns feed two coarse columns.
-__global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
+__global__ void __launch_bounds__(128, 8) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                            const float* __restrict__ b, LevelArr C, MaskView cm,
                                                            float* __restrict__ cb, GridReduce red, int rows) {
     constexpr int CR = QS_CHUNK;
@@ -318,14 +321,10 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
                 }
             }
         };
-        Chunk A, B;
-        load(A, y0);
-        for (int yb = y0; yb < y1; yb += 2 * CR) {
-            if (yb + CR < y1) load(B, yb + CR);
+        for (int yb = y0; yb < y1; yb += CR) {
+            Chunk A;
+            load(A, yb);
             compute(A, yb);
-            if (yb + CR >= y1) break;
-            if (yb + 2 * CR < y1) load(A, yb + 2 * CR);
-            compute(B, yb + CR);
         }
     }
     const double tot = (double)block_sum_f(sq);
@@ -333,7 +332,7 @@ __global__ void __launch_bounds__(128) k_restrict_residual(LevelArr F, MaskView 
 }
 
 // ||b - A x||^2 per channel on one level (quad strips, FP32).
-__global__ void __launch_bounds__(128) k_level_residual_norm(LevelArr F, MaskView fm, const float* __restrict__ x,
+__global__ void __launch_bounds__(128, 8) k_level_residual_norm(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                              const float* __restrict__ b, GridReduce red, int rows) {
     constexpr int CR = QS_CHUNK;
     const int ch = blockIdx.z;
@@ -382,14 +381,10 @@ __global__ void __launch_bounds__(128) k_level_residual_norm(LevelArr F, MaskVie
                 }
             }
         };
-        Chunk A, B;
-        load(A, y0);
-        for (int yb = y0; yb < y1; yb += 2 * CR) {
-            if (yb + CR < y1) load(B, yb + CR);
+        for (int yb = y0; yb < y1; yb += CR) {
+            Chunk A;
+            load(A, yb);
             compute(A, yb);
-            if (yb + CR >= y1) break;
-            if (yb + 2 * CR < y1) load(A, yb + 2 * CR);
-            compute(B, yb + CR);
         }
     }
     const double tot = (double)block_sum_f(sq);
@@ -664,8 +659,10 @@ struct ResArgs {
 // holds it there (every refinement step writes it, and the V-cycle
 // correction is zero on known pixels), so d is read only by the other INIT
 // modes, once the row's mask word has arrived.
+// Seven CTAs per SM (at most 72 registers): the latency of the row loads is
+// hidden by more resident warps rather than by a second register buffer.
 template <int RHS, int INIT>
-__global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
+__global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
     constexpr int RC = RES_CHUNK;
     constexpr bool LOAD_D = (RHS == RHS_DATA) && (INIT != INIT_UPDATE);
     constexpr bool HAS_U = (INIT == INIT_KEEP || INIT == INIT_UPDATE);
@@ -858,14 +855,10 @@ __global__ void __launch_bounds__(128) k_residual_df(ResArgs a) {
                 }
             }
         };
-        Chunk A, B;
-        load(A, y0);
-        for (int yb = y0; yb < y1; yb += 2 * RC) {
-            if (yb + RC < y1) load(B, yb + RC);
+        for (int yb = y0; yb < y1; yb += RC) {
+            Chunk A;
+            load(A, yb);
             compute(A, yb);
-            if (yb + RC >= y1) break;
-            if (yb + 2 * RC < y1) load(A, yb + 2 * RC);
-            compute(B, yb + RC);
         }
     }
     const double tot = (double)block_sum_f(rr);
