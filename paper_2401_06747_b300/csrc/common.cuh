@@ -31,6 +31,17 @@ struct MaskView {
     }
 };
 
+// Programmatic dependent launch (sm_90 and later). The multigrid kernels are
+// launched with programmatic stream serialisation: a kernel's CTAs may be
+// scheduled while its predecessor in the stream is still finishing, run the
+// part that reads only launch arguments and the mask (unchanged during a
+// solve), and then wait in pdl_wait() until the predecessor grid has
+// completed and its writes are visible. pdl_trigger() at a kernel's start
+// lets its own successor be scheduled early. Launched without the attribute,
+// both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(HDI_FULL, v, o);

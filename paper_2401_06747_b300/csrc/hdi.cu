@@ -43,6 +43,7 @@ const ParamDef kParams[] = {
     {"tonal_method", &Params::tonal_method, 0, 1},
     {"tonal_mse_gain", &Params::tonal_mse_gain, 0, 0.5},
     {"tonal_init", &Params::tonal_init, 0, 1},
+    {"pdl", &Params::pdl, 0, 1},
     {"vi_max_iter", &Params::vi_max_iter, 0, 1000},
     {"vi_tau", &Params::vi_tau, 1e-3, 2.0},
     {"vi_weight", &Params::vi_weight, 0, 2},
@@ -306,12 +307,13 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     const dim3 blocks(L.nbx, L.nby, nch);   // one CTA per (subdomain, channel)
     if (l == 0) tstart(kT_Oras);
     const bool full = L.W >= 32 && L.H >= 32;
+    const bool pd = p.pdl >= 0.5;
     if (zero) {
-        if (full) k_oras<true, true><<<blocks, kLocalThreads, 0, stream>>>(a);
-        else k_oras<true, false><<<blocks, kLocalThreads, 0, stream>>>(a);
+        if (full) launch_k(pd, k_oras<true, true>, blocks, dim3(kLocalThreads), stream, a);
+        else launch_k(pd, k_oras<true, false>, blocks, dim3(kLocalThreads), stream, a);
     } else {
-        if (full) k_oras<false, true><<<blocks, kLocalThreads, 0, stream>>>(a);
-        else k_oras<false, false><<<blocks, kLocalThreads, 0, stream>>>(a);
+        if (full) launch_k(pd, k_oras<false, true>, blocks, dim3(kLocalThreads), stream, a);
+        else launch_k(pd, k_oras<false, false>, blocks, dim3(kLocalThreads), stream, a);
     }
     ++launches;
     if (l == 0) tstop();
@@ -351,8 +353,8 @@ void Ctx::vcycle(int l) {
         const int qr = quad_rows(L.H, L.W, nch);
         dim3 blk(128), grd = quad_grid(L.H, L.W, nch, qr);
         if (l == 0) tstart(kT_Restrict);
-        k_restrict_residual<<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, arr(l + 1), mview(l + 1), C.b,
-                                                     reducer(l + 1, grd.x * grd.y), qr);
+        launch_k(p.pdl >= 0.5, k_restrict_residual, grd, blk, stream, arr(l), mview(l), (const float*)L.xa,
+                 (const float*)L.b, arr(l + 1), mview(l + 1), C.b, reducer(l + 1, grd.x * grd.y), qr);
         ++launches;
         if (l == 0) tstop();
     }
@@ -361,8 +363,8 @@ void Ctx::vcycle(int l) {
         const int qr = quad_rows(L.H, L.W, nch);
         dim3 grd = quad_grid(L.H, L.W, nch, qr), blk(128);
         if (l == 0) tstart(kT_Prolong);
-        k_prolong<0><<<grd, blk, 0, stream>>>(arr(l), mview(l), L.xa, L.b, L.xb, arr(l + 1), C.xa,
-                                              reducer(l, grd.x * grd.y), qr);
+        launch_k(p.pdl >= 0.5, k_prolong<0>, grd, blk, stream, arr(l), mview(l), (const float*)L.xa,
+                 (const float*)L.b, L.xb, arr(l + 1), (const float*)C.xa, reducer(l, grd.x * grd.y), qr);
         ++launches;
         if (l == 0) tstop();
     }
@@ -385,7 +387,8 @@ void Ctx::residual_norm_level(int l, const float* x, int slot) {
     const Level& L = lev[l];
     const int qr = quad_rows(L.H, L.W, nch);
     dim3 grd = quad_grid(L.H, L.W, nch, qr), blk(128);
-    k_level_residual_norm<<<grd, blk, 0, stream>>>(arr(l), mview(l), x, L.b, reducer(slot, grd.x * grd.y), qr);
+    launch_k(p.pdl >= 0.5, k_level_residual_norm, grd, blk, stream, arr(l), mview(l), x, (const float*)L.b,
+             reducer(slot, grd.x * grd.y), qr);
     ++launches;
 }
 
@@ -439,7 +442,7 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
     a.red_b = c.reducer(kSlotB64, grd.x * grd.y);
     a.want_b = want_b ? 1 : 0;
     c.tstart(kT_Residual);
-    k_residual_df<RHS, INIT><<<grd, blk, 0, c.stream>>>(a);
+    launch_k(c.p.pdl >= 0.5, k_residual_df<RHS, INIT>, grd, blk, c.stream, a);
     ++c.launches;
     c.tstop();
 }

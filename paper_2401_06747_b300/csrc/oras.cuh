@@ -238,10 +238,12 @@ struct OrasArgs {
 template <bool ZERO, bool FULL>
 __global__ void __launch_bounds__(kLocalThreads, 10) k_oras(OrasArgs a) {
     __shared__ LocalShared sh;
+    pdl_trigger();
     const int bx = blockIdx.x, by = blockIdx.y, ch = blockIdx.z;   // grid (nbx, nby, nch)
     const int x0 = sub_origin(bx, a.W, a.stride), y0 = sub_origin(by, a.H, a.stride);
-    const double rn2 = a.rnorm2[ch];
     const LocalGeom g = make_geom(x0, y0, a.H, a.W, a.m.ch(ch), a.theta, sh);
+    pdl_wait();   // x, b and the residual norm come from the preceding kernels
+    const double rn2 = a.rnorm2[ch];
     const int c0 = 2 * g.c, r0 = g.r0;
     const int gx = x0 + c0;                       // absolute column of .x
     const int cx0 = min(gx, a.W - 1), cx1 = min(gx + 1, a.W - 1);

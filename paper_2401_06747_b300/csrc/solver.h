@@ -2,6 +2,7 @@
 // multigrid hierarchy and the solver drivers' declarations.
 #pragma once
 #include <cstdarg>
+#include <utility>
 #include <string>
 #include <cuda_runtime.h>
 #include "../../include/hdi.h"
@@ -31,6 +32,7 @@ struct Params {
     double tonal_fine_pre = 2;      // fine_pre inside the tonal inner solves
     double tonal_fine_post = 1;     // fine_post inside the tonal inner solves
     double tonal_anderson = 8;      // Anderson window on the RAS iteration (0 = plain Alg. 2)
+    double pdl = 1;                 // programmatic dependent launch of the multigrid kernels
     double tonal_method = 0;        // 0: RAS (Alg. 2), 1: CGNR (Sec. 5.1)
     double tonal_mse_gain = 0;      // > 0: also stop once an iteration improves the MSE by less (relative)
     double tonal_init = 0;          // 0: g0 (or f on the mask); 1: Voronoi initialisation (Sec. 5.3) first
@@ -102,6 +104,23 @@ constexpr int kMaxTimed = 2048;   // timed launches buffered between flushes
 enum { kT_Oras = 0, kT_Residual, kT_Prolong, kT_Restrict, kT_Echo, kT_Gram, kT_Local, kT_Anderson };
 // double-float vectors of level-0 size
 enum { kF = 0, kU0, kU1, kG, kY0, kY1, kW0, kW1, kP, kNumDF };
+
+// Launch with programmatic stream serialisation (see pdl_wait in
+// common.cuh) when `pdl` is set, else a plain launch.
+template <typename... K, typename... A>
+inline cudaError_t launch_k(bool pdl, void (*k)(K...), dim3 grid, dim3 block, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 struct Ctx {
     int device = 0;

@@ -254,12 +254,14 @@ __global__ void __launch_bounds__(128, 8) k_restrict_residual(LevelArr F, MaskVi
                                                            float* __restrict__ cb, GridReduce red, int rows) {
     constexpr int CR = QS_CHUNK;
     static_assert(CR == 2, "one coarse row per chunk");
+    pdl_trigger();
     const int ch = blockIdx.z;
     fm = fm.ch(ch);
     cm = cm.ch(ch);
     const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * rows;
     const int y1 = min(y0 + rows, F.H);
     const QuadLane q = quad_lane(blockIdx.x * QS_COLS, F, fm);
+    pdl_wait();
     const float* xc = x + ch * F.cs;
     const float* bc = b + ch * F.cs;
     float sq = 0.f;
@@ -335,11 +337,13 @@ __global__ void __launch_bounds__(128, 8) k_restrict_residual(LevelArr F, MaskVi
 __global__ void __launch_bounds__(128, 8) k_level_residual_norm(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                              const float* __restrict__ b, GridReduce red, int rows) {
     constexpr int CR = QS_CHUNK;
+    pdl_trigger();
     const int ch = blockIdx.z;
     fm = fm.ch(ch);
     const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * rows;
     const int y1 = min(y0 + rows, F.H);
     const QuadLane q = quad_lane(blockIdx.x * QS_COLS, F, fm);
+    pdl_wait();
     const float* xc = x + ch * F.cs;
     const float* bc = b + ch * F.cs;
     float sq = 0.f;
@@ -412,11 +416,13 @@ __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const 
                                                  LevelArr C, const float* __restrict__ e, GridReduce red, int rows) {
     constexpr int CR = QS_CHUNK;
     constexpr int NS = CR / 2 + 2;   // coarse rows per chunk: (yb/2 - 1) .. (yb/2 + CR/2)
+    pdl_trigger();
     const int ch = blockIdx.z;
     fm = fm.ch(ch);
     const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * rows;
     const int y1 = min(y0 + rows, F.H);
     const QuadLane q = quad_lane(blockIdx.x * QS_COLS, F, fm);
+    pdl_wait();
     const int lane = q.lane;
     const float* xc = (MODE == 0) ? xin + ch * F.cs : nullptr;
     const float* bc = b + ch * F.cs;
@@ -672,7 +678,9 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
     const int H = a.F.H, W = a.F.W;
     const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * a.rows;
     const int y1 = min(y0 + a.rows, H);
+    pdl_trigger();
     const QuadLane q = quad_lane(blockIdx.x * QS_COLS, a.F, m);
+    pdl_wait();
     const int lane = q.lane;
     const long long co = ch * a.F.cs;
     float rr = 0.f, bb2 = 0.f;
