@@ -495,6 +495,11 @@ __global__ void __launch_bounds__(32 * kLocalWarps) k_tonal_local(LocalSolveArgs
     constexpr int NT = 4;                 // rows of v per lane and pass: 128 per pass
     __shared__ float xs[4 * kTonalMaxM];
     __shared__ float ps[kLocalWarps][4][NT * 32];
+    // Only the final accumulation into `out` depends on the previous colour's
+    // launch (r and the factors were complete before the colours started), so
+    // the products run while that launch finishes; pdl_wait() guards the
+    // writes.
+    pdl_trigger();
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int cx = a.color % 3, cy = a.color / 3;
     const int hx = class_count(cx, a.nbx);
@@ -549,6 +554,7 @@ __global__ void __launch_bounds__(32 * kLocalWarps) k_tonal_local(LocalSolveArgs
         for (int c = 0; c < 4; ++c)
 #pragma unroll
             for (int t = 0; t < NT; ++t) ps[wl][c][t * 32 + lane] = y[c][t];
+        pdl_wait();
         __syncthreads();
         for (int k = threadIdx.x; k < NT * 32 && base + k < m; k += 32 * kLocalWarps) {
             const int code = lst[base + k];
@@ -713,6 +719,7 @@ int Ctx::mask_list() {
 
 void Ctx::tonal_local(float* out) {
     const Level& L0 = lev[0];
+    tstart(kT_Local);   // the nine colour launches as one timed unit
     for (int color = 0; color < 9; ++color) {
         LocalSolveArgs a;
         a.F = arr(0);
@@ -731,11 +738,10 @@ void Ctx::tonal_local(float* out) {
         const int hy = class_count(color / 3, L0.nby);
         const long long blocks = (long long)hx * hy;
         if (blocks <= 0) continue;
-        tstart(kT_Local);
-        k_tonal_local<<<(unsigned)blocks, 32 * kLocalWarps, 0, stream>>>(a);
+        launch_k(p.pdl >= 0.5, k_tonal_local, dim3((unsigned)blocks), dim3(32 * kLocalWarps), stream, a);
         ++launches;
-        tstop();
     }
+    tstop();
 }
 
 template <int K>
