@@ -13,6 +13,7 @@
 //   P     : bilinear interpolation between coarse cell centres (weights
 //           9/16, 3/16, 3/16, 1/16), constant extension at the border.
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 
 // ---------------------------------------------------------------- masks ---
@@ -249,6 +250,8 @@ __device__ __forceinline__ void quad_residual(const QuadLane& q, const float (&c
 // r = b - A x on level F with 2x2 sums into the coarse right-hand side
 // (restriction, Sec. 3.2), zero on coarse known pixels, and ||r_c||^2 per
 // channel. Quad strips: the lane's four columns feed two coarse columns.
+// Warps whose strip and row block (with the rows above and below) lie inside
+// the image run a variant without border tests or clamped rows (IN).
 __global__ void __launch_bounds__(128, 8) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                            const float* __restrict__ b, LevelArr C, MaskView cm,
                                                            float* __restrict__ cb, GridReduce red, int rows) {
@@ -260,17 +263,21 @@ __global__ void __launch_bounds__(128, 8) k_restrict_residual(LevelArr F, MaskVi
     cm = cm.ch(ch);
     const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * rows;
     const int y1 = min(y0 + rows, F.H);
-    const QuadLane q = quad_lane(blockIdx.x * QS_COLS, F, fm);
+    const int x0 = blockIdx.x * QS_COLS;
+    const QuadLane q = quad_lane(x0, F, fm);
+    const bool interior = x0 > 0 && x0 + QS_COLS < F.W && y0 > 0 && y0 + rows + 1 <= F.H;
     pdl_wait();
     const float* xc = x + ch * F.cs;
     const float* bc = b + ch * F.cs;
     float sq = 0.f;
-    if (y0 < F.H) {
+    auto body = [&](auto in_tag) {
+        constexpr bool IN = decltype(in_tag)::value;
         const uint32_t* mrow = fm.bits + q.mword;
         const int X = q.c0 >> 1;                  // first of the lane's two coarse columns
         const uint32_t* cmw = cm.bits + min(X >> 5, cm.wpitch - 1);
+        auto rowc = [&](int y) { return IN ? y : min(y, F.H - 1); };
         float up[4] = {0.f, 0.f, 0.f, 0.f}, cen[4];
-        if (y0 > 0) f4_to(*reinterpret_cast<const float4*>(xc + (size_t)(y0 - 1) * F.pitch + q.cq), up);
+        if (IN || y0 > 0) f4_to(*reinterpret_cast<const float4*>(xc + (size_t)(y0 - 1) * F.pitch + q.cq), up);
         f4_to(*reinterpret_cast<const float4*>(xc + (size_t)y0 * F.pitch + q.cq), cen);
         float pair[2] = {0.f, 0.f};
         struct Chunk {
@@ -281,33 +288,49 @@ __global__ void __launch_bounds__(128, 8) k_restrict_residual(LevelArr F, MaskVi
         auto load = [&](Chunk& c, int yb) {
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
-                const size_t ry = (size_t)min(yb + k, F.H - 1) * F.pitch;
-                c.Xd[k] = *reinterpret_cast<const float4*>(xc + (size_t)min(yb + k + 1, F.H - 1) * F.pitch + q.cq);
+                const size_t ry = (size_t)rowc(yb + k) * F.pitch;
+                c.Xd[k] = *reinterpret_cast<const float4*>(xc + (size_t)rowc(yb + k + 1) * F.pitch + q.cq);
                 c.Bv[k] = *reinterpret_cast<const float4*>(bc + ry + q.cq);
                 c.Hv[k] = q.hon ? xc[ry + q.hcol] : 0.f;
-                c.Mw[k] = mrow[(size_t)min(yb + k, F.H - 1) * fm.wpitch];
+                c.Mw[k] = mrow[(size_t)rowc(yb + k) * fm.wpitch];
             }
-            c.Cw = cmw[(size_t)min(yb >> 1, C.H - 1) * cm.wpitch];   // CR == 2: one coarse row
+            c.Cw = cmw[(size_t)(IN ? (yb >> 1) : min(yb >> 1, C.H - 1)) * cm.wpitch];   // one coarse row
         };
         auto compute = [&](const Chunk& c, int yb) {
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
                 const int y = yb + k;
-                if (y >= y1) break;
+                if (!IN && y >= y1) break;
                 float dn[4], bv[4], r[4];
                 f4_to(c.Xd[k], dn);
                 f4_to(c.Bv[k], bv);
-                quad_residual(q, cen, up, dn, bv, c.Hv[k], y > 0, y + 1 < F.H, r);
+                if (IN) {
+                    // all neighbours inside: b - (4 c - left - right - up - down)
+                    float lw = __shfl_up_sync(HDI_FULL, cen[3], 1);
+                    float rw = __shfl_down_sync(HDI_FULL, cen[0], 1);
+                    if (q.lane == 0) lw = c.Hv[k];
+                    if (q.lane == 31) rw = c.Hv[k];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float l = (j == 0) ? lw : cen[j - 1];
+                        const float rr = (j == 3) ? rw : cen[j + 1];
+                        const float lap = ((cen[j] - l) + (cen[j] - rr)) + ((cen[j] - up[j]) + (cen[j] - dn[j]));
+                        r[j] = bv[j] - lap;
+                    }
+                } else {
+                    quad_residual(q, cen, up, dn, bv, c.Hv[k], y > 0, y + 1 < F.H, r);
+                }
+                const uint32_t nib = c.Mw[k] >> q.shift;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const bool unk = q.act[j] && !((c.Mw[k] >> (q.shift + j)) & 1u);
+                    const bool unk = (IN || q.act[j]) && !((nib >> j) & 1u);
                     pair[j >> 1] += unk ? r[j] : 0.f;
                 }
-                if ((y & 1) || y + 1 == F.H) {
+                if ((y & 1) || (!IN && y + 1 == F.H)) {
                     const int Y = y >> 1;
 #pragma unroll
                     for (int t = 0; t < 2; ++t) {
-                        const bool ok = q.act[2 * t] && X + t < C.W;
+                        const bool ok = IN || (q.act[2 * t] && X + t < C.W);
                         const float v = ((c.Cw >> ((X & 31) + t)) & 1u) ? 0.f : pair[t];
                         if (ok) {
                             cb[ch * C.cs + (size_t)Y * C.pitch + X + t] = v;
@@ -328,7 +351,9 @@ __global__ void __launch_bounds__(128, 8) k_restrict_residual(LevelArr F, MaskVi
             load(A, yb);
             compute(A, yb);
         }
-    }
+    };
+    if (interior) body(std::true_type{});
+    else if (y0 < F.H) body(std::false_type{});
     const double tot = (double)block_sum_f(sq);
     grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
 }
@@ -680,15 +705,18 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
     const int y1 = min(y0 + a.rows, H);
     pdl_trigger();
     const QuadLane q = quad_lane(blockIdx.x * QS_COLS, a.F, m);
+    const bool interior = blockIdx.x > 0 && (blockIdx.x + 1) * QS_COLS < W && y0 > 0 && y0 + a.rows + 1 <= H;
     pdl_wait();
     const int lane = q.lane;
     const long long co = ch * a.F.cs;
     float rr = 0.f, bb2 = 0.f;
-    if (y0 < H) {
+    auto body = [&](auto in_tag) {
+        constexpr bool IN = decltype(in_tag)::value;   // no border tests, no clamped rows
         const uint32_t* mrow = m.bits + q.mword;
         const uint32_t* hrow = m.bits + (q.hcol >> 5);
         const int hbit = q.hcol & 31;
-        auto at = [&](int y, int col) { return co + (size_t)min(y, H - 1) * a.F.pitch + col; };
+        auto rowc = [&](int y) { return IN ? y : min(y, H - 1); };
+        auto at = [&](int y, int col) { return co + (size_t)rowc(y) * a.F.pitch + col; };
         auto ld4 = [&](const float* p, size_t i) { return *reinterpret_cast<const float4*>(p + i); };
         // iterate value after the INIT transform, from the loaded sources
         auto value = [&](bool known, float uh, float ul, float e, float dh, float dl, float& h, float& l) {
@@ -712,7 +740,7 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
         // the lane's four values of row y (all loads inside)
         auto row_value = [&](int y, float (&h)[4], float (&l)[4]) {
             const size_t i = at(y, q.cq);
-            const uint32_t w = mrow[(size_t)min(y, H - 1) * m.wpitch];
+            const uint32_t w = mrow[(size_t)rowc(y) * m.wpitch];
             float uh[4] = {0.f, 0.f, 0.f, 0.f}, ul[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
             float dh[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
             if (HAS_U) { f4_to(ld4(a.uin.hi, i), uh); f4_to(ld4(a.uin.lo, i), ul); }
@@ -723,7 +751,7 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
         };
         float uph[4] = {0.f, 0.f, 0.f, 0.f}, upl[4] = {0.f, 0.f, 0.f, 0.f}, ch_[4], cl[4];
         row_value(y0, ch_, cl);
-        if (y0 > 0) row_value(y0 - 1, uph, upl);
+        if (IN || y0 > 0) row_value(y0 - 1, uph, upl);
         struct Chunk {
             float4 Uh[RC], Ul[RC], E[RC];          // rows yb+1 .. yb+RC
             float4 Dh[RC], Dl[RC], Yh[RC], Yl[RC];   // RHS_SOURCE: d and y of rows yb .. yb+RC-1
@@ -734,14 +762,14 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         auto load = [&](Chunk& c, int yb) {
 #pragma unroll
-            for (int k = 0; k <= RC; ++k) c.Mw[k] = mrow[(size_t)min(yb + k, H - 1) * m.wpitch];
+            for (int k = 0; k <= RC; ++k) c.Mw[k] = mrow[(size_t)rowc(yb + k) * m.wpitch];
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 const size_t id = at(yb + k + 1, q.cq), ih = at(yb + k, q.hcol), ic = at(yb + k, q.cq);
                 c.Uh[k] = HAS_U ? ld4(a.uin.hi, id) : z4;
                 c.Ul[k] = HAS_U ? ld4(a.uin.lo, id) : z4;
                 c.E[k] = HAS_E ? ld4(a.x32, id) : z4;
-                c.Hm[k] = q.hon ? hrow[(size_t)min(yb + k, H - 1) * m.wpitch] : 0u;
+                c.Hm[k] = q.hon ? hrow[(size_t)rowc(yb + k) * m.wpitch] : 0u;
                 c.HUh[k] = (HAS_U && q.hon) ? a.uin.hi[ih] : 0.f;
                 c.HUl[k] = (HAS_U && q.hon) ? a.uin.lo[ih] : 0.f;
                 c.HE[k] = (HAS_E && q.hon) ? a.x32[ih] : 0.f;
@@ -769,9 +797,9 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 const int y = yb + k;
-                if (y >= y1) break;
+                if (!IN && y >= y1) break;
                 float dnh[4] = {0.f, 0.f, 0.f, 0.f}, dnl[4] = {0.f, 0.f, 0.f, 0.f};
-                if (y + 1 < H) {
+                if (IN || y + 1 < H) {
                     float uh[4], ul[4], e[4], dh[4], dl[4];
                     f4_to(c.Uh[k], uh);
                     f4_to(c.Ul[k], ul);
@@ -808,7 +836,7 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
                     const bool known = (c.Mw[k] >> (q.shift + j)) & 1u;
                     float r = 0.f;
                     if (known) {
-                        if (RHS == RHS_DATA && q.act[j]) { const float bh = cjh + cjl; bb2 += bh * bh; }
+                        if (RHS == RHS_DATA && (IN || q.act[j])) { const float bh = cjh + cjl; bb2 += bh * bh; }
                     } else {
                         // A u = 4 u_c - (sum of the 4 neighbours), an absent
                         // neighbour replaced by u_c (zero difference): the
@@ -816,10 +844,10 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
                         // parts added in FP32
                         const float lh = (j == 0) ? lwh : ch_[j - 1], ll = (j == 0) ? lwl : cl[j - 1];
                         const float rh = (j == 3) ? rwh : ch_[j + 1], rl = (j == 3) ? rwl : cl[j + 1];
-                        const float n0h = q.lin[j] ? lh : cjh, n0l = q.lin[j] ? ll : cjl;
-                        const float n1h = q.rin[j] ? rh : cjh, n1l = q.rin[j] ? rl : cjl;
-                        const float n2h = (y > 0) ? uph[j] : cjh, n2l = (y > 0) ? upl[j] : cjl;
-                        const float n3h = (y + 1 < H) ? dnh[j] : cjh, n3l = (y + 1 < H) ? dnl[j] : cjl;
+                        const float n0h = (IN || q.lin[j]) ? lh : cjh, n0l = (IN || q.lin[j]) ? ll : cjl;
+                        const float n1h = (IN || q.rin[j]) ? rh : cjh, n1l = (IN || q.rin[j]) ? rl : cjl;
+                        const float n2h = (IN || y > 0) ? uph[j] : cjh, n2l = (IN || y > 0) ? upl[j] : cjl;
+                        const float n3h = (IN || y + 1 < H) ? dnh[j] : cjh, n3l = (IN || y + 1 < H) ? dnl[j] : cjl;
                         float sa, ea, sb, eb, sh, eh;
                         two_sum(n0h, n1h, sa, ea);
                         two_sum(n2h, n3h, sb, eb);
@@ -831,7 +859,7 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
                         if (RHS == RHS_SOURCE) {
                             float bh, bl;
                             df_add(sdh[j], sdl[j], -syh[j], -syl[j], bh, bl);
-                            if (q.act[j]) bb2 += bh * bh;
+                            if (IN || q.act[j]) bb2 += bh * bh;
                             float rh2, rl2;
                             df_add(bh, bl, -ah, -al, rh2, rl2);
                             r = rh2 + rl2;
@@ -840,10 +868,10 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
                         }
                     }
                     orr[j] = r;
-                    if (q.act[j]) rr += r * r;
+                    if (IN || q.act[j]) rr += r * r;
                 }
                 const size_t idx = co + (size_t)y * a.F.pitch + q.c0;
-                if (q.act[3]) {
+                if (IN || q.act[3]) {
                     *reinterpret_cast<float4*>(a.uout.hi + idx) = make_float4(oh[0], oh[1], oh[2], oh[3]);
                     *reinterpret_cast<float4*>(a.uout.lo + idx) = make_float4(ol[0], ol[1], ol[2], ol[3]);
                     *reinterpret_cast<float4*>(a.r32 + idx) = make_float4(orr[0], orr[1], orr[2], orr[3]);
@@ -868,7 +896,9 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
             load(A, yb);
             compute(A, yb);
         }
-    }
+    };
+    if (interior) body(std::true_type{});
+    else if (y0 < H) body(std::false_type{});
     const double tot = (double)block_sum_f(rr);
     grid_reduce_commit(a.red_r, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
     if (a.want_b) {
