@@ -247,6 +247,23 @@ __device__ __forceinline__ void quad_residual(const QuadLane& q, const float (&c
     }
 }
 
+// quad_residual for a lane whose four columns, their left and right
+// neighbours and the rows above and below all lie inside the image.
+__device__ __forceinline__ void quad_residual_interior(int lane, const float (&c)[4], const float (&u)[4],
+                                                      const float (&d)[4], const float (&bv)[4], float hv,
+                                                      float (&r)[4]) {
+    float lw = __shfl_up_sync(HDI_FULL, c[3], 1);
+    float rw = __shfl_down_sync(HDI_FULL, c[0], 1);
+    if (lane == 0) lw = hv;
+    if (lane == 31) rw = hv;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float l = (j == 0) ? lw : c[j - 1];
+        const float rr = (j == 3) ? rw : c[j + 1];
+        r[j] = bv[j] - (((c[j] - l) + (c[j] - rr)) + ((c[j] - u[j]) + (c[j] - d[j])));
+    }
+}
+
 // r = b - A x on level F with 2x2 sums into the coarse right-hand side
 // (restriction, Sec. 3.2), zero on coarse known pixels, and ||r_c||^2 per
 // channel. Quad strips: the lane's four columns feed two coarse columns.
@@ -305,18 +322,7 @@ __global__ void __launch_bounds__(128, 8) k_restrict_residual(LevelArr F, MaskVi
                 f4_to(c.Xd[k], dn);
                 f4_to(c.Bv[k], bv);
                 if (IN) {
-                    // all neighbours inside: b - (4 c - left - right - up - down)
-                    float lw = __shfl_up_sync(HDI_FULL, cen[3], 1);
-                    float rw = __shfl_down_sync(HDI_FULL, cen[0], 1);
-                    if (q.lane == 0) lw = c.Hv[k];
-                    if (q.lane == 31) rw = c.Hv[k];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float l = (j == 0) ? lw : cen[j - 1];
-                        const float rr = (j == 3) ? rw : cen[j + 1];
-                        const float lap = ((cen[j] - l) + (cen[j] - rr)) + ((cen[j] - up[j]) + (cen[j] - dn[j]));
-                        r[j] = bv[j] - lap;
-                    }
+                    quad_residual_interior(q.lane, cen, up, dn, bv, c.Hv[k], r);
                 } else {
                     quad_residual(q, cen, up, dn, bv, c.Hv[k], y > 0, y + 1 < F.H, r);
                 }
@@ -367,15 +373,19 @@ __global__ void __launch_bounds__(128, 8) k_level_residual_norm(LevelArr F, Mask
     fm = fm.ch(ch);
     const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * rows;
     const int y1 = min(y0 + rows, F.H);
-    const QuadLane q = quad_lane(blockIdx.x * QS_COLS, F, fm);
+    const int x0 = blockIdx.x * QS_COLS;
+    const QuadLane q = quad_lane(x0, F, fm);
+    const bool interior = x0 > 0 && x0 + QS_COLS < F.W && y0 > 0 && y0 + rows + 1 <= F.H;
     pdl_wait();
     const float* xc = x + ch * F.cs;
     const float* bc = b + ch * F.cs;
     float sq = 0.f;
-    if (y0 < F.H) {
+    auto body = [&](auto in_tag) {
+        constexpr bool IN = decltype(in_tag)::value;   // no border tests, no clamped rows
+        auto rowc = [&](int y) { return IN ? y : min(y, F.H - 1); };
         const uint32_t* mrow = fm.bits + q.mword;
         float up[4] = {0.f, 0.f, 0.f, 0.f}, cen[4];
-        if (y0 > 0) f4_to(*reinterpret_cast<const float4*>(xc + (size_t)(y0 - 1) * F.pitch + q.cq), up);
+        if (IN || y0 > 0) f4_to(*reinterpret_cast<const float4*>(xc + (size_t)(y0 - 1) * F.pitch + q.cq), up);
         f4_to(*reinterpret_cast<const float4*>(xc + (size_t)y0 * F.pitch + q.cq), cen);
         struct Chunk {
             float4 Xd[CR], Bv[CR];
@@ -385,25 +395,27 @@ __global__ void __launch_bounds__(128, 8) k_level_residual_norm(LevelArr F, Mask
         auto load = [&](Chunk& c, int yb) {
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
-                const size_t ry = (size_t)min(yb + k, F.H - 1) * F.pitch;
-                c.Xd[k] = *reinterpret_cast<const float4*>(xc + (size_t)min(yb + k + 1, F.H - 1) * F.pitch + q.cq);
+                const size_t ry = (size_t)rowc(yb + k) * F.pitch;
+                c.Xd[k] = *reinterpret_cast<const float4*>(xc + (size_t)rowc(yb + k + 1) * F.pitch + q.cq);
                 c.Bv[k] = *reinterpret_cast<const float4*>(bc + ry + q.cq);
                 c.Hv[k] = q.hon ? xc[ry + q.hcol] : 0.f;
-                c.Mw[k] = mrow[(size_t)min(yb + k, F.H - 1) * fm.wpitch];
+                c.Mw[k] = mrow[(size_t)rowc(yb + k) * fm.wpitch];
             }
         };
         auto compute = [&](const Chunk& c, int yb) {
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
                 const int y = yb + k;
-                if (y >= y1) break;
+                if (!IN && y >= y1) break;
                 float dn[4], bv[4], r[4];
                 f4_to(c.Xd[k], dn);
                 f4_to(c.Bv[k], bv);
-                quad_residual(q, cen, up, dn, bv, c.Hv[k], y > 0, y + 1 < F.H, r);
+                if (IN) quad_residual_interior(q.lane, cen, up, dn, bv, c.Hv[k], r);
+                else quad_residual(q, cen, up, dn, bv, c.Hv[k], y > 0, y + 1 < F.H, r);
+                const uint32_t nib = c.Mw[k] >> q.shift;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const bool unk = q.act[j] && !((c.Mw[k] >> (q.shift + j)) & 1u);
+                    const bool unk = (IN || q.act[j]) && !((nib >> j) & 1u);
                     if (unk) sq += r[j] * r[j];
                     up[j] = cen[j];
                     cen[j] = dn[j];
@@ -415,7 +427,9 @@ __global__ void __launch_bounds__(128, 8) k_level_residual_norm(LevelArr F, Mask
             load(A, yb);
             compute(A, yb);
         }
-    }
+    };
+    if (interior) body(std::true_type{});
+    else if (y0 < F.H) body(std::false_type{});
     const double tot = (double)block_sum_f(sq);
     grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
 }
