@@ -76,8 +76,11 @@ typedef struct {
 } hdi_stats;
 
 /* Create a context on `device`, ordered on `cuda_stream` (a cudaStream_t;
- * NULL = the legacy default stream). */
-int hdi_create(hdi_ctx** ctx, int device, void* cuda_stream);
+ * NULL = the legacy default stream). `config_json` (may be NULL) is a flat
+ * JSON object of parameter values, e.g. {"oras_theta": 0.3, "pdl": 1}, with
+ * the names and ranges of hdi_set_param; a syntax error, an unknown name or
+ * an out-of-range value returns HDI_ERR_INVALID_ARG and creates nothing. */
+int hdi_create(hdi_ctx** ctx, int device, void* cuda_stream, const char* config_json);
 
 /* Release the context and its workspace. NULL is accepted. */
 int hdi_destroy(hdi_ctx* ctx);

@@ -11,6 +11,7 @@ loading fails loudly if the library is missing.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 
 import numpy as np
@@ -70,7 +71,7 @@ def load(path: str | None = None):
         raise RuntimeError(f"libhdi.so not found at {path}; run paper_2401_06747_b300/build.py")
     lib = ctypes.CDLL(path)
     P = ctypes.POINTER
-    lib.hdi_create.argtypes = [P(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p]
+    lib.hdi_create.argtypes = [P(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p, ctypes.c_char_p]
     lib.hdi_destroy.argtypes = [ctypes.c_void_p]
     lib.hdi_set_param.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_double]
     lib.hdi_get_param.argtypes = [ctypes.c_void_p, ctypes.c_char_p, P(ctypes.c_double)]
@@ -142,11 +143,10 @@ class Context:
         s = 0
         if stream is not None:
             s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-        rc = self.lib.hdi_create(ctypes.byref(self.h), device, ctypes.c_void_p(s))
+        cfg = json.dumps({k: float(v) for k, v in params.items()}).encode() if params else None
+        rc = self.lib.hdi_create(ctypes.byref(self.h), device, ctypes.c_void_p(s), cfg)
         if rc != HDI_OK:
-            raise HdiError(rc, "hdi_create failed")
-        for k, v in params.items():
-            self.set_param(k, v)
+            raise HdiError(rc, "hdi_create failed" + (f" (config {cfg.decode()})" if cfg else ""))
 
     def close(self):
         if self.h:

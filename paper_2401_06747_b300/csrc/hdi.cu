@@ -650,13 +650,58 @@ int Ctx::load_mask(const hdi_mask* m, long long* ones, int plane, bool pyramid) 
     return HDI_OK;
 }
 
+// Flat JSON object of parameter values, {"name": number, ...}, applied on
+// top of the defaults; false on a syntax error, an unknown name or a value
+// outside the parameter's range.
+static bool parse_config(const char* js, Params& out) {
+    const char* q = js;
+    auto ws = [&]() { while (*q == ' ' || *q == '\t' || *q == '\n' || *q == '\r') ++q; };
+    ws();
+    if (*q++ != '{') return false;
+    ws();
+    if (*q == '}') { ++q; ws(); return *q == 0; }
+    for (;;) {
+        ws();
+        if (*q++ != '"') return false;
+        const char* k0 = q;
+        while (*q && *q != '"') ++q;
+        if (*q != '"') return false;
+        const std::string key(k0, q - k0);
+        ++q;
+        ws();
+        if (*q++ != ':') return false;
+        ws();
+        char* end = nullptr;
+        const double v = strtod(q, &end);
+        if (end == q) return false;
+        q = end;
+        bool found = false;
+        for (const auto& d : kParams) {
+            if (key == d.name) {
+                if (!(v >= d.lo && v <= d.hi)) return false;
+                out.*(d.field) = v;
+                found = true;
+                break;
+            }
+        }
+        if (!found) return false;
+        ws();
+        if (*q == ',') { ++q; continue; }
+        if (*q++ != '}') return false;
+        ws();
+        return *q == 0;
+    }
+}
+
 // ------------------------------------------------------------ C ABI ---
 
 extern "C" {
 
-int hdi_create(hdi_ctx** out, int device, void* stream) {
+int hdi_create(hdi_ctx** out, int device, void* stream, const char* config_json) {
     if (!out) return HDI_ERR_INVALID_ARG;
     *out = nullptr;
+    Params cfg;
+    if (config_json && !parse_config(config_json, cfg)) return HDI_ERR_INVALID_ARG;
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
         cudaGetLastError();
@@ -676,6 +721,7 @@ int hdi_create(hdi_ctx** out, int device, void* stream) {
         return HDI_ERR_CUDA;
     }
     c->d_chmask = (int*)((char*)c->flags + 256);
+    c->p = cfg;
     *out = reinterpret_cast<hdi_ctx*>(c);
     return HDI_OK;
 }

@@ -33,7 +33,7 @@ def test_version_and_error_paths_without_gpu():
     lib = hdi.load()
     assert b"sm_103a" in lib.hdi_version()
     assert lib.hdi_destroy(None) == 0
-    assert lib.hdi_create(None, 0, None) == -1
+    assert lib.hdi_create(None, 0, None, None) == -1
     assert lib.hdi_inpaint(None, None, None, None, None, 1e-6, None) == -1
     assert lib.hdi_last_error(None) == b"null context"
 
@@ -49,3 +49,21 @@ def test_parameter_names_documented():
     for name in ["oras_theta", "oras_eta", "oras_max_local", "coarse_eta", "max_vcycles",
                  "tonal_max_iter", "tonal_inner_ratio", "hbm_budget_gb"]:
         assert name in text
+
+
+def test_create_config_json_is_validated_before_the_device():
+    """Malformed or invalid configurations are refused with INVALID_ARG (-1)
+    whether or not a GPU is present; a valid one gets as far as the device
+    (CUDA error -5 on a machine without a GPU)."""
+    lib = hdi.load()
+    h = ctypes.c_void_p()
+    for bad in (b"{", b'{"oras_theta": }', b'{"no_such_param": 1}', b'{"oras_theta": 5}', b'[1]',
+                b'{"oras_theta": 0.3,}', b'{"oras_theta" 0.3}'):
+        assert lib.hdi_create(ctypes.byref(h), 0, None, bad) == -1, bad
+    rc = lib.hdi_create(ctypes.byref(h), 0, None, b' { "oras_theta" : 0.25 , "pdl": 0 } ')
+    if rc == 0:
+        v = ctypes.c_double()
+        assert lib.hdi_get_param(h, b"oras_theta", ctypes.byref(v)) == 0 and v.value == 0.25
+        lib.hdi_destroy(h)
+    else:
+        assert rc == -5
