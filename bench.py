@@ -52,13 +52,13 @@ def workload_config(extra=None):
 
 # ------------------------------------------------------------ CPU oracle ---
 
-def oracle_sample_seconds(crop: int) -> float:
+def oracle_sample_seconds(crop: int, channel: int = 0) -> float:
     """Time the oracle (inpaint + tonal, FP64) on one channel of a crop."""
     import numpy as np
     from synthdata import synth_image, random_mask
     from oracle import inpaint, tonal
     from oracle import laplace as lp
-    f = synth_image(H4K, W4K, IMAGE_SEEDS[0])[:crop, :crop].copy()
+    f = synth_image(H4K, W4K, IMAGE_SEEDS[channel])[:crop, :crop].copy()
     c = random_mask(H4K, W4K, DENSITY, MASK_SEED)[:crop, :crop].copy()
     if c.sum() == 0:
         c[0, 0] = 1
@@ -85,6 +85,26 @@ def cpu_baseline() -> dict:
     return {"value": scale_to_metric(secs, CROP), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"oracle inpaint + tonal (FP64, SuperLU + CG) on channel 0 of the {CROP}x{CROP} top-left crop "
                       f"of the workload took {secs:.2f} s; scaled by pixel count to 3840x2160x3"}
+
+
+def cpu_baseline_per_channel() -> dict:
+    """The oracle with one single-threaded process per colour channel (the
+    channels are independent problems), all three run at once on the crop;
+    the wall time of the three is scaled like the one-channel figure."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    t0 = time.perf_counter()
+    procs = [subprocess.Popen([sys.executable, "-c", "import sys; sys.path.insert(0, %r); import bench; "
+                               "print(bench.oracle_sample_seconds(%d, %d))" % (ROOT, CROP, c)],
+                              env=env, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+             for c in range(CH)]
+    for p in procs:
+        p.communicate(timeout=600)
+    wall = time.perf_counter() - t0
+    # three channels of the crop in `wall` seconds: per channel-crop equivalent wall / 3
+    return {"value": scale_to_metric(wall / CH, CROP), "unit": UNIT, "cores": CH, "kind": "oracle",
+            "sample": f"oracle inpaint + tonal on the three channels of the {CROP}x{CROP} crop in {CH} concurrent "
+                      f"single-threaded processes took {wall:.2f} s (wall, including process start); scaled by pixel "
+                      f"count to 3840x2160x3"}
 
 
 # ---------------------------------------------------------------- clocks ---
@@ -315,6 +335,7 @@ def run_hdi(args, rank, world):
            "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
+        out["cpu_baseline_per_channel"] = cpu_baseline_per_channel()
     elif rank == 0 and world > 1:
         out["cpu_baseline"] = None
     if rank == 0:
