@@ -138,11 +138,12 @@ __device__ __forceinline__ void grid_reduce_commit(const GridReduce& R, int ch, 
 // last subdomain is shifted back to end at the image border, so that every
 // subdomain is a full 32 pixels whenever n >= 32 (same count and the same
 // owned cores as the plain stride placement).
-__host__ __device__ __forceinline__ int sub_origin(int b, int n, int s) {
-    if (n < 32) return 0;
+__host__ __device__ __forceinline__ int sub_origin_n(int b, int n, int s, int size) {
+    if (n < size) return 0;
     const int o = b * s;
-    return o > n - 32 ? n - 32 : o;
+    return o > n - size ? n - size : o;
 }
+__host__ __device__ __forceinline__ int sub_origin(int b, int n, int s) { return sub_origin_n(b, n, s, 32); }
 
 // Number of overlapping subdomains of side `size` with overlap `ov` along an
 // axis of n pixels: ceil((n - ov) / (size - ov)), at least 1 (Sec. 3.3).

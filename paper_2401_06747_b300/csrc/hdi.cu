@@ -43,6 +43,7 @@ const ParamDef kParams[] = {
     {"tonal_method", &Params::tonal_method, 0, 1},
     {"tonal_mse_gain", &Params::tonal_mse_gain, 0, 0.5},
     {"tonal_init", &Params::tonal_init, 0, 1},
+    {"tonal_block", &Params::tonal_block, 0, 64},
     {"pdl", &Params::pdl, 0, 1},
     {"vi_max_iter", &Params::vi_max_iter, 0, 1000},
     {"vi_tau", &Params::vi_tau, 1e-3, 2.0},

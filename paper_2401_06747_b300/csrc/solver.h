@@ -35,6 +35,7 @@ struct Params {
     double pdl = 1;                 // programmatic dependent launch of the multigrid kernels
     double tonal_method = 0;        // 0: RAS (Alg. 2), 1: CGNR (Sec. 5.1)
     double tonal_mse_gain = 0;      // > 0: also stop once an iteration improves the MSE by less (relative)
+    double tonal_block = 0;         // RAS subdomain side: 32, 64 (Sec. 5.2 uses 64), 0: 64 below 3% density
     double tonal_init = 0;          // 0: g0 (or f on the mask); 1: Voronoi initialisation (Sec. 5.3) first
     double vi_max_iter = 20;        // Richardson steps of the Voronoi initialisation
     double vi_tau = 1.0;            // its step size
@@ -203,6 +204,7 @@ struct Ctx {
     int inpaint_batch(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, hdi_stats* st);
     int read_slot(int slot, double* out);
     int tonal_setup();
+    int t_blk = 32, t_nbx = 0, t_nby = 0, t_maxm = 0;   // RAS tiling of the last tonal set-up
     void tonal_residual(DFc y, DFc w);
     void tonal_local(float* out);
     int tonal_aa_step(int n, const float* fvfull, DF G);

@@ -23,8 +23,9 @@
 #include "oras.cuh"
 #include "anderson.cuh"
 #include "cgnr.cuh"
+#include "local64.cuh"
 
-constexpr int kTonalMaxM = 1024;  // mask pixels per 32x32 subdomain (all of them)
+constexpr int kTonalMaxM = 4096;  // mask pixels per 64x64 subdomain (all of them)
 constexpr int kGramSmem = 208;    // subdomains with more mask pixels factor G_i in global memory
 
 // ----------------------------------------------------------- setup kernels ---
@@ -32,44 +33,60 @@ constexpr int kGramSmem = 208;    // subdomains with more mask pixels factor G_i
 // Valid-column mask of a subdomain of width w (bits 0..w-1).
 __device__ __forceinline__ uint32_t cols_valid(int w) { return w >= 32 ? 0xffffffffu : ((1u << w) - 1u); }
 
+// Mask bits of row ly of a blk x blk subdomain (blk = 32 or 64), columns
+// 32 * half .. 32 * half + 31 (zero outside the subdomain).
+__device__ __forceinline__ uint32_t sub_row_bits(const MaskView& m, int x0, int y0, int w, int h, int ly, int half) {
+    if (ly >= h || 32 * half >= w) return 0u;
+    return m.window(x0 + 32 * half, y0 + ly) & cols_valid(w - 32 * half);
+}
+
 // m_i = number of mask pixels in subdomain i (warp per subdomain, lane = row).
-__global__ void k_tonal_count(MaskView m, int nbx, int nby, int stride, int* __restrict__ cnt) {
+__global__ void k_tonal_count(MaskView m, int nbx, int nby, int stride, int blk, int* __restrict__ cnt) {
     const int wid = blockIdx.x * 4 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (wid >= nbx * nby) return;
     const int by = wid / nbx, bx = wid - by * nbx;
-    const int x0 = sub_origin(bx, m.W, stride), y0 = sub_origin(by, m.H, stride);
-    const int w = min(32, m.W - x0), h = min(32, m.H - y0);
+    const int x0 = sub_origin_n(bx, m.W, stride, blk), y0 = sub_origin_n(by, m.H, stride, blk);
+    const int w = min(blk, m.W - x0), h = min(blk, m.H - y0);
     int c = 0;
-    if (lane < h) c = __popc(m.window(x0, y0 + lane) & cols_valid(w));
+    for (int ly = lane; ly < blk; ly += 32)
+        for (int half = 0; half < blk / 32; ++half) c += __popc(sub_row_bits(m, x0, y0, w, h, ly, half));
     c = __reduce_add_sync(HDI_FULL, c);
     if (lane == 0) cnt[wid] = c;
 }
 
-// Local pixel codes (ly * 32 + lx) of the mask pixels of each subdomain, in
-// raster order, at list + off[i].
-__global__ void k_tonal_list(MaskView m, int nbx, int nby, int stride, const int* __restrict__ off,
+// Local pixel codes (ly * blk + lx) of the mask pixels of each subdomain,
+// in raster order, at list + off[i] (lane = row; rows 32.. in a second round).
+__global__ void k_tonal_list(MaskView m, int nbx, int nby, int stride, int blk, const int* __restrict__ off,
                              uint16_t* __restrict__ list, int* __restrict__ owner) {
     const int wid = blockIdx.x * 4 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (wid >= nbx * nby) return;
     const int by = wid / nbx, bx = wid - by * nbx;
-    const int x0 = sub_origin(bx, m.W, stride), y0 = sub_origin(by, m.H, stride);
-    const int w = min(32, m.W - x0), h = min(32, m.H - y0);
-    uint32_t bits = (lane < h) ? (m.window(x0, y0 + lane) & cols_valid(w)) : 0u;
-    int c = __popc(bits);
-    int incl = c;
+    const int x0 = sub_origin_n(bx, m.W, stride, blk), y0 = sub_origin_n(by, m.H, stride, blk);
+    const int w = min(blk, m.W - x0), h = min(blk, m.H - y0);
+    int base = off[wid];
+    for (int r0 = 0; r0 < blk; r0 += 32) {
+        const int ly = r0 + lane;
+        uint32_t bits[2] = {sub_row_bits(m, x0, y0, w, h, ly, 0), blk > 32 ? sub_row_bits(m, x0, y0, w, h, ly, 1) : 0u};
+        const int c = __popc(bits[0]) + __popc(bits[1]);
+        int incl = c;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(HDI_FULL, incl, o);
-        if (lane >= o) incl += t;
-    }
-    int pos = off[wid] + incl - c;
-    while (bits) {
-        const int lx = __ffs(bits) - 1;
-        bits &= bits - 1;
-        owner[pos] = wid;
-        list[pos++] = (uint16_t)(lane * 32 + lx);
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(HDI_FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int pos = base + incl - c;
+        for (int half = 0; half < 2; ++half) {
+            uint32_t b = bits[half];
+            while (b) {
+                const int lx = 32 * half + __ffs(b) - 1;
+                b &= b - 1;
+                owner[pos] = wid;
+                list[pos++] = (uint16_t)(ly * blk + lx);
+            }
+        }
+        base += __shfl_sync(HDI_FULL, incl, 31);
     }
 }
 
@@ -79,7 +96,7 @@ struct EchoArgs {
     const int* off;          // [nb + 1] exclusive prefix of m_i
     const uint16_t* list;
     const int* owner;        // [sum m_i] subdomain of each echo
-    float* echo;             // [sum m_i][32 rows][32 lanes]
+    float* echo;             // [sum m_i][blk rows][blk columns]
     float rtol2;
     int maxit;
     unsigned long long* iters;
@@ -122,6 +139,40 @@ __global__ void __launch_bounds__(kLocalThreads, 8) k_tonal_echo(EchoArgs a) {
     for (int k = 0; k < 8; ++k) *reinterpret_cast<float2*>(out + (r0 + k) * 32 + c0) = V[k];
 }
 
+// The same on 64x64 subdomains: one CTA of eight warps per (subdomain, mask
+// pixel k); x = S e_k stored row-major over the 64x64 tile.
+__global__ void __launch_bounds__(kL64Threads, 2) k_tonal_echo64(EchoArgs a) {
+    __shared__ Shared64 sh;
+    const long long e = blockIdx.x;
+    const int total = a.off[a.nb];
+    if (e >= total) return;
+    const int i = a.owner[e];
+    const int by = i / a.nbx, bx = i - by * a.nbx;
+    const int x0 = sub_origin_n(bx, a.m.W, a.stride, 64), y0 = sub_origin_n(by, a.m.H, a.stride, 64);
+    const Geom64 g = make_geom64(x0, y0, a.m.H, a.m.W, a.m, sh);
+    const int code = a.list[e];
+    const int ky = code >> 6, kx = code & 63;
+    const int c0 = 2 * g.cp, r0 = g.r0;
+    float2 R[8], V[8];
+    float2 a0 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int y = r0 + k;
+        const bool nx = (c0 == kx && (y == ky - 1 || y == ky + 1)) || (y == ky && (c0 == kx - 1 || c0 == kx + 1));
+        const bool ny =
+            (c0 + 1 == kx && (y == ky - 1 || y == ky + 1)) || (y == ky && (c0 + 1 == kx - 1 || c0 + 1 == kx + 1));
+        R[k].x = (nx && ((g.um >> (2 * k)) & 1u)) ? -1.f : 0.f;
+        R[k].y = (ny && ((g.um >> (2 * k + 1)) & 1u)) ? -1.f : 0.f;
+        a0 = __ffma2_rn(R[k], R[k], a0);
+    }
+    const float rr0 = cta_sum64(a0.x + a0.y, sh, 3);
+    const int it = cg64(g, sh, V, R, a.rtol2 * rr0, a.maxit);
+    if (a.iters && threadIdx.x == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
+    float* out = a.echo + (size_t)e * 4096;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) *reinterpret_cast<float2*>(out + (r0 + k) * 64 + c0) = V[k];
+}
+
 
 // Shared-memory floats of k_tonal_gram for subdomains of up to m mask pixels.
 __host__ __device__ inline int gram_round4(int m) { return (m + 3) & ~3; }
@@ -133,7 +184,7 @@ __host__ __device__ inline size_t gram_smem_floats(int m) {
 // G_i = I + S_i^T S_i and its inverse (full m x m, row-major) at
 // fac + goff[i]. One CTA of 256 threads per subdomain.
 // Products: each thread accumulates one 4x4 block of the lower triangle of G
-// (m rounded up to a multiple of 4); with few blocks the 1024 pixels are
+// (m rounded up to a multiple of 4); with few blocks the npx pixels are
 // split into ks interleaved slices whose partial blocks are added in a fixed
 // order. Pixels are staged 32 at a time in shared memory, transposed, so a
 // thread reads four echoes' values of one pixel with one 16-byte load.
@@ -144,7 +195,7 @@ __host__ __device__ inline size_t gram_smem_floats(int m) {
 // symmetric matrix-vector product.
 __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off, const long long* __restrict__ goff,
                                                     const float* __restrict__ echo, float* __restrict__ fac,
-                                                    unsigned* bad) {
+                                                    unsigned* bad, int npx) {
     extern __shared__ __align__(16) float sm[];
     const int i = blockIdx.x;
     const int m = off[i + 1] - off[i];
@@ -159,7 +210,7 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
     float* G = sm;                                 // m x gs
     float* Es = sm + (((size_t)m * gs + 3) & ~(size_t)3);   // [32][es], 16-byte aligned rows
     float* part = Es + 32 * es;                    // [ks][nblk][16] (ks > 1)
-    const float* E = echo + (size_t)off[i] * 1024;
+    const float* E = echo + (size_t)off[i] * npx;
     for (int b0 = 0; b0 < nblk; b0 += 256) {       // rounds of up to 256 blocks (ks == 1 when > 1 round)
         const int slot = tid % (ks > 1 ? nblk : 256);
         const int sl = tid / (ks > 1 ? nblk : 256);
@@ -177,11 +228,11 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-        for (int p0 = 0; p0 < 1024; p0 += 32) {
+        for (int p0 = 0; p0 < npx; p0 += 32) {
             __syncthreads();
             for (int q = tid; q < m4 * 32; q += 256) {
                 const int k = q >> 5, pp = q & 31;
-                Es[pp * es + k] = (k < m) ? E[(size_t)k * 1024 + p0 + pp] : 0.f;
+                Es[pp * es + k] = (k < m) ? E[(size_t)k * npx + p0 + pp] : 0.f;
             }
             __syncthreads();
             if (on) {
@@ -288,12 +339,12 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
 // product uses the same register blocks (pixels staged in shared memory); the
 // Cholesky factor and W = L^{-1} (as W^T in the upper triangle) are formed
 // in place, G_i^{-1} = W^T W is written to the subdomain's echo block, which
-// the product no longer needs (m_i x 1024 >= m_i x m_i floats), and copied
+// the product no longer needs (m_i x npx >= m_i x m_i floats), and copied
 // back. Threads own rows r = tid, tid + 256, ...
 __global__ void __launch_bounds__(256) k_tonal_gram_big(const int* __restrict__ off,
                                                         const long long* __restrict__ goff,
                                                         float* __restrict__ echo, float* __restrict__ fac,
-                                                        unsigned* bad) {
+                                                        unsigned* bad, int npx) {
     extern __shared__ __align__(16) float sm[];
     const int i = blockIdx.x;
     const int m = off[i + 1] - off[i];
@@ -308,7 +359,7 @@ __global__ void __launch_bounds__(256) k_tonal_gram_big(const int* __restrict__ 
     float* col = dinv + m4;                // [m]: the current column of L
     float* sd = col + m4;                  // [1]: the current diagonal
     float* G = fac + goff[i];              // m x m
-    float* E = echo + (size_t)off[i] * 1024;
+    float* E = echo + (size_t)off[i] * npx;
     // G = I + S^T S, lower triangle, 4x4 blocks
     for (long long b0 = 0; b0 < nblk; b0 += 256) {
         const long long bidx = b0 + tid;
@@ -325,11 +376,11 @@ __global__ void __launch_bounds__(256) k_tonal_gram_big(const int* __restrict__ 
         for (int aa = 0; aa < 4; ++aa)
 #pragma unroll
             for (int bb = 0; bb < 4; ++bb) acc[aa][bb] = 0.f;
-        for (int p0 = 0; p0 < 1024; p0 += 32) {
+        for (int p0 = 0; p0 < npx; p0 += 32) {
             __syncthreads();
             for (int q = tid; q < m4 * 32; q += 256) {
                 const int k = q >> 5, pp = q & 31;
-                Es[pp * es + k] = (k < m) ? E[(size_t)k * 1024 + p0 + pp] : 0.f;
+                Es[pp * es + k] = (k < m) ? E[(size_t)k * npx + p0 + pp] : 0.f;
             }
             __syncthreads();
             if (on) {
@@ -453,6 +504,7 @@ __global__ void __launch_bounds__(256) k_tonal_residual(LevelArr F, MaskView m, 
 struct LocalSolveArgs {
     LevelArr F;
     int nbx, nby, stride, nch, color;
+    int blk, lb;             // subdomain side (32 or 64) and its log2
     const int* off;
     const long long* goff;
     const uint16_t* list;
@@ -463,12 +515,12 @@ struct LocalSolveArgs {
 
 // Number of subdomains covering coordinate x along an axis of n pixels
 // (1 or 2; the last subdomain sits at sub_origin(nb - 1, n, stride)).
-__device__ __forceinline__ int cover_count(int x, int nb, int stride, int n) {
+__device__ __forceinline__ int cover_count(int x, int nb, int stride, int n, int blk) {
     if (nb == 1) return 1;
     const int hi = min(nb - 2, x / stride);
-    const int lo = max(0, (x - 31 + stride - 1) / stride);
+    const int lo = max(0, (x - (blk - 1) + stride - 1) / stride);
     int c = (hi >= lo) ? hi - lo + 1 : 0;
-    if (x >= sub_origin(nb - 1, n, stride)) ++c;
+    if (x >= sub_origin_n(nb - 1, n, stride, blk)) ++c;
     return c;
 }
 
@@ -493,7 +545,7 @@ __host__ __device__ __forceinline__ int class_member(int c, int q, int nb) { ret
 constexpr int kLocalWarps = 4;
 __global__ void __launch_bounds__(32 * kLocalWarps) k_tonal_local(LocalSolveArgs a) {
     constexpr int NT = 4;                 // rows of v per lane and pass: 128 per pass
-    __shared__ float xs[4 * kTonalMaxM];
+    extern __shared__ float xs[];   // [4][m]: the channels' r at the mask pixels
     __shared__ float ps[kLocalWarps][4][NT * 32];
     // Only the final accumulation into `out` depends on the previous colour's
     // launch (r and the factors were complete before the colours started), so
@@ -514,10 +566,10 @@ __global__ void __launch_bounds__(32 * kLocalWarps) k_tonal_local(LocalSolveArgs
     const int nch = a.nch;   // 1..4 (image channels)
     const uint16_t* lst = a.list + a.off[i];
     const float* __restrict__ Gi = a.fac + a.goff[i];
-    const int x0 = sub_origin(bx, a.F.W, a.stride), y0 = sub_origin(by, a.F.H, a.stride);
+    const int x0 = sub_origin_n(bx, a.F.W, a.stride, a.blk), y0 = sub_origin_n(by, a.F.H, a.stride, a.blk);
     auto pixel = [&](int k) {
         const int code = lst[k];
-        return (size_t)(y0 + (code >> 5)) * a.F.pitch + x0 + (code & 31);
+        return (size_t)(y0 + (code >> a.lb)) * a.F.pitch + x0 + (code & (a.blk - 1));
     };
     for (int k = threadIdx.x; k < m; k += 32 * kLocalWarps) {
         const size_t p = pixel(k);
@@ -558,8 +610,9 @@ __global__ void __launch_bounds__(32 * kLocalWarps) k_tonal_local(LocalSolveArgs
         __syncthreads();
         for (int k = threadIdx.x; k < NT * 32 && base + k < m; k += 32 * kLocalWarps) {
             const int code = lst[base + k];
-            const int px = x0 + (code & 31), py = y0 + (code >> 5);
-            const int mult = cover_count(px, a.nbx, a.stride, a.F.W) * cover_count(py, a.nby, a.stride, a.F.H);
+            const int px = x0 + (code & (a.blk - 1)), py = y0 + (code >> a.lb);
+            const int mult =
+                cover_count(px, a.nbx, a.stride, a.F.W, a.blk) * cover_count(py, a.nby, a.stride, a.F.H, a.blk);
             const size_t p = (size_t)py * a.F.pitch + px;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -579,9 +632,17 @@ __global__ void __launch_bounds__(32 * kLocalWarps) k_tonal_local(LocalSolveArgs
 
 int Ctx::tonal_setup() {
     int rc;
-    const Level& L0 = lev[0];
-    const int nb = L0.nbx * L0.nby;
-    const int stride = 32 - kOv;
+    // RAS subdomain side: 64 (the paper's block) couples the subdomains
+    // better at sparse masks, 32 keeps the local factors cheap at denser ones
+    // (measured crossover between 2% and 4% at 4K)
+    const double density = (double)mlist_n / ((double)H * W);
+    const int blk = (p.tonal_block >= 48) ? 64 : (p.tonal_block >= 16 ? 32 : (density < 0.03 ? 64 : 32));
+    const int npx = blk * blk;
+    const int stride = blk - kOv;
+    t_blk = blk;
+    t_nbx = tile_count(W, blk, kOv);
+    t_nby = tile_count(H, blk, kOv);
+    const int nb = t_nbx * t_nby;
     // counts
     std::vector<int> cnt(nb), off(nb + 1);
     std::vector<long long> goff(nb + 1);
@@ -589,7 +650,7 @@ int Ctx::tonal_setup() {
     const int ncnt = std::max(nb, H) + 1;
     if ((rc = tws.reserve(*this, std::max(tws.cap, (size_t)ncnt * 24 + 4096), "tonal counts"))) return rc;
     dcnt = (int*)tws.take((size_t)ncnt * 4);
-    k_tonal_count<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), L0.nbx, L0.nby, stride, dcnt);
+    k_tonal_count<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), t_nbx, t_nby, stride, blk, dcnt);
     ++launches;
     cudaMemcpyAsync(cnt.data(), dcnt, (size_t)nb * 4, cudaMemcpyDeviceToHost, stream);
     if ((rc = sync("tonal subdomain counts"))) return rc;
@@ -601,6 +662,7 @@ int Ctx::tonal_setup() {
         goff[i + 1] = goff[i] + (long long)cnt[i] * cnt[i];
         maxm = std::max(maxm, cnt[i]);
     }
+    t_maxm = maxm;
     const long long total = off[nb];
     const int M = mlist_n;   // the mask list (built by the caller)
     const int mwin = (int)p.tonal_anderson;
@@ -619,14 +681,14 @@ int Ctx::tonal_setup() {
     acc((size_t)(nb + 1) * 8);
     acc((size_t)total * 2);
     acc((size_t)total * 4);
-    acc((size_t)total * 1024 * 4);
+    acc((size_t)total * npx * 4);
     acc((size_t)goff[nb] * 4);
     if ((rc = tws.reserve(*this, bytes, "tonal local factors"))) return rc;
     t_off = (int*)tws.take((size_t)(nb + 1) * 4);
     t_goff = (long long*)tws.take((size_t)(nb + 1) * 8);
     t_list = (uint16_t*)tws.take((size_t)total * 2);
     int* t_owner = (int*)tws.take((size_t)total * 4);
-    t_echo = (float*)tws.take((size_t)total * 1024 * 4);
+    t_echo = (float*)tws.take((size_t)total * npx * 4);
     t_fac = (float*)tws.take((size_t)goff[nb] * 4);
     aa_idx = mlist;
     aa_fv = (float*)tws.take((size_t)nch * M * 4);
@@ -642,13 +704,13 @@ int Ctx::tonal_setup() {
     aa_M = M;
     cudaMemcpyAsync(t_off, off.data(), (size_t)(nb + 1) * 4, cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(t_goff, goff.data(), (size_t)(nb + 1) * 8, cudaMemcpyHostToDevice, stream);
-    k_tonal_list<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), L0.nbx, L0.nby, stride, t_off, t_list, t_owner);
+    k_tonal_list<<<(nb + 3) / 4, 128, 0, stream>>>(mview(0), t_nbx, t_nby, stride, blk, t_off, t_list, t_owner);
     ++launches;
     if (total > 0) {
         EchoArgs ea;
         ea.m = mview(0);
-        ea.nbx = L0.nbx;
-        ea.nby = L0.nby;
+        ea.nbx = t_nbx;
+        ea.nby = t_nby;
         ea.stride = stride;
         ea.nb = nb;
         ea.off = t_off;
@@ -659,19 +721,20 @@ int Ctx::tonal_setup() {
         ea.maxit = (int)p.tonal_echo_max_iter;
         ea.iters = counters + kCntEcho;
         tstart(kT_Echo);
-        k_tonal_echo<<<(unsigned)total, kLocalThreads, 0, stream>>>(ea);
+        if (blk == 64) k_tonal_echo64<<<(unsigned)total, kL64Threads, 0, stream>>>(ea);
+        else k_tonal_echo<<<(unsigned)total, kLocalThreads, 0, stream>>>(ea);
         ++launches;
         tstop();
         const size_t shm = gram_smem_floats(std::min(maxm, kGramSmem)) * 4;
         cudaFuncSetAttribute(k_tonal_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         cudaMemsetAsync(flags, 0, 4, stream);
         tstart(kT_Gram);
-        k_tonal_gram<<<nb, 256, shm, stream>>>(t_off, t_goff, t_echo, t_fac, flags);
+        k_tonal_gram<<<nb, 256, shm, stream>>>(t_off, t_goff, t_echo, t_fac, flags, npx);
         ++launches;
         if (maxm > kGramSmem) {
             const size_t shb = ((size_t)32 * (gram_round4(maxm) + 4) + 2 * gram_round4(maxm) + 4) * 4;
             cudaFuncSetAttribute(k_tonal_gram_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
-            k_tonal_gram_big<<<nb, 256, shb, stream>>>(t_off, t_goff, t_echo, t_fac, flags);
+            k_tonal_gram_big<<<nb, 256, shb, stream>>>(t_off, t_goff, t_echo, t_fac, flags, npx);
             ++launches;
         }
         tstop();
@@ -718,14 +781,18 @@ int Ctx::mask_list() {
 }
 
 void Ctx::tonal_local(float* out) {
-    const Level& L0 = lev[0];
+    const size_t shm = (size_t)4 * std::max(t_maxm, 1) * 4;
+    if (shm > 48 * 1024)
+        cudaFuncSetAttribute(k_tonal_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     tstart(kT_Local);   // the nine colour launches as one timed unit
     for (int color = 0; color < 9; ++color) {
         LocalSolveArgs a;
         a.F = arr(0);
-        a.nbx = L0.nbx;
-        a.nby = L0.nby;
-        a.stride = 32 - kOv;
+        a.nbx = t_nbx;
+        a.nby = t_nby;
+        a.stride = t_blk - kOv;
+        a.blk = t_blk;
+        a.lb = (t_blk == 64) ? 6 : 5;
         a.nch = nch;
         a.color = color;
         a.off = t_off;
@@ -734,11 +801,21 @@ void Ctx::tonal_local(float* out) {
         a.fac = t_fac;
         a.r = tres;
         a.out = out;
-        const int hx = class_count(color % 3, L0.nbx);
-        const int hy = class_count(color / 3, L0.nby);
+        const int hx = class_count(color % 3, t_nbx);
+        const int hy = class_count(color / 3, t_nby);
         const long long blocks = (long long)hx * hy;
         if (blocks <= 0) continue;
-        launch_k(p.pdl >= 0.5, k_tonal_local, dim3((unsigned)blocks), dim3(32 * kLocalWarps), stream, a);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)blocks);
+        cfg.blockDim = dim3(32 * kLocalWarps);
+        cfg.dynamicSmemBytes = shm;
+        cfg.stream = stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = (p.pdl >= 0.5) ? 1 : 0;
+        cudaLaunchKernelEx(&cfg, k_tonal_local, a);
         ++launches;
     }
     tstop();

@@ -91,3 +91,29 @@ def test_dense_subdomains(H, W, d, block):
     assert normal_residual(f64, c, g.astype(np.float64)).max() <= 2e-6
     assert np.abs(g - ref).max() <= 0.05
     assert np.all(g[:, c == 0] == 0)
+
+
+@pytest.mark.parametrize("H,W,d,seed", [(150, 210, 0.005, 31), (77, 131, 0.02, 32), (130, 60, 0.1, 33),
+                                        (40, 50, 0.05, 34)])
+def test_block64_reaches_the_optimum(H, W, d, seed):
+    """RAS on 64x64 subdomains (the paper's block size, tonal_block = 64): the
+    same minimiser as the oracle, including images narrower than a block."""
+    f = synth_rgb(H, W, seeds=(seed, seed + 10, seed + 20), dtype=np.float32)
+    c = random_mask(H, W, d, seed + 100)
+    if c.sum() == 0:
+        c[H // 2, W // 2] = 1
+    g, st = run(f, c, 1e-6, tonal_block=64)
+    f64 = f.astype(np.float64)
+    ref = tonal_ref(f64, c)
+    assert st["rel_res"] <= 1e-6
+    assert normal_residual(f64, c, g.astype(np.float64)).max() <= 2e-6
+    assert np.abs(g - ref).max() <= 0.05
+    assert np.all(g[:, c == 0] == 0)
+
+
+def test_block64_gray_fp64_tight():
+    f = synth_image(200, 180, 35)
+    c = random_mask(200, 180, 0.01, 36)
+    g, st = run(f, c, 1e-10, tonal_block=64)
+    assert st["rel_res"] <= 1e-10
+    assert np.abs(g - tonal_ref(f, c)).max() <= 1e-5
