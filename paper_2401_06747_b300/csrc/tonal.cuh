@@ -5,7 +5,8 @@
 //      (A~ acts on U as L_UU, Sec. 5.1); r_K = (f - y)_K + sum_{n in N(k) cap U} w_n.
 //      Both solves are warm-started from the previous outer iteration
 //      (Sec. 5.2, first paragraph after Alg. 2).
-//   2. For every 32x32 subdomain i (overlap 6, the ORAS tiling of level 0):
+//   2. For every subdomain i (32x32, the ORAS tiling of level 0, or the
+//      paper's 64x64, overlap 6 in both):
 //      B_i^T B_i v_i = R_i r with B_i the subdomain's inpainting operator under
 //      homogeneous Neumann conditions at the subdomain boundary (Sec. 5.2).
 //   3. g <- g + sum_i R_i^T D_i v_i, D_i = 1 / multiplicity ("simple
@@ -15,10 +16,12 @@
 // matrices B_i^T B_i = I + S_i^T S_i (S_i = L_UU,i^{-1} L_UK,i, in the mask
 // pixel coordinates of the subdomain) are the same in every outer iteration.
 // They are built once per call: S_i e_k (the negated local inpainting echo of
-// mask pixel k) by warp-level CG on the Neumann subdomain problem, the Gram
-// matrix I + S^T S by a small tiled product, and its Cholesky factor in
-// shared memory. Each outer iteration then solves the local systems exactly
-// by two triangular solves instead of the paper's inner CGNR iterations.
+// mask pixel k) by CG on the Neumann subdomain problem (two warps per 32x32
+// subdomain, eight per 64x64 one), the Gram matrix I + S^T S by a tiled
+// product, its Cholesky factor and from it the explicit inverse. Each outer
+// iteration then solves the local systems exactly by one dense symmetric
+// matrix-vector product per subdomain instead of the paper's inner CGNR
+// iterations.
 #pragma once
 #include "oras.cuh"
 #include "anderson.cuh"
