@@ -234,7 +234,8 @@ const char* hdi_version(void);
  *                             improves the MSE by less than this relative amount (Sec. 6: 1e-3)
  *   tonal_block       [0]     RAS subdomain side: 32 or 64 (the paper's 64, overlap 6); 0 picks 64
  *                             below 3% mask density and 32 above (64 converges in fewer outer
- *                             iterations at sparse masks, 32 keeps the local factors cheap at dense ones)
+ *                             iterations at sparse masks, 32 keeps the local factors cheap at dense ones;
+ *                             a 64x64 block holding more than 1024 mask pixels switches the call to 32)
  *   tonal_init        [0]     0: start from g0 (f on the mask if g0 is NULL); 1: first run the
  *                             Voronoi initialisation (Sec. 5.3) from f: Richardson steps
  *                             g += vi_tau C W (f - A^-1 C g), one inpainting each, kept while the MSE falls

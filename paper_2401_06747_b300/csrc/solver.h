@@ -204,6 +204,7 @@ struct Ctx {
     int inpaint_batch(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, hdi_stats* st);
     int read_slot(int slot, double* out);
     int tonal_setup();
+    int tonal_setup_blk(int blk);
     int t_blk = 32, t_nbx = 0, t_nby = 0, t_maxm = 0;   // RAS tiling of the last tonal set-up
     void tonal_residual(DFc y, DFc w);
     void tonal_local(float* out);

@@ -634,12 +634,21 @@ __global__ void __launch_bounds__(32 * kLocalWarps) k_tonal_local(LocalSolveArgs
 // ------------------------------------------------------------ the driver ---
 
 int Ctx::tonal_setup() {
-    int rc;
     // RAS subdomain side: 64 (the paper's block) couples the subdomains
     // better at sparse masks, 32 keeps the local factors cheap at denser ones
     // (measured crossover between 2% and 4% at 4K)
     const double density = (double)mlist_n / ((double)H * W);
     const int blk = (p.tonal_block >= 48) ? 64 : (p.tonal_block >= 16 ? 32 : (density < 0.03 ? 64 : 32));
+    int rc = tonal_setup_blk(blk);
+    // a 64x64 block with more than 1024 mask pixels (a densely known region)
+    // would need an m x m factorisation of up to 4096^2 in one CTA: such masks
+    // take the 32x32 blocks instead
+    if (rc == HDI_OK && blk == 64 && t_maxm > 1024) rc = tonal_setup_blk(32);
+    return rc;
+}
+
+int Ctx::tonal_setup_blk(int blk) {
+    int rc;
     const int npx = blk * blk;
     const int stride = blk - kOv;
     t_blk = blk;
@@ -666,6 +675,7 @@ int Ctx::tonal_setup() {
         maxm = std::max(maxm, cnt[i]);
     }
     t_maxm = maxm;
+    if (blk == 64 && maxm > 1024) return HDI_OK;   // the caller retries with 32x32 blocks
     const long long total = off[nb];
     const int M = mlist_n;   // the mask list (built by the caller)
     const int mwin = (int)p.tonal_anderson;

@@ -117,3 +117,17 @@ def test_block64_gray_fp64_tight():
     g, st = run(f, c, 1e-10, tonal_block=64)
     assert st["rel_res"] <= 1e-10
     assert np.abs(g - tonal_ref(f, c)).max() <= 1e-5
+
+
+def test_block64_falls_back_on_a_densely_known_block():
+    """A fully known 70x70 region at 1% density elsewhere: some 64x64 block holds
+    more than 1024 mask pixels, so the call runs on 32x32 blocks; the result is
+    still the optimum."""
+    H, W = 160, 200
+    f = synth_rgb(H, W, seeds=(41, 42, 43), dtype=np.float32)
+    c = random_mask(H, W, 0.01, 44)
+    c[40:110, 60:130] = 1
+    g, st = run(f, c, 1e-6, tonal_block=64)
+    f64 = f.astype(np.float64)
+    assert st["rel_res"] <= 1e-6
+    assert np.abs(g - tonal_ref(f64, c)).max() <= 0.05
