@@ -61,12 +61,14 @@ __device__ __forceinline__ LocalGeom make_geom(int x0, int y0, int H, int W, con
     g.c = lane & 15;
     g.r0 = 16 * (t >> 5) + 8 * (lane >> 4);
     const int c0 = 2 * g.c;
-    // lane l of each warp fetches the mask word of row l (rows past the subdomain read as known)
-    const uint32_t wrow = (lane < g.h) ? m.window(x0, y0 + lane) : ~0u;
+    // lane l < 16 of warp w fetches the mask word of row 16 w + l, the warp's
+    // rows (rows past the subdomain read as known)
+    const int wr = 16 * (t >> 5) + (lane & 15);
+    const uint32_t wrow = (lane < 16 && wr < g.h) ? m.window(x0, y0 + wr) : ~0u;
     uint32_t um = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const uint32_t kn = __shfl_sync(HDI_FULL, wrow, g.r0 + k) >> c0;   // bit 0: column c0, bit 1: c0 + 1
+        const uint32_t kn = __shfl_sync(HDI_FULL, wrow, g.r0 - 16 * (t >> 5) + k) >> c0;   // bit 0: column c0, bit 1: c0 + 1
         const bool u0 = c0 < g.w && !(kn & 1u), u1 = c0 + 1 < g.w && !(kn & 2u);
         um |= (u0 ? 1u : 0u) << (2 * k);
         um |= (u1 ? 1u : 0u) << (2 * k + 1);
