@@ -176,9 +176,10 @@ __device__ __forceinline__ int local_cg(const LocalGeom& g, LocalShared& sh, flo
         // rows r0-1 / r0+8: the other octet of the warp, or the other warp
         const float2 xu = shfl_xor2(P[7], 16), xd = shfl_xor2(P[0], 16);
         const float2 b2 = make_float2(beta, beta);
-        float2 up = xu, dn = xd;
-        if (oct == 0) up = __ffma2_rn(b2, sh.seam[par][0][1][g.c], sh.seam[par][0][0][g.c]);
-        if (oct == 1) dn = __ffma2_rn(b2, sh.seam[par][1][1][g.c], sh.seam[par][1][0][g.c]);
+        // octet 0 takes row 15 (its row above), octet 1 row 16 (its row below):
+        // one pair of loads per thread, addressed by the octet
+        const float2 sn = __ffma2_rn(b2, sh.seam[par][oct][1][g.c], sh.seam[par][oct][0][g.c]);
+        const float2 up = (oct == 0) ? sn : xu, dn = (oct == 1) ? sn : xd;
         local_apply<FULL>(g, sh, P, up, dn, Q);
         a0 = make_float2(0.f, 0.f);
         a1 = a0;
