@@ -173,13 +173,14 @@ __device__ __forceinline__ int local_cg(const LocalGeom& g, LocalShared& sh, flo
     int it = 0;
     while (rr > thresh && it < maxit) {
         const int par = it & 1;
-        // rows r0-1 / r0+8: the other octet of the warp, or the other warp
-        const float2 xu = shfl_xor2(P[7], 16), xd = shfl_xor2(P[0], 16);
+        // rows r0-1 / r0+8: one comes from the other octet of the warp (octet
+        // 0 sends its last row, octet 1 its first, one exchange), the other
+        // from the other warp through shared memory (octet 0 takes row 15,
+        // octet 1 row 16: one pair of loads, addressed by the octet)
+        const float2 xo = shfl_xor2((oct == 0) ? P[7] : P[0], 16);
         const float2 b2 = make_float2(beta, beta);
-        // octet 0 takes row 15 (its row above), octet 1 row 16 (its row below):
-        // one pair of loads per thread, addressed by the octet
         const float2 sn = __ffma2_rn(b2, sh.seam[par][oct][1][g.c], sh.seam[par][oct][0][g.c]);
-        const float2 up = (oct == 0) ? sn : xu, dn = (oct == 1) ? sn : xd;
+        const float2 up = (oct == 0) ? sn : xo, dn = (oct == 1) ? sn : xo;
         local_apply<FULL>(g, sh, P, up, dn, Q);
         a0 = make_float2(0.f, 0.f);
         a1 = a0;
