@@ -176,11 +176,10 @@ __device__ __forceinline__ StripHalo strip_halo(int lane, int px, int pxc, int W
 // stacks four warps on consecutive row blocks of one strip. Lanes 0 and 31
 // read the neighbouring strips' edge columns; lanes past the image still
 // take part in the shuffles with clamped loads. Rows are walked in chunks of
-// QS_CHUNK, every load of a chunk issued before its arithmetic. The
-// prolongation keeps two chunk buffers (the next chunk's loads in flight
-// while the current one is computed); the residual and restriction kernels
-// keep one and run at 64-72 registers instead, so that more resident warps
-// hide the load latency (measured faster on the 4K RGB workload).
+// QS_CHUNK, every load of a chunk issued before its arithmetic. The kernels
+// keep one chunk buffer and run at 64-72 registers (7-8 CTAs per SM): more
+// resident warps hide the load latency better than a second buffer with the
+// next chunk's loads in flight (measured faster on the 4K RGB workload).
 #define QS_COLS 128
 #define QS_CHUNK 2
 
@@ -450,7 +449,7 @@ __global__ void __launch_bounds__(128, 8) k_level_residual_norm(LevelArr F, Mask
 // column without further coarse loads. Each coarse row is interpolated once
 // and reused by the fine rows above and below it.
 template <int MODE>
-__global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const float* __restrict__ xin,
+__global__ void __launch_bounds__(128, 7) k_prolong(LevelArr F, MaskView fm, const float* __restrict__ xin,
                                                  const float* __restrict__ b, float* __restrict__ xout,
                                                  LevelArr C, const float* __restrict__ e, GridReduce red, int rows) {
     constexpr int CR = QS_CHUNK;
@@ -614,14 +613,10 @@ __global__ void __launch_bounds__(128) k_prolong(LevelArr F, MaskView fm, const 
                 SH[j] = SH[NS - 2 + j];
             }
         };
-        Chunk A, B;
-        load(A, y0);
-        for (int yb = y0; yb < y1; yb += 2 * CR) {
-            if (yb + CR < y1) load(B, yb + CR);
+        for (int yb = y0; yb < y1; yb += CR) {
+            Chunk A;
+            load(A, yb);
             compute(A, yb);
-            if (yb + CR >= y1) break;
-            if (yb + 2 * CR < y1) load(A, yb + 2 * CR);
-            compute(B, yb + CR);
         }
     }
     const double tot = (double)block_sum_f(sq);
