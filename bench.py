@@ -192,9 +192,15 @@ def all_max(x: float, world: int) -> float:
 # Algorithmic bytes per pixel and channel of one launch of each timed class
 # (FP32 = 4 B, double-float = 8 B, bit-packed mask = 1/8 B):
 #   oras_fine     : read x, b, mask; write x                      12.125
+#                   (8.125 for a sweep that starts from x = 0)
 #   residual_fine : read u (8), e (4), mask; write u (8), r (4)   24.125
+#                   for the inpainting update; the library counts each
+#                   variant (the tonal adjoint form also reads d and y,
+#                   8 B each: 40.125)
 #   prolong_fine  : read x, b, e_H/4, mask; write x               13.125
 #   restrict_fine : read x, b, mask; write b_H/4                   9.125
+# The library sums these per timed launch (Context.timing_bytes); the table
+# is the fallback for a library that reports none.
 ALGO_BYTES_PER_VALUE = {"oras_fine": 12.125, "residual_fine": 24.125, "prolong_fine": 13.125,
                         "restrict_fine": 9.125}
 # The level-0 ORAS sweep is bound by FP32 arithmetic, not by HBM: its local CG
@@ -257,6 +263,7 @@ def run_hdi(args, rank, world):
     torch.cuda.synchronize()
     barrier(world)
     launches = ctx.launch_count() - l0
+    kb = ctx.timing_bytes()
     kt = ctx.timing(enable=False, reset=True)
     clocks = sampler.stop()
     t_max = all_max(total_ms, world)
@@ -282,7 +289,7 @@ def run_hdi(args, rank, world):
 
     def hbm_entry(k):
         kms, kn = kt[k]
-        b = ALGO_BYTES_PER_VALUE[k] * values
+        b = kb.get(k, 0.0) / kn if kn and kb.get(k, 0.0) > 0 else ALGO_BYTES_PER_VALUE[k] * values
         gbs = b / ((kms / max(kn, 1)) / 1e3) / 1e9 if kn else 0.0
         return {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
                 "algorithmic_bytes_per_launch": b, "launches": kn, "avg_ms": round(kms / max(kn, 1), 4)}

@@ -183,6 +183,17 @@ int64_t hdi_launch_count(const hdi_ctx* ctx);
 int hdi_timing(hdi_ctx* ctx, int enable, int reset, double* ms, int64_t* launches);
 const char* hdi_timing_name(int i);
 
+/* Algorithmic HBM bytes of the launches hdi_timing has timed since its last
+ * reset, per class (same order): for each launch, the bytes its arithmetic
+ * must move once per value of the finest level (iterate, right-hand side,
+ * mask bits, outputs; no halo or overlap re-reads), summed. The streaming
+ * classes count them (oras_fine, residual_fine, prolong_fine, restrict_fine);
+ * the others report 0. Divided by the class's milliseconds it gives the
+ * achieved bandwidth. bytes: HDI_TIMING_CLASSES doubles (out). Drains the
+ * context's stream like hdi_timing. Returns HDI_ERR_INVALID_ARG for a null
+ * argument. */
+int hdi_timing_bytes(hdi_ctx* ctx, double* bytes);
+
 /* Inpainting that allocates no device memory. The paper has no counterpart;
  * this entry point exists for callers that cannot call cudaMalloc while they
  * run, for instance code executing inside a CUDA stream capture, a real-time

@@ -55,7 +55,7 @@ class Stats(ctypes.Structure):
 
 SYMBOLS = ["hdi_create", "hdi_destroy", "hdi_set_param", "hdi_get_param", "hdi_inpaint",
            "hdi_tonal_opt", "hdi_densify_step", "hdi_densify", "hdi_last_error", "hdi_version", "hdi_launch_count",
-           "hdi_timing", "hdi_timing_name", "hdi_inpaint_noalloc", "hdi_inpaint_batch"]
+           "hdi_timing", "hdi_timing_bytes", "hdi_timing_name", "hdi_inpaint_noalloc", "hdi_inpaint_batch"]
 TIMING_CLASSES = 8
 
 _lib = None
@@ -87,6 +87,7 @@ def load(path: str | None = None):
     lib.hdi_launch_count.argtypes = [ctypes.c_void_p]
     lib.hdi_launch_count.restype = ctypes.c_int64
     lib.hdi_timing.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int64)]
+    lib.hdi_timing_bytes.argtypes = [ctypes.c_void_p, P(ctypes.c_double)]
     lib.hdi_timing_name.restype = ctypes.c_char_p
     lib.hdi_inpaint_batch.argtypes = [ctypes.c_void_p, ctypes.c_int, P(Image), P(Mask), P(Image), ctypes.c_double,
                                       P(Stats)]
@@ -237,6 +238,13 @@ class Context:
         n = (ctypes.c_int64 * TIMING_CLASSES)()
         self._check(self.lib.hdi_timing(self.h, int(enable), int(reset), ms, n))
         return {self.lib.hdi_timing_name(i).decode(): (ms[i], n[i]) for i in range(TIMING_CLASSES)}
+
+    def timing_bytes(self) -> dict:
+        """Algorithmic HBM bytes of the timed launches per class {name: bytes}
+        since the last timing reset (0 for the classes that do not count them)."""
+        b = (ctypes.c_double * TIMING_CLASSES)()
+        self._check(self.lib.hdi_timing_bytes(self.h, b))
+        return {self.lib.hdi_timing_name(i).decode(): b[i] for i in range(TIMING_CLASSES)}
 
 
 def inpaint_noalloc(f, mask, out, tol: float = 1e-6, device: int = 0, stream=None) -> dict:

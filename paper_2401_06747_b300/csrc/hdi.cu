@@ -128,10 +128,11 @@ size_t Ctx::other_bytes() const { return ws.cap + tws.cap + dws.cap + vws.cap + 
 
 // Device-time bookkeeping per kernel class (CUDA events on the context's
 // stream around each timed launch; resolved after the stream drains).
-void Ctx::tstart(int cls) {
+void Ctx::tstart(int cls, double bytes) {
     if (!timing || !tev) return;
     if (tn >= kMaxTimed && tflush()) return;
     tcls[tn] = cls;
+    tbyt[tn] = bytes;
     cudaEventRecord(tev[2 * tn], stream);
 }
 void Ctx::tstop() {
@@ -148,6 +149,7 @@ int Ctx::tflush() {
         cudaEventElapsedTime(&ms, tev[2 * i], tev[2 * i + 1]);
         ttot[tcls[i]] += ms;
         tcnt[tcls[i]] += 1;
+        tbytes[tcls[i]] += tbyt[i];
     }
     tn = 0;
     return HDI_OK;
@@ -306,7 +308,8 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     a.rnorm2 = rnorm2;
     a.iters = iters;
     const dim3 blocks(L.nbx, L.nby, nch);   // one CTA per (subdomain, channel)
-    if (l == 0) tstart(kT_Oras);
+    // read x (unless it starts at 0), b and the mask bits, write x: once per value
+    if (l == 0) tstart(kT_Oras, (zero ? 8.125 : 12.125) * (double)nch * L.H * L.W);
     const bool full = L.W >= 32 && L.H >= 32;
     const bool pd = p.pdl >= 0.5;
     if (zero) {
@@ -353,7 +356,8 @@ void Ctx::vcycle(int l) {
     {
         const int qr = quad_rows(L.H, L.W, nch);
         dim3 blk(128), grd = quad_grid(L.H, L.W, nch, qr);
-        if (l == 0) tstart(kT_Restrict);
+        // read x, b and the mask bits, write a quarter value of b_H per value
+        if (l == 0) tstart(kT_Restrict, 9.125 * (double)nch * L.H * L.W);
         launch_k(p.pdl >= 0.5, k_restrict_residual, grd, blk, stream, arr(l), mview(l), (const float*)L.xa,
                  (const float*)L.b, arr(l + 1), mview(l + 1), C.b, reducer(l + 1, grd.x * grd.y), qr);
         ++launches;
@@ -363,7 +367,8 @@ void Ctx::vcycle(int l) {
     {
         const int qr = quad_rows(L.H, L.W, nch);
         dim3 grd = quad_grid(L.H, L.W, nch, qr), blk(128);
-        if (l == 0) tstart(kT_Prolong);
+        // read x, b, a quarter value of e_H and the mask bits, write x
+        if (l == 0) tstart(kT_Prolong, 13.125 * (double)nch * L.H * L.W);
         launch_k(p.pdl >= 0.5, k_prolong<0>, grd, blk, stream, arr(l), mview(l), (const float*)L.xa,
                  (const float*)L.b, L.xb, arr(l + 1), (const float*)C.xa, reducer(l, grd.x * grd.y), qr);
         ++launches;
@@ -442,7 +447,15 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
     a.red_r = c.reducer(kSlotR64, grd.x * grd.y);
     a.red_b = c.reducer(kSlotB64, grd.x * grd.y);
     a.want_b = want_b ? 1 : 0;
-    c.tstart(kT_Residual);
+    // algorithmic bytes per value: write u (double-float) and r (FP32), read
+    // the mask bits, u, e, the source terms d and y as the variant needs them
+    // (the data that INIT_KEEP / FROM32 / ZERO take on known pixels only is
+    // not counted)
+    constexpr bool HAS_U = (INIT == INIT_KEEP || INIT == INIT_UPDATE);
+    constexpr bool HAS_E = (INIT == INIT_UPDATE || INIT == INIT_FROM32);
+    const double bpv = 12.125 + (HAS_U ? 8.0 : 0.0) + (HAS_E ? 4.0 : 0.0) +
+                       (RHS == RHS_SOURCE ? 8.0 + (y.hi ? 8.0 : 0.0) : 0.0);
+    c.tstart(kT_Residual, bpv * (double)c.nch * c.H * c.W);
     launch_k(c.p.pdl >= 0.5, k_residual_df<RHS, INIT>, grd, blk, c.stream, a);
     ++c.launches;
     c.tstop();
@@ -802,12 +815,21 @@ int hdi_timing(hdi_ctx* h, int enable, int reset, double* ms, int64_t* launches)
     if (launches)
         for (int i = 0; i < HDI_TIMING_CLASSES; ++i) launches[i] = c->tcnt[i];
     if (reset)
-        for (int i = 0; i < HDI_TIMING_CLASSES; ++i) { c->ttot[i] = 0.0; c->tcnt[i] = 0; }
+        for (int i = 0; i < HDI_TIMING_CLASSES; ++i) { c->ttot[i] = 0.0; c->tcnt[i] = 0; c->tbytes[i] = 0.0; }
     if (enable && !c->tev) {
         c->tev = new cudaEvent_t[2 * kMaxTimed];
         for (int i = 0; i < 2 * kMaxTimed; ++i) cudaEventCreate(&c->tev[i]);
     }
     c->timing = enable != 0;
+    return HDI_OK;
+}
+
+int hdi_timing_bytes(hdi_ctx* h, double* bytes) {
+    if (!h || !bytes) return HDI_ERR_INVALID_ARG;
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    int rc = c->tflush();
+    if (rc) return rc;
+    for (int i = 0; i < HDI_TIMING_CLASSES; ++i) bytes[i] = c->tbytes[i];
     return HDI_OK;
 }
 

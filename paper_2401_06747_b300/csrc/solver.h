@@ -157,9 +157,11 @@ struct Ctx {
     cudaEvent_t* tev = nullptr;
     int tn = 0;
     int tcls[kMaxTimed];
+    double tbyt[kMaxTimed];
     double ttot[HDI_TIMING_CLASSES] = {};
     int64_t tcnt[HDI_TIMING_CLASSES] = {};
-    void tstart(int cls);
+    double tbytes[HDI_TIMING_CLASSES] = {};
+    void tstart(int cls, double bytes = 0.0);   // bytes: algorithmic HBM bytes of the launch
     void tstop();
     int tflush();
     // tonal local factors (valid for the mask of the current tonal call)

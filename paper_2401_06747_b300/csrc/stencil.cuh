@@ -268,7 +268,7 @@ __device__ __forceinline__ void quad_residual_interior(int lane, const float (&c
 // channel. Quad strips: the lane's four columns feed two coarse columns.
 // Warps whose strip and row block (with the rows above and below) lie inside
 // the image run a variant without border tests or clamped rows (IN).
-__global__ void __launch_bounds__(128, 8) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
+__global__ void __launch_bounds__(128, 7) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
                                                            const float* __restrict__ b, LevelArr C, MaskView cm,
                                                            float* __restrict__ cb, GridReduce red, int rows) {
     constexpr int CR = QS_CHUNK;

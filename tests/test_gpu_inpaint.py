@@ -117,3 +117,36 @@ def test_errors():
     with pytest.raises(hdi.HdiError) as e:
         k.inpaint(fn, dev(random_mask(20, 20, 0.1, 1)), out)
     assert e.value.code == -6
+
+
+def test_timing_classes_and_algorithmic_bytes():
+    """The per-class event timing and the library's algorithmic byte counts:
+    one inpainting and one tonal optimisation with timing on; every
+    streaming class reports the bytes its launches must move (13.125 B per
+    value for the prolongation, 9.125 for the restriction, 8.125-12.125 for
+    the ORAS sweeps, 24.125 for the inpainting residual update and up to
+    40.125 for the tonal adjoint residual), the others none."""
+    need_gpu()
+    H, W = 200, 260
+    f = synth_rgb(H, W, seeds=(61, 62, 63), dtype=np.float32)
+    c = random_mask(H, W, 0.04, 64)
+    k = ctx()
+    fd, cd = dev(f), dev(c)
+    out = torch.empty_like(fd)
+    values = 3 * H * W
+    k.timing(enable=True, reset=True)
+    k.inpaint(fd, cd, out, tol=1e-6)
+    b, t = k.timing_bytes(), k.timing(enable=True, reset=True)
+    for name, bpv in (("prolong_fine", 13.125), ("restrict_fine", 9.125)):
+        assert t[name][1] > 0 and b[name] == pytest.approx(bpv * values * t[name][1], rel=1e-12)
+    n = t["oras_fine"][1]
+    assert n > 0 and 8.125 * values * n <= b["oras_fine"] <= 12.125 * values * n
+    n = t["residual_fine"][1]
+    assert n > 0 and 12.125 * values * n <= b["residual_fine"] <= 24.125 * values * n
+    assert all(b[x] == 0.0 for x in ("tonal_echo", "tonal_gram", "tonal_local", "anderson"))
+    k.tonal_opt(fd, cd, out, tol=1e-6)
+    b, t = k.timing_bytes(), k.timing(enable=False, reset=True)
+    n = t["residual_fine"][1]
+    assert b["residual_fine"] > 24.125 * values * n / 2 and b["residual_fine"] <= 40.125 * values * n
+    assert t["tonal_echo"][1] > 0 and b["tonal_echo"] == 0.0
+    assert all(v[0] > 0 for x, v in t.items() if v[1] > 0)
