@@ -145,13 +145,17 @@ __global__ void __launch_bounds__(256) k_aa_gather(AAArgs a, int new_slot) {
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int c = 0; c < a.nch; ++c)
-        for (int q = 0; q < ND; ++q) {
-            double s = 0.0;
-            for (int p = threadIdx.x; p < a.nparts; p += 256) s += __ldcg(a.partials + ((size_t)c * ND + q) * a.nparts + p);
-            s = block_sum_d(s);
-            if (threadIdx.x == 0) a.out[c * ND + q] = s;
-        }
+    // the last CTA sums the partials of every (channel, dot) pair, one warp
+    // per pair (fixed order: lane-strided sums, then the warp tree), with no
+    // block-wide barrier between pairs
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < a.nch * ND; j += 8) {
+        const double* src = a.partials + (size_t)j * a.nparts;   // [channel][dot] = j
+        double s = 0.0;
+        for (int p = lane; p < a.nparts; p += 32) s += __ldcg(src + p);
+        s = warp_sum_d(s);
+        if (lane == 0) a.out[j] = s;
+    }
     if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
