@@ -96,27 +96,56 @@ __global__ void __launch_bounds__(256) k_aa_gather(AAArgs a, int new_slot) {
     };
     const size_t co = (size_t)ch * a.M;
     const size_t vs = (size_t)a.nch * a.M;   // stride between window slots
-    for (int i = part * 256 + threadIdx.x; i < a.M; i += a.nparts * 256) {
-        const float f = a.fvfull[ch * a.cs + a.idx[i]];
-        a.fv[co + i] = f;
-        if (new_slot >= 0) {
-            a.dF[(size_t)new_slot * vs + co + i] = f - a.fvprev[co + i];
+    const int stride = a.nparts * 256;
+    // U elements per thread and round: all their loads are issued before the
+    // arithmetic (the kernel runs one or two CTAs per SM, so the load latency
+    // is hidden by loads in flight rather than by resident warps). The
+    // newest difference dF[slot] is formed here (f_n - f_{n-1}); the older
+    // ones are read.
+    constexpr int U = 4;
+    constexpr int KD = K > 0 ? K : 1;
+    for (int i0 = part * 256 + threadIdx.x; i0 < a.M; i0 += U * stride) {
+        int ix[U];
+        float f[U], fp[U], d[U][KD];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * stride;
+            ix[u] = (i < a.M) ? a.idx[i] : 0;
         }
-        a.fvprev[co + i] = f;
-        if (K > 0) {
-            float d[K > 0 ? K : 1];
 #pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const int s = (a.slot - j + a.mwin * 4) % a.mwin;
-                d[j] = a.dF[(size_t)s * vs + co + i];
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * stride;
+            const bool ok = i < a.M;
+            f[u] = ok ? a.fvfull[ch * a.cs + ix[u]] : 0.f;
+            fp[u] = ok ? a.fvprev[co + i] : 0.f;
+#pragma unroll
+            for (int j = 1; j < K; ++j) {
+                const int sl = (a.slot - j + a.mwin * 4) % a.mwin;
+                d[u][j] = ok ? a.dF[(size_t)sl * vs + co + i] : 0.f;
             }
-            int q = 0;
+        }
 #pragma unroll
-            for (int r = 0; r < K; ++r)
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * stride;
+            if (i >= a.M) break;
+            const float df = f[u] - fp[u];
+            a.fv[co + i] = f[u];
+            if (new_slot >= 0) a.dF[(size_t)new_slot * vs + co + i] = df;   // slot j = 0 of the window
+            a.fvprev[co + i] = f[u];
+            d[u][0] = df;
+        }
+        if (K > 0) {
 #pragma unroll
-                for (int c = r; c < K; ++c) acc(q++, d[r] * d[c]);
+            for (int u = 0; u < U; ++u) {
+                if (i0 + u * stride >= a.M) break;
+                int q = 0;
 #pragma unroll
-            for (int r = 0; r < K; ++r) acc(q++, d[r] * f);
+                for (int r = 0; r < K; ++r)
+#pragma unroll
+                    for (int c = r; c < K; ++c) acc(q++, d[u][r] * d[u][c]);
+#pragma unroll
+                for (int r = 0; r < K; ++r) acc(q++, d[u][r] * f[u]);
+            }
         }
     }
     if (K == 0) return;

@@ -834,8 +834,20 @@ void Ctx::tonal_local(float* out) {
     tstop();
 }
 
+// One wave of k_aa_gather<K>: its resident CTAs per SM (the K = 8 form holds
+// 44 compensated sums per thread and runs one CTA per SM) times the SMs,
+// shared among the channels, at most kAAParts per channel.
 template <int K>
-static void launch_aa_gather(const AAArgs& a, int new_slot, cudaStream_t s) {
+static void launch_aa_gather(AAArgs a, int new_slot, int device, cudaStream_t s) {
+    static int occ = 0;
+    if (occ == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_aa_gather<K>, 256, 0) != cudaSuccess || v < 1) v = 1;
+        occ = v;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1) sms = 1;
+    a.nparts = std::max(1, std::min({kAAParts, sms * occ / a.nch, (a.M + 255) / 256}));
     k_aa_gather<K><<<dim3(a.nparts, a.nch), 256, 0, s>>>(a, new_slot);
 }
 
@@ -914,15 +926,15 @@ int Ctx::tonal_aa_step(int n, const float* fvfull, DF G) {
     tstart(kT_Anderson);
     ++launches;
     switch (k) {
-        case 0: launch_aa_gather<0>(a, new_slot, stream); break;
-        case 1: launch_aa_gather<1>(a, new_slot, stream); break;
-        case 2: launch_aa_gather<2>(a, new_slot, stream); break;
-        case 3: launch_aa_gather<3>(a, new_slot, stream); break;
-        case 4: launch_aa_gather<4>(a, new_slot, stream); break;
-        case 5: launch_aa_gather<5>(a, new_slot, stream); break;
-        case 6: launch_aa_gather<6>(a, new_slot, stream); break;
-        case 7: launch_aa_gather<7>(a, new_slot, stream); break;
-        default: launch_aa_gather<8>(a, new_slot, stream); break;
+        case 0: launch_aa_gather<0>(a, new_slot, device, stream); break;
+        case 1: launch_aa_gather<1>(a, new_slot, device, stream); break;
+        case 2: launch_aa_gather<2>(a, new_slot, device, stream); break;
+        case 3: launch_aa_gather<3>(a, new_slot, device, stream); break;
+        case 4: launch_aa_gather<4>(a, new_slot, device, stream); break;
+        case 5: launch_aa_gather<5>(a, new_slot, device, stream); break;
+        case 6: launch_aa_gather<6>(a, new_slot, device, stream); break;
+        case 7: launch_aa_gather<7>(a, new_slot, device, stream); break;
+        default: launch_aa_gather<8>(a, new_slot, device, stream); break;
     }
     tstop();
     if (k > 0) {
