@@ -447,6 +447,7 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
     a.red_r = c.reducer(kSlotR64, grd.x * grd.y);
     a.red_b = c.reducer(kSlotB64, grd.x * grd.y);
     a.want_b = want_b ? 1 : 0;
+    a.d_lo_zero = (c.f_lo_zero && d.lo == c.dfv[kF].lo) ? 1 : 0;
     // algorithmic bytes per value: write u (double-float) and r (FP32), read
     // the mask bits, u, e, the source terms d and y as the variant needs them
     // (the data that INIT_KEEP / FROM32 / ZERO take on known pixels only is
@@ -454,7 +455,7 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
     constexpr bool HAS_U = (INIT == INIT_KEEP || INIT == INIT_UPDATE);
     constexpr bool HAS_E = (INIT == INIT_UPDATE || INIT == INIT_FROM32);
     const double bpv = 12.125 + (HAS_U ? 8.0 : 0.0) + (HAS_E ? 4.0 : 0.0) +
-                       (RHS == RHS_SOURCE ? 8.0 + (y.hi ? 8.0 : 0.0) : 0.0);
+                       (RHS == RHS_SOURCE ? (a.d_lo_zero ? 4.0 : 8.0) + (y.hi ? 8.0 : 0.0) : 0.0);
     c.tstart(kT_Residual, bpv * (double)c.nch * c.H * c.W);
     launch_k(c.p.pdl >= 0.5, k_residual_df<RHS, INIT>, grd, blk, c.stream, a);
     ++c.launches;
@@ -547,6 +548,7 @@ int Ctx::check_image(const hdi_image* im, const char* name, int H_, int W_, int 
 // Copies a caller image into the internal FP64 layout (device or host source).
 int Ctx::load_image(const hdi_image* im, DF dst, float* lo2, int c0) {
     const int nc = im->channels;
+    if (dst.hi == dfv[kF].hi && im->dtype == HDI_F64) f_lo_zero = false;   // callers set it before loading f
     if (c0) {
         const long long off = (long long)c0 * lev[0].cs;
         dst.hi += off;
@@ -982,6 +984,7 @@ int Ctx::inpaint_batch(int n, const hdi_image* f, const hdi_mask* m, hdi_image* 
         }
         if ((rc = setup(f[g[0]].height, f[g[0]].width, C, (int)g.size()))) return rc;
         cudaMemcpyAsync(d_chmask, chmask.data(), chmask.size() * 4, cudaMemcpyHostToDevice, stream);
+        f_lo_zero = true;
         for (size_t j = 0; j < g.size(); ++j) {
             long long ones = 0;
             if ((rc = load_mask(&m[g[j]], &ones, (int)j, j + 1 == g.size()))) return rc;
@@ -1051,6 +1054,7 @@ int Ctx::inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, 
     long long ones = 0;
     if ((rc = load_mask(mask, &ones))) return rc;
     if (ones == 0) return fail(HDI_ERR_EMPTY_MASK, "empty mask: A is singular");
+    f_lo_zero = true;
     if ((rc = load_image(f, dfv[kF], flo2))) return rc;
     SolveSpec s;
     s.u[0] = dfv[kU0];
@@ -1230,6 +1234,7 @@ extern "C" int hdi_inpaint_noalloc(int device, void* cuda_stream, const hdi_imag
     long long ones = 0;
     if ((rc = c.load_mask(mask, &ones))) return rc;
     if (ones == 0) return HDI_ERR_EMPTY_MASK;
+    c.f_lo_zero = true;
     if ((rc = c.load_image(f, c.dfv[kF], c.flo2))) return rc;
     SolveSpec s;
     s.u[0] = c.dfv[kU0];

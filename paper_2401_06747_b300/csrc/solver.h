@@ -161,6 +161,7 @@ struct Ctx {
     double ttot[HDI_TIMING_CLASSES] = {};
     int64_t tcnt[HDI_TIMING_CLASSES] = {};
     double tbytes[HDI_TIMING_CLASSES] = {};
+    bool f_lo_zero = false;   // the low words of f are all zero (every image of the call was FP32)
     void tstart(int cls, double bytes = 0.0);   // bytes: algorithmic HBM bytes of the launch
     void tstop();
     int tflush();

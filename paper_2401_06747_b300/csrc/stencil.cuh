@@ -691,6 +691,7 @@ struct ResArgs {
     GridReduce red_r;     // ||r||^2 per channel
     GridReduce red_b;     // ||b||^2 per channel (only if want_b)
     int want_b;
+    int d_lo_zero;        // d.lo is all zero (FP32 data): its loads are skipped
 };
 
 // Quad strips like the FP32 kernels (lane = four columns, float4 loads of
@@ -754,7 +755,10 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
             float dh[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
             if (HAS_U) { f4_to(ld4(a.uin.hi, i), uh); f4_to(ld4(a.uin.lo, i), ul); }
             if (HAS_E) f4_to(ld4(a.x32, i), e);
-            if (LOAD_D) { f4_to(ld4(a.d.hi, i), dh); f4_to(ld4(a.d.lo, i), dl); }
+            if (LOAD_D) {
+                f4_to(ld4(a.d.hi, i), dh);
+                if (!a.d_lo_zero) f4_to(ld4(a.d.lo, i), dl);
+            }
 #pragma unroll
             for (int j = 0; j < 4; ++j) value((w >> (q.shift + j)) & 1u, uh[j], ul[j], e[j], dh[j], dl[j], h[j], l[j]);
         };
@@ -784,7 +788,7 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
                 c.HE[k] = (HAS_E && q.hon) ? a.x32[ih] : 0.f;
                 if (RHS == RHS_SOURCE) {
                     c.Dh[k] = ld4(a.d.hi, ic);
-                    c.Dl[k] = ld4(a.d.lo, ic);
+                    c.Dl[k] = a.d_lo_zero ? z4 : ld4(a.d.lo, ic);
                     c.Yh[k] = a.y.hi ? ld4(a.y.hi, ic) : z4;
                     c.Yl[k] = a.y.hi ? ld4(a.y.lo, ic) : z4;
                 }
@@ -795,10 +799,10 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
                     const uint32_t kb = (c.Mw[k + 1] >> q.shift) & 15u;
                     const size_t id = at(yb + k + 1, q.cq), ih = at(yb + k, q.hcol);
                     c.KDh[k] = kb ? ld4(a.d.hi, id) : z4;
-                    c.KDl[k] = kb ? ld4(a.d.lo, id) : z4;
+                    c.KDl[k] = (kb && !a.d_lo_zero) ? ld4(a.d.lo, id) : z4;
                     const bool kh = q.hon && ((c.Hm[k] >> hbit) & 1u);
                     c.HDh[k] = kh ? a.d.hi[ih] : 0.f;
-                    c.HDl[k] = kh ? a.d.lo[ih] : 0.f;
+                    c.HDl[k] = (kh && !a.d_lo_zero) ? a.d.lo[ih] : 0.f;
                 }
             }
         };

@@ -977,6 +977,7 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     if (ones == 0) return fail(HDI_ERR_EMPTY_MASK, "empty mask: A is singular");
     const DFc F = cview(dfv[kF]);
     DF G = dfv[kG];
+    f_lo_zero = true;
     if ((rc = load_image(f, dfv[kF]))) return rc;
     if (g0) {
         if ((rc = load_image(g0, G))) return rc;
