@@ -454,7 +454,9 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
     // not counted)
     constexpr bool HAS_U = (INIT == INIT_KEEP || INIT == INIT_UPDATE);
     constexpr bool HAS_E = (INIT == INIT_UPDATE || INIT == INIT_FROM32);
-    const double bpv = 12.125 + (HAS_U ? 8.0 : 0.0) + (HAS_E ? 4.0 : 0.0) +
+    // INIT_KEEP rewrites only the known pixels of u in place
+    const double known = c.mask_ones > 0 ? std::min(1.0, (double)c.mask_ones / ((double)c.H * c.W)) : 0.0;
+    const double bpv = 12.125 - (INIT == INIT_KEEP ? 8.0 * (1.0 - known) : 0.0) + (HAS_U ? 8.0 : 0.0) + (HAS_E ? 4.0 : 0.0) +
                        (RHS == RHS_SOURCE ? (a.d_lo_zero ? 4.0 : 8.0) + (y.hi ? 8.0 : 0.0) : 0.0);
     c.tstart(kT_Residual, bpv * (double)c.nch * c.H * c.W);
     launch_k(c.p.pdl >= 0.5, k_residual_df<RHS, INIT>, grd, blk, c.stream, a);
@@ -487,8 +489,7 @@ int Ctx::solve(SolveSpec& s) {
         fmg(s.d);
         residual(s.rhs, INIT_FROM32, none, ub[cur], lev[0].xa, s.d, s.y, true);
     } else if (s.start == START_WARM) {
-        residual(s.rhs, INIT_KEEP, cview(ub[cur]), ub[1 - cur], nullptr, s.d, s.y, true);
-        cur = 1 - cur;
+        residual(s.rhs, INIT_KEEP, cview(ub[cur]), ub[cur], nullptr, s.d, s.y, true);   // in place
     } else {
         residual(s.rhs, INIT_ZERO, none, ub[cur], nullptr, s.d, s.y, true);
     }

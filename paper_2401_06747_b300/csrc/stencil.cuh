@@ -674,8 +674,11 @@ enum { RHS_DATA = 0, RHS_SOURCE = 1 };
 //   INIT_FROM32 : u = x (FP32 FMG result)
 //   INIT_ZERO   : u = 0
 // In every mode known pixels take their Dirichlet value (d, or 0 for
-// RHS_SOURCE), so u_K is exact. The result goes to uout, which must not alias
-// uin (neighbouring tiles read uin as their halo).
+// RHS_SOURCE), so u_K is exact. INIT_KEEP works in place (uout = uin) and
+// stores only the known pixels: every reader takes a known pixel's value
+// from d, never from u, so no tile depends on the order of those stores.
+// The other modes write every pixel to uout, which must not alias uin
+// (neighbouring tiles read uin as their halo).
 enum { INIT_KEEP = 0, INIT_UPDATE = 1, INIT_FROM32 = 2, INIT_ZERO = 3 };
 
 struct ResArgs {
@@ -884,7 +887,24 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
                     if (IN || q.act[j]) rr += r * r;
                 }
                 const size_t idx = co + (size_t)y * a.F.pitch + q.c0;
-                if (IN || q.act[3]) {
+                if (INIT == INIT_KEEP) {
+                    // in place: only the known pixels change (to their
+                    // Dirichlet value); readers take known pixels from d, so
+                    // the order of these stores and their loads is immaterial
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if ((IN || q.act[j]) && ((c.Mw[k] >> (q.shift + j)) & 1u)) {
+                            a.uout.hi[idx + j] = oh[j];
+                            a.uout.lo[idx + j] = ol[j];
+                        }
+                    if (IN || q.act[3]) {
+                        *reinterpret_cast<float4*>(a.r32 + idx) = make_float4(orr[0], orr[1], orr[2], orr[3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (q.act[j]) a.r32[idx + j] = orr[j];
+                    }
+                } else if (IN || q.act[3]) {
                     *reinterpret_cast<float4*>(a.uout.hi + idx) = make_float4(oh[0], oh[1], oh[2], oh[3]);
                     *reinterpret_cast<float4*>(a.uout.lo + idx) = make_float4(ol[0], ol[1], ol[2], ol[3]);
                     *reinterpret_cast<float4*>(a.r32 + idx) = make_float4(orr[0], orr[1], orr[2], orr[3]);
