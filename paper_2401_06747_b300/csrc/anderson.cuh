@@ -148,44 +148,47 @@ __global__ void __launch_bounds__(256) k_aa_gather(AAArgs a, int new_slot) {
             }
         }
     }
-    if (K == 0) return;
-    // block reduce all dots at once: warp sums in FP64, one shared-memory
-    // exchange, then thread q adds the warps' values of dot q
-    __shared__ double wsum[8][NA];
+    if constexpr (K == 0) {
+        return;
+    } else {
+        // block reduce all dots at once: warp sums in FP64, one shared-memory
+        // exchange, then thread q adds the warps' values of dot q
+        __shared__ double wsum[8][NA];
 #pragma unroll
-    for (int q = 0; q < ND; ++q) {
-        const double t = warp_sum_d((double)as[q] + (double)ae[q]);
-        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5][q] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < ND) {
-        double t = 0.0;
+        for (int q = 0; q < ND; ++q) {
+            const double t = warp_sum_d((double)as[q] + (double)ae[q]);
+            if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5][q] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < ND) {
+            double t = 0.0;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) t += wsum[w][threadIdx.x];
-        a.partials[((size_t)ch * ND + threadIdx.x) * a.nparts + part] = t;
-        __threadfence();   // each writer publishes its partial before the ticket
+            for (int w = 0; w < 8; ++w) t += wsum[w][threadIdx.x];
+            a.partials[((size_t)ch * ND + threadIdx.x) * a.nparts + part] = t;
+            __threadfence();   // each writer publishes its partial before the ticket
+        }
+        __shared__ bool last;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned t = atomicAdd(a.ticket, 1u);
+            last = (t == (unsigned)(a.nparts * a.nch - 1));
+        }
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+        // the last CTA sums the partials of every (channel, dot) pair, one warp
+        // per pair (fixed order: lane-strided sums, then the warp tree), with no
+        // block-wide barrier between pairs
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int j = warp; j < a.nch * ND; j += 8) {
+            const double* src = a.partials + (size_t)j * a.nparts;   // [channel][dot] = j
+            double s = 0.0;
+            for (int p = lane; p < a.nparts; p += 32) s += __ldcg(src + p);
+            s = warp_sum_d(s);
+            if (lane == 0) a.out[j] = s;
+        }
+        if (threadIdx.x == 0) *a.ticket = 0u;
     }
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned t = atomicAdd(a.ticket, 1u);
-        last = (t == (unsigned)(a.nparts * a.nch - 1));
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // the last CTA sums the partials of every (channel, dot) pair, one warp
-    // per pair (fixed order: lane-strided sums, then the warp tree), with no
-    // block-wide barrier between pairs
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int j = warp; j < a.nch * ND; j += 8) {
-        const double* src = a.partials + (size_t)j * a.nparts;   // [channel][dot] = j
-        double s = 0.0;
-        for (int p = lane; p < a.nparts; p += 32) s += __ldcg(src + p);
-        s = warp_sum_d(s);
-        if (lane == 0) a.out[j] = s;
-    }
-    if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
 // step = beta f_n - sum_j gamma_j (dX_j + beta dF_j);  g += step;  dX[write_slot] = step.

@@ -339,10 +339,8 @@ void Ctx::vcycle(int l) {
     const int npre = (l == 0) ? (int)p.fine_pre : 1;
     const int npost = (l == 0) ? (int)p.fine_post : 1;
     // pre-smoothing: the first sweep starts from x = 0
-    bool have_x = false;
     if (npre > 0) {
         oras(l, true, nullptr, L.xa, pre_norm, false, it);
-        have_x = true;
         for (int i = 1; i < npre; ++i) {
             residual_norm_level(l, L.xa, l);
             oras(l, false, L.xa, L.xb, scal + l * kMaxCh, false, it);
@@ -351,7 +349,6 @@ void Ctx::vcycle(int l) {
     } else {
         cudaMemsetAsync(L.xa, 0, (size_t)nch * L.cs * 4, stream);
     }
-    (void)have_x;
     Level& C = lev[l + 1];
     {
         const int qr = quad_rows(L.H, L.W, nch);

@@ -1156,7 +1156,7 @@ int Ctx::tonal_cgnr(SolveSpec& sw, const double* btf2, double tol, int& it, doub
     spw.d = cview(P);
     spw.max_iter = (int)p.max_vcycles;
     double r2[kMaxCh], e2[kMaxCh];
-    double rel_prev = 1.0, mse_prev = 0.0;
+    double mse_prev = 0.0;
     sw.start = START_WARM;
     // z = B^T (f - y) and the figures of the current iterate
     auto evaluate = [&](double tin) -> int {
@@ -1196,7 +1196,6 @@ int Ctx::tonal_cgnr(SolveSpec& sw, const double* btf2, double tol, int& it, doub
             break;
         }
         const double tin = std::max(1e-13, std::min(p.tonal_inner_max, ratio * rel_max));
-        rel_prev = rel_max;
         mse_prev = mse_last;
         // w = B p
         spw.cur = 0;
@@ -1217,6 +1216,5 @@ int Ctx::tonal_cgnr(SolveSpec& sw, const double* btf2, double tol, int& it, doub
                                                                scal + kSlotCgZ * kMaxCh, 0);
         ++launches;
     }
-    (void)rel_prev;
     return cuda_check(cudaGetLastError(), "CGNR");
 }
