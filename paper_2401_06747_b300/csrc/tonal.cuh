@@ -179,9 +179,14 @@ __global__ void __launch_bounds__(kL64Threads, 2) k_tonal_echo64(EchoArgs a) {
 
 // Shared-memory floats of k_tonal_gram for subdomains of up to m mask pixels.
 __host__ __device__ inline int gram_round4(int m) { return (m + 3) & ~3; }
+// The staged pixels and the partial blocks of the sliced product share one
+// region (the partial blocks are written after the last staged round).
+__host__ __device__ inline size_t gram_stage_floats(int m4) {
+    return (size_t)32 * (m4 + 4) > 256 * 16 ? (size_t)32 * (m4 + 4) : (size_t)256 * 16;
+}
 __host__ __device__ inline size_t gram_smem_floats(int m) {
     const int m4 = gram_round4(m);
-    return (size_t)m * (m | 1) + 4 + (size_t)32 * (m4 + 4) + 256 * 16 + m4;
+    return (size_t)m * (m | 1) + 4 + gram_stage_floats(m4) + m4;
 }
 
 // G_i = I + S_i^T S_i and its inverse (full m x m, row-major) at
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
     const int es = m4 + 4;                         // row stride of the staged pixels
     float* G = sm;                                 // m x gs
     float* Es = sm + (((size_t)m * gs + 3) & ~(size_t)3);   // [32][es], 16-byte aligned rows
-    float* part = Es + 32 * es;                    // [ks][nblk][16] (ks > 1)
+    float* part = Es;                              // [ks][nblk][16] (ks > 1), after the last staged round
     const float* E = echo + (size_t)off[i] * npx;
     for (int b0 = 0; b0 < nblk; b0 += 256) {       // rounds of up to 256 blocks (ks == 1 when > 1 round)
         const int slot = tid % (ks > 1 ? nblk : 256);
@@ -251,6 +256,7 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
             }
         }
         if (ks > 1) {
+            __syncthreads();   // every thread is done reading the staged pixels that part overwrites
             if (on) {
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
     __syncthreads();
     // W = L^{-1}; thread j owns column j of W, stored as row j of W^T:
     // Wt[j][k] = W[k][j] at G[j * gs + k] for k > j, the diagonal in dinv.
-    float* dinv = part + 256 * 16;
+    float* dinv = Es + gram_stage_floats(m4);
     if (r < m) {
         const float dj = 1.f / G[r * gs + r];
         dinv[r] = dj;
