@@ -56,3 +56,29 @@ def test_batch_specs_sample_host_buffers():
     for (f, c), o, s in zip(data, outs, st):
         assert s["rel_res"] <= 1e-6
         assert rel_residual(o.astype(np.float64), f.astype(np.float64), c).max() <= 1.5e-6
+
+
+def test_batch_mixed_dtypes_keep_fp64_data_exact():
+    """FP32 and FP64 images of one size class in one batch: the FP64 image's
+    data words below FP32 precision are used (its known pixels come back
+    bit for bit, its residual meets the tolerance) although the other images
+    of the system are FP32."""
+    need_gpu()
+    H, W = 96, 128
+    a = synth_rgb(H, W, seeds=(71, 72, 73))                    # FP32
+    b = synth_image(H, W, 74)[None]                            # FP64, not FP32-representable
+    c = synth_image(H, W, 75).astype(np.float32)[None]         # FP32
+    ms = [random_mask(H, W, 0.05, s) for s in (76, 77, 78)]
+    assert np.any(b != b.astype(np.float32))
+    k = ctx()
+    fs = [dev(a), dev(b), dev(c)]
+    outs = [torch.empty_like(x) for x in fs]
+    st = k.inpaint_batch(fs, [dev(m) for m in ms], outs, tol=1e-6)
+    for f, m, o, s in zip((a, b, c), ms, outs, st):
+        u = o.cpu().numpy().astype(np.float64)
+        assert s["rel_res"] <= 1e-6
+        assert rel_residual(u, f.astype(np.float64), m).max() <= 1.5e-6
+        assert np.abs(u - inpaint_ref(f.astype(np.float64), m)).max() <= 1e-3
+    ub = outs[1].cpu().numpy()
+    known = ms[1].astype(bool)
+    assert np.array_equal(ub[0][known], b[0][known])
