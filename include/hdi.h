@@ -100,7 +100,9 @@ int hdi_get_param(const hdi_ctx* ctx, const char* name, double* value);
  *              are ignored (u_K = f_K is enforced).
  *   u     out: solution, same shape and dtype as f (may alias u0).
  *   tol      : per-channel relative residual ||C f - A u|| / ||C f||, in (0,1),
- *              evaluated in FP64 on the FP64 iterate kept on the GPU.
+ *              evaluated on the GPU's double-float iterate (two FP32 words,
+ *              about 48 significant bits) with FP64 accumulation of the
+ *              norms; the returned u is that iterate rounded to the dtype.
  *   st   out : statistics, may be NULL. */
 int hdi_inpaint(hdi_ctx* ctx, const hdi_image* f, const hdi_mask* mask,
                 const hdi_image* u0, hdi_image* u, double tol, hdi_stats* st);
@@ -196,13 +198,14 @@ int hdi_timing_bytes(hdi_ctx* ctx, double* bytes);
 
 /* Inpainting that allocates no device memory. The paper has no counterpart;
  * this entry point exists for callers that cannot call cudaMalloc while they
- * run, for instance code executing inside a CUDA stream capture, a real-time
- * or interrupt-like loop with a fixed memory plan, or a host process whose
- * allocator is owned by another runtime. It solves the same system as
- * hdi_inpaint (cold start, default parameters) with the same kernels, but
- * takes no context and keeps its whole workspace in a 24 MiB array in
- * device global memory that the library declares statically: every GPU that
- * loads libhdi holds that array until the process exits.
+ * run: a real-time loop with a fixed memory plan that must not wait on the
+ * device allocator, or a host process whose GPU memory is owned by another
+ * runtime (a framework's caching allocator that has reserved the device).
+ * It solves the same system as hdi_inpaint (cold start, default parameters)
+ * with the same kernels, but takes no context and keeps its whole workspace
+ * in a 24 MiB array in device global memory that the library declares
+ * statically: every GPU that loads libhdi holds that array until the
+ * process exits.
  *   device, cuda_stream : GPU index and stream (NULL = legacy default)
  *   f, mask, u          : as for hdi_inpaint, but all three must be DEVICE
  *                         buffers (host buffers would need staging memory)
@@ -212,13 +215,22 @@ int hdi_timing_bytes(hdi_ctx* ctx, double* bytes);
  * channel values (e.g. 400x400 RGB or 700x700 grey); larger images return
  * HDI_ERR_INVALID_ARG before any GPU work. Host buffers, a null pointer or
  * tol outside (0,1) also return HDI_ERR_INVALID_ARG.
+ * Synchronisation: like hdi_inpaint, each call waits for its stream after
+ * checking the mask and the image (a flag copied to the host), once per
+ * refinement step (the per-channel residual norms copied to the host for
+ * the stop test) and after writing u.
+ * Current device: the call makes `device` current and restores the calling
+ * thread's current device before it returns.
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress (the device made current first); make that first
- * call before any stream capture. All calls share the one array and it
- * keeps the previous call's contents (the entry point clears what must
- * start at zero): calls that overlap on the GPU, from any thread or stream,
- * race and corrupt each other. No error message is kept; the return code
- * (hdi_status) is the only report. */
+ * cudaGetSymbolAddress (with the device current) and caches it for the
+ * process; a cudaDeviceReset invalidates the cached address. All calls on
+ * one device share that device's array, and it keeps the previous call's
+ * contents (the entry point clears what must start at zero): calls on the
+ * same device that overlap, on the GPU or from two host threads, race and
+ * corrupt each other. Calls on different devices use different arrays and
+ * different host-side copies of the residual norms and do not interfere.
+ * No error message is kept; the return code (hdi_status) is the only
+ * report. */
 int hdi_inpaint_noalloc(int device, void* cuda_stream, const hdi_image* f, const hdi_mask* mask,
                         hdi_image* u, double tol, hdi_stats* st);
 

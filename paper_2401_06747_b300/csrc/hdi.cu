@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <climits>
+#include <atomic>
 
 #include "../../include/hdi.h"
 #include "common.cuh"
@@ -1101,8 +1102,26 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
 constexpr int kNoAllocMaxDevices = 64;
-void* g_noalloc_ptr[kNoAllocMaxDevices] = {};   // device address of the scratch, per device
-double g_noalloc_hscal[2 * kMaxCh];             // host mirror of the reduction outputs
+// Device address of the scratch, per device (looked up once per device;
+// a cudaDeviceReset invalidates it and is not detected).
+std::atomic<void*> g_noalloc_ptr[kNoAllocMaxDevices];
+// Host mirror of the reduction outputs, one per device: calls on different
+// devices read their residual norms into different rows.
+double g_noalloc_hscal[kNoAllocMaxDevices][2 * kMaxCh];
+
+// Restores the calling thread's current device when the entry point returns.
+struct DeviceRestore {
+    int prev = -1;
+    DeviceRestore() {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+    }
+    ~DeviceRestore() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 // Carves the inpainting workspace of an H x W x nch image out of `base`
 // (the same layout rules as Ctx::setup, restricted to the buffers the
@@ -1199,30 +1218,35 @@ extern "C" int hdi_inpaint_noalloc(int device, void* cuda_stream, const hdi_imag
     if (f->location != HDI_DEVICE || mask->location != HDI_DEVICE || u->location != HDI_DEVICE)
         return HDI_ERR_INVALID_ARG;   // host buffers would need a staging allocation
     if (!(tol > 0.0 && tol < 1.0)) return HDI_ERR_INVALID_ARG;
+    DeviceRestore restore;   // the caller's current device is put back on every return
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
         return HDI_ERR_CUDA;
     }
-    if (!g_noalloc_ptr[device]) {
+    void* scratch = g_noalloc_ptr[device].load(std::memory_order_acquire);
+    if (!scratch) {
         // One-time set-up on this device, with the device current: the
         // array's name is only a host-side stand-in, so look up its address.
+        // Two threads racing here look up the same address; both stores
+        // write that value.
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return HDI_ERR_CUDA;
         }
-        g_noalloc_ptr[device] = p;
+        g_noalloc_ptr[device].store(p, std::memory_order_release);
+        scratch = p;
     }
     Ctx c;
     c.device = device;
     c.stream = (cudaStream_t)cuda_stream;
-    c.hscal = g_noalloc_hscal;
+    c.hscal = g_noalloc_hscal[device];
     int rc;
     if ((rc = c.check_image(f, "f", -1, 0, 0))) return rc;
     if ((rc = c.check_image(u, "u", f->height, f->width, f->channels))) return rc;
     if (u->dtype != f->dtype) return HDI_ERR_INVALID_ARG;
-    if (noalloc_layout(c, (char*)g_noalloc_ptr[device], kNoAllocBytes, f->height, f->width, f->channels) >
+    if (noalloc_layout(c, (char*)scratch, kNoAllocBytes, f->height, f->width, f->channels) >
         kNoAllocBytes)
         return HDI_ERR_INVALID_ARG;   // image too large for the static scratch
     // The scratch keeps the previous call's contents: clear what must start at zero.

@@ -1,5 +1,5 @@
 """Host-side pieces of bench.py's roofline that need no GPU: the algorithmic
-byte table, the derived FP32 peak, and the committed ncu summaries the bench
+byte table, the derived FP32 peak (SM count read from the device), and the committed ncu summaries the bench
 reads its DRAM traffic from (each names the command that made it, runs only
 committed entry points and leaves the GPU clocks alone)."""
 
@@ -23,9 +23,19 @@ def test_algorithmic_bytes_follow_from_the_vectors_each_class_moves():
     assert b["restrict_fine"] == FP32 + FP32 + MASK + FP32 / 4     # read x, b, mask; write b_H
 
 
-def test_derived_fp32_peak():
-    assert abs(bench.FP32_PEAK_TFLOPS - 148 * 128 * 2 * 2.032e9 / 1e12) < 1e-9
-    assert 76.9 < bench.FP32_PEAK_TFLOPS < 77.1
+def test_derived_fp32_peak(monkeypatch):
+    """SMs from the device attribute x 128 FP32 lanes x 2 flop/FMA x the
+    maximum SM clock (a stand-in device reports 148 SMs)."""
+    import types
+    torch = __import__("torch")
+    props = types.SimpleNamespace(multi_processor_count=148)
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: props)
+    peak, src = bench.fp32_peak_tflops(0, {"sm_max_mhz": 2032.0})
+    assert abs(peak - 148 * 128 * 2 * 2.032e9 / 1e12) < 1e-9
+    assert 76.9 < peak < 77.1
+    assert "148 SMs" in src and "2032 MHz" in src
+    peak, src = bench.fp32_peak_tflops(0, {})
+    assert 76.9 < peak < 77.1 and "fallback" in src
 
 
 def test_profile_summaries_carry_traffic_and_their_commands():

@@ -1,13 +1,15 @@
 """The allocation-free inpainting entry point (hdi_inpaint_noalloc).
 
-Some callers cannot allocate device memory while they run (code inside a
-CUDA stream capture, loops with a fixed memory plan, processes whose device
-allocator belongs to another runtime). hdi_inpaint_noalloc serves them from
-a statically declared device array instead of a context workspace. These
-tests call it through the C ABI and check it against hdi_inpaint on two
-calls in a row with different images, masks and sizes, so that contents
-left in the shared array by the first call cannot leak into the second.
-The file is named to be collected last.
+Some callers cannot allocate device memory while they run (a real-time loop
+with a fixed memory plan, a process whose GPU memory belongs to another
+runtime's allocator). hdi_inpaint_noalloc serves them from a statically
+declared device array instead of a context workspace. These tests call it
+through the C ABI and check it against hdi_inpaint on two calls in a row
+with different images, masks and sizes, so that contents left in the shared
+array by the first call cannot leak into the second; near its size limit
+(400x400 RGB fits, 440x440 RGB does not); on a side stream; and that it
+puts the caller's current device back. The file is named to be collected
+last.
 """
 
 import ctypes
@@ -32,15 +34,16 @@ def noalloc_fn():
     return fn, hdi
 
 
-def solve_both(f, c, tol):
+def solve_both(f, c, tol, stream=None):
     fn, hdi = noalloc_fn()
     fd, cd = dev(f), dev(c)
     ref = torch.empty_like(fd)
     ctx().inpaint(fd, cd, ref, tol=tol)
+    torch.cuda.synchronize()
     out = torch.full_like(fd, float("nan"))
     st = hdi.Stats()
-    stream = torch.cuda.current_stream().cuda_stream
-    rc = fn(0, ctypes.c_void_p(stream), ctypes.byref(hdi.image_of(fd)), ctypes.byref(hdi.mask_of(cd)),
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = fn(0, ctypes.c_void_p(s.cuda_stream), ctypes.byref(hdi.image_of(fd)), ctypes.byref(hdi.mask_of(cd)),
             ctypes.byref(hdi.image_of(out)), tol, ctypes.byref(st))
     torch.cuda.synchronize()
     return rc, out.cpu().numpy(), ref.cpu().numpy(), st
@@ -78,3 +81,47 @@ def test_rejects_images_beyond_the_static_scratch():
     rc = fn(0, None, ctypes.byref(hdi.image_of(fh)), ctypes.byref(hdi.mask_of(ch)), ctypes.byref(hdi.image_of(oh)),
             1e-6, None)
     assert rc == -1
+
+
+def test_just_under_the_size_limit_and_on_a_side_stream():
+    """400x400 RGB (480,000 values) fits the 24 MiB array; the call runs on
+    a stream other than the current one."""
+    need_gpu()
+    f = synth_rgb(400, 400, seeds=(41, 42, 43), dtype=np.float32)
+    c = random_mask(400, 400, 0.05, 44)
+    side = torch.cuda.Stream()
+    rc, out, ref, st = solve_both(f, c, 1e-6, stream=side)
+    assert rc == 0 and st.rel_res <= 1e-6
+    assert np.abs(out - ref).max() <= 1e-3
+
+
+def test_just_over_the_size_limit_is_refused():
+    """440x440 RGB (580,800 values) needs more than the 24 MiB array."""
+    need_gpu()
+    fn, hdi = noalloc_fn()
+    f = torch.zeros((3, 440, 440), dtype=torch.float32, device="cuda")
+    c = torch.ones((440, 440), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(f)
+    rc = fn(0, None, ctypes.byref(hdi.image_of(f)), ctypes.byref(hdi.mask_of(c)), ctypes.byref(hdi.image_of(out)),
+            1e-6, None)
+    assert rc == -1
+
+
+def test_restores_the_callers_current_device():
+    need_gpu()
+    fn, hdi = noalloc_fn()
+    lib = hdi.load()
+    f = dev(synth_image(32, 48, 45).astype(np.float32)[None])
+    c = dev(random_mask(32, 48, 0.1, 46))
+    out = torch.empty_like(f)
+    before = torch.cuda.current_device()
+    rc = fn(0, None, ctypes.byref(hdi.image_of(f)), ctypes.byref(hdi.mask_of(c)), ctypes.byref(hdi.image_of(out)),
+            1e-6, None)
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert torch.cuda.current_device() == before
+    # an out-of-range device index is refused before any device is touched
+    rc = fn(1 << 20, None, ctypes.byref(hdi.image_of(f)), ctypes.byref(hdi.mask_of(c)),
+            ctypes.byref(hdi.image_of(out)), 1e-6, None)
+    assert rc == -1
+    assert lib is not None
