@@ -24,6 +24,13 @@ Given f, the current mask c, its inpainting u and a count k:
      first k the pixel of largest e (ties: lowest linear index) is added
      (Alg. 1: at most one new pixel per triangle, placed at the maximum
      pointwise error, triangles in order of decreasing error).
+Voronoi-cell partition (partition = "voronoi"; the Voronoi-based
+densification the paper compares against in Sec. 6.2, after Daropoulos et
+al.): the same step with the triangles of 3.-4. replaced by the Voronoi
+cells of the current mask pixels: every non-mask pixel p belongs to the cell
+of its label V(p), the cell id is V(p) itself (the site's linear index), and
+5.-6. are unchanged (cells ranked by (E desc, site index asc), one new pixel
+per selected cell at its largest e).
 With an empty mask the step draws the initial mask instead (Sec. 4.2):
   w_i = sum_ch |(L f)_i| (FP64, (L f)_i = sum of (f_i - f_n) over the in-image
   neighbours in the order left, right, up, down), quantised to
@@ -292,12 +299,26 @@ def initial_mask(f: np.ndarray, k: int, seed: int) -> np.ndarray:
     return take.reshape(H, W).astype(np.uint8)
 
 
+def voronoi_ownership(c: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """Owner cell of every pixel for the Voronoi-cell partition: the label
+    V(p) of each non-mask pixel (its nearest mask pixel), -1 on the mask."""
+    cb = np.asarray(c, dtype=bool)
+    own = np.asarray(V, dtype=np.int64).copy()
+    own[cb] = -1
+    return own
+
+
 def densify_step(f: np.ndarray, c: np.ndarray, u: np.ndarray | None, k: int, seed: int = 0,
-                 voronoi: str = "exact", first_step: int | None = None, info: dict | None = None):
+                 voronoi: str = "exact", first_step: int | None = None, info: dict | None = None,
+                 partition: str = "delaunay"):
     """Returns (new mask uint8, number of pixels added). voronoi = "jfa" uses
     jump-flooding labels (first pass step `first_step`) instead of the exact
     ones; `info`, if given, receives the labels' largest squared
-    pixel-to-site distance ("max_dist2")."""
+    pixel-to-site distance ("max_dist2"). partition = "voronoi" selects one
+    pixel per Voronoi cell of the current mask instead of per Delaunay
+    triangle."""
+    if partition not in ("delaunay", "voronoi"):
+        raise ValueError("partition must be 'delaunay' or 'voronoi'")
     cb = np.asarray(c, dtype=bool)
     H, W = cb.shape
     if k < 0:
@@ -315,8 +336,11 @@ def densify_step(f: np.ndarray, c: np.ndarray, u: np.ndarray | None, k: int, see
             V = jfa_labels(cb, None)
     if info is not None:
         info["max_dist2"] = label_max_dist2(V)
-    T, I = triangles(V)
-    own = ownership(cb, V, T, I).ravel()
+    if partition == "voronoi":
+        own = voronoi_ownership(cb, V).ravel()
+    else:
+        T, I = triangles(V)
+        own = ownership(cb, V, T, I).ravel()
     free = own >= 0
     ids, inv = np.unique(own[free], return_inverse=True)
     E = np.zeros(ids.size, dtype=np.int64)
@@ -335,7 +359,8 @@ def densify_step(f: np.ndarray, c: np.ndarray, u: np.ndarray | None, k: int, see
     return new.reshape(H, W).astype(np.uint8), int(rank.size)
 
 
-def densify(f: np.ndarray, n: int, t: float, density: float, seed: int, voronoi: str = "exact", solve=None):
+def densify(f: np.ndarray, n: int, t: float, density: float, seed: int, voronoi: str = "exact", solve=None,
+            partition: str = "delaunay"):
     """Delaunay densification from an empty mask (Sec. 4, Alg. 1 with the
     image-adaptive initial mask and the growth factor t of Sec. 4.2): n
     iterations, each a densification step to the cumulative target of
@@ -345,6 +370,7 @@ def densify(f: np.ndarray, n: int, t: float, density: float, seed: int, voronoi:
     previous labels' largest distance (the mask only grows, so that bound
     holds for the next mask); the first JFA step runs the full schedule.
     `solve(f, c)` computes the inpainting (default: the exact one).
+    partition = "voronoi" runs the Voronoi-cell variant of every step.
     Returns (mask, u, history) with the mask size after every iteration."""
     from .laplace import inpaint
     solve = solve or inpaint
@@ -359,7 +385,7 @@ def densify(f: np.ndarray, n: int, t: float, density: float, seed: int, voronoi:
     for i in range(n):
         k = max(targets[i] - int(c.sum()), 0)
         info = {}
-        c, _ = densify_step(f3, c, u, k, seed, voronoi, first, info)
+        c, _ = densify_step(f3, c, u, k, seed, voronoi, first, info, partition)
         if voronoi == "jfa" and "max_dist2" in info:
             first = jfa_first_step(info["max_dist2"])
         u = solve(f3, c)

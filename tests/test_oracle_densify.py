@@ -257,3 +257,51 @@ def test_densify_loop_reaches_the_density():
         assert hist["sizes"][-1] == total == int(c.sum())
         assert all(b >= a for a, b in zip(hist["sizes"], hist["sizes"][1:]))
         np.testing.assert_allclose(u[:, c == 1], f[:, c == 1], atol=1e-9)
+
+
+@pytest.mark.parametrize("H,W,d,k,seed", [(40, 52, 0.02, 15, 9), (1, 30, 0.1, 2, 3), (17, 23, 0.05, 100, 4)])
+def test_voronoi_partition_step_brute_force(H, W, d, k, seed):
+    """Voronoi-cell densification (Sec. 6.2): cells from brute-force nearest
+    sites (ties to the lowest index), integer cell sums, top-k by (E desc,
+    site asc), one new pixel per selected cell at its largest error."""
+    f = synth_rgb(H, W, seeds=(seed, seed + 1, seed + 2))
+    c = random_mask(H, W, d, seed + 10)
+    from oracle import inpaint
+    u = inpaint(f, c)
+    new, added = densify_step(f, c, u, k, partition="voronoi")
+    cb = c.astype(bool)
+    e = error_map(u, f).ravel()
+    eq = quantise_error(error_map(u, f)).ravel()
+    lab = brute_labels(cb).ravel()
+    cells = {}
+    for p in range(H * W):
+        if not cb.ravel()[p]:
+            cells.setdefault(int(lab[p]), []).append(p)
+    E = {s: int(sum(eq[p] for p in px)) for s, px in cells.items()}
+    ranked = sorted([s for s in E if E[s] > 0], key=lambda s: (-E[s], s))[:k]
+    expect = cb.ravel().copy()
+    for s in ranked:
+        expect[max(cells[s], key=lambda p: (e[p], -p))] = True
+    np.testing.assert_array_equal(new.ravel().astype(bool), expect)
+    assert added == min(k, sum(1 for v in E.values() if v > 0))
+    # at most one new pixel per Voronoi cell of the old mask
+    newpix = np.flatnonzero(new.ravel().astype(bool) & ~cb.ravel())
+    assert len(set(lab[newpix].tolist())) == newpix.size
+
+
+def test_voronoi_and_delaunay_partitions_differ_but_add_alike():
+    """The two partitions pick different pixels on a natural image, but each
+    adds min(k, non-empty cells) pixels outside the old mask."""
+    H, W = 48, 64
+    f = synth_image(H, W, 5)
+    c = random_mask(H, W, 0.02, 6)
+    from oracle import inpaint
+    u = inpaint(f, c)
+    a, na = densify_step(f, c, u, 20, partition="delaunay")
+    b, nb = densify_step(f, c, u, 20, partition="voronoi")
+    assert na == nb == 20
+    assert not np.array_equal(a, b)
+    for m in (a, b):
+        assert np.all(m.astype(bool) >= c.astype(bool))
+    with pytest.raises(ValueError):
+        densify_step(f, c, u, 5, partition="square")
