@@ -34,6 +34,10 @@ DENSITY = 0.04
 MASK_SEED = 1001
 IMAGE_SEEDS = (1, 2, 3)
 TOL = 1e-6
+# The inpainting of the 4K step is solved to 1e-7: at 1e-6 the residual gate
+# holds but max |u - u*| reached 1.4e-3 on channel 0 against the FP64 oracle,
+# above the 1e-3 gate; 1e-7 meets both (one more V-cycle).
+TOL_INPAINT = 1e-7
 METRIC = "4K RGB inpaint+tonal-opt solves/s at rel-res 1e-6"
 UNIT = "solves/s"
 CROP = 512            # oracle sample: one channel, CROP x CROP, top-left crop of the workload
@@ -42,8 +46,10 @@ REF_CROP = 256        # per-step sample of the reference arm
 
 def workload_config(extra=None):
     cfg = {"workload": "3840x2160 RGB FP32, 4% random mask (seed 1001), channel seeds 1/2/3; "
-                       "cold inpaint to rel-res 1e-6 + tonal optimisation to rel-res 1e-6",
+                       "cold inpaint to rel-res 1e-7 (so that max|u-u*| <= 1e-3 also holds) + tonal optimisation "
+                       "to rel-res 1e-6",
            "height": H4K, "width": W4K, "channels": CH, "mask_density": DENSITY, "tol": TOL,
+           "inpaint_tol": TOL_INPAINT,
            "l2_policy": "L2 flushed (256 MB write) between timed steps; working set several GB"}
     if extra:
         cfg.update(extra)
@@ -253,7 +259,7 @@ def run_hdi(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
-        s1 = ctx.inpaint(fd, cd, u, tol=TOL)
+        s1 = ctx.inpaint(fd, cd, u, tol=TOL_INPAINT)
         s2 = ctx.tonal_opt(fd, cd, g, tol=TOL)
         return s1, s2
 
@@ -342,12 +348,12 @@ def run_hdi(args, rank, world):
     ch = torch.from_numpy(c).pin_memory()
     uh = torch.empty_like(fh).pin_memory()
     gh = torch.empty_like(fh).pin_memory()
-    ctx.inpaint(fh, ch, uh, tol=TOL)
+    ctx.inpaint(fh, ch, uh, tol=TOL_INPAINT)
     ctx.tonal_opt(fh, ch, gh, tol=TOL)
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ctx.inpaint(fh, ch, uh, tol=TOL)
+        ctx.inpaint(fh, ch, uh, tol=TOL_INPAINT)
         ctx.tonal_opt(fh, ch, gh, tol=TOL)
     torch.cuda.synchronize()
     te = all_max(time.perf_counter() - t0, world)
@@ -405,8 +411,12 @@ def run_reference(args, rank, world):
 
 def run_batch(args, rank, world):
     """64 images of uneven sizes {256x256, 512x384, 1024x768, 1920x1080,
-    2048x1080}, grey/RGB, mask density U[1%, 10%]: batched solve (one launch
-    per phase per size class) against one solve per image."""
+    2048x1080}, grey/RGB, mask density U[1%, 10%]: the batched
+    mixed-precision solve against one call per image, in the mixed-precision
+    form and in the plain FP32 form (FP32 iterate and residual, no
+    double-float refinement), all at the same relative residual (1e-5, which
+    the plain FP32 form reaches on every image; the mixed forms are also
+    timed at 1e-6, which the FP32 form cannot reach)."""
     import numpy as np
     import torch
     import paper_2401_06747_b300 as hdi
@@ -423,17 +433,22 @@ def run_batch(args, rank, world):
     outs = [torch.empty_like(x) for x in fs]
     stream = torch.cuda.current_stream()
     ctx = hdi.Context(local, stream=stream)
+    ctx32 = hdi.Context(local, stream=stream, inpaint_fp32=1)
     pix = sum(x.numel() for x in fs)
+    tol_eq = 1e-5
 
-    def batched():
-        return ctx.inpaint_batch(fs, ms, outs, tol=TOL)
+    def batched(tol):
+        return lambda: ctx.inpaint_batch(fs, ms, outs, tol=tol)
 
-    def single():
-        return [ctx.inpaint(f, m, o, tol=TOL) for f, m, o in zip(fs, ms, outs)]
+    def single(c, tol):
+        return lambda: [c.inpaint(f, m, o, tol=tol, allow_not_converged=True) for f, m, o in zip(fs, ms, outs)]
 
+    forms = (("per_image_fp32", single(ctx32, tol_eq), tol_eq), ("per_image_mixed", single(ctx, tol_eq), tol_eq),
+             ("batched_mixed", batched(tol_eq), tol_eq), ("per_image_mixed_1e-6", single(ctx, TOL), TOL),
+             ("batched_mixed_1e-6", batched(TOL), TOL))
     res = {}
-    for name, fn in (("per_image", single), ("batched", batched)):
-        for _ in range(args.warmup):
+    for name, fn, tol in forms:
+        for _ in range(max(args.warmup, 1)):
             fn()
         torch.cuda.synchronize()
         barrier(world)
@@ -445,15 +460,18 @@ def run_batch(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_ = all_max(e0.elapsed_time(e1), world)
-        res[name] = {"images_per_s": world * args.steps * len(fs) / (ms_ / 1e3), "ms_per_batch": ms_ / args.steps,
-                     "max_rel_res": max(s["rel_res"] for s in st)}
-    out = {"metric": "64-image uneven batch: inpaint solves/s at rel-res 1e-6", "value": round(res["batched"]["images_per_s"], 3),
-           "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": round(res["batched"]["ms_per_batch"], 3), "higher_is_better": True, "scaling": "weak",
+        res[name] = {"tol": tol, "images_per_s": round(world * args.steps * len(fs) / (ms_ / 1e3), 2),
+                     "ms_per_batch": round(ms_ / args.steps, 3), "max_rel_res": max(x["rel_res"] for x in st),
+                     "all_converged": all(x["status"] == 0 for x in st),
+                     "vcycles": sum(x["vcycles"] for x in st)}
+    head = res["batched_mixed"]
+    out = {"metric": "64-image uneven batch: inpaint solves/s at equal accuracy (rel-res 1e-5)",
+           "value": head["images_per_s"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": head["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"{len(fs)} images from batch_specs(seed 200): sizes 256x256..2048x1080, grey/RGB, "
-                                  f"density U[1%,10%]; {pix} values", "per_image_form": res["per_image"],
-                      "batched_form": res["batched"]}}
+                                  f"density U[1%,10%]; {pix} values", "forms": res,
+                      "batched_vs_plain_fp32": round(head["images_per_s"] / res["per_image_fp32"]["images_per_s"], 3)}}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -671,7 +689,8 @@ def run_prof(args, rank, world):
     out = torch.empty_like(fd)
     st = None
     for _ in range(args.solves):
-        st = ctx.inpaint(fd, cd, out, tol=TOL) if args.kind == "inpaint" else ctx.tonal_opt(fd, cd, out, tol=TOL)
+        st = (ctx.inpaint(fd, cd, out, tol=TOL_INPAINT) if args.kind == "inpaint"
+              else ctx.tonal_opt(fd, cd, out, tol=TOL))
     torch.cuda.synchronize()
     print(st)
 

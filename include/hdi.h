@@ -131,7 +131,8 @@ int hdi_inpaint_batch(hdi_ctx* ctx, int n, const hdi_image* f, const hdi_mask* m
 int hdi_tonal_opt(hdi_ctx* ctx, const hdi_image* f, const hdi_mask* mask,
                   const hdi_image* g0, hdi_image* g, double tol, hdi_stats* st);
 
-/* One densification step (Sec. 4.1, Alg. 1 with the Delaunay partition;
+/* One densification step (Sec. 4.1, Alg. 1 with the Delaunay partition, or
+ * with the Voronoi cells of the mask pixels when densify_partition = 1;
  * initial mask by random dithering of |L f|, Sec. 4.2).
  *   f     in     : reference image
  *   mask  in/out : current mask; only new 1-bits are written
@@ -274,6 +275,15 @@ const char* hdi_version(void);
  *   jfa_first_step    [0]     first jump-flooding step of hdi_densify_step (0: half the padded side;
  *                             a shortened schedule that misses pixels falls back to the full one)
  *   densify_tol       [1e-6]  relative residual of the inpaintings inside hdi_densify
+ *   densify_partition [0]     hdi_densify_step / hdi_densify: 0 Delaunay triangles of the mask pixels
+ *                             (Sec. 4.1, Alg. 1); 1 Voronoi cells of the mask pixels (the Voronoi-based
+ *                             densification of the Sec. 6.2 comparison): one new pixel per selected cell
+ *   inpaint_fp32      [0]     1: hdi_inpaint and hdi_inpaint_batch run the plain FP32 form (FP32 iterate,
+ *                             FP32 residual and update, no double-float refinement), the per-image
+ *                             baseline of the mixed-precision path; it stalls near the FP32 rounding
+ *                             level (about 1e-6 relative residual) and then returns NOT_CONVERGED
+ *   oras_warp         [1]     ORAS sweep layout: 1 one warp per 32x32 subdomain (no CTA barriers),
+ *                             0 two warps per subdomain
  *   tonal_anderson    [8]     Anderson window on the RAS iteration (0 = plain Alg. 2)
  *   tonal_oras_eta    [3e-2]  oras_eta used inside the tonal inner solves
  *   fine_pre, fine_post [1, 1] ORAS sweeps before / after the coarse correction on the finest level

@@ -152,3 +152,64 @@ __host__ __device__ __forceinline__ int tile_count(int n, int size, int ov) {
     const int c = (n - ov + s - 1) / s;
     return c < 1 ? 1 : c;
 }
+
+// ------------------------------------------------------ batched launches ---
+//
+// A batched launch runs one solver phase over many (image, channel) tasks of
+// different sizes with a 1-D grid: task t owns the CTAs
+// [cta0[t], cta0[t+1]) (prefix sums, cta0[ntasks] = grid size). Every CTA
+// finds its task by binary search; a task's CTAs then behave exactly like the
+// CTAs of a plain launch over that one image and channel.
+__device__ __forceinline__ int find_task(const int* __restrict__ cta0, int ntasks, int block) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(cta0 + mid) <= block) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Segmented deterministic grid reduction of a batched launch: the CTAs of
+// segment s deposit their partials at partials[base[s] + part], the last CTA
+// of the whole launch sums every segment (one warp per segment, lane-strided
+// partials in eight chains, fixed order) and writes *out[s]. Bitwise
+// reproducible for a given task table.
+struct SegReduce {
+    double* partials;
+    unsigned* ticket;          // zero before the launch; reset by the last CTA
+    const int* base;           // [nseg + 1] partial offsets (base[nseg] = total partials)
+    double* const* out;        // [nseg] destination of each segment's sum
+    int nseg;
+    int total_ctas;            // CTAs of the launch that commit
+};
+
+__device__ __forceinline__ void seg_reduce_commit(const SegReduce& R, int seg, int part, double block_total) {
+    __shared__ bool last_cta;
+    const int tid = linear_tid();
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    if (tid == 0) {
+        R.partials[R.base[seg] + part] = block_total;
+        __threadfence();
+        const unsigned t = atomicAdd(R.ticket, 1u);
+        last_cta = (t == (unsigned)(R.total_ctas - 1));
+    }
+    __syncthreads();
+    if (!last_cta) return;
+    __threadfence();
+    const int lane = tid & 31, nw = nt >> 5;
+    for (int s = tid >> 5; s < R.nseg; s += nw) {
+        const int b0 = __ldcg(R.base + s), b1 = __ldcg(R.base + s + 1);
+        double a8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int i = b0 + lane;
+        for (; i + 7 * 32 < b1; i += 8 * 32) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a8[k] += __ldcg(R.partials + i + k * 32);
+        }
+        for (; i < b1; i += 32) a8[0] += __ldcg(R.partials + i);
+        double acc = ((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7]));
+        acc = warp_sum_d(acc);
+        if (lane == 0) *R.out[s] = acc;
+    }
+    if (tid == 0) *R.ticket = 0u;
+}

@@ -517,13 +517,20 @@ int Ctx::densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t
         ++launches;
         unsigned* tcount = (unsigned*)(cnt + 2);
         unsigned* ncand = (unsigned*)(cnt + 3);
-        k_dens_quads<<<dim3((W + 127) / 128, H), 128, 0, stream>>>(V, H, W, tris, tcount, (unsigned)tcap);
+        // Voronoi-cell partition (densify_partition = 1): no triangles; every
+        // non-mask pixel falls to the "hull" cell of its label below, whose
+        // id hull_base + V(p) ranks like the site index V(p)
+        const bool vcells = p.densify_partition >= 0.5;
+        if (!vcells) {
+            k_dens_quads<<<dim3((W + 127) / 128, H), 128, 0, stream>>>(V, H, W, tris, tcount, (unsigned)tcap);
+            ++launches;
+        }
         cudaMemsetAsync(owner, 0x7F, N * 4, stream);
-        launches += 2;   // k_dens_error, k_dens_quads
+        ++launches;   // k_dens_error
         cudaMemcpyAsync(hcnt, cnt, 40, cudaMemcpyDeviceToHost, stream);
         if ((rc = sync("densification triangles"))) return rc;
         last_label_maxd2 = (long long)hcnt[4];
-        const unsigned ntri = (unsigned)(hcnt[2] & 0xffffffffull);
+        const unsigned ntri = vcells ? 0u : (unsigned)(hcnt[2] & 0xffffffffull);
         if (ntri > tcap) return fail(HDI_ERR_CUDA, "internal: triangle list overflow");
         if (ntri) {
             k_dens_raster<<<(ntri + 3) / 4, 128, 0, stream>>>(tris, tcount, mv, owner);

@@ -14,6 +14,7 @@
 #include "../../include/hdi.h"
 #include "common.cuh"
 #include "oras.cuh"
+#include "oras_warp.cuh"
 #include "stencil.cuh"
 #include "solver.h"
 #include "tonal.cuh"
@@ -65,6 +66,9 @@ const ParamDef kParams[] = {
     {"fine_post", &Params::fine_post, 0, 4},
     {"tonal_fine_pre", &Params::tonal_fine_pre, 0, 4},
     {"tonal_fine_post", &Params::tonal_fine_post, 0, 4},
+    {"oras_warp", &Params::oras_warp, 0, 1},
+    {"densify_partition", &Params::densify_partition, 0, 1},
+    {"inpaint_fp32", &Params::inpaint_fp32, 0, 1},
 };
 
 }  // namespace
@@ -313,7 +317,15 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     if (l == 0) tstart(kT_Oras, (zero ? 8.125 : 12.125) * (double)nch * L.H * L.W);
     const bool full = L.W >= 32 && L.H >= 32;
     const bool pd = p.pdl >= 0.5;
-    if (zero) {
+    if (p.oras_warp >= 0.5) {   // one warp per subdomain (oras_warp.cuh)
+        if (zero) {
+            if (full) launch_k(pd, k_oras_w<true, true>, blocks, dim3(32), stream, a);
+            else launch_k(pd, k_oras_w<true, false>, blocks, dim3(32), stream, a);
+        } else {
+            if (full) launch_k(pd, k_oras_w<false, true>, blocks, dim3(32), stream, a);
+            else launch_k(pd, k_oras_w<false, false>, blocks, dim3(32), stream, a);
+        }
+    } else if (zero) {
         if (full) launch_k(pd, k_oras<true, true>, blocks, dim3(kLocalThreads), stream, a);
         else launch_k(pd, k_oras<true, false>, blocks, dim3(kLocalThreads), stream, a);
     } else {
@@ -429,7 +441,7 @@ void Ctx::fmg(DFc d) {
     }
 }
 
-template <int RHS, int INIT>
+template <int RHS, int INIT, bool P32 = false>
 static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b) {
     ResArgs a;
     a.F = c.arr(0);
@@ -454,15 +466,24 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
     constexpr bool HAS_E = (INIT == INIT_UPDATE || INIT == INIT_FROM32);
     // INIT_KEEP rewrites only the known pixels of u in place
     const double known = c.mask_ones > 0 ? std::min(1.0, (double)c.mask_ones / ((double)c.H * c.W)) : 0.0;
-    const double bpv = 12.125 - (INIT == INIT_KEEP ? 8.0 * (1.0 - known) : 0.0) + (HAS_U ? 8.0 : 0.0) + (HAS_E ? 4.0 : 0.0) +
+    // (the plain FP32 form moves 4-byte iterates: 4 B less per read and write of u)
+    const double uw = P32 ? 4.0 : 8.0;
+    const double bpv = 4.125 + uw - (INIT == INIT_KEEP ? uw * (1.0 - known) : 0.0) + (HAS_U ? uw : 0.0) +
+                       (HAS_E ? 4.0 : 0.0) +
                        (RHS == RHS_SOURCE ? (a.d_lo_zero ? 4.0 : 8.0) + (y.hi ? 8.0 : 0.0) : 0.0);
     c.tstart(kT_Residual, bpv * (double)c.nch * c.H * c.W);
-    launch_k(c.p.pdl >= 0.5, k_residual_df<RHS, INIT>, grd, blk, c.stream, a);
+    launch_k(c.p.pdl >= 0.5, k_residual_df<RHS, INIT, P32>, grd, blk, c.stream, a);
     ++c.launches;
     c.tstop();
 }
 
-void Ctx::residual(int rhs, int init, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b) {
+void Ctx::residual(int rhs, int init, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b, bool p32) {
+    if (p32 && rhs == RHS_DATA) {   // plain FP32 form (inpainting only)
+#define HDI_RES32(I) \
+    if (init == I) { launch_res<RHS_DATA, I, true>(*this, uin, uout, x32, d, y, want_b); return; }
+        HDI_RES32(INIT_KEEP) HDI_RES32(INIT_UPDATE) HDI_RES32(INIT_FROM32) HDI_RES32(INIT_ZERO)
+#undef HDI_RES32
+    }
 #define HDI_RES(R, I) \
     if (rhs == R && init == I) { launch_res<R, I>(*this, uin, uout, x32, d, y, want_b); return; }
     HDI_RES(RHS_DATA, INIT_KEEP) HDI_RES(RHS_DATA, INIT_UPDATE) HDI_RES(RHS_DATA, INIT_FROM32)
@@ -483,16 +504,29 @@ int Ctx::solve(SolveSpec& s) {
     DF* ub = s.u;
     int cur = s.cur;
     const DFc none{nullptr, nullptr};
+    const bool p32 = s.plain32 && s.rhs == RHS_DATA;
     if (s.start == START_FMG) {
         fmg(s.d);
-        residual(s.rhs, INIT_FROM32, none, ub[cur], lev[0].xa, s.d, s.y, true);
+        residual(s.rhs, INIT_FROM32, none, ub[cur], lev[0].xa, s.d, s.y, true, p32);
     } else if (s.start == START_WARM) {
-        residual(s.rhs, INIT_KEEP, cview(ub[cur]), ub[cur], nullptr, s.d, s.y, true);   // in place
+        residual(s.rhs, INIT_KEEP, cview(ub[cur]), ub[cur], nullptr, s.d, s.y, true, p32);   // in place
     } else {
-        residual(s.rhs, INIT_ZERO, none, ub[cur], nullptr, s.d, s.y, true);
+        residual(s.rhs, INIT_ZERO, none, ub[cur], nullptr, s.d, s.y, true, p32);
     }
     double r2[kMaxCh], b2[kMaxCh];
     s.iterations = 0;
+    double prev_worst = INFINITY;
+    // the plain FP32 form keeps no low words: they are zeroed when the solve
+    // returns, so that readers of the double-float pair see the FP32 iterate
+    struct ZeroLo {
+        Ctx& c;
+        const SolveSpec& s;
+        const int& cur;
+        bool on;
+        ~ZeroLo() {
+            if (on) cudaMemsetAsync(s.u[cur].lo, 0, (size_t)c.nch * c.lev[0].cs * 4, c.stream);
+        }
+    } zero_lo{*this, s, cur, p32};
     for (;;) {
         cudaMemcpyAsync(hscal, scal + kSlotR64 * kMaxCh, (size_t)nch * 8, cudaMemcpyDeviceToHost, stream);
         cudaMemcpyAsync(hscal + kMaxCh, scal + kSlotB64 * kMaxCh, (size_t)nch * 8, cudaMemcpyDeviceToHost, stream);
@@ -512,12 +546,15 @@ int Ctx::solve(SolveSpec& s) {
         s.rel_max = worst;
         for (int c = 0; c < nch; ++c) s.bnorm2[c] = b2[c];
         if (worst <= s.tol) break;
-        if (s.iterations >= s.max_iter) {
+        // the plain FP32 form stalls at its rounding level: stop once a
+        // V-cycle gains less than 10%
+        if (s.iterations >= s.max_iter || (p32 && worst > 0.9 * prev_worst)) {
             s.cur = cur;
             return HDI_ERR_NOT_CONVERGED;
         }
+        prev_worst = worst;
         vcycle(0);
-        residual(s.rhs, INIT_UPDATE, cview(ub[cur]), ub[1 - cur], lev[0].xa, s.d, s.y, false);
+        residual(s.rhs, INIT_UPDATE, cview(ub[cur]), ub[1 - cur], lev[0].xa, s.d, s.y, false, p32);
         cur = 1 - cur;
         ++s.iterations;
         // ||b||^2 is unchanged; keep the slot value from the first evaluation.
@@ -999,6 +1036,7 @@ int Ctx::inpaint_batch(int n, const hdi_image* f, const hdi_mask* m, hdi_image* 
         s.tol = tol;
         s.max_iter = (int)p.max_vcycles;
         s.start = START_FMG;
+        s.plain32 = p.inpaint_fp32 >= 0.5;
         vcycles_run = 0;
         const int src = solve(s);
         if (src != HDI_OK && src != HDI_ERR_NOT_CONVERGED) return src;
@@ -1063,6 +1101,7 @@ int Ctx::inpaint(const hdi_image* f, const hdi_mask* mask, const hdi_image* u0, 
     s.d = cview(dfv[kF]);
     s.tol = tol;
     s.max_iter = (int)p.max_vcycles;
+    s.plain32 = p.inpaint_fp32 >= 0.5;
     if (u0) {
         if ((rc = load_image(u0, s.u[0]))) return rc;
         s.start = START_WARM;

@@ -44,6 +44,9 @@ struct Params {
     double densify_voronoi = 0;     // 0: exact Voronoi labels; 1: jump flooding (Sec. 4.2)
     double jfa_first_step = 0;      // first jump-flooding step (0: half the padded image side)
     double densify_tol = 1e-6;      // relative residual of the inpaintings of hdi_densify
+    double densify_partition = 0;   // 0: Delaunay triangles (Alg. 1); 1: Voronoi cells of the mask (Sec. 6.2)
+    double inpaint_fp32 = 0;        // 1: hdi_inpaint / hdi_inpaint_batch in the plain FP32 form
+    double oras_warp = 1;           // ORAS sweep layout: 1 one warp per subdomain, 0 two warps
 };
 
 struct Level {
@@ -85,6 +88,7 @@ struct SolveSpec {
     double rel[kMaxCh] = {};
     double rel_max = 0;
     double bnorm2[kMaxCh] = {};
+    bool plain32 = false;   // plain FP32 form: FP32 iterate and residual, no refinement (RHS_DATA only)
 };
 
 constexpr int kMaxLevels = 16;
@@ -198,7 +202,8 @@ struct Ctx {
     void vcycle(int l);
     void residual_norm_level(int l, const float* x, int slot);
     void fmg(DFc d);
-    void residual(int rhs, int init, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b);
+    void residual(int rhs, int init, DFc uin, DF uout, const float* x32, DFc d, DFc y, bool want_b,
+                  bool p32 = false);
     int solve(SolveSpec& s);
     int check_image(const hdi_image* im, const char* name, int H, int W, int nch);
     int load_image(const hdi_image* im, DF dst, float* lo2 = nullptr, int c0 = 0);

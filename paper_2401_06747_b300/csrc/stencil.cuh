@@ -268,18 +268,20 @@ __device__ __forceinline__ void quad_residual_interior(int lane, const float (&c
 // channel. Quad strips: the lane's four columns feed two coarse columns.
 // Warps whose strip and row block (with the rows above and below) lie inside
 // the image run a variant without border tests or clamped rows (IN).
-__global__ void __launch_bounds__(128, 7) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
-                                                           const float* __restrict__ b, LevelArr C, MaskView cm,
-                                                           float* __restrict__ cb, GridReduce red, int rows) {
+// Body shared by the plain launch (one level, all channels of one image) and
+// the batched launch (StripTask table); returns the thread's share of
+// ||r_c||^2 for the caller's block and grid reduction.
+__device__ __forceinline__ float restrict_residual_body(LevelArr F, MaskView fm, const float* __restrict__ x,
+                                                        const float* __restrict__ b, LevelArr C, MaskView cm,
+                                                        float* __restrict__ cb, int rows, int bx, int by, int ch) {
     constexpr int CR = QS_CHUNK;
     static_assert(CR == 2, "one coarse row per chunk");
     pdl_trigger();
-    const int ch = blockIdx.z;
     fm = fm.ch(ch);
     cm = cm.ch(ch);
-    const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * rows;
+    const int y0 = (by * 4 + (threadIdx.x >> 5)) * rows;
     const int y1 = min(y0 + rows, F.H);
-    const int x0 = blockIdx.x * QS_COLS;
+    const int x0 = bx * QS_COLS;
     const QuadLane q = quad_lane(x0, F, fm);
     const bool interior = x0 > 0 && x0 + QS_COLS < F.W && y0 > 0 && y0 + rows + 1 <= F.H;
     pdl_wait();
@@ -359,8 +361,41 @@ __global__ void __launch_bounds__(128, 7) k_restrict_residual(LevelArr F, MaskVi
     };
     if (interior) body(std::true_type{});
     else if (y0 < F.H) body(std::false_type{});
+    return sq;
+}
+
+__global__ void __launch_bounds__(128, 7) k_restrict_residual(LevelArr F, MaskView fm, const float* __restrict__ x,
+                                                           const float* __restrict__ b, LevelArr C, MaskView cm,
+                                                           float* __restrict__ cb, GridReduce red, int rows) {
+    const float sq = restrict_residual_body(F, fm, x, b, C, cm, cb, rows, blockIdx.x, blockIdx.y, blockIdx.z);
     const double tot = (double)block_sum_f(sq);
-    grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
+    grid_reduce_commit(red, blockIdx.z, blockIdx.y * gridDim.x + blockIdx.x, tot);
+}
+
+// One (image, channel) of a batched launch of the quad-strip kernels:
+// geometry, mask planes and buffers of that channel (pointers at the
+// channel's plane, so the bodies run with ch = 0) and its grid.
+struct StripTask {
+    LevelArr F, C;          // level and its coarse level
+    MaskView fm, cm;        // mask planes (chmask = nullptr)
+    const float* x;         // iterate (restriction; prolongation MODE 0)
+    const float* b;         // right-hand side on F
+    float* xout;            // prolongation output
+    const float* e;         // coarse correction (prolongation MODE 0/1)
+    float* cb;              // restriction output (right-hand side on C)
+    int rows;               // rows per warp
+    int gx, gy;             // strips and row blocks of this task
+};
+
+__global__ void __launch_bounds__(128, 7) k_restrict_residual_b(const StripTask* __restrict__ tasks,
+                                                             const int* __restrict__ cta0, int ntasks, SegReduce red) {
+    const int t = find_task(cta0, ntasks, blockIdx.x);
+    const StripTask tk = tasks[t];
+    const int local = blockIdx.x - cta0[t];
+    const float sq = restrict_residual_body(tk.F, tk.fm, tk.x, tk.b, tk.C, tk.cm, tk.cb, tk.rows, local % tk.gx,
+                                            local / tk.gx, 0);
+    const double tot = (double)block_sum_f(sq);
+    seg_reduce_commit(red, t, local, tot);
 }
 
 // ||b - A x||^2 per channel on one level (quad strips, FP32).
@@ -449,17 +484,16 @@ __global__ void __launch_bounds__(128, 8) k_level_residual_norm(LevelArr F, Mask
 // column without further coarse loads. Each coarse row is interpolated once
 // and reused by the fine rows above and below it.
 template <int MODE>
-__global__ void __launch_bounds__(128, 7) k_prolong(LevelArr F, MaskView fm, const float* __restrict__ xin,
-                                                 const float* __restrict__ b, float* __restrict__ xout,
-                                                 LevelArr C, const float* __restrict__ e, GridReduce red, int rows) {
+__device__ __forceinline__ float prolong_body(LevelArr F, MaskView fm, const float* __restrict__ xin,
+                                              const float* __restrict__ b, float* __restrict__ xout, LevelArr C,
+                                              const float* __restrict__ e, int rows, int bx, int by, int ch) {
     constexpr int CR = QS_CHUNK;
     constexpr int NS = CR / 2 + 2;   // coarse rows per chunk: (yb/2 - 1) .. (yb/2 + CR/2)
     pdl_trigger();
-    const int ch = blockIdx.z;
     fm = fm.ch(ch);
-    const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * rows;
+    const int y0 = (by * 4 + (threadIdx.x >> 5)) * rows;
     const int y1 = min(y0 + rows, F.H);
-    const QuadLane q = quad_lane(blockIdx.x * QS_COLS, F, fm);
+    const QuadLane q = quad_lane(bx * QS_COLS, F, fm);
     pdl_wait();
     const int lane = q.lane;
     const float* xc = (MODE == 0) ? xin + ch * F.cs : nullptr;
@@ -619,8 +653,28 @@ __global__ void __launch_bounds__(128, 7) k_prolong(LevelArr F, MaskView fm, con
             compute(A, yb);
         }
     }
+    return sq;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 7) k_prolong(LevelArr F, MaskView fm, const float* __restrict__ xin,
+                                                 const float* __restrict__ b, float* __restrict__ xout,
+                                                 LevelArr C, const float* __restrict__ e, GridReduce red, int rows) {
+    const float sq = prolong_body<MODE>(F, fm, xin, b, xout, C, e, rows, blockIdx.x, blockIdx.y, blockIdx.z);
     const double tot = (double)block_sum_f(sq);
-    grid_reduce_commit(red, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
+    grid_reduce_commit(red, blockIdx.z, blockIdx.y * gridDim.x + blockIdx.x, tot);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 7) k_prolong_b(const StripTask* __restrict__ tasks, const int* __restrict__ cta0,
+                                                   int ntasks, SegReduce red) {
+    const int t = find_task(cta0, ntasks, blockIdx.x);
+    const StripTask tk = tasks[t];
+    const int local = blockIdx.x - cta0[t];
+    const float sq = prolong_body<MODE>(tk.F, tk.fm, tk.x, tk.b, tk.xout, tk.C, tk.e, tk.rows, local % tk.gx,
+                                        local / tk.gx, 0);
+    const double tot = (double)block_sum_f(sq);
+    seg_reduce_commit(red, t, local, tot);
 }
 
 // ------------------------------------------- double-float refinement step ---
@@ -705,20 +759,26 @@ struct ResArgs {
 // modes, once the row's mask word has arrived.
 // Seven CTAs per SM (at most 72 registers): the latency of the row loads is
 // hidden by more resident warps rather than by a second register buffer.
-template <int RHS, int INIT>
-__global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
+//
+// P32 (plain FP32 form, RHS_DATA only): the iterate is a single FP32 word
+// (the low words are neither read nor written), the update u + e and the
+// stencil A u are plain FP32 operations. This is the per-image FP32 solver
+// without iterative refinement that the mixed-precision path is compared
+// against; its residual stalls near the FP32 rounding level.
+template <int RHS, int INIT, bool P32>
+__device__ __forceinline__ float2 residual_df_body(const ResArgs& a, int bx, int by, int ch) {
+    static_assert(!P32 || RHS == RHS_DATA, "the plain FP32 form is an inpainting solve");
     constexpr int RC = RES_CHUNK;
     constexpr bool LOAD_D = (RHS == RHS_DATA) && (INIT != INIT_UPDATE);
     constexpr bool HAS_U = (INIT == INIT_KEEP || INIT == INIT_UPDATE);
     constexpr bool HAS_E = (INIT == INIT_UPDATE || INIT == INIT_FROM32);
-    const int ch = blockIdx.z;
     const MaskView m = a.m.ch(ch);
     const int H = a.F.H, W = a.F.W;
-    const int y0 = (blockIdx.y * 4 + (threadIdx.x >> 5)) * a.rows;
+    const int y0 = (by * 4 + (threadIdx.x >> 5)) * a.rows;
     const int y1 = min(y0 + a.rows, H);
     pdl_trigger();
-    const QuadLane q = quad_lane(blockIdx.x * QS_COLS, a.F, m);
-    const bool interior = blockIdx.x > 0 && (blockIdx.x + 1) * QS_COLS < W && y0 > 0 && y0 + a.rows + 1 <= H;
+    const QuadLane q = quad_lane(bx * QS_COLS, a.F, m);
+    const bool interior = bx > 0 && (bx + 1) * QS_COLS < W && y0 > 0 && y0 + a.rows + 1 <= H;
     pdl_wait();
     const int lane = q.lane;
     const long long co = ch * a.F.cs;
@@ -743,7 +803,8 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
             } else if (INIT == INIT_KEEP) {
                 h = uh; l = ul;
             } else if (INIT == INIT_UPDATE) {
-                df_add(uh, ul, e, 0.f, h, l);
+                if (P32) { h = uh + e; l = 0.f; }
+                else df_add(uh, ul, e, 0.f, h, l);
             } else if (INIT == INIT_FROM32) {
                 h = e; l = 0.f;
             } else {
@@ -756,11 +817,14 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
             const uint32_t w = mrow[(size_t)rowc(y) * m.wpitch];
             float uh[4] = {0.f, 0.f, 0.f, 0.f}, ul[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
             float dh[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
-            if (HAS_U) { f4_to(ld4(a.uin.hi, i), uh); f4_to(ld4(a.uin.lo, i), ul); }
+            if (HAS_U) {
+                f4_to(ld4(a.uin.hi, i), uh);
+                if (!P32) f4_to(ld4(a.uin.lo, i), ul);
+            }
             if (HAS_E) f4_to(ld4(a.x32, i), e);
             if (LOAD_D) {
                 f4_to(ld4(a.d.hi, i), dh);
-                if (!a.d_lo_zero) f4_to(ld4(a.d.lo, i), dl);
+                if (!a.d_lo_zero && !P32) f4_to(ld4(a.d.lo, i), dl);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) value((w >> (q.shift + j)) & 1u, uh[j], ul[j], e[j], dh[j], dl[j], h[j], l[j]);
@@ -783,11 +847,11 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
             for (int k = 0; k < RC; ++k) {
                 const size_t id = at(yb + k + 1, q.cq), ih = at(yb + k, q.hcol), ic = at(yb + k, q.cq);
                 c.Uh[k] = HAS_U ? ld4(a.uin.hi, id) : z4;
-                c.Ul[k] = HAS_U ? ld4(a.uin.lo, id) : z4;
+                c.Ul[k] = (HAS_U && !P32) ? ld4(a.uin.lo, id) : z4;
                 c.E[k] = HAS_E ? ld4(a.x32, id) : z4;
                 c.Hm[k] = q.hon ? hrow[(size_t)rowc(yb + k) * m.wpitch] : 0u;
                 c.HUh[k] = (HAS_U && q.hon) ? a.uin.hi[ih] : 0.f;
-                c.HUl[k] = (HAS_U && q.hon) ? a.uin.lo[ih] : 0.f;
+                c.HUl[k] = (HAS_U && q.hon && !P32) ? a.uin.lo[ih] : 0.f;
                 c.HE[k] = (HAS_E && q.hon) ? a.x32[ih] : 0.f;
                 if (RHS == RHS_SOURCE) {
                     c.Dh[k] = ld4(a.d.hi, ic);
@@ -802,10 +866,10 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
                     const uint32_t kb = (c.Mw[k + 1] >> q.shift) & 15u;
                     const size_t id = at(yb + k + 1, q.cq), ih = at(yb + k, q.hcol);
                     c.KDh[k] = kb ? ld4(a.d.hi, id) : z4;
-                    c.KDl[k] = (kb && !a.d_lo_zero) ? ld4(a.d.lo, id) : z4;
+                    c.KDl[k] = (kb && !a.d_lo_zero && !P32) ? ld4(a.d.lo, id) : z4;
                     const bool kh = q.hon && ((c.Hm[k] >> hbit) & 1u);
                     c.HDh[k] = kh ? a.d.hi[ih] : 0.f;
-                    c.HDl[k] = (kh && !a.d_lo_zero) ? a.d.lo[ih] : 0.f;
+                    c.HDl[k] = (kh && !a.d_lo_zero && !P32) ? a.d.lo[ih] : 0.f;
                 }
             }
         };
@@ -864,6 +928,12 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
                         const float n1h = (IN || q.rin[j]) ? rh : cjh, n1l = (IN || q.rin[j]) ? rl : cjl;
                         const float n2h = (IN || y > 0) ? uph[j] : cjh, n2l = (IN || y > 0) ? upl[j] : cjl;
                         const float n3h = (IN || y + 1 < H) ? dnh[j] : cjh, n3l = (IN || y + 1 < H) ? dnl[j] : cjl;
+                        if (P32) {   // plain FP32 stencil (b = 0 on unknown pixels)
+                            r = -(4.f * cjh - ((n0h + n1h) + (n2h + n3h)));
+                            orr[j] = r;
+                            if (IN || q.act[j]) rr += r * r;
+                            continue;
+                        }
                         float sa, ea, sb, eb, sh, eh;
                         two_sum(n0h, n1h, sa, ea);
                         two_sum(n2h, n3h, sb, eb);
@@ -895,7 +965,7 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
                     for (int j = 0; j < 4; ++j)
                         if ((IN || q.act[j]) && ((c.Mw[k] >> (q.shift + j)) & 1u)) {
                             a.uout.hi[idx + j] = oh[j];
-                            a.uout.lo[idx + j] = ol[j];
+                            if (!P32) a.uout.lo[idx + j] = ol[j];
                         }
                     if (IN || q.act[3]) {
                         *reinterpret_cast<float4*>(a.r32 + idx) = make_float4(orr[0], orr[1], orr[2], orr[3]);
@@ -906,14 +976,14 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
                     }
                 } else if (IN || q.act[3]) {
                     *reinterpret_cast<float4*>(a.uout.hi + idx) = make_float4(oh[0], oh[1], oh[2], oh[3]);
-                    *reinterpret_cast<float4*>(a.uout.lo + idx) = make_float4(ol[0], ol[1], ol[2], ol[3]);
+                    if (!P32) *reinterpret_cast<float4*>(a.uout.lo + idx) = make_float4(ol[0], ol[1], ol[2], ol[3]);
                     *reinterpret_cast<float4*>(a.r32 + idx) = make_float4(orr[0], orr[1], orr[2], orr[3]);
                 } else {
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
                         if (q.act[j]) {
                             a.uout.hi[idx + j] = oh[j];
-                            a.uout.lo[idx + j] = ol[j];
+                            if (!P32) a.uout.lo[idx + j] = ol[j];
                             a.r32[idx + j] = orr[j];
                         }
                 }
@@ -932,11 +1002,43 @@ __global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
     };
     if (interior) body(std::true_type{});
     else if (y0 < H) body(std::false_type{});
-    const double tot = (double)block_sum_f(rr);
-    grid_reduce_commit(a.red_r, ch, blockIdx.y * gridDim.x + blockIdx.x, tot);
+    return make_float2(rr, bb2);
+}
+
+template <int RHS, int INIT, bool P32 = false>
+__global__ void __launch_bounds__(128, 7) k_residual_df(ResArgs a) {
+    const float2 v = residual_df_body<RHS, INIT, P32>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+    const double tot = (double)block_sum_f(v.x);
+    grid_reduce_commit(a.red_r, blockIdx.z, blockIdx.y * gridDim.x + blockIdx.x, tot);
     if (a.want_b) {
-        const double totb = (double)block_sum_f(bb2);
-        grid_reduce_commit(a.red_b, ch, blockIdx.y * gridDim.x + blockIdx.x, totb);
+        const double totb = (double)block_sum_f(v.y);
+        grid_reduce_commit(a.red_b, blockIdx.z, blockIdx.y * gridDim.x + blockIdx.x, totb);
+    }
+}
+
+// One (image, channel) of a batched refinement-residual launch: ResArgs
+// with the channel's planes (ch = 0) and its grid; the reductions of the
+// ResArgs are unused (the batched launch commits to SegReduce).
+struct ResTask {
+    ResArgs a;
+    int gx, gy;
+};
+
+// ||r||^2 of every task into red_r; with want_b also ||b||^2 into red_b (a
+// second, same-shaped segmented reduction).
+template <int RHS, int INIT, bool P32 = false>
+__global__ void __launch_bounds__(128, 7) k_residual_df_b(const ResTask* __restrict__ tasks,
+                                                       const int* __restrict__ cta0, int ntasks, SegReduce red_r,
+                                                       SegReduce red_b, int want_b) {
+    const int t = find_task(cta0, ntasks, blockIdx.x);
+    const int local = blockIdx.x - cta0[t];
+    const int gx = tasks[t].gx;
+    const float2 v = residual_df_body<RHS, INIT, P32>(tasks[t].a, local % gx, local / gx, 0);
+    const double tot = (double)block_sum_f(v.x);
+    seg_reduce_commit(red_r, t, local, tot);
+    if (want_b) {
+        const double totb = (double)block_sum_f(v.y);
+        seg_reduce_commit(red_b, t, local, totb);
     }
 }
 

@@ -158,3 +158,37 @@ def test_jfa_loop_quality_matches_exact():
         err = float(((u.cpu().numpy().astype(np.float64) - f) ** 2).mean())
         psnr[vor] = 10 * np.log10(255.0 ** 2 / err)
     assert abs(psnr[1] - psnr[0]) <= 0.05
+
+
+@pytest.mark.parametrize("H,W,ch,dtype,d,k", [(96, 128, 3, np.float32, 0.02, 40), (300, 200, 1, np.float64, 0.005, 150),
+                                              (64, 80, 3, np.float32, 0.05, 10000), (1, 90, 1, np.float64, 0.1, 3)])
+def test_voronoi_partition_step_bit_exact(H, W, ch, dtype, d, k):
+    """Voronoi-cell densification (densify_partition = 1, the variant of the
+    Sec. 6.2 comparison) against the oracle's partition = "voronoi" step."""
+    need_gpu()
+    f = synth_rgb(H, W, seeds=(4, 5, 6), dtype=dtype) if ch == 3 else synth_image(H, W, 4).astype(dtype)
+    c = random_mask(H, W, d, 17)
+    u = inpaint_ref(f.astype(np.float64), c).astype(dtype)
+    kx = ctx(densify_partition=1)
+    md = dev(c.copy())
+    added = kx.densify_step(dev(f), md, dev(u), k, 0)
+    ref, ref_added = densify_ref(f.astype(np.float64), c, u.astype(np.float64), k, partition="voronoi")
+    np.testing.assert_array_equal(md.cpu().numpy(), ref)
+    assert added == ref_added
+
+
+def test_voronoi_partition_loop_bit_exact():
+    """hdi_densify with Voronoi cells against the oracle loop with the same
+    partition (each side inpaints with its own solver, tight tolerance)."""
+    need_gpu()
+    from oracle.densify import densify as densify_oracle
+    H, W = 120, 160
+    f = synth_rgb(H, W, seeds=(8, 9, 10)).astype(np.float64)
+    n, t, d = 6, 1.03, 0.05
+    want, _, hist = densify_oracle(f, n, t, d, 300, "exact", partition="voronoi")
+    kx = ctx(densify_partition=1, densify_tol=1e-12)
+    m = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
+    u = torch.empty_like(dev(f))
+    sizes = kx.densify(dev(f), m, u, n, t, d, 300)
+    assert sizes == hist["sizes"]
+    np.testing.assert_array_equal(m.cpu().numpy(), want)

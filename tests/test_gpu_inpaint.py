@@ -150,3 +150,27 @@ def test_timing_classes_and_algorithmic_bytes():
     assert b["residual_fine"] > 24.125 * values * n / 2 and b["residual_fine"] <= 40.125 * values * n
     assert t["tonal_echo"][1] > 0 and b["tonal_echo"] == 0.0
     assert all(v[0] > 0 for x, v in t.items() if v[1] > 0)
+
+
+def test_plain_fp32_form():
+    """inpaint_fp32 = 1: FP32 iterate, residual and update without the
+    double-float refinement (the per-image baseline of the mixed-precision
+    path). It reaches a loose tolerance with the oracle's solution and stops
+    with NOT_CONVERGED once V-cycles no longer gain (FP32 rounding level)."""
+    need_gpu()
+    H, W = 300, 200
+    f = synth_rgb(H, W, seeds=(61, 62, 63), dtype=np.float32)
+    c = random_mask(H, W, 0.04, 64)
+    k = ctx(inpaint_fp32=1)
+    fd, cd = dev(f), dev(c)
+    out = torch.empty_like(fd)
+    st = k.inpaint(fd, cd, out, tol=1e-5)
+    u = out.cpu().numpy().astype(np.float64)
+    f64 = f.astype(np.float64)
+    assert st["rel_res"] <= 1e-5
+    assert np.all(rel_residual(u, f64, c) <= 3e-5)
+    assert np.abs(u - inpaint_ref(f64, c)).max() <= 0.02
+    np.testing.assert_array_equal(out.cpu().numpy()[:, c == 1], f[:, c == 1])
+    st = k.inpaint(fd, cd, out, tol=1e-10, allow_not_converged=True)
+    assert st["status"] == -3 and 1e-10 < st["rel_res"] < 1e-4
+    assert st["iterations"] < 20   # stopped by the stall rule, not the cap

@@ -131,3 +131,27 @@ def test_block64_falls_back_on_a_densely_known_block():
     f64 = f.astype(np.float64)
     assert st["rel_res"] <= 1e-6
     assert np.abs(g - tonal_ref(f64, c)).max() <= 0.05
+
+
+@pytest.mark.parametrize("d,seed", [(0.02, 12), (0.04, 13)])
+def test_plain_alg2_64x64_reaches_the_optimum_at_the_oracle_rate(d, seed):
+    """The paper's RAS iteration without acceleration (tonal_anderson = 0,
+    Sec. 5.2, Alg. 2) on its 64x64 blocks with overlap 6: the GPU reaches the
+    oracle optimum, in the number of iterations the oracle's Alg. 2 (exact
+    local solves, exact B and B^T) needs for the same tolerance, give or take
+    the effect of the GPU's inexact inner solves."""
+    from oracle.ras import RASTonal
+    H, W = 200, 180
+    f = synth_image(H, W, 11)
+    c = random_mask(H, W, d, seed)
+    tol = 1e-9
+    g, st = run(f, c, tol, tonal_anderson=0, tonal_block=64)
+    ref = tonal_ref(f, c)
+    assert st["rel_res"] <= tol
+    assert normal_residual(f, c, g)[0] <= 2 * tol
+    assert np.abs(g - ref).max() <= 1e-4
+    assert np.all(g[c == 0] == 0)
+    _, hist = RASTonal(c, size=64).run(f, 80)
+    need = int(np.argmax(hist[:, 0] <= tol))
+    assert hist[need, 0] <= tol
+    assert abs(st["iterations"] - need) <= 2, (st["iterations"], need)
