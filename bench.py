@@ -434,24 +434,28 @@ def run_batch(args, rank, world):
     stream = torch.cuda.current_stream()
     ctx = hdi.Context(local, stream=stream)
     ctx32 = hdi.Context(local, stream=stream, inpaint_fp32=1)
+    ctxc = hdi.Context(local, stream=stream, batch_engine=0)
     pix = sum(x.numel() for x in fs)
     tol_eq = 1e-5
 
-    def batched(tol):
-        return lambda: ctx.inpaint_batch(fs, ms, outs, tol=tol)
+    def batched(tol, c=ctx):
+        return lambda: c.inpaint_batch(fs, ms, outs, tol=tol)
 
     def single(c, tol):
         return lambda: [c.inpaint(f, m, o, tol=tol, allow_not_converged=True) for f, m, o in zip(fs, ms, outs)]
 
+    # batched_mixed: the engine (one launch per phase across all sizes);
+    # batched_classes: images of one size stacked as channels, classes in turn
     forms = (("per_image_fp32", single(ctx32, tol_eq), tol_eq), ("per_image_mixed", single(ctx, tol_eq), tol_eq),
-             ("batched_mixed", batched(tol_eq), tol_eq), ("per_image_mixed_1e-6", single(ctx, TOL), TOL),
-             ("batched_mixed_1e-6", batched(TOL), TOL))
+             ("batched_mixed", batched(tol_eq), tol_eq), ("batched_classes", batched(tol_eq, ctxc), tol_eq),
+             ("per_image_mixed_1e-6", single(ctx, TOL), TOL), ("batched_mixed_1e-6", batched(TOL), TOL))
     res = {}
     for name, fn, tol in forms:
         for _ in range(max(args.warmup, 1)):
             fn()
         torch.cuda.synchronize()
         barrier(world)
+        l0 = ctx.launch_count() + ctxc.launch_count() + ctx32.launch_count()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -460,7 +464,9 @@ def run_batch(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_ = all_max(e0.elapsed_time(e1), world)
+        nl = ctx.launch_count() + ctxc.launch_count() + ctx32.launch_count() - l0
         res[name] = {"tol": tol, "images_per_s": round(world * args.steps * len(fs) / (ms_ / 1e3), 2),
+                     "launches_per_batch": round(nl / args.steps),
                      "ms_per_batch": round(ms_ / args.steps, 3), "max_rel_res": max(x["rel_res"] for x in st),
                      "all_converged": all(x["status"] == 0 for x in st),
                      "vcycles": sum(x["vcycles"] for x in st)}
@@ -610,16 +616,20 @@ def run_densify(args, rank, world):
     # the paper's spatial-optimisation setting through hdi_densify (Sec. 6.2:
     # 20 iterations to 5%), exact and jump-flooding labels, t = 1 and 1.03
     import math
+    # partition: Delaunay triangles (the paper's method) or Voronoi cells (the
+    # Sec. 6.2 comparison), at 5% and 10%
     runs = []
-    for vor, t in ((0, 1.0), (1, 1.0), (0, 1.03), (1, 1.03)):
-        c2 = hdi.Context(local, stream=stream, densify_voronoi=vor)
+    for part, vor, t, dens in ((0, 0, 1.0, 0.05), (0, 1, 1.0, 0.05), (0, 0, 1.03, 0.05), (0, 1, 1.03, 0.05),
+                               (1, 0, 1.0, 0.05), (1, 0, 1.03, 0.05), (0, 0, 1.0, 0.10), (1, 0, 1.0, 0.10)):
+        c2 = hdi.Context(local, stream=stream, densify_voronoi=vor, densify_partition=part)
         m = torch.zeros((H4K, W4K), dtype=torch.uint8, device="cuda")
         u = torch.empty_like(f)
-        c2.densify(f, m, u, 20, t, 0.05, 300)
+        c2.densify(f, m, u, 20, t, dens, 300)
         torch.cuda.synchronize()
-        t20, sizes = _timed(lambda: (m.zero_(), c2.densify(f, m, u, 20, t, 0.05, 300))[1], stream, 1)
+        t20, sizes = _timed(lambda: (m.zero_(), c2.densify(f, m, u, 20, t, dens, 300))[1], stream, 1)
         err = float(((u - f).double() ** 2).mean().item())
-        runs.append({"voronoi": "jfa" if vor else "exact", "t": t, "iterations": 20, "ms": round(t20, 2),
+        runs.append({"partition": "voronoi cells" if part else "delaunay", "labels": "jfa" if vor else "exact",
+                     "t": t, "density": dens, "iterations": 20, "ms": round(t20, 2),
                      "mask_pixels": sizes[-1], "psnr_db": round(10 * math.log10(255.0 ** 2 / err), 3)})
     out = {"metric": "C4 densify loop: 4K RGB, 8 x 0.5% steps + warm re-inpaint + tonal, loops/s",
            "value": round(1e3 / ms_, 4), "unit": "loops/s", "n_gpus": world, "steps": args.steps,
@@ -627,7 +637,7 @@ def run_densify(args, rank, world):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "3840x2160 RGB (seeds 1/2/3), empty mask, densify seed 300", "mask_pixels": ones,
                       "tonal": {k: st[k] for k in ("iterations", "vcycles", "rel_res", "mse")},
-                      "densify_20_to_5pct": runs}}
+                      "densify_20_iterations": runs}}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -667,7 +677,9 @@ def run_serve(args, rank, world):
            "p50_ms": round(res["p50_ms"], 2), "p99_ms": round(res["p99_ms"], 2),
            "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, 512^2..3840x2160, "
                                   f"70/25/5 inpaint/tonal/densify-to-3 percent, budget {args.budget_gb} GB",
-                      "kinds": kinds, "per_kind": per_kind, "inpaint_batches": res["inpaint_batches"]}}
+                      "kinds": kinds, "per_kind": per_kind, "engine_steps": res["engine_steps"],
+                      "max_inpaint_in_flight": res["max_inpaint_in_flight"],
+                      "worker_workspace_bytes": res["worker_workspace_bytes"]}}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -688,6 +700,18 @@ def run_prof(args, rank, world):
     cd = torch.from_numpy(c).cuda()
     out = torch.empty_like(fd)
     st = None
+    if args.kind == "densify":
+        # one densification step (Alg. 1) from the 4% mask and its inpainting,
+        # Delaunay then Voronoi-cell partition
+        ctx.inpaint(fd, cd, out, tol=TOL)
+        for part in (0, 1):
+            ctx.set_param("densify_partition", part)
+            for _ in range(args.solves):
+                md = cd.clone()
+                st = ctx.densify_step(fd, md, out, int(round(0.005 * args.height * args.width)), 300)
+        torch.cuda.synchronize()
+        print({"added": st})
+        return
     for _ in range(args.solves):
         st = (ctx.inpaint(fd, cd, out, tol=TOL_INPAINT) if args.kind == "inpaint"
               else ctx.tonal_opt(fd, cd, out, tol=TOL))
@@ -704,7 +728,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["4k", "batch", "serve", "sweep", "densify", "tonal", "prof"],
                     default="4k")
-    ap.add_argument("--kind", choices=["inpaint", "tonal"], default="inpaint", help="--workload prof: solve kind")
+    ap.add_argument("--kind", choices=["inpaint", "tonal", "densify"], default="inpaint",
+                    help="--workload prof: solve kind")
     ap.add_argument("--solves", type=int, default=2, help="--workload prof: number of solves")
     ap.add_argument("--height", type=int, default=H4K, help="--workload prof: image height")
     ap.add_argument("--width", type=int, default=W4K, help="--workload prof: image width")

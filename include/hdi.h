@@ -107,18 +107,59 @@ int hdi_get_param(const hdi_ctx* ctx, const char* name, double* value);
 int hdi_inpaint(hdi_ctx* ctx, const hdi_image* f, const hdi_mask* mask,
                 const hdi_image* u0, hdi_image* u, double tol, hdi_stats* st);
 
-/* Batched inpainting of n independent images of uneven sizes (1..4
- * channels each, each with its own mask), e.g. a request batch. Images with
- * the same height and width form one size class and are solved as ONE
- * system whose channels are all their channels: every solver phase (ORAS
- * sweep, transfer, residual) is a single kernel launch over all subdomains
- * and pixels of the class, and the refinement loop runs until every channel
- * of the class meets tol. Size classes are processed one after another.
+/* Batched inpainting of n independent images of uneven sizes (any number of
+ * channels each, each with its own mask), e.g. a request batch. By default
+ * (batch_engine = 1) the images go through the batched engine below: every
+ * solver phase (ORAS sweep on a level, restriction, prolongation, data
+ * pyramid, refinement residual) is ONE kernel launch over all images of all
+ * sizes in flight, driven by a (request, channel) task table, and each image
+ * stops at its own tolerance. Images are admitted while their workspaces fit
+ * hbm_budget_gb; the rest join as earlier ones finish. batch_engine = 0
+ * stacks images of one size as the channels of one system and runs the size
+ * classes one after another (also the path of the plain FP32 form).
  *   f[n], masks[n], u[n] : as for hdi_inpaint (arrays of descriptors)
  *   st[n]                : per-image statistics (may be NULL)
  * Returns HDI_ERR_NOT_CONVERGED if any image missed tol (others are valid). */
 int hdi_inpaint_batch(hdi_ctx* ctx, int n, const hdi_image* f, const hdi_mask* masks, hdi_image* u,
                       double tol, hdi_stats* st);
+
+/* Batched inpainting engine with continuous admission: requests (images of
+ * any size) join and leave at V-cycle boundaries. The paper has no
+ * counterpart; it serves many inpainting solves of uneven sizes at once
+ * (Sec. 2.1 systems, Sec. 3 solver). Each hdi_engine_step runs reduced full
+ * multigrid for the requests submitted since the previous step and one
+ * V-cycle plus the double-float refinement update for every other request,
+ * each phase as one kernel launch over all requests' (channel, tile) work;
+ * requests whose relative residual meets their tolerance are finished (u
+ * written) and reported. The engine owns one stream-ordered workspace per
+ * request in flight (hdi_engine_request_bytes) and admits a request only
+ * while the sum stays within its budget.
+ *   hdi_engine_create : device, stream (NULL = legacy default), parameters as
+ *                       for hdi_create, budget_gb > 0 for the workspaces
+ *   hdi_engine_submit : f, mask, u as for hdi_inpaint (device or host), tol in
+ *                       (0,1), tag returned when the request finishes. Uploads
+ *                       and checks the inputs (waits for the stream); returns
+ *                       HDI_ERR_OUT_OF_MEMORY without side effects when the
+ *                       request does not fit the budget now. u must stay valid
+ *                       until the request is reported.
+ *   hdi_engine_step   : one step (waits for the stream at its end); writes up
+ *                       to `capacity` finished requests' tags and statistics
+ *                       (st.status: HDI_OK, NOT_CONVERGED after max_vcycles,
+ *                       NONFINITE) and their count to *ndone; finished
+ *                       requests beyond capacity are reported by later calls.
+ *   hdi_engine_status : requests in flight, workspace bytes in use, budget.
+ *   hdi_engine_request_bytes : workspace one request of that shape needs.
+ * One host thread at a time per engine. */
+typedef struct hdi_engine hdi_engine;
+int hdi_engine_create(hdi_engine** engine, int device, void* cuda_stream, const char* config_json, double budget_gb);
+int hdi_engine_destroy(hdi_engine* engine);
+int hdi_engine_submit(hdi_engine* engine, const hdi_image* f, const hdi_mask* mask, hdi_image* u, double tol,
+                      int64_t tag);
+int hdi_engine_step(hdi_engine* engine, int64_t* tags, hdi_stats* stats, int capacity, int* ndone);
+int hdi_engine_status(const hdi_engine* engine, int64_t* in_flight, int64_t* bytes_in_use, int64_t* budget_bytes);
+int64_t hdi_engine_request_bytes(int32_t height, int32_t width, int32_t channels);
+int64_t hdi_engine_launch_count(const hdi_engine* engine);
+const char* hdi_engine_last_error(const hdi_engine* engine);
 
 /* Tonal optimisation (Sec. 5, Eq. "tonal-opt-minimisation"): g minimising
  * ||f - A^{-1} C g||_2 with g = 0 off the mask, by restricted additive
@@ -164,6 +205,12 @@ int hdi_densify_step(hdi_ctx* ctx, const hdi_image* f, hdi_mask* mask,
 int hdi_densify(hdi_ctx* ctx, const hdi_image* f, hdi_mask* mask, hdi_image* u, int32_t n, double t,
                 double density, uint64_t seed, int64_t* sizes);
 
+/* Device bytes the context currently holds for its workspaces (all solver
+ * workspaces, host-buffer staging and the batched engine's requests in
+ * flight); workspaces grow to the largest call served and are kept until
+ * hdi_destroy. -1 for a null context. */
+int64_t hdi_workspace_bytes(const hdi_ctx* ctx);
+
 /* Number of kernels this context has launched since it was created. */
 int64_t hdi_launch_count(const hdi_ctx* ctx);
 
@@ -181,8 +228,11 @@ int64_t hdi_launch_count(const hdi_ctx* ctx);
  *   4 tonal_echo    local inpainting echoes of the RAS subdomains (Sec. 5.2)
  *   5 tonal_gram    local Gram matrices and their Cholesky factors
  *   6 tonal_local   local solves and weighted extension (Alg. 2, steps 2-3)
- *   7 anderson      Anderson acceleration of the RAS iteration */
-#define HDI_TIMING_CLASSES 8
+ *   7 anderson      Anderson acceleration of the RAS iteration
+ *   8 coarse_levels every V-cycle's work below the finest level (all coarse
+ *                   sweeps, transfers and the coarsest solve), one interval
+ *                   per V-cycle */
+#define HDI_TIMING_CLASSES 9
 int hdi_timing(hdi_ctx* ctx, int enable, int reset, double* ms, int64_t* launches);
 const char* hdi_timing_name(int i);
 
@@ -282,6 +332,10 @@ const char* hdi_version(void);
  *                             FP32 residual and update, no double-float refinement), the per-image
  *                             baseline of the mixed-precision path; it stalls near the FP32 rounding
  *                             level (about 1e-6 relative residual) and then returns NOT_CONVERGED
+ *   batch_engine      [1]     hdi_inpaint_batch: 1 the batched engine (one launch per phase across
+ *                             sizes), 0 size classes stacked as channels, one class after another
+ *   strip_rows        [0]     rows per warp of the quad-strip kernels (restriction, prolongation,
+ *                             residuals; even, >= 2); 0 chooses by level size
  *   oras_warp         [1]     ORAS sweep layout: 1 one warp per 32x32 subdomain (no CTA barriers),
  *                             0 two warps per subdomain
  *   tonal_anderson    [8]     Anderson window on the RAS iteration (0 = plain Alg. 2)

@@ -55,8 +55,10 @@ class Stats(ctypes.Structure):
 
 SYMBOLS = ["hdi_create", "hdi_destroy", "hdi_set_param", "hdi_get_param", "hdi_inpaint",
            "hdi_tonal_opt", "hdi_densify_step", "hdi_densify", "hdi_last_error", "hdi_version", "hdi_launch_count",
-           "hdi_timing", "hdi_timing_bytes", "hdi_timing_name", "hdi_inpaint_noalloc", "hdi_inpaint_batch"]
-TIMING_CLASSES = 8
+           "hdi_timing", "hdi_timing_bytes", "hdi_timing_name", "hdi_inpaint_noalloc", "hdi_inpaint_batch",
+           "hdi_engine_create", "hdi_engine_destroy", "hdi_engine_submit", "hdi_engine_step", "hdi_engine_status",
+           "hdi_engine_request_bytes", "hdi_engine_launch_count", "hdi_engine_last_error", "hdi_workspace_bytes"]
+TIMING_CLASSES = 9
 
 _lib = None
 
@@ -86,6 +88,8 @@ def load(path: str | None = None):
     lib.hdi_version.restype = ctypes.c_char_p
     lib.hdi_launch_count.argtypes = [ctypes.c_void_p]
     lib.hdi_launch_count.restype = ctypes.c_int64
+    lib.hdi_workspace_bytes.argtypes = [ctypes.c_void_p]
+    lib.hdi_workspace_bytes.restype = ctypes.c_int64
     lib.hdi_timing.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int64)]
     lib.hdi_timing_bytes.argtypes = [ctypes.c_void_p, P(ctypes.c_double)]
     lib.hdi_timing_name.restype = ctypes.c_char_p
@@ -93,6 +97,18 @@ def load(path: str | None = None):
                                       P(Stats)]
     lib.hdi_inpaint_noalloc.argtypes = [ctypes.c_int, ctypes.c_void_p, P(Image), P(Mask), P(Image),
                                         ctypes.c_double, P(Stats)]
+    lib.hdi_engine_create.argtypes = [P(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p, ctypes.c_char_p,
+                                      ctypes.c_double]
+    lib.hdi_engine_destroy.argtypes = [ctypes.c_void_p]
+    lib.hdi_engine_submit.argtypes = [ctypes.c_void_p, P(Image), P(Mask), P(Image), ctypes.c_double, ctypes.c_int64]
+    lib.hdi_engine_step.argtypes = [ctypes.c_void_p, P(ctypes.c_int64), P(Stats), ctypes.c_int, P(ctypes.c_int)]
+    lib.hdi_engine_status.argtypes = [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)]
+    lib.hdi_engine_request_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    lib.hdi_engine_request_bytes.restype = ctypes.c_int64
+    lib.hdi_engine_launch_count.argtypes = [ctypes.c_void_p]
+    lib.hdi_engine_launch_count.restype = ctypes.c_int64
+    lib.hdi_engine_last_error.argtypes = [ctypes.c_void_p]
+    lib.hdi_engine_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -185,8 +201,8 @@ class Context:
         return st.as_dict()
 
     def inpaint_batch(self, fs, masks, outs, tol: float = 1e-6, allow_not_converged=False) -> list:
-        """Batched inpainting of independent images (lists of tensors/arrays);
-        images of equal size are solved together, one launch per phase."""
+        """Batched inpainting of independent images of any sizes (lists of
+        tensors/arrays): one launch per solver phase over all of them."""
         n = len(fs)
         FI = (Image * n)(*[image_of(x) for x in fs])
         MI = (Mask * n)(*[mask_of(x) for x in masks])
@@ -232,6 +248,11 @@ class Context:
     def launch_count(self) -> int:
         return self.lib.hdi_launch_count(self.h)
 
+    def workspace_bytes(self) -> int:
+        """Device bytes the context's workspaces hold now (they grow to the
+        largest call served and stay until the context is closed)."""
+        return self.lib.hdi_workspace_bytes(self.h)
+
     def timing(self, enable: bool = True, reset: bool = False) -> dict:
         """Per-class device time {name: (ms, launches)} since the last reset."""
         ms = (ctypes.c_double * TIMING_CLASSES)()
@@ -247,12 +268,83 @@ class Context:
         return {self.lib.hdi_timing_name(i).decode(): b[i] for i in range(TIMING_CLASSES)}
 
 
+class Engine:
+    """Batched inpainting engine (hdi_engine_*): requests of any size are
+    submitted while their workspaces fit the budget, every step advances all
+    requests in flight by one V-cycle (new ones by full multigrid) with one
+    launch per solver phase, and finished requests are returned by step()."""
+
+    def __init__(self, device: int = 0, stream=None, budget_gb: float = 120.0, **params):
+        self.lib = load()
+        self.h = ctypes.c_void_p()
+        s = 0
+        if stream is not None:
+            s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        cfg = json.dumps({k: float(v) for k, v in params.items()}).encode() if params else None
+        rc = self.lib.hdi_engine_create(ctypes.byref(self.h), device, ctypes.c_void_p(s), cfg, float(budget_gb))
+        if rc != HDI_OK:
+            raise HdiError(rc, "hdi_engine_create failed")
+        self._held = {}   # tag -> buffers that must outlive the request
+
+    def close(self):
+        if self.h:
+            self.lib.hdi_engine_destroy(self.h)
+            self.h = ctypes.c_void_p()
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, f, mask, out, tol: float = 1e-6, tag: int = 0) -> bool:
+        """Admit one request; False (nothing changed) if its workspace does not
+        fit the budget now."""
+        fi, mi, oi = image_of(f), mask_of(mask), image_of(out)
+        rc = self.lib.hdi_engine_submit(self.h, ctypes.byref(fi), ctypes.byref(mi), ctypes.byref(oi), float(tol),
+                                        int(tag))
+        if rc == -4:
+            return False
+        if rc != HDI_OK:
+            raise HdiError(rc, self.lib.hdi_engine_last_error(self.h).decode())
+        self._held[int(tag)] = (f, mask, out)
+        return True
+
+    def step(self, capacity: int = 1024) -> list:
+        """One step; returns [(tag, stats dict)] of the requests that finished."""
+        tags = (ctypes.c_int64 * capacity)()
+        sts = (Stats * capacity)()
+        nd = ctypes.c_int()
+        rc = self.lib.hdi_engine_step(self.h, tags, sts, capacity, ctypes.byref(nd))
+        if rc != HDI_OK:
+            raise HdiError(rc, self.lib.hdi_engine_last_error(self.h).decode())
+        out = []
+        for i in range(nd.value):
+            self._held.pop(int(tags[i]), None)
+            out.append((int(tags[i]), sts[i].as_dict()))
+        return out
+
+    def status(self) -> dict:
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self.lib.hdi_engine_status(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return {"in_flight": a.value, "bytes_in_use": b.value, "budget_bytes": c.value}
+
+    def launch_count(self) -> int:
+        return self.lib.hdi_engine_launch_count(self.h)
+
+    @staticmethod
+    def request_bytes(height: int, width: int, channels: int) -> int:
+        """Workspace bytes the engine reserves for one request of this shape."""
+        return load().hdi_engine_request_bytes(int(height), int(width), int(channels))
+
+
 def inpaint_noalloc(f, mask, out, tol: float = 1e-6, device: int = 0, stream=None) -> dict:
     """hdi_inpaint_noalloc: inpainting for callers that must not allocate
-    device memory (for example inside a stream capture). f, mask and out must
-    be CUDA tensors; the workspace is the library's static 24 MiB device
-    array, so images beyond about 500,000 pixel x channel values are refused
-    and calls that overlap on the GPU race with each other."""
+    device memory while they run. f, mask and out must be CUDA tensors; the
+    workspace is the library's static 24 MiB device array, so images beyond
+    about 500,000 pixel x channel values are refused and calls on one device
+    that overlap race with each other."""
     lib = load()
     s = 0
     if stream is not None:

@@ -1,12 +1,17 @@
 """Autotuner for the solver parameters that set speed but not the result.
 
 The inpainting and tonal solves stop at the same relative residual whatever
-the Robin weight of the ORAS interfaces, the local CG stop fractions or the
-inner-solve tolerances are, so these can be chosen per GPU and problem class
-by timing: each candidate set runs the real solve (through the C ABI) on a
-representative input, the fastest one that converges wins. Results are kept
-in a JSON cache keyed by GPU name, size class, channel count, mask-density
-bucket and solve kind, and applied by creating a Context with them.
+the Robin weight of the ORAS interfaces, the local CG stop fractions, the
+inner-solve tolerances or the kernels' tiling are, so these can be chosen per
+GPU and problem class by timing: each candidate set runs the real solve
+(through the C ABI) on a representative input, the fastest one that
+converges wins. Two stages: first the tiling and layout choices (the ORAS
+subdomain layout -- one warp or two per 32x32 subdomain --, the rows per warp
+of the streaming strip kernels, and for tonal optimisation the RAS block
+side, 32 or 64), then the scalar parameters with the best tiling. Results are
+kept in a JSON cache keyed by GPU name, size class, channel count,
+mask-density bucket and solve kind, and applied by creating a Context with
+them.
 
     best = tune(ctx_device, f, mask, kind="inpaint")      # dict of parameters
     ctx = Context(0, **best)
@@ -28,6 +33,16 @@ TONAL_GRID = {
     "tonal_oras_eta": (1e-2, 3e-2),
     "tonal_inner_ratio": (0.05, 0.1, 0.2),
     "tonal_fine_pre": (1, 2),
+}
+# tiling and layout (stage 1); strip_rows 0 = chosen by level size
+INPAINT_SHAPES = {
+    "oras_warp": (0, 1),
+    "strip_rows": (0, 8, 16),
+}
+TONAL_SHAPES = {
+    "oras_warp": (0, 1),
+    "strip_rows": (0, 16),
+    "tonal_block": (32, 64),
 }
 
 
@@ -68,15 +83,17 @@ def save_cache(path: str, cache: dict) -> None:
 
 
 def tune(device: int, f, mask, kind: str = "inpaint", tol: float = 1e-6, reps: int = 2,
-         cache_path: str | None = None, grid: dict | None = None) -> dict:
+         cache_path: str | None = None, grid: dict | None = None, shapes: dict | None = None) -> dict:
     """Fastest converging parameter set for solves like (f, mask).
 
     f, mask: device tensors as for Context.inpaint / tonal_opt. Every
     candidate runs one untimed solve and then `reps` timed ones (CUDA events
     on the current stream); candidates that do not reach `tol` are dropped.
-    With `cache_path` the result is read from / stored in that JSON file."""
+    Stage 1 times the tiling grid `shapes` (default INPAINT_SHAPES /
+    TONAL_SHAPES; {} skips it), stage 2 the parameter grid `grid` with the
+    best tiling. With `cache_path` the result is read from / stored in that
+    JSON file."""
     import torch
-    from . import Context
 
     H, W = int(mask.shape[-2]), int(mask.shape[-1])
     ch = 1 if f.dim() == 2 else int(f.shape[0])
@@ -85,11 +102,32 @@ def tune(device: int, f, mask, kind: str = "inpaint", tol: float = 1e-6, reps: i
     cache = load_cache(cache_path) if cache_path else {}
     if key in cache:
         return dict(cache[key]["params"])
+    if shapes is None:
+        shapes = INPAINT_SHAPES if kind == "inpaint" else TONAL_SHAPES
     grid = grid or (INPAINT_GRID if kind == "inpaint" else TONAL_GRID)
+    table = []
+    base = {}
+    if shapes:
+        base, _, t1 = _search(device, f, mask, kind, tol, reps, candidates(shapes), {})
+        table += [dict(row, stage="tiling") for row in t1]
+    best, best_ms, t2 = _search(device, f, mask, kind, tol, reps, candidates(grid), base)
+    table += [dict(row, stage="parameters") for row in t2]
+    if cache_path:
+        cache[key] = {"params": best, "ms": round(best_ms, 3), "table": table}
+        save_cache(cache_path, cache)
+    return dict(best)
+
+
+def _search(device, f, mask, kind, tol, reps, cands, base):
+    """Times every candidate (merged over `base`); returns the fastest
+    converging set, its time and the table of all candidates."""
+    import torch
+    from . import Context
     stream = torch.cuda.current_stream(device)
     out = torch.empty_like(f)
     best, best_ms, table = None, math.inf, []
-    for cand in candidates(grid):
+    for c in cands:
+        cand = dict(base, **c)
         ctx = Context(device, stream=stream, **cand)
         run = (lambda: ctx.inpaint(f, mask, out, tol=tol, allow_not_converged=True)) if kind == "inpaint" else \
               (lambda: ctx.tonal_opt(f, mask, out, tol=tol, allow_not_converged=True))
@@ -108,7 +146,4 @@ def tune(device: int, f, mask, kind: str = "inpaint", tol: float = 1e-6, reps: i
         ctx.close()
     if best is None:
         raise RuntimeError("no candidate parameter set converged")
-    if cache_path:
-        cache[key] = {"params": best, "ms": round(best_ms, 3), "table": table}
-        save_cache(cache_path, cache)
-    return dict(best)
+    return best, best_ms, table

@@ -69,6 +69,8 @@ const ParamDef kParams[] = {
     {"oras_warp", &Params::oras_warp, 0, 1},
     {"densify_partition", &Params::densify_partition, 0, 1},
     {"inpaint_fp32", &Params::inpaint_fp32, 0, 1},
+    {"batch_engine", &Params::batch_engine, 0, 1},
+    {"strip_rows", &Params::strip_rows, 0, 64},
 };
 
 }  // namespace
@@ -97,7 +99,10 @@ int Ctx::sync(const char* what) {
 }
 
 void Arena::release() {
-    if (base) cudaFree(base);
+    if (base) {
+        if (async) cudaFreeAsync(base, astream);
+        else cudaFree(base);
+    }
     base = nullptr;
     cap = used = 0;
 }
@@ -364,7 +369,7 @@ void Ctx::vcycle(int l) {
     }
     Level& C = lev[l + 1];
     {
-        const int qr = quad_rows(L.H, L.W, nch);
+        const int qr = qrows(L.H, L.W, nch);
         dim3 blk(128), grd = quad_grid(L.H, L.W, nch, qr);
         // read x, b and the mask bits, write a quarter value of b_H per value
         if (l == 0) tstart(kT_Restrict, 9.125 * (double)nch * L.H * L.W);
@@ -373,9 +378,12 @@ void Ctx::vcycle(int l) {
         ++launches;
         if (l == 0) tstop();
     }
+    // the levels below the finest as one timed block per V-cycle
+    if (l == 0) tstart(kT_Coarse);
     vcycle(l + 1);
+    if (l == 0) tstop();
     {
-        const int qr = quad_rows(L.H, L.W, nch);
+        const int qr = qrows(L.H, L.W, nch);
         dim3 grd = quad_grid(L.H, L.W, nch, qr), blk(128);
         // read x, b, a quarter value of e_H and the mask bits, write x
         if (l == 0) tstart(kT_Prolong, 13.125 * (double)nch * L.H * L.W);
@@ -401,7 +409,7 @@ void Ctx::vcycle(int l) {
 // coarse level's zero-filled scratch is avoided: a plain residual pass).
 void Ctx::residual_norm_level(int l, const float* x, int slot) {
     const Level& L = lev[l];
-    const int qr = quad_rows(L.H, L.W, nch);
+    const int qr = qrows(L.H, L.W, nch);
     dim3 grd = quad_grid(L.H, L.W, nch, qr), blk(128);
     launch_k(p.pdl >= 0.5, k_level_residual_norm, grd, blk, stream, arr(l), mview(l), x, (const float*)L.b,
              reducer(slot, grd.x * grd.y), qr);
@@ -424,7 +432,7 @@ void Ctx::fmg(DFc d) {
     }
     const int L = nlev - 1;
     {
-        const int qr = quad_rows(lev[L].H, lev[L].W, nch);
+        const int qr = qrows(lev[L].H, lev[L].W, nch);
         dim3 grd = quad_grid(lev[L].H, lev[L].W, nch, qr), blk(128);
         k_prolong<2><<<grd, blk, 0, stream>>>(arr(L), mview(L), nullptr, lev[L].b, lev[L].xb, arr(L), nullptr,
                                               reducer(L, grd.x * grd.y), qr);
@@ -432,7 +440,7 @@ void Ctx::fmg(DFc d) {
         oras(L, false, lev[L].xb, lev[L].xa, scal + L * kMaxCh, true, nullptr);
     }
     for (int l = L - 1; l >= 0; --l) {
-        const int qr = quad_rows(lev[l].H, lev[l].W, nch);
+        const int qr = qrows(lev[l].H, lev[l].W, nch);
         dim3 grd = quad_grid(lev[l].H, lev[l].W, nch, qr), blk(128);
         k_prolong<1><<<grd, blk, 0, stream>>>(arr(l), mview(l), nullptr, lev[l].b, lev[l].xb, arr(l + 1),
                                               lev[l + 1].xa, reducer(l, grd.x * grd.y), qr);
@@ -452,7 +460,7 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
     a.d = d;
     a.y = y;
     a.r32 = c.lev[0].b;
-    a.rows = quad_rows(c.H, c.W, c.nch);
+    a.rows = c.qrows(c.H, c.W, c.nch);
     dim3 grd = quad_grid(c.H, c.W, c.nch, a.rows), blk(128);
     a.red_r = c.reducer(kSlotR64, grd.x * grd.y);
     a.red_b = c.reducer(kSlotB64, grd.x * grd.y);
@@ -624,7 +632,7 @@ int Ctx::load_image(const hdi_image* im, DF dst, float* lo2, int c0) {
     return HDI_OK;
 }
 
-int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2, int c0) {
+int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2, int c0, bool wait) {
     const int nc = im->channels;
     if (c0) {
         const long long off = (long long)c0 * lev[0].cs;
@@ -660,6 +668,7 @@ int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* kn
             if (e != cudaSuccess) return cuda_check(e, "device-to-host copy");
         }
     }
+    if (!wait) return cuda_check(cudaGetLastError(), "image download");
     return sync("image download");
 }
 
@@ -789,6 +798,7 @@ int hdi_destroy(hdi_ctx* h) {
     c->vws.release();
     c->lws.release();
     c->stage.release();
+    engine_delete(c->eng);
     if (c->flags) cudaFree(c->flags);
     if (c->tev) {
         for (int i = 0; i < 2 * kMaxTimed; ++i) cudaEventDestroy(c->tev[i]);
@@ -832,6 +842,12 @@ const char* hdi_last_error(const hdi_ctx* h) {
 
 const char* hdi_version(void) { return "hdi 0.1 (sm_103a)"; }
 
+int64_t hdi_workspace_bytes(const hdi_ctx* h) {
+    if (!h) return -1;
+    const Ctx* c = reinterpret_cast<const Ctx*>(h);
+    return (int64_t)c->other_bytes() + (c->eng ? (int64_t)engine_used_bytes(c->eng) : 0);
+}
+
 int64_t hdi_launch_count(const hdi_ctx* h) {
     if (!h) return -1;
     return reinterpret_cast<const Ctx*>(h)->launches;
@@ -839,7 +855,8 @@ int64_t hdi_launch_count(const hdi_ctx* h) {
 
 const char* hdi_timing_name(int i) {
     static const char* names[HDI_TIMING_CLASSES] = {"oras_fine", "residual_fine", "prolong_fine", "restrict_fine",
-                                                    "tonal_echo", "tonal_gram", "tonal_local", "anderson"};
+                                                    "tonal_echo", "tonal_gram", "tonal_local", "anderson",
+                                                    "coarse_levels"};
     return (i >= 0 && i < HDI_TIMING_CLASSES) ? names[i] : "";
 }
 
@@ -978,6 +995,8 @@ int Ctx::densify_run(const hdi_image* f, hdi_mask* mask, hdi_image* u, int n, do
 
 // ------------------------------------------------------------ batch ---
 
+#include "engine.cuh"
+
 // Images of one size class are stacked as the channels of one system (each
 // channel reads its own image's mask plane), so every phase of the solver is
 // one launch over all their subdomains and pixels. Size classes run in turn.
@@ -993,6 +1012,50 @@ int Ctx::inpaint_batch(int n, const hdi_image* f, const hdi_mask* m, hdi_image* 
         if (m[i].height != f[i].height || m[i].width != f[i].width)
             return fail(HDI_ERR_INVALID_ARG, "mask[%d]: shape does not match", i);
     }
+    if (p.batch_engine >= 0.5 && p.inpaint_fp32 < 0.5) return inpaint_batch_engine(n, f, m, u, tol, st);
+    return inpaint_batch_classes(n, f, m, u, tol, st);
+}
+
+// All images through the batched engine (engine.cuh): admitted as the
+// budget allows, stepped together, each leaving when it converges.
+int Ctx::inpaint_batch_engine(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, hdi_stats* st) {
+    if (!eng) {
+        eng = new Engine();
+        eng->device = device;
+        eng->stream = stream;
+    }
+    Engine& e = *eng;
+    e.p = p;
+    e.budget = p.hbm_budget_gb * 1e9;
+    std::vector<int64_t> tags(std::max(n, 1));
+    std::vector<hdi_stats> sts(std::max(n, 1));
+    int next = 0, done = 0, worst = HDI_OK, rc;
+    const int64_t l0 = e.launches;
+    while (done < n) {
+        while (next < n) {
+            rc = e.submit(&f[next], &m[next], &u[next], tol, next);
+            if (rc == HDI_ERR_OUT_OF_MEMORY && !e.reqs.empty()) break;   // admitted when others finish
+            if (rc) return fail(rc, "batch image %d: %s", next, e.err.c_str());
+            ++next;
+        }
+        int nd = 0;
+        if ((rc = e.step(tags.data(), sts.data(), n, &nd))) return fail(rc, "batch: %s", e.err.c_str());
+        for (int i = 0; i < nd; ++i) {
+            const int idx = (int)tags[i];
+            if (st) st[idx] = sts[i];
+            if (sts[i].status == HDI_ERR_NOT_CONVERGED) worst = HDI_ERR_NOT_CONVERGED;
+            else if (sts[i].status != HDI_OK) return fail(sts[i].status, "batch image %d failed: %s", idx, e.err.c_str());
+        }
+        done += nd;
+    }
+    launches += e.launches - l0;
+    return worst;
+}
+
+// Images of one size form one system (size classes in turn).
+int Ctx::inpaint_batch_classes(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol,
+                               hdi_stats* st) {
+    int rc;
     // group by size, keeping input order inside a class; split classes above kMaxCh channels
     std::vector<std::vector<int>> groups;
     std::vector<int> done(n, 0);
@@ -1320,3 +1383,83 @@ extern "C" int hdi_inpaint_noalloc(int device, void* cuda_stream, const hdi_imag
     }
     return src;
 }
+
+// ------------------------------------------------------- engine C ABI ---
+
+extern "C" {
+
+int hdi_engine_create(hdi_engine** out, int device, void* stream, const char* config_json, double budget_gb) {
+    if (!out) return HDI_ERR_INVALID_ARG;
+    *out = nullptr;
+    Params cfg;
+    if (config_json && !parse_config(config_json, cfg)) return HDI_ERR_INVALID_ARG;
+    if (!(budget_gb > 0.0)) return HDI_ERR_INVALID_ARG;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return HDI_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return HDI_ERR_CUDA;
+    Engine* e = new Engine();
+    e->device = device;
+    e->stream = (cudaStream_t)stream;
+    e->p = cfg;
+    e->budget = budget_gb * 1e9;
+    *out = reinterpret_cast<hdi_engine*>(e);
+    return HDI_OK;
+}
+
+int hdi_engine_destroy(hdi_engine* h) {
+    delete reinterpret_cast<Engine*>(h);
+    return HDI_OK;
+}
+
+int hdi_engine_submit(hdi_engine* h, const hdi_image* f, const hdi_mask* mask, hdi_image* u, double tol, int64_t tag) {
+    if (!h) return HDI_ERR_INVALID_ARG;
+    Engine* e = reinterpret_cast<Engine*>(h);
+    if (cudaSetDevice(e->device) != cudaSuccess) return HDI_ERR_CUDA;
+    return e->submit(f, mask, u, tol, tag);
+}
+
+int hdi_engine_step(hdi_engine* h, int64_t* tags, hdi_stats* stats, int capacity, int* ndone) {
+    if (!h || !ndone || capacity < 0) return HDI_ERR_INVALID_ARG;
+    Engine* e = reinterpret_cast<Engine*>(h);
+    if (cudaSetDevice(e->device) != cudaSuccess) return HDI_ERR_CUDA;
+    // first the finished requests an earlier call could not report
+    int k = 0;
+    while (k < capacity && !e->pending_tags.empty()) {
+        if (tags) tags[k] = e->pending_tags.front();
+        if (stats) stats[k] = e->pending_stats.front();
+        e->pending_tags.erase(e->pending_tags.begin());
+        e->pending_stats.erase(e->pending_stats.begin());
+        ++k;
+    }
+    int nd = 0;
+    const int rc = e->step(tags ? tags + k : nullptr, stats ? stats + k : nullptr, capacity - k, &nd);
+    *ndone = k + nd;
+    return rc;
+}
+
+int hdi_engine_status(const hdi_engine* h, int64_t* in_flight, int64_t* bytes_in_use, int64_t* budget_bytes) {
+    if (!h) return HDI_ERR_INVALID_ARG;
+    const Engine* e = reinterpret_cast<const Engine*>(h);
+    if (in_flight) *in_flight = (int64_t)e->reqs.size();
+    if (bytes_in_use) *bytes_in_use = (int64_t)e->used;
+    if (budget_bytes) *budget_bytes = (int64_t)e->budget;
+    return HDI_OK;
+}
+
+int64_t hdi_engine_request_bytes(int32_t height, int32_t width, int32_t channels) {
+    if (height < 1 || width < 1 || channels < 1 || channels > kMaxCh) return -1;
+    return (int64_t)lean_bytes(height, width, channels);
+}
+
+int64_t hdi_engine_launch_count(const hdi_engine* h) {
+    return h ? reinterpret_cast<const Engine*>(h)->launches : 0;
+}
+
+const char* hdi_engine_last_error(const hdi_engine* h) {
+    return h ? reinterpret_cast<const Engine*>(h)->err.c_str() : "";
+}
+
+}  // extern "C"

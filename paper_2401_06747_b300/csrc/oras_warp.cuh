@@ -106,15 +106,17 @@ __device__ __forceinline__ void wapply(const WarpGeom& g, const WarpShared& sh, 
     }
 }
 
-// Sum of the lane's packed products, two accumulators for latency.
+// Sum of the lane's packed products, four accumulators (short dependency
+// chains: the products of a row are ready at different times).
 __device__ __forceinline__ float wdot(const float2 (&A)[kWarpRows], const float2 (&B)[kWarpRows]) {
-    float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+    float2 a[4];
 #pragma unroll
-    for (int k = 0; k < kWarpRows; ++k) {
-        if (k & 1) a1 = __ffma2_rn(A[k], B[k], a1);
-        else a0 = __ffma2_rn(A[k], B[k], a0);
-    }
-    return (a0.x + a0.y) + (a1.x + a1.y);
+    for (int j = 0; j < 4; ++j) a[j] = __fmul2_rn(A[j], B[j]);
+#pragma unroll
+    for (int k = 4; k < kWarpRows; ++k) a[k & 3] = __ffma2_rn(A[k], B[k], a[k & 3]);
+    const float2 s01 = __fadd2_rn(a[0], a[1]), s23 = __fadd2_rn(a[2], a[3]);
+    const float2 s = __fadd2_rn(s01, s23);
+    return s.x + s.y;
 }
 
 // Local CG on A_i v = r from v = 0 (r: right-hand side in, final residual
@@ -344,6 +346,14 @@ struct OrasTask {
     int full;
 };
 
+// Subdomains of levels narrower or lower than 32 pixels (the coarsest levels
+// of small images) take the general body through a call, so that its
+// registers do not weigh on the full-size body of the batched kernel.
+template <bool ZERO>
+__device__ __noinline__ void oras_w_edge(const OrasArgs& a, int bx, int by, WarpShared& sh) {
+    oras_w_body<ZERO, false>(a, bx, by, 0, sh);
+}
+
 // Batched ORAS sweep over tasks of different sizes, one CTA per (task,
 // subdomain); the branch on the task's geometry is uniform over the CTA.
 template <bool ZERO>
@@ -355,5 +365,5 @@ __global__ void __launch_bounds__(32, 12) k_oras_wb(const OrasTask* __restrict__
     const OrasArgs& a = tasks[t].a;
     const int nbx = a.nbx;
     if (tasks[t].full) oras_w_body<ZERO, true>(a, local % nbx, local / nbx, 0, sh);
-    else oras_w_body<ZERO, false>(a, local % nbx, local / nbx, 0, sh);
+    else oras_w_edge<ZERO>(a, local % nbx, local / nbx, sh);
 }

@@ -46,6 +46,8 @@ struct Params {
     double densify_tol = 1e-6;      // relative residual of the inpaintings of hdi_densify
     double densify_partition = 0;   // 0: Delaunay triangles (Alg. 1); 1: Voronoi cells of the mask (Sec. 6.2)
     double inpaint_fp32 = 0;        // 1: hdi_inpaint / hdi_inpaint_batch in the plain FP32 form
+    double batch_engine = 1;        // hdi_inpaint_batch: 1 the batched engine (all sizes per launch), 0 size classes
+    double strip_rows = 0;          // rows per warp of the quad-strip kernels (even, >= 2); 0: chosen by size
     double oras_warp = 1;           // ORAS sweep layout: 1 one warp per subdomain, 0 two warps
 };
 
@@ -60,11 +62,16 @@ struct Level {
 };
 
 struct Ctx;
+struct Engine;   // batched engine (engine.cuh)
+void engine_delete(Engine* e);
+size_t engine_used_bytes(const Engine* e);
 
 // One cudaMalloc'd block carved into 256-byte aligned pieces.
 struct Arena {
     void* base = nullptr;
     size_t cap = 0, used = 0;
+    bool async = false;              // allocated with cudaMallocAsync on astream (released with cudaFreeAsync)
+    cudaStream_t astream = nullptr;
     int reserve(Ctx& c, size_t bytes, const char* what);
     void* take(size_t bytes);
     void release();
@@ -106,7 +113,7 @@ constexpr int kCntOnes = 0;
 constexpr int kCntLocal = 1;
 constexpr int kCntEcho = 2;
 constexpr int kMaxTimed = 2048;   // timed launches buffered between flushes
-enum { kT_Oras = 0, kT_Residual, kT_Prolong, kT_Restrict, kT_Echo, kT_Gram, kT_Local, kT_Anderson };
+enum { kT_Oras = 0, kT_Residual, kT_Prolong, kT_Restrict, kT_Echo, kT_Gram, kT_Local, kT_Anderson, kT_Coarse };
 // double-float vectors of level-0 size
 enum { kF = 0, kU0, kU1, kG, kY0, kY1, kW0, kW1, kP, kNumDF };
 
@@ -193,7 +200,10 @@ struct Ctx {
     int sync(const char* what);
     size_t other_bytes() const;
     int setup(int H, int W, int nch, int nmask = 1);
+    int setup_lean(int H, int W, int nch, cudaStream_t s);   // one request of the batched engine (engine.cuh)
     GridReduce reducer(int slot, int nparts) const;
+    // rows per warp of the quad-strip kernels: the strip_rows parameter, else by size
+    int qrows(int H_, int W_, int n) const { return p.strip_rows >= 2 ? ((int)p.strip_rows / 2) * 2 : quad_rows(H_, W_, n); }
     LevelArr arr(int l) const;
     MaskView mview(int l) const;
     void build_mask_pyramid();
@@ -207,9 +217,13 @@ struct Ctx {
     int solve(SolveSpec& s);
     int check_image(const hdi_image* im, const char* name, int H, int W, int nch);
     int load_image(const hdi_image* im, DF dst, float* lo2 = nullptr, int c0 = 0);
-    int store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2 = nullptr, int c0 = 0);
+    int store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2 = nullptr, int c0 = 0,
+                    bool wait = true);
     int load_mask(const hdi_mask* m, long long* ones, int plane = 0, bool pyramid = true);
     int inpaint_batch(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, hdi_stats* st);
+    int inpaint_batch_engine(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, hdi_stats* st);
+    int inpaint_batch_classes(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, hdi_stats* st);
+    Engine* eng = nullptr;     // batched engine of hdi_inpaint_batch (created on first use)
     int read_slot(int slot, double* out);
     int tonal_setup();
     int tonal_setup_blk(int blk);

@@ -1099,3 +1099,49 @@ __global__ void k_data_to_f32(DFc d, LevelArr F, MaskView m, float* __restrict__
     const size_t idx = ch * F.cs + (size_t)y * F.pitch + x;
     out[idx] = m.ch(ch).known(x, y) ? d.hi[idx] + d.lo[idx] : 0.f;
 }
+
+// ------------------------------------------------ batched FMG set-up ---
+
+// One (image, channel) of the batched FMG data kernels: level geometry and
+// mask plane, the channel's planes, and the task's blocks along x.
+struct PixTask {
+    LevelArr F, C;       // level (fine) and coarse level (data restriction)
+    MaskView fm;         // mask plane of F
+    DFc d;               // data on F (k_data_to_f32_b)
+    const float* fb;     // FP32 data on F (k_restrict_data_b)
+    float* out;          // output plane (on F for k_data_to_f32_b, on C for k_restrict_data_b)
+    int gx;              // blocks along x
+};
+
+// Batched k_data_to_f32: 128 threads per block over 128 columns of one row.
+__global__ void k_data_to_f32_b(const PixTask* __restrict__ tasks, const int* __restrict__ cta0, int ntasks) {
+    const int t = find_task(cta0, ntasks, blockIdx.x);
+    const int local = blockIdx.x - cta0[t];
+    const PixTask& tk = tasks[t];
+    const int x = (local % tk.gx) * blockDim.x + threadIdx.x;
+    const int y = local / tk.gx;
+    if (x >= tk.F.W || y >= tk.F.H) return;
+    const size_t idx = (size_t)y * tk.F.pitch + x;
+    tk.out[idx] = tk.fm.known(x, y) ? tk.d.hi[idx] + tk.d.lo[idx] : 0.f;
+}
+
+// Batched k_restrict_data: 32 x 8 threads per block over the coarse level.
+__global__ void k_restrict_data_b(const PixTask* __restrict__ tasks, const int* __restrict__ cta0, int ntasks) {
+    const int t = find_task(cta0, ntasks, blockIdx.x);
+    const int local = blockIdx.x - cta0[t];
+    const PixTask& tk = tasks[t];
+    const int X = (local % tk.gx) * blockDim.x + threadIdx.x;
+    const int Y = (local / tk.gx) * blockDim.y + threadIdx.y;
+    if (X >= tk.C.W || Y >= tk.C.H) return;
+    float s = 0.f;
+    int n = 0;
+    for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+            const int x = 2 * X + dx, y = 2 * Y + dy;
+            if (x < tk.F.W && y < tk.F.H && tk.fm.known(x, y)) {
+                s += tk.fb[(size_t)y * tk.F.pitch + x];
+                ++n;
+            }
+        }
+    tk.out[(size_t)Y * tk.C.pitch + X] = n ? s / (float)n : 0.f;
+}

@@ -1,16 +1,28 @@
 """Continuous-batching request server over libhdi.
 
 Requests (inpaint / tonal / densify-to-density) arrive over time. The server
-keeps their data on the device from admission to completion, admits them while
-an HBM budget allows, and overlaps their work on the GPU:
+keeps their data on the device from admission to completion, admits them in
+arrival order while one HBM budget allows, and overlaps their work on the GPU:
 
-  * inpaint requests are served by a batching loop: every batched call
-    (`hdi_inpaint_batch`, one launch per solver phase per size class) takes
-    all inpaint requests admitted so far; requests that arrive while a batch
-    is on the GPU join the next call;
+  * inpaint requests are served by the library's batched engine
+    (hdi_engine_*): every engine step advances all inpaint requests in
+    flight by one V-cycle, each solver phase one kernel launch over all of
+    them whatever their sizes, and requests that arrive meanwhile join at the
+    next V-cycle boundary (their full multigrid runs in that step); each
+    request leaves as soon as its own residual meets the tolerance;
   * tonal and densification requests are served by worker threads, each
     with its own library context on its own CUDA stream, so their kernels run
-    concurrently with the inpaint batches.
+    concurrently with the engine's steps. (Their outer iterations carry
+    per-request state -- local factorisations, Anderson history,
+    densification schedules -- so they are not merged into the engine.)
+
+Admission: the budget counts what the library reports it holds -- the
+engine's workspace for each inpaint request (hdi_engine_request_bytes) and
+the worker contexts' workspaces (hdi_workspace_bytes, which grow to the
+largest request served) -- plus the request tensors the server keeps on the
+device. A tonal or densification request is charged the growth its worker's
+workspace needs, estimated from the workspace bytes per pixel value the
+library reported for the largest request of that kind so far.
 
 All library calls release the GIL (ctypes), so the host threads only
 schedule; every step of every solve runs in the library's kernels. Latency is
@@ -26,10 +38,10 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-# Estimated device bytes per pixel x channel of a request's resident state and
-# the share of workspace it implies (inputs, outputs, multigrid hierarchy,
-# double-float vectors; tonal adds the local factors and Anderson history).
-BYTES_PER_VALUE = {"inpaint": 120, "tonal": 300, "densify": 200}
+# First estimate of the workspace per pixel value of a tonal / densification
+# request (double-float vectors, multigrid levels, local factors, Anderson
+# history), until the library has reported a measured one.
+INITIAL_BYTES_PER_VALUE = {"tonal": 300.0, "densify": 200.0}
 
 
 @dataclass
@@ -41,7 +53,7 @@ class Request:
     mask: object              # host array (H, W) uint8 (densify: ignored, starts empty)
     density: float = 0.03     # densify target
     seed: int = 0
-    bytes: int = 0
+    bytes: int = 0            # budget charged while the request is resident
     # filled by the server
     admitted: float = -1.0
     done: float = -1.0
@@ -69,39 +81,62 @@ class Budget:
             self.used -= n
             self.cv.notify_all()
 
+    def hold(self, n: int):
+        """Charges bytes that are already allocated (no limit check)."""
+        with self.cv:
+            self.used += n
 
-def request_bytes(kind: str, f) -> int:
+
+def tensor_bytes(f) -> int:
+    """Device bytes of a request's resident tensors: f and u (FP32) and the mask."""
     ch, H, W = f.shape
-    return int(BYTES_PER_VALUE[kind] * ch * H * W)
+    return int(8 * ch * H * W + H * W)
 
 
 class Server:
-    def __init__(self, device: int = 0, budget_gb: float = 120.0, workers: int = 2, tol: float = 1e-6,
-                 max_batch: int = 64):
+    def __init__(self, device: int = 0, budget_gb: float = 120.0, workers: int = 2, tol: float = 1e-6):
         import torch
         import paper_2401_06747_b300 as hdi
         self.torch = torch
         self.hdi = hdi
         self.device = device
         self.tol = tol
-        self.max_batch = max_batch
         self.budget = Budget(int(budget_gb * 1e9))
         self.inp_stream = torch.cuda.Stream(device=device)
-        self.inp_ctx = hdi.Context(device, stream=self.inp_stream)
+        # the engine's own limit is the whole budget: the server's budget is
+        # the one that binds
+        self.engine = hdi.Engine(device, stream=self.inp_stream, budget_gb=budget_gb)
         self.w_streams = [torch.cuda.Stream(device=device) for _ in range(workers)]
-        self.w_ctxs = [hdi.Context(device, stream=s) for s in self.w_streams]
+        self.w_ctxs = [hdi.Context(device, stream=s, hbm_budget_gb=budget_gb) for s in self.w_streams]
+        self.w_bytes = [0] * workers                  # workspace bytes each worker context holds
+        self.bpv = dict(INITIAL_BYTES_PER_VALUE)      # workspace bytes per value, by kind
+        self.calibrated = {k: False for k in self.bpv}  # bpv measured by the library yet
         self.lock = threading.Lock()
         self.pending = collections.deque()      # arrived, not admitted
-        self.inp_ready = []                     # admitted inpaint requests
+        self.inp_new = collections.deque()      # admitted inpaint requests, not yet in the engine
         self.work_q = collections.deque()       # admitted tonal / densify requests
+        self.inflight = {}                      # engine tag -> request
         self.done = []
         self.t0 = 0.0
         self.closed = False
-        self.batches = 0
+        self.steps = 0
+        self.max_inflight = 0
 
     # ---------------------------------------------------------- helpers ---
     def now(self) -> float:
         return time.perf_counter() - self.t0
+
+    def _charge(self, r: Request) -> int:
+        """Budget bytes of a request: the library's workspace for it plus its
+        tensors. Worker requests are charged the workspace growth of the
+        largest worker context they might need."""
+        ch, H, W = r.f.shape
+        if r.kind == "inpaint":
+            ws = self.hdi.Engine.request_bytes(H, W, ch)
+        else:
+            need = int(self.bpv[r.kind] * ch * H * W)
+            ws = max(0, need - min(self.w_bytes))
+        return int(ws + tensor_bytes(r.f))
 
     def _to_device(self, r: Request, stream):
         torch = self.torch
@@ -126,39 +161,46 @@ class Server:
 
     # --------------------------------------------------------- admission ---
     def _admit(self):
+        """Admits arrived requests in arrival order while the budget allows."""
         with self.lock:
             while self.pending:
                 r = self.pending[0]
+                r.bytes = self._charge(r)
                 if not self.budget.try_take(r.bytes):
                     break
                 self.pending.popleft()
                 r.admitted = self.now()
-                if r.kind == "inpaint":
-                    self.inp_ready.append(r)
-                else:
-                    self.work_q.append(r)
+                (self.inp_new if r.kind == "inpaint" else self.work_q).append(r)
 
     # ----------------------------------------------------------- loops ---
     def _inpaint_loop(self):
+        eng = self.engine
         while True:
             self._admit()
             with self.lock:
-                batch = self.inp_ready[: self.max_batch]
-                self.inp_ready = self.inp_ready[self.max_batch:]
-                finished = self.closed and not self.pending and not self.inp_ready and not batch
+                new = list(self.inp_new)
+                self.inp_new.clear()
+                finished = self.closed and not self.pending and not new and not self.inflight
             if finished:
                 return
-            if not batch:
+            # requests join at this V-cycle boundary
+            for r in new:
+                self._to_device(r, self.inp_stream)
+                if not eng.submit(r.fd, r.md, r.out, tol=self.tol, tag=r.id):
+                    # cannot happen while the server's budget binds; wait one step
+                    with self.lock:
+                        self.inp_new.appendleft(r)
+                    break
+                self.inflight[r.id] = r
+            self.max_inflight = max(self.max_inflight, len(self.inflight))
+            if not self.inflight:
                 time.sleep(0.0005)
                 continue
-            for r in batch:
-                self._to_device(r, self.inp_stream)
-            st = self.inp_ctx.inpaint_batch([r.fd for r in batch], [r.md for r in batch], [r.out for r in batch],
-                                           tol=self.tol, allow_not_converged=True)
-            self.batches += 1
-            for r, s in zip(batch, st):
-                r.stats = s
+            for tag, st in eng.step():
+                r = self.inflight.pop(tag)
+                r.stats = st
                 self._finish(r, self.inp_stream)
+            self.steps += 1
 
     def _worker_loop(self, i: int):
         ctx, stream = self.w_ctxs[i], self.w_streams[i]
@@ -177,13 +219,25 @@ class Server:
                 r.stats = ctx.tonal_opt(r.fd, r.md, r.out, tol=self.tol, allow_not_converged=True)
             else:
                 r.stats = densify_to(ctx, r.fd, r.md, r.out, r.density, r.seed, self.tol)
+            # the library's report of this worker's workspace: its growth
+            # stays charged (the workspace is kept for later requests), and
+            # when it grew to fit this request it calibrates the charge of
+            # the next requests of this kind
+            ws = ctx.workspace_bytes()
+            ch, H, W = r.f.shape
+            with self.lock:
+                grown = max(0, ws - self.w_bytes[i])
+                if grown:
+                    self.bpv[r.kind] = ws / float(ch * H * W) if not self.calibrated[r.kind] else \
+                        max(self.bpv[r.kind], ws / float(ch * H * W))
+                    self.calibrated[r.kind] = True
+                self.w_bytes[i] = ws
+            self.budget.hold(grown)
             self._finish(r, stream)
 
     # ------------------------------------------------------------- run ---
     def run(self, requests: list[Request]) -> dict:
         """Replays `requests` at their arrival times and serves them."""
-        for r in requests:
-            r.bytes = request_bytes(r.kind, r.f)
         self.t0 = time.perf_counter()
         threads = [threading.Thread(target=self._inpaint_loop, daemon=True)]
         threads += [threading.Thread(target=self._worker_loop, args=(i,), daemon=True) for i in range(len(self.w_ctxs))]
@@ -203,7 +257,8 @@ class Server:
         lat = np.array([r.done - r.arrival for r in self.done])
         return {"requests": len(self.done), "wall_s": wall, "solves_per_s": len(self.done) / wall,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "inpaint_batches": self.batches}
+                "engine_steps": self.steps, "max_inpaint_in_flight": self.max_inflight,
+                "worker_workspace_bytes": list(self.w_bytes)}
 
 
 def densify_to(ctx, fd, md, out, density: float, seed: int, tol: float, step: float = 0.005) -> dict:

@@ -18,6 +18,10 @@ def test_keys_and_candidates():
     c = autotune.candidates({"b": (1, 2), "a": (3,)})
     assert c == [{"a": 3, "b": 1}, {"a": 3, "b": 2}]
     assert len(autotune.candidates(autotune.INPAINT_GRID)) == 12
+    # tiling stage: subdomain layout, strip rows, RAS block side
+    assert len(autotune.candidates(autotune.INPAINT_SHAPES)) == 6
+    assert len(autotune.candidates(autotune.TONAL_SHAPES)) == 8
+    assert {c["tonal_block"] for c in autotune.candidates(autotune.TONAL_SHAPES)} == {32, 64}
 
 
 def test_cache_round_trip(tmp_path):
@@ -38,11 +42,14 @@ def test_tune_on_gpu(tmp_path):
     c = dev(random_mask(192, 256, 0.04, 5))
     p = str(tmp_path / "tune.json")
     grid = {"oras_theta": (0.2, 0.3), "oras_eta": (1e-2, 1e-3)}
-    best = autotune.tune(0, f, c, "inpaint", tol=1e-6, cache_path=p, grid=grid)
+    shapes = {"oras_warp": (0, 1), "strip_rows": (0, 8)}
+    best = autotune.tune(0, f, c, "inpaint", tol=1e-6, cache_path=p, grid=grid, shapes=shapes)
     assert best["oras_theta"] in (0.2, 0.3) and best["oras_eta"] in (1e-2, 1e-3)
+    assert best["oras_warp"] in (0, 1) and best["strip_rows"] in (0, 8)
     cache = json.load(open(p))
     (entry,) = cache.values()
-    assert entry["params"] == best and len(entry["table"]) == 4
+    assert entry["params"] == best and len(entry["table"]) == 8
+    assert {r["stage"] for r in entry["table"]} == {"tiling", "parameters"}
     assert autotune.tune(0, f, c, "inpaint", cache_path=p, grid=grid) == best   # from the cache
     out = torch.empty_like(f)
     st = hdi.Context(0, **best).inpaint(f, c, out, tol=1e-6)

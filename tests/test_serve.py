@@ -6,7 +6,7 @@ import threading
 import numpy as np
 import pytest
 
-from paper_2401_06747_b300.serve import Budget, request_bytes, Request
+from paper_2401_06747_b300.serve import Budget, tensor_bytes, Request
 
 
 def test_budget_admission_is_bounded_and_thread_safe():
@@ -38,9 +38,27 @@ def test_budget_admission_is_bounded_and_thread_safe():
     assert b.used == 0 and max(seen) <= 1000
 
 
-def test_request_bytes_scale_with_size():
+def test_tensor_bytes_and_held_workspace():
     f = np.zeros((3, 100, 200), np.float32)
-    assert request_bytes("tonal", f) > request_bytes("inpaint", f) > 0
+    assert tensor_bytes(f) == 8 * 3 * 100 * 200 + 100 * 200
+    b = Budget(1000)
+    b.hold(900)                         # workspace already allocated is charged without a check
+    assert not b.try_take(200)
+    b.give(900)
+    assert b.try_take(200)
+
+
+def test_engine_request_bytes_from_the_library():
+    """The inpaint charge is the library's own workspace figure for the shape
+    (no GPU needed to compute it): it grows with the pixel count and the
+    channels."""
+    import paper_2401_06747_b300 as hdi
+    a = hdi.Engine.request_bytes(100, 200, 1)
+    b = hdi.Engine.request_bytes(100, 200, 3)
+    c = hdi.Engine.request_bytes(200, 400, 3)
+    assert 0 < a < b < c
+    assert 40 * 3 * 100 * 200 < b < 80 * 3 * 100 * 200
+    assert hdi.Engine.request_bytes(0, 5, 1) == -1
 
 
 @pytest.mark.gpu
@@ -63,6 +81,7 @@ def test_results_in_the_mix_equal_results_alone():
     srv = Server(0, budget_gb=1.0, workers=2)
     res = srv.run(reqs)
     assert res["requests"] == len(reqs)
+    assert res["engine_steps"] > 0 and res["max_inpaint_in_flight"] >= 2
     alone = hdi.Context(0)
     for r in srv.done:
         fd = torch.from_numpy(r.f).cuda()
