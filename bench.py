@@ -662,8 +662,9 @@ def run_serve(args, rank, world):
         f, m = serving_inputs(s, base)
         reqs.append(Request(id=s["id"], kind=s["kind"], arrival=s["arrival"], f=f, mask=m, density=0.03, seed=s["seed"]))
     warm = Server(local, budget_gb=args.budget_gb)
-    warm.run([Request(id=-1, kind=r.kind, arrival=0.0, f=r.f, mask=r.mask, seed=r.seed) for r in reqs[:6]])
-    srv = Server(local, budget_gb=args.budget_gb)
+    warm.run([Request(id=-1 - i, kind=r.kind, arrival=0.0, f=r.f, mask=r.mask, seed=r.seed)
+              for i, r in enumerate(reqs[:6])])
+    srv = Server(local, budget_gb=args.budget_gb, log=True)
     barrier(world)
     res = srv.run(reqs)
     kinds = {k: sum(1 for r in reqs if r.kind == k) for k in ("inpaint", "tonal", "densify")}
@@ -678,7 +679,7 @@ def run_serve(args, rank, world):
            "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, 512^2..3840x2160, "
                                   f"70/25/5 inpaint/tonal/densify-to-3 percent, budget {args.budget_gb} GB",
                       "kinds": kinds, "per_kind": per_kind, "engine_steps": res["engine_steps"],
-                      "max_inpaint_in_flight": res["max_inpaint_in_flight"],
+                      "max_inpaint_in_flight": res["max_inpaint_in_flight"], "errors": res["errors"],
                       "worker_workspace_bytes": res["worker_workspace_bytes"]}}
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -10,6 +10,7 @@
 #include <chrono>
 #include <climits>
 #include <atomic>
+#include <mutex>
 
 #include "../../include/hdi.h"
 #include "common.cuh"

@@ -34,8 +34,10 @@ struct WarpShared {
     float2 xkeep[kWarpRows][32];   // iterate at the lane's pixels (interior subdomains)
 };
 
-__device__ __forceinline__ WarpGeom make_wgeom(int x0, int y0, int H, int W, const MaskView& m, float theta,
-                                               WarpShared& sh) {
+// Geometry of subdomain (x0, y0) from the mask window of row `lane` held by
+// each lane (all ones past the subdomain); writes the lane's mask floats.
+__device__ __forceinline__ WarpGeom make_wgeom_rows(int x0, int y0, int H, int W, uint32_t wrow, float theta,
+                                                    WarpShared& sh) {
     const int lane = threadIdx.x & 31;
     WarpGeom g;
     g.x0 = x0;
@@ -45,8 +47,6 @@ __device__ __forceinline__ WarpGeom make_wgeom(int x0, int y0, int H, int W, con
     g.c = lane & 15;
     g.r0 = 16 * (lane >> 4);
     const int c0 = 2 * g.c;
-    // lane l fetches the mask window of row l (rows past the subdomain read as known)
-    const uint32_t wrow = (lane < g.h) ? m.window(x0, y0 + lane) : ~0u;
     uint32_t um = 0;
 #pragma unroll
     for (int k = 0; k < kWarpRows; ++k) {
@@ -74,6 +74,14 @@ __device__ __forceinline__ WarpGeom make_wgeom(int x0, int y0, int H, int W, con
     g.dmid = make_float2(g.dh.x + 2.f, g.dh.y + 2.f);
     g.dlast = make_float2(g.dh.x + vl, g.dh.y + vl);
     return g;
+}
+
+__device__ __forceinline__ WarpGeom make_wgeom(int x0, int y0, int H, int W, const MaskView& m, float theta,
+                                               WarpShared& sh) {
+    const int lane = threadIdx.x & 31;
+    // lane l fetches the mask window of row l (rows past the subdomain read as known)
+    const uint32_t wrow = (lane < min(32, H - y0)) ? m.window(x0, y0 + lane) : ~0u;
+    return make_wgeom_rows(x0, y0, H, W, wrow, theta, sh);
 }
 
 template <bool FULL>

@@ -653,6 +653,29 @@ int Ctx::tonal_setup() {
     return rc;
 }
 
+// Dynamic shared memory of k_tonal_gram_big for m mask pixels.
+static inline size_t gram_big_smem_bytes(int m) {
+    return ((size_t)32 * (gram_round4(m) + 4) + 2 * gram_round4(m) + 4) * 4;
+}
+
+// The Gram kernels' dynamic shared memory limits, set once per device at
+// the largest size any call can launch with (m <= kGramSmem for
+// k_tonal_gram, m <= 1024 mask pixels per subdomain for k_tonal_gram_big).
+// The limit is a property of the function shared by every context and
+// thread of the process: setting it per call to the call's own size let a
+// concurrent call on another stream lower it between another call's setting
+// and its launch. A launch's own size still sets its occupancy.
+static void tonal_smem_limits(int device) {
+    static std::once_flag once[64];
+    if (device < 0 || device >= 64) return;
+    std::call_once(once[device], [] {
+        cudaFuncSetAttribute(k_tonal_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(gram_smem_floats(kGramSmem) * 4));
+        cudaFuncSetAttribute(k_tonal_gram_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gram_big_smem_bytes(1024));
+    });
+}
+
 int Ctx::tonal_setup_blk(int blk) {
     int rc;
     const int npx = blk * blk;
@@ -745,14 +768,13 @@ int Ctx::tonal_setup_blk(int blk) {
         ++launches;
         tstop();
         const size_t shm = gram_smem_floats(std::min(maxm, kGramSmem)) * 4;
-        cudaFuncSetAttribute(k_tonal_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        tonal_smem_limits(device);
         cudaMemsetAsync(flags, 0, 4, stream);
         tstart(kT_Gram);
         k_tonal_gram<<<nb, 256, shm, stream>>>(t_off, t_goff, t_echo, t_fac, flags, npx);
         ++launches;
         if (maxm > kGramSmem) {
-            const size_t shb = ((size_t)32 * (gram_round4(maxm) + 4) + 2 * gram_round4(maxm) + 4) * 4;
-            cudaFuncSetAttribute(k_tonal_gram_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
+            const size_t shb = gram_big_smem_bytes(maxm);
             k_tonal_gram_big<<<nb, 256, shb, stream>>>(t_off, t_goff, t_echo, t_fac, flags, npx);
             ++launches;
         }
@@ -800,9 +822,7 @@ int Ctx::mask_list() {
 }
 
 void Ctx::tonal_local(float* out) {
-    const size_t shm = (size_t)4 * std::max(t_maxm, 1) * 4;
-    if (shm > 48 * 1024)
-        cudaFuncSetAttribute(k_tonal_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const size_t shm = (size_t)4 * std::max(t_maxm, 1) * 4;   // at most 16 KB (m_i <= 1024)
     tstart(kT_Local);   // the nine colour launches as one timed unit
     for (int color = 0; color < 9; ++color) {
         LocalSolveArgs a;

@@ -32,6 +32,7 @@ measured per request from its arrival to the completion of its result.
 from __future__ import annotations
 
 import collections
+import sys
 import threading
 import time
 from dataclasses import dataclass, field
@@ -94,7 +95,8 @@ def tensor_bytes(f) -> int:
 
 
 class Server:
-    def __init__(self, device: int = 0, budget_gb: float = 120.0, workers: int = 2, tol: float = 1e-6):
+    def __init__(self, device: int = 0, budget_gb: float = 120.0, workers: int = 2, tol: float = 1e-6,
+                 log: bool = False):
         import torch
         import paper_2401_06747_b300 as hdi
         self.torch = torch
@@ -116,11 +118,14 @@ class Server:
         self.inp_new = collections.deque()      # admitted inpaint requests, not yet in the engine
         self.work_q = collections.deque()       # admitted tonal / densify requests
         self.inflight = {}                      # engine tag -> request
+        self.next_tag = 0                       # engine tags (request ids need not be unique)
+        self.errors = []                        # (request id, message) of failed requests
         self.done = []
         self.t0 = 0.0
         self.closed = False
         self.steps = 0
         self.max_inflight = 0
+        self.log = log
 
     # ---------------------------------------------------------- helpers ---
     def now(self) -> float:
@@ -148,16 +153,24 @@ class Server:
                 r.md = torch.from_numpy(r.mask).to(f"cuda:{self.device}", non_blocking=True)
             r.out = torch.empty_like(r.fd)
 
-    def _finish(self, r: Request, stream):
+    def _finish(self, r: Request, stream, error: str | None = None):
         stream.synchronize()
-        res = r.out.cpu().numpy()
-        mask = r.md.cpu().numpy() if r.kind == "densify" else None
-        r.result = (res, mask)
+        if error is None:
+            res = r.out.cpu().numpy()
+            mask = r.md.cpu().numpy() if r.kind == "densify" else None
+            r.result = (res, mask)
+        else:
+            r.result = None
+            r.stats = {"error": error}
         r.done = self.now()
-        del r.fd, r.md, r.out
+        for name in ("fd", "md", "out"):
+            if hasattr(r, name):
+                delattr(r, name)
         self.budget.give(r.bytes)
         with self.lock:
             self.done.append(r)
+            if error is not None:
+                self.errors.append((r.id, error))
 
     # --------------------------------------------------------- admission ---
     def _admit(self):
@@ -184,14 +197,30 @@ class Server:
             if finished:
                 return
             # requests join at this V-cycle boundary
-            for r in new:
+            for j, r in enumerate(new):
                 self._to_device(r, self.inp_stream)
-                if not eng.submit(r.fd, r.md, r.out, tol=self.tol, tag=r.id):
-                    # cannot happen while the server's budget binds; wait one step
+                tag = self.next_tag
+                try:
+                    ok = eng.submit(r.fd, r.md, r.out, tol=self.tol, tag=tag)
+                except self.hdi.HdiError as ex:   # invalid input: reported, not served
+                    self._finish(r, self.inp_stream, str(ex))
+                    continue
+                if not ok and not self.inflight:
+                    # the device itself is short of memory (the server's budget
+                    # binds before the engine's): give back PyTorch's cached
+                    # blocks once, then fail the request rather than wait
+                    self.torch.cuda.empty_cache()
+                    ok = eng.submit(r.fd, r.md, r.out, tol=self.tol, tag=tag)
+                    if not ok:
+                        self._finish(r, self.inp_stream, "does not fit the device memory")
+                        continue
+                if not ok:
+                    # retry after the requests in flight have taken a step
                     with self.lock:
-                        self.inp_new.appendleft(r)
+                        self.inp_new.extendleft(reversed(new[j:]))
                     break
-                self.inflight[r.id] = r
+                self.next_tag += 1
+                self.inflight[tag] = r
             self.max_inflight = max(self.max_inflight, len(self.inflight))
             if not self.inflight:
                 time.sleep(0.0005)
@@ -215,10 +244,14 @@ class Server:
                 time.sleep(0.0005)
                 continue
             self._to_device(r, stream)
-            if r.kind == "tonal":
-                r.stats = ctx.tonal_opt(r.fd, r.md, r.out, tol=self.tol, allow_not_converged=True)
-            else:
-                r.stats = densify_to(ctx, r.fd, r.md, r.out, r.density, r.seed, self.tol)
+            try:
+                if r.kind == "tonal":
+                    r.stats = ctx.tonal_opt(r.fd, r.md, r.out, tol=self.tol, allow_not_converged=True)
+                else:
+                    r.stats = densify_to(ctx, r.fd, r.md, r.out, r.density, r.seed, self.tol)
+            except Exception as ex:   # the request fails, the server goes on
+                self._finish(r, stream, f"{type(ex).__name__}: {ex}")
+                continue
             # the library's report of this worker's workspace: its growth
             # stays charged (the workspace is kept for later requests), and
             # when it grew to fit this request it calibrates the charge of
@@ -243,22 +276,38 @@ class Server:
         threads += [threading.Thread(target=self._worker_loop, args=(i,), daemon=True) for i in range(len(self.w_ctxs))]
         for t in threads:
             t.start()
+        last = [0.0]
+
+        def heartbeat():
+            if self.log and self.now() - last[0] >= 5.0:
+                last[0] = self.now()
+                with self.lock:
+                    line = (f"[serve] t={self.now():.1f}s done={len(self.done)} pending={len(self.pending)} "
+                            f"inpaint_new={len(self.inp_new)} in_engine={len(self.inflight)} "
+                            f"worker_queue={len(self.work_q)} budget={self.budget.used / 1e9:.2f}/"
+                            f"{self.budget.limit / 1e9:.1f} GB steps={self.steps} errors={len(self.errors)} "
+                            f"threads_alive={sum(t.is_alive() for t in threads)}")
+                print(line, file=sys.stderr, flush=True)
+
         for r in sorted(requests, key=lambda q: q.arrival):
             dt = r.arrival - self.now()
             if dt > 0:
                 time.sleep(dt)
             with self.lock:
                 self.pending.append(r)
+            heartbeat()
         with self.lock:
             self.closed = True
-        for t in threads:
-            t.join()
+        while any(t.is_alive() for t in threads):
+            for t in threads:
+                t.join(timeout=1.0)
+            heartbeat()
         wall = self.now()
         lat = np.array([r.done - r.arrival for r in self.done])
         return {"requests": len(self.done), "wall_s": wall, "solves_per_s": len(self.done) / wall,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "engine_steps": self.steps, "max_inpaint_in_flight": self.max_inflight,
-                "worker_workspace_bytes": list(self.w_bytes)}
+                "worker_workspace_bytes": list(self.w_bytes), "errors": list(self.errors)}
 
 
 def densify_to(ctx, fd, md, out, density: float, seed: int, tol: float, step: float = 0.005) -> dict:
