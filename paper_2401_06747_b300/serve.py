@@ -19,10 +19,13 @@ arrival order while one HBM budget allows, and overlaps their work on the GPU:
 Admission: the budget counts what the library reports it holds -- the
 engine's workspace for each inpaint request (hdi_engine_request_bytes) and
 the worker contexts' workspaces (hdi_workspace_bytes, which grow to the
-largest request served) -- plus the request tensors the server keeps on the
-device. A tonal or densification request is charged the growth its worker's
-workspace needs, estimated from the workspace bytes per pixel value the
-library reported for the largest request of that kind so far.
+largest request served and are kept) -- plus the request tensors the server
+keeps on the device. A tonal or densification request reserves an upper
+bound of the workspace it may add (bytes per pixel value of the library's
+layout for that kind) while it runs; afterwards the reservation is replaced
+by the growth the library reports, which stays charged. A request that does
+not fit runs once nothing but those kept workspaces is charged, so a large
+request at the head of the queue cannot block it.
 
 All library calls release the GIL (ctypes), so the host threads only
 schedule; every step of every solve runs in the library's kernels. Latency is
@@ -39,10 +42,11 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-# First estimate of the workspace per pixel value of a tonal / densification
-# request (double-float vectors, multigrid levels, local factors, Anderson
-# history), until the library has reported a measured one.
-INITIAL_BYTES_PER_VALUE = {"tonal": 300.0, "densify": 200.0}
+# Upper bound of the workspace a tonal / densification request may add to a
+# worker context, per pixel value: double-float vectors (9 x 8 B), multigrid
+# levels (~16 B), local factors and Anderson history (tonal), FP64 copies,
+# label and cell arrays (densification).
+BYTES_PER_VALUE = {"tonal": 300.0, "densify": 200.0}
 
 
 @dataclass
@@ -63,16 +67,19 @@ class Request:
 
 
 class Budget:
-    """Admission control by an HBM byte budget (thread safe)."""
+    """Admission control by an HBM byte budget (thread safe). `held` bytes
+    are allocations that stay (the worker contexts' workspaces); a request
+    that does not fit is admitted when nothing else is charged."""
 
     def __init__(self, limit: int):
         self.limit = int(limit)
         self.used = 0
+        self.held = 0
         self.cv = threading.Condition()
 
     def try_take(self, n: int) -> bool:
         with self.cv:
-            if self.used + n <= self.limit or self.used == 0:
+            if self.used + n <= self.limit or self.used == self.held:
                 self.used += n
                 return True
             return False
@@ -83,9 +90,10 @@ class Budget:
             self.cv.notify_all()
 
     def hold(self, n: int):
-        """Charges bytes that are already allocated (no limit check)."""
+        """Charges bytes that are already allocated and stay (no limit check)."""
         with self.cv:
             self.used += n
+            self.held += n
 
 
 def tensor_bytes(f) -> int:
@@ -111,8 +119,6 @@ class Server:
         self.w_streams = [torch.cuda.Stream(device=device) for _ in range(workers)]
         self.w_ctxs = [hdi.Context(device, stream=s, hbm_budget_gb=budget_gb) for s in self.w_streams]
         self.w_bytes = [0] * workers                  # workspace bytes each worker context holds
-        self.bpv = dict(INITIAL_BYTES_PER_VALUE)      # workspace bytes per value, by kind
-        self.calibrated = {k: False for k in self.bpv}  # bpv measured by the library yet
         self.lock = threading.Lock()
         self.pending = collections.deque()      # arrived, not admitted
         self.inp_new = collections.deque()      # admitted inpaint requests, not yet in the engine
@@ -132,15 +138,14 @@ class Server:
         return time.perf_counter() - self.t0
 
     def _charge(self, r: Request) -> int:
-        """Budget bytes of a request: the library's workspace for it plus its
-        tensors. Worker requests are charged the workspace growth of the
-        largest worker context they might need."""
+        """Budget bytes of a request while it runs: the library's workspace
+        for it (exact for the engine, an upper bound of the growth for the
+        worker contexts) plus its tensors."""
         ch, H, W = r.f.shape
         if r.kind == "inpaint":
             ws = self.hdi.Engine.request_bytes(H, W, ch)
         else:
-            need = int(self.bpv[r.kind] * ch * H * W)
-            ws = max(0, need - min(self.w_bytes))
+            ws = int(BYTES_PER_VALUE[r.kind] * ch * H * W)
         return int(ws + tensor_bytes(r.f))
 
     def _to_device(self, r: Request, stream):
@@ -253,17 +258,11 @@ class Server:
                 self._finish(r, stream, f"{type(ex).__name__}: {ex}")
                 continue
             # the library's report of this worker's workspace: its growth
-            # stays charged (the workspace is kept for later requests), and
-            # when it grew to fit this request it calibrates the charge of
-            # the next requests of this kind
+            # stays charged (the workspace is kept for later requests) in
+            # place of the reservation, which _finish gives back
             ws = ctx.workspace_bytes()
-            ch, H, W = r.f.shape
             with self.lock:
                 grown = max(0, ws - self.w_bytes[i])
-                if grown:
-                    self.bpv[r.kind] = ws / float(ch * H * W) if not self.calibrated[r.kind] else \
-                        max(self.bpv[r.kind], ws / float(ch * H * W))
-                    self.calibrated[r.kind] = True
                 self.w_bytes[i] = ws
             self.budget.hold(grown)
             self._finish(r, stream)

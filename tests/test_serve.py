@@ -43,9 +43,10 @@ def test_tensor_bytes_and_held_workspace():
     assert tensor_bytes(f) == 8 * 3 * 100 * 200 + 100 * 200
     b = Budget(1000)
     b.hold(900)                         # workspace already allocated is charged without a check
-    assert not b.try_take(200)
-    b.give(900)
-    assert b.try_take(200)
+    assert b.try_take(200)              # nothing but held bytes charged: runs (cannot block the queue)
+    assert not b.try_take(50)           # now it does not fit
+    b.give(200)
+    assert b.try_take(100)
 
 
 def test_engine_request_bytes_from_the_library():
