@@ -334,6 +334,10 @@ const char* hdi_version(void);
  *                             level (about 1e-6 relative residual) and then returns NOT_CONVERGED
  *   batch_engine      [1]     hdi_inpaint_batch: 1 the batched engine (one launch per phase across
  *                             sizes), 0 size classes stacked as channels, one class after another
+ *   mg_truncate       [1]     end the multigrid hierarchy at its first level whose pixels are all
+ *                             known (the any-of-4 mask restriction fills the coarse masks): every
+ *                             coarser level's correction is exactly zero, so results are unchanged
+ *                             bit for bit; 0 keeps every level down to 32 x 32
  *   strip_rows        [0]     rows per warp of the quad-strip kernels (restriction, prolongation,
  *                             residuals; even, >= 2); 0 chooses by level size
  *   oras_warp         [1]     ORAS sweep layout: 1 one warp per 32x32 subdomain (no CTA barriers),

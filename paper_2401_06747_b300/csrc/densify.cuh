@@ -109,24 +109,50 @@ __global__ void k_dens_error(DensImg a, double* __restrict__ e, long long* __res
 // -------------------------------------------------------------- Voronoi ---
 
 // Per column: the nearest known row to each row (ties to the upper row), or
-// -1 if the column holds no known pixel.
-__global__ void k_vor_columns(MaskView m, int* __restrict__ ys) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= m.W) return;
-    int last = -1;
-    for (int y = 0; y < m.H; ++y) {
-        if (m.known(x, y)) last = y;
-        ys[(size_t)y * m.W + x] = last;
+// -1 if the column holds no known pixel. A block of 32 columns x 32 row
+// segments: each thread scans its segment for its last and first known row,
+// the segments' results meet in shared memory (the nearest known row above
+// the segment is the last one of the nearest segment above that has one,
+// likewise below), and each thread then walks its segment again to write
+// the nearest row of every pixel. A warp reads one mask word per row and
+// writes 32 consecutive columns.
+constexpr int kVorSeg = 32;
+__global__ void __launch_bounds__(32 * kVorSeg) k_vor_columns(MaskView m, int* __restrict__ ys) {
+    __shared__ int lastk[kVorSeg][32], firstk[kVorSeg][32];
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int sg = threadIdx.y;
+    const int len = (m.H + kVorSeg - 1) / kVorSeg;
+    const int ya = min(sg * len, m.H), yb = min(ya + len, m.H);
+    const bool col = x < m.W;
+    int last = -1, first = -1;
+    if (col)
+        for (int y = ya; y < yb; ++y)
+            if (m.known(x, y)) {
+                if (first < 0) first = y;
+                last = y;
+            }
+    lastk[sg][threadIdx.x] = last;
+    firstk[sg][threadIdx.x] = first;
+    __syncthreads();
+    if (!col) return;
+    int up = -1;   // nearest known row above the segment
+    for (int t = sg - 1; t >= 0 && up < 0; --t) up = lastk[t][threadIdx.x];
+    int next = -1;   // nearest known row below the segment
+    for (int t = sg + 1; t < kVorSeg && next < 0; ++t) next = firstk[t][threadIdx.x];
+    // downward: nearest known row at or above y
+    for (int y = ya; y < yb; ++y) {
+        if (m.known(x, y)) up = y;
+        ys[(size_t)y * m.W + x] = up;
     }
-    int next = -1;
-    for (int y = m.H - 1; y >= 0; --y) {
+    // upward: combine with the nearest known row at or below y
+    for (int y = yb - 1; y >= ya; --y) {
         if (m.known(x, y)) next = y;
         const size_t i = (size_t)y * m.W + x;
-        const int up = ys[i];
+        const int u = ys[i];
         int best;
-        if (up < 0) best = next;
-        else if (next < 0) best = up;
-        else best = (y - up <= next - y) ? up : next;
+        if (u < 0) best = next;
+        else if (next < 0) best = u;
+        else best = (y - u <= next - y) ? u : next;
         ys[i] = best;
     }
 }
@@ -226,43 +252,63 @@ __device__ __forceinline__ long long orient2(long long ax, long long ay, long lo
     return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
 }
 
-__device__ __forceinline__ void push_tri(int a, int b, int c, int id, int W, Tri* list, unsigned* count,
-                                         unsigned cap) {
-    const long long o = orient2(a % W, a / W, b % W, b / W, c % W, c / W);
-    if (o == 0) return;
-    const unsigned slot = atomicAdd(count, 1u);
-    if (slot >= cap) return;
-    Tri t;
-    t.v[0] = a; t.v[1] = b; t.v[2] = c;
-    t.id = id;
-    list[slot] = t;
+// Appends of one warp's triangles (0, 1 or 2 per thread) with one atomic
+// per warp: the list order is immaterial (ownership takes the minimum id).
+__device__ __forceinline__ void push_tris(const Tri (&t)[2], int n, Tri* list, unsigned* count, unsigned cap) {
+    const int lane = threadIdx.x & 31;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(HDI_FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(HDI_FULL, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && total) base = atomicAdd(count, (unsigned)total);
+    base = __shfl_sync(HDI_FULL, base, 31);
+    const unsigned slot = base + (unsigned)(incl - n);
+    for (int k = 0; k < n; ++k)
+        if (slot + k < cap) list[slot + k] = t[k];
+}
+
+__device__ __forceinline__ void add_tri(Tri (&t)[2], int& n, int a, int b, int c, int id, int W) {
+    if (orient2(a % W, a / W, b % W, b / W, c % W, c / W) == 0) return;   // collinear: dropped
+    t[n].v[0] = a;
+    t[n].v[1] = b;
+    t[n].v[2] = c;
+    t[n].id = id;
+    ++n;
 }
 
 __global__ void k_dens_quads(const int* __restrict__ V, int H, int W, Tri* __restrict__ list, unsigned* count,
                              unsigned cap) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
-    if (x >= W - 1 || y >= H - 1) return;
-    const int a = V[(size_t)y * W + x];          // TL
-    const int b = V[(size_t)y * W + x + 1];      // TR
-    const int c = V[(size_t)(y + 1) * W + x + 1];// BR
-    const int d = V[(size_t)(y + 1) * W + x];    // BL
-    const int q = y * (W - 1) + x;
-    const bool ab = a == b, ac = a == c, ad = a == d, bc = b == c, bd = b == d, cd = c == d;
-    const int pairs = ab + ac + ad + bc + bd + cd;
-    if (pairs == 0) {   // four distinct sites in cyclic order a, b, c, d
-        push_tri(a, b, c, 2 * q, W, list, count, cap);
-        push_tri(a, c, d, 2 * q + 1, W, list, count, cap);
-    } else if (pairs == 1) {   // exactly three distinct sites
-        int s0 = a, s1, s2;
-        if (ab) { s1 = c; s2 = d; }
-        else if (ac) { s1 = b; s2 = d; }
-        else if (ad) { s1 = b; s2 = c; }
-        else if (bc) { s1 = b; s2 = d; }
-        else if (bd) { s1 = b; s2 = c; }
-        else { s1 = b; s2 = c; }   // cd
-        push_tri(s0, s1, s2, 2 * q, W, list, count, cap);
+    Tri t[2];
+    int n = 0;
+    if (x < W - 1 && y < H - 1) {
+        const int a = V[(size_t)y * W + x];          // TL
+        const int b = V[(size_t)y * W + x + 1];      // TR
+        const int c = V[(size_t)(y + 1) * W + x + 1];// BR
+        const int d = V[(size_t)(y + 1) * W + x];    // BL
+        const int q = y * (W - 1) + x;
+        const bool ab = a == b, ac = a == c, ad = a == d, bc = b == c, bd = b == d, cd = c == d;
+        const int pairs = ab + ac + ad + bc + bd + cd;
+        if (pairs == 0) {   // four distinct sites in cyclic order a, b, c, d
+            add_tri(t, n, a, b, c, 2 * q, W);
+            add_tri(t, n, a, c, d, 2 * q + 1, W);
+        } else if (pairs == 1) {   // exactly three distinct sites
+            int s1, s2;
+            if (ab) { s1 = c; s2 = d; }
+            else if (ac) { s1 = b; s2 = d; }
+            else if (ad) { s1 = b; s2 = c; }
+            else if (bc) { s1 = b; s2 = d; }
+            else if (bd) { s1 = b; s2 = c; }
+            else { s1 = b; s2 = c; }   // cd
+            add_tri(t, n, a, s1, s2, 2 * q, W);
+        }
     }
+    push_tris(t, n, list, count, cap);
 }
 
 // Warp per triangle occurrence: closed-triangle containment by integer
@@ -332,31 +378,88 @@ __global__ void k_dens_argmax(MaskView m, const int* __restrict__ owner, const d
 // ------------------------------------------------------------ selection ---
 
 // Candidate list: cells with E > 0.
-__global__ void k_dens_candidates(const unsigned long long* __restrict__ E, int ncell, int* __restrict__ cand,
-                                  unsigned* ncand) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ncell || E[i] == 0) return;
-    cand[atomicAdd(ncand, 1u)] = i;
+// Candidate list (cells with E > 0) in any order (the selection depends on
+// the keys only), and the largest E (emax), which gives the selection its
+// highest nonzero digit. A block of 256 threads scans 2048 cells (eight per
+// thread, coalesced): one atomic per block for its slots, and the maximum
+// only when the block's exceeds the value already stored.
+constexpr int kCandPer = 8;
+__global__ void __launch_bounds__(256) k_dens_candidates(const unsigned long long* __restrict__ E, int ncell,
+                                                         int* __restrict__ cand, unsigned* ncand,
+                                                         unsigned long long* emax) {
+    __shared__ unsigned wsum[8];
+    __shared__ unsigned long long wmax[8];
+    __shared__ unsigned base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long b0 = (long long)blockIdx.x * (256 * kCandPer);
+    unsigned long long e[kCandPer];
+    unsigned n = 0;
+    unsigned long long m = 0;
+#pragma unroll
+    for (int k = 0; k < kCandPer; ++k) {
+        const long long i = b0 + k * 256 + threadIdx.x;
+        e[k] = (i < ncell) ? E[i] : 0ull;
+        n += e[k] != 0;
+        m = e[k] > m ? e[k] : m;
+    }
+    // exclusive prefix of n over the block: warp scan, then the warp totals
+    unsigned incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(HDI_FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(HDI_FULL, m, o);
+        m = v > m ? v : m;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    if (lane == 0) wmax[wid] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        unsigned long long bm = 0;
+        for (int w = 0; w < 8; ++w) {
+            const unsigned t = wsum[w];
+            wsum[w] = tot;
+            tot += t;
+            bm = wmax[w] > bm ? wmax[w] : bm;
+        }
+        base = tot ? atomicAdd(ncand, tot) : 0u;
+        if (bm > *(volatile unsigned long long*)emax) atomicMax(emax, bm);
+    }
+    __syncthreads();
+    unsigned slot = base + wsum[wid] + incl - n;
+#pragma unroll
+    for (int k = 0; k < kCandPer; ++k)
+        if (e[k]) cand[slot++] = (int)(b0 + k * 256 + threadIdx.x);
 }
 
 // Histogram of one 16-bit digit of the key among candidates whose higher
 // digits equal `prefix`. Key = E (mode 0) or the cell id among E == tieE
-// (mode 1).
+// (mode 1). Lanes of a warp with the same bin add once (the keys of a
+// selection concentrate in few bins).
 __global__ void k_dens_hist(const int* __restrict__ cand, const unsigned* ncand,
                             const unsigned long long* __restrict__ E, int mode, unsigned long long tieE,
                             int shift, unsigned long long prefix, unsigned* __restrict__ hist) {
     const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *ncand) return;
-    const int c = cand[i];
-    unsigned long long key;
-    if (mode == 0) key = E[c];
-    else {
-        if (E[c] != tieE) return;
-        key = (unsigned long long)c;
+    unsigned bin = 0xFFFFFFFFu;   // no contribution
+    if (i < *ncand) {
+        const int c = cand[i];
+        unsigned long long key = 0;
+        bool ok = true;
+        if (mode == 0) key = E[c];
+        else {
+            ok = E[c] == tieE;
+            key = (unsigned long long)c;
+        }
+        const unsigned long long hi = (shift + 16 >= 64) ? 0ull : (key >> (shift + 16));
+        if (ok && hi == prefix) bin = (unsigned)((key >> shift) & 0xFFFFull);
     }
-    const unsigned long long hi = (shift + 16 >= 64) ? 0ull : (key >> (shift + 16));
-    if (hi != prefix) return;
-    atomicAdd(hist + ((key >> shift) & 0xFFFFull), 1u);
+    const unsigned same = __match_any_sync(HDI_FULL, bin);
+    const int lane = threadIdx.x & 31;
+    if (bin != 0xFFFFFFFFu && lane == __ffs(same) - 1) atomicAdd(hist + bin, (unsigned)__popc(same));
 }
 
 // Select cells with E > T, or E == T and id <= Tid; set their argmax pixel.
@@ -365,14 +468,18 @@ __global__ void k_dens_commit(const int* __restrict__ cand, const unsigned* ncan
                               const int* __restrict__ arg, int W, uint8_t* __restrict__ mask, long long rs,
                               unsigned long long* added) {
     const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *ncand) return;
-    const int c = cand[i];
-    const unsigned long long ec = E[c];
-    if (ec > T || (ec == T && (long long)c <= Tid)) {
-        const int p = arg[c];
-        mask[(size_t)(p / W) * rs + p % W] = 1;
-        atomicAdd(added, 1ull);
+    bool sel = false;
+    if (i < *ncand) {
+        const int c = cand[i];
+        const unsigned long long ec = E[c];
+        if (ec > T || (ec == T && (long long)c <= Tid)) {
+            const int p = arg[c];
+            mask[(size_t)(p / W) * rs + p % W] = 1;
+            sel = true;
+        }
     }
+    const unsigned ball = __ballot_sync(HDI_FULL, sel);
+    if ((threadIdx.x & 31) == 0 && ball) atomicAdd(added, (unsigned long long)__popc(ball));
 }
 
 // Plain FP64 copy of a caller image (any strides) into [nch][H][W].
@@ -465,7 +572,7 @@ int Ctx::densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t
     img.W = W;
     img.nch = nch;
     dim3 grow((W + 127) / 128, H);
-    unsigned long long hcnt[5] = {0, 0, 0, 0, 0};
+    unsigned long long hcnt[6] = {0, 0, 0, 0, 0, 0};
     if (ones == 0) {
         long long* wq = eq;   // reuse
         k_dens_lapw<<<grow, 128, 0, stream>>>(img, wq, cnt + 1);
@@ -508,13 +615,17 @@ int Ctx::densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t
                 first = full;
             }
         } else {
-            k_vor_columns<<<(W + 127) / 128, 128, 0, stream>>>(mv, ys);
+            k_vor_columns<<<(W + 31) / 32, dim3(32, kVorSeg), 0, stream>>>(mv, ys);
             k_vor_rows<<<grow, 128, 0, stream>>>(ys, H, W, V);
             launches += 2;
         }
+        // the labels' largest distance bounds the next jump-flooding schedule
+        // (hdi_densify with densify_voronoi = 1); exact labels need none
         cudaMemsetAsync(cnt + 4, 0, 8, stream);
-        k_label_maxd2<<<grow, 128, 0, stream>>>(V, H, W, cnt + 4);
-        ++launches;
+        if (p.densify_voronoi >= 0.5) {
+            k_label_maxd2<<<grow, 128, 0, stream>>>(V, H, W, cnt + 4);
+            ++launches;
+        }
         unsigned* tcount = (unsigned*)(cnt + 2);
         unsigned* ncand = (unsigned*)(cnt + 3);
         // Voronoi-cell partition (densify_partition = 1): no triangles; every
@@ -541,9 +652,10 @@ int Ctx::densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t
         cudaMemsetAsync(arg, 0x7F, ncell * 4, stream);
         k_dens_cells<<<grow, 128, 0, stream>>>(mv, V, owner, eq, e, E, emax, hull_base);
         k_dens_argmax<<<grow, 128, 0, stream>>>(mv, owner, e, emax, arg);
-        k_dens_candidates<<<(unsigned)((ncell + 255) / 256), 256, 0, stream>>>(E, (int)ncell, cand, ncand);
+        k_dens_candidates<<<(unsigned)((ncell + 256 * kCandPer - 1) / (256 * kCandPer)), 256, 0, stream>>>(
+            E, (int)ncell, cand, ncand, cnt + 5);
         launches += 3;
-        cudaMemcpyAsync(hcnt, cnt, 32, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(hcnt, cnt, 48, cudaMemcpyDeviceToHost, stream);
         if ((rc = sync("densification cells"))) return rc;
         const unsigned nc = (unsigned)(hcnt[3] & 0xffffffffull);
         unsigned long long T = 0;
@@ -553,7 +665,11 @@ int Ctx::densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t
             std::vector<unsigned> h(65536);
             unsigned long long need = (unsigned long long)k, prefix = 0;
             const unsigned blocks = (nc + 255) / 256;
-            for (int shift = 48; shift >= 0 && need > 0; shift -= 16) {
+            // digits above the largest E are 0 for every key: start below them
+            const unsigned long long emax_h = hcnt[5];
+            int top = 0;
+            while (top < 48 && (emax_h >> (top + 16)) != 0) top += 16;
+            for (int shift = top; shift >= 0 && need > 0; shift -= 16) {
                 cudaMemsetAsync(hist, 0, 65536 * 4, stream);
                 k_dens_hist<<<blocks, 256, 0, stream>>>(cand, ncand, E, 0, 0, shift, prefix, hist);
                 ++launches;

@@ -214,7 +214,7 @@ struct Engine {
         for (EngReq* r : S) {
             Ctx& c = r->c;
             const Level& L = c.lev[l];
-            const bool coarsest = (l == c.nlev - 1);
+            const bool coarsest = (l == c.nlev_run - 1);
             const double eta = (l > 0 && p.coarse_level_eta > 0) ? p.coarse_level_eta : p.oras_eta;
             for (int ch = 0; ch < c.nch; ++ch) {
                 OrasTask t{};
@@ -294,7 +294,7 @@ struct Engine {
         rec_oras(l, true, S, false);
         std::vector<EngReq*> N;
         for (EngReq* r : S)
-            if (l < r->c.nlev - 1) N.push_back(r);
+            if (l < r->c.nlev_run - 1) N.push_back(r);
         if (N.empty()) return;
         rec_strip(EK_RESTRICT, l, N);
         rec_vcycle(l + 1, N);
@@ -305,7 +305,7 @@ struct Engine {
     // Reduced full multigrid (as Ctx::fmg) over the new requests A.
     void rec_fmg(const std::vector<EngReq*>& A) {
         int maxl = 0;
-        for (EngReq* r : A) maxl = std::max(maxl, r->c.nlev);
+        for (EngReq* r : A) maxl = std::max(maxl, r->c.nlev_run);
         {   // level-0 right-hand side C f in FP32
             std::vector<PixTask> tasks;
             std::vector<int> ctas;
@@ -331,7 +331,7 @@ struct Engine {
             std::vector<int> ctas;
             for (EngReq* r : A) {
                 Ctx& c = r->c;
-                if (l >= c.nlev) continue;
+                if (l >= c.nlev_run) continue;
                 const Level& F = c.lev[l - 1];
                 const Level& C = c.lev[l];
                 for (int ch = 0; ch < c.nch; ++ch) {
@@ -351,8 +351,8 @@ struct Engine {
         for (int l = maxl - 1; l >= 0; --l) {
             std::vector<EngReq*> start, up, all;
             for (EngReq* r : A) {
-                if (l == r->c.nlev - 1) start.push_back(r);
-                else if (l < r->c.nlev - 1) up.push_back(r);
+                if (l == r->c.nlev_run - 1) start.push_back(r);
+                else if (l < r->c.nlev_run - 1) up.push_back(r);
             }
             rec_strip(EK_PROLONG2, l, start);   // coarsest: x = b on known pixels, 0 elsewhere
             rec_strip(EK_PROLONG1, l, up);      // finer levels: interpolate the coarser solution
@@ -555,6 +555,7 @@ int Ctx::setup_lean(int H_, int W_, int nch_, cudaStream_t s) {
     W = W_;
     nch = nch_;
     nlev = nl;
+    nlev_run = nl;
     nmask = 1;
     stream = s;
     cudaMemsetAsync(counters, 0, 64 * 8, s);

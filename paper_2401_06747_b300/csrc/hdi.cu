@@ -72,6 +72,7 @@ const ParamDef kParams[] = {
     {"inpaint_fp32", &Params::inpaint_fp32, 0, 1},
     {"batch_engine", &Params::batch_engine, 0, 1},
     {"strip_rows", &Params::strip_rows, 0, 64},
+    {"mg_truncate", &Params::mg_truncate, 0, 1},
 };
 
 }  // namespace
@@ -214,7 +215,7 @@ int Ctx::setup(int H_, int W_, int nch_, int nmask_) {
     acc(64 * 8);                                              // counters / flags
     int rc = ws.reserve(*this, bytes, "inpainting workspace");
     if (rc) { H = W = nch = 0; return rc; }
-    H = H_; W = W_; nch = nch_; nlev = nl; nmask = nmask_;
+    H = H_; W = W_; nch = nch_; nlev = nl; nlev_run = nl; nmask = nmask_;
     for (int l = 0; l < nl; ++l) {
         Level& L = lev[l];
         L.H = sizes[l].first;
@@ -284,11 +285,14 @@ MaskView Ctx::mview(int l) const {
 }
 
 // Builds the coarse masks from the level-0 bits (any-of-4, Sec. 3.3).
+// Counts each coarse level's known pixels (all mask planes) into
+// counters[kCntLevelKnown + l].
 void Ctx::build_mask_pyramid() {
+    cudaMemsetAsync(counters + kCntLevelKnown, 0, kMaxLevels * 8, stream);
     for (int l = 0; l + 1 < nlev; ++l) {
         const Level& C = lev[l + 1];
         dim3 blk(64), grd((C.wp + 63) / 64, C.H, nmask);
-        k_restrict_mask<<<grd, blk, 0, stream>>>(mview(l), C.bits, C.H, C.W, C.wp);
+        k_restrict_mask<<<grd, blk, 0, stream>>>(mview(l), C.bits, C.H, C.W, C.wp, counters + kCntLevelKnown + l + 1);
         ++launches;
     }
 }
@@ -350,7 +354,7 @@ void Ctx::vcycle(int l) {
     Level& L = lev[l];
     const double* pre_norm = (l == 0) ? scal + kSlotR64 * kMaxCh : scal + l * kMaxCh;
     unsigned long long* it = (l == 0) ? counters + kCntLocal : nullptr;
-    if (l == nlev - 1) {
+    if (l == nlev_run - 1) {
         oras(l, true, nullptr, L.xa, pre_norm, true, it);
         if (l == 0) ++vcycles_run;
         return;
@@ -426,12 +430,12 @@ void Ctx::fmg(DFc d) {
         k_data_to_f32<<<grd, 128, 0, stream>>>(d, arr(0), mview(0), lev[0].b);
         ++launches;
     }
-    for (int l = 1; l < nlev; ++l) {
+    for (int l = 1; l < nlev_run; ++l) {
         dim3 blk(32, 8), grd((lev[l].W + 31) / 32, (lev[l].H + 7) / 8, nch);
         k_restrict_data<<<grd, blk, 0, stream>>>(arr(l - 1), mview(l - 1), lev[l - 1].b, arr(l), lev[l].b);
         ++launches;
     }
-    const int L = nlev - 1;
+    const int L = nlev_run - 1;
     {
         const int qr = qrows(lev[L].H, lev[L].W, nch);
         dim3 grd = quad_grid(lev[L].H, lev[L].W, nch, qr), blk(128);
@@ -701,14 +705,28 @@ int Ctx::load_mask(const hdi_mask* m, long long* ones, int plane, bool pyramid) 
     ++launches;
     if (pyramid) build_mask_pyramid();
     unsigned long long cnt = 0;
+    unsigned long long lk[kMaxLevels] = {};
     unsigned bad = 0;
     cudaMemcpyAsync(&cnt, counters + kCntOnes, 8, cudaMemcpyDeviceToHost, stream);
     cudaMemcpyAsync(&bad, flags, 4, cudaMemcpyDeviceToHost, stream);
+    if (pyramid) cudaMemcpyAsync(lk, counters + kCntLevelKnown, kMaxLevels * 8, cudaMemcpyDeviceToHost, stream);
     int rc = sync("mask upload");
     if (rc) return rc;
     if (bad) return fail(HDI_ERR_INVALID_ARG, "mask: values must be 0 or 1");
     *ones = (long long)cnt;
     mask_ones = (long long)cnt;
+    if (pyramid) {
+        // a level whose pixels are all known (every plane) has the exact
+        // coarse correction 0, and so has every level below it: the solves
+        // stop their hierarchy there (the level itself stays as the trivial
+        // coarsest level)
+        nlev_run = nlev;
+        for (int l = 1; l < nlev && p.mg_truncate >= 0.5; ++l)
+            if (lk[l] == (unsigned long long)nmask * lev[l].H * lev[l].W) {
+                nlev_run = l + 1;
+                break;
+            }
+    }
     return HDI_OK;
 }
 
@@ -1308,6 +1326,7 @@ size_t noalloc_layout(Ctx& c, char* base, size_t cap, int H_, int W_, int nch_) 
         c.W = W_;
         c.nch = nch_;
         c.nlev = nl;
+        c.nlev_run = nl;
     }
     return off;
 }

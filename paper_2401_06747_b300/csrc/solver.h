@@ -47,6 +47,7 @@ struct Params {
     double densify_partition = 0;   // 0: Delaunay triangles (Alg. 1); 1: Voronoi cells of the mask (Sec. 6.2)
     double inpaint_fp32 = 0;        // 1: hdi_inpaint / hdi_inpaint_batch in the plain FP32 form
     double batch_engine = 1;        // hdi_inpaint_batch: 1 the batched engine (all sizes per launch), 0 size classes
+    double mg_truncate = 1;         // end the hierarchy at its first fully known level (exact)
     double strip_rows = 0;          // rows per warp of the quad-strip kernels (even, >= 2); 0: chosen by size
     double oras_warp = 1;           // ORAS sweep layout: 1 one warp per subdomain, 0 two warps
 };
@@ -112,6 +113,7 @@ constexpr int kSlotViE = 23;      // Voronoi initialisation: ||f - u||^2
 constexpr int kCntOnes = 0;
 constexpr int kCntLocal = 1;
 constexpr int kCntEcho = 2;
+constexpr int kCntLevelKnown = 16;   // [kMaxLevels] known pixels per level of the mask pyramid
 constexpr int kMaxTimed = 2048;   // timed launches buffered between flushes
 enum { kT_Oras = 0, kT_Residual, kT_Prolong, kT_Restrict, kT_Echo, kT_Gram, kT_Local, kT_Anderson, kT_Coarse };
 // double-float vectors of level-0 size
@@ -146,6 +148,9 @@ struct Ctx {
     Arena lws;     // list of mask pixels (tonal optimisation)
     Arena stage;   // host staging
     int H = 0, W = 0, nch = 0, nlev = 0;
+    // levels the solves use: the hierarchy ends at its first level whose
+    // pixels are all known (every coarser level's correction is exactly 0)
+    int nlev_run = 0;
     int nmask = 1;             // mask planes (1 = shared by all channels)
     int* d_chmask = nullptr;   // [kMaxCh] mask plane of each channel (batched solves)
     Level lev[kMaxLevels];

@@ -61,15 +61,17 @@ __device__ __forceinline__ uint32_t even_bits(uint64_t x) {
     return (uint32_t)x;
 }
 
-// Coarse mask bit = OR of the 2x2 children (Sec. 3.3).
-__global__ void k_restrict_mask(MaskView f, uint32_t* __restrict__ cbits, int cH, int cW, int cwp) {
+// Coarse mask bit = OR of the 2x2 children (Sec. 3.3). `known` (may be
+// null) accumulates the coarse level's known pixels over all planes.
+__global__ void k_restrict_mask(MaskView f, uint32_t* __restrict__ cbits, int cH, int cW, int cwp,
+                                unsigned long long* known) {
     const int wx = blockIdx.x * blockDim.x + threadIdx.x;
     const int Y = blockIdx.y;
-    if (Y >= cH || wx >= cwp) return;
+    const bool valid = Y < cH && wx < cwp;
     f.bits += (size_t)blockIdx.z * f.cstride;           // mask plane
     cbits += (size_t)blockIdx.z * (size_t)cH * cwp;
     uint32_t out = 0;
-    if (wx * 32 < cW) {
+    if (valid && wx * 32 < cW) {
         const int fw = 2 * wx;   // fine words 2wx, 2wx+1 hold this word's children
         uint64_t r = 0;
         for (int fy = 2 * Y; fy <= 2 * Y + 1 && fy < f.H; ++fy) {
@@ -79,10 +81,14 @@ __global__ void k_restrict_mask(MaskView f, uint32_t* __restrict__ cbits, int cH
             r |= lo | (hi << 32);
         }
         out = even_bits(r | (r >> 1));
-        const int valid = cW - wx * 32;
-        if (valid < 32) out &= (1u << valid) - 1u;
+        const int nvalid = cW - wx * 32;
+        if (nvalid < 32) out &= (1u << nvalid) - 1u;
     }
-    cbits[(size_t)Y * cwp + wx] = out;
+    if (valid) cbits[(size_t)Y * cwp + wx] = out;
+    if (known) {
+        const unsigned n = __reduce_add_sync(HDI_FULL, (unsigned)__popc(out));
+        if ((threadIdx.x & 31) == 0 && n) atomicAdd(known, (unsigned long long)n);
+    }
 }
 
 // --------------------------------------------------------- level arrays ---

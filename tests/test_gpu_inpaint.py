@@ -174,3 +174,29 @@ def test_plain_fp32_form():
     st = k.inpaint(fd, cd, out, tol=1e-10, allow_not_converged=True)
     assert st["status"] == -3 and 1e-10 < st["rel_res"] < 1e-4
     assert st["iterations"] < 20   # stopped by the stall rule, not the cap
+
+
+def test_hierarchy_truncation_is_exact():
+    """mg_truncate = 1 ends the hierarchy at its first fully known level (at
+    4% density the any-of-4 mask restriction leaves no unknown pixel from
+    the fifth level on): the same results bit for bit as the full hierarchy,
+    for inpainting and tonal optimisation, with fewer launches."""
+    need_gpu()
+    H, W = 768, 1024
+    f = synth_rgb(H, W, seeds=(91, 92, 93), dtype=np.float32)
+    c = random_mask(H, W, 0.04, 94)
+    fd, cd = dev(f), dev(c)
+    res, launches = [], []
+    for tr in (0, 1):
+        k = ctx(mg_truncate=tr)
+        u = torch.empty_like(fd)
+        g = torch.empty_like(fd)
+        s1 = k.inpaint(fd, cd, u, tol=1e-7)
+        s2 = k.tonal_opt(fd, cd, g, tol=1e-6)
+        res.append((u.cpu().numpy(), g.cpu().numpy(), s1, s2))
+        launches.append(k.launch_count())
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    np.testing.assert_array_equal(res[0][1], res[1][1])
+    assert res[0][2]["local_iters"] == res[1][2]["local_iters"]
+    assert res[0][3]["vcycles"] == res[1][3]["vcycles"]
+    assert launches[1] < launches[0]
