@@ -33,7 +33,8 @@ struct EngReq {
     hdi_image out{};            // caller's u
     int64_t tag = 0;
     double tol = 1e-6;
-    int state = 0;              // 0: admitted, waiting for FMG; 1: in refinement
+    int state = 0;              // -1: inputs loading; 0: admitted, waiting for FMG; 1: in refinement
+    int rb = -1;                // readback slot of its input checks while loading
     int cur = 0;                // iterate pair holding u
     int iterations = 0;         // refinement steps
     int vcycles = 0;
@@ -471,6 +472,11 @@ struct Engine {
     }
 
     // ------------------------------------------------------------ API ---
+    static constexpr int kReadbackSlots = 4096;   // requests whose inputs may load at once
+    LoadReadback* hrb = nullptr;                  // pinned readbacks of their input checks
+    int nloading = 0;
+    int submit_async(const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, int64_t tag);
+    int finalize_loads(std::vector<std::pair<int64_t, int>>* failed);
     int submit(const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, int64_t tag);
     int step(int64_t* tags, hdi_stats* stats, int cap, int* ndone);
     int finish(EngReq* r, unsigned long long* li);
@@ -480,65 +486,77 @@ struct Engine {
     ~Engine();
 };
 
-// Workspace of one request: the lean layout of Ctx::setup_lean.
-static size_t lean_bytes(int H_, int W_, int nch_) {
-    size_t bytes = 0;
-    auto acc = [&](size_t b) { bytes += ((b + 255) & ~(size_t)255); };
-    int h = H_, w = W_, nl = 0;
+// Workspace of one request (the lean layout of Ctx::setup_lean): first the
+// parts that start at zero -- the mask bits of every level, the counters,
+// the norms and the flags -- in one contiguous block (one memset), then the
+// level arrays and the double-float vectors.
+struct LeanPlan {
+    int nl = 0;
+    int h[kMaxLevels], w[kMaxLevels];
+    size_t zero_bytes = 0, bytes = 0;
+};
+static inline size_t lean_align(size_t b) { return (b + 255) & ~(size_t)255; }
+static LeanPlan lean_plan(int H_, int W_, int nch_) {
+    LeanPlan L;
+    int h = H_, w = W_;
     for (;;) {
-        const int P = round_up(w, 32);
-        const int wp = (w + 31) / 32 + 1;
-        acc((size_t)h * wp * 4);
-        for (int k = 0; k < 3; ++k) acc((size_t)nch_ * h * P * 4);
-        ++nl;
-        if (std::max(h, w) <= 32 || nl >= kMaxLevels) break;
+        L.h[L.nl] = h;
+        L.w[L.nl] = w;
+        ++L.nl;
+        if (std::max(h, w) <= 32 || L.nl >= kMaxLevels) break;
         h = (h + 1) / 2;
         w = (w + 1) / 2;
     }
+    size_t z = 0;
+    for (int l = 0; l < L.nl; ++l) z += lean_align((size_t)L.h[l] * ((L.w[l] + 31) / 32 + 1) * 4);
+    z += lean_align(64 * 8) + lean_align((size_t)kSlots * kMaxCh * 8) + lean_align(256 + kMaxCh * 4);
+    L.zero_bytes = z;
+    size_t b = z;
+    for (int l = 0; l < L.nl; ++l) b += 3 * lean_align((size_t)nch_ * L.h[l] * round_up(L.w[l], 32) * 4);
     const size_t n32 = (size_t)nch_ * H_ * round_up(W_, 32);
-    for (int k = 0; k < 3; ++k) acc(n32 * 8);   // f, u ping-pong (double-float)
-    acc(n32 * 4);                                // third component of f
-    acc((size_t)kSlots * kMaxCh * 8);            // norms
-    acc(64 * 8);                                 // counters
-    acc(256 + kMaxCh * 4);                       // flags
-    return bytes;
+    b += 3 * lean_align(n32 * 8) + lean_align(n32 * 4);
+    L.bytes = b;
+    return L;
 }
+static size_t lean_bytes(int H_, int W_, int nch_) { return lean_plan(H_, W_, nch_).bytes; }
 
 // Lean set-up of a request context: the buffers of one inpainting solve
 // only, allocated stream-ordered (cudaMallocAsync) on `s`.
 int Ctx::setup_lean(int H_, int W_, int nch_, cudaStream_t s) {
     if (nch_ < 1 || nch_ > kMaxCh) return fail(HDI_ERR_INVALID_ARG, "request: 1 to %d channels", kMaxCh);
-    const size_t bytes = lean_bytes(H_, W_, nch_);
+    const LeanPlan plan = lean_plan(H_, W_, nch_);
     ws.astream = s;
     ws.async = true;
     {
-        cudaError_t e = cudaMallocAsync(&ws.base, bytes, s);
+        cudaError_t e = cudaMallocAsync(&ws.base, plan.bytes, s);
         if (e != cudaSuccess) {
             ws.base = nullptr;
             cudaGetLastError();
-            return fail(HDI_ERR_OUT_OF_MEMORY, "request workspace: cudaMallocAsync(%zu) failed", bytes);
+            return fail(HDI_ERR_OUT_OF_MEMORY, "request workspace: cudaMallocAsync(%zu) failed", plan.bytes);
         }
-        ws.cap = bytes;
+        ws.cap = plan.bytes;
         ws.used = 0;
     }
-    int h = H_, w = W_, nl = 0;
-    for (;;) {
-        Level& L = lev[nl];
-        L.H = h;
-        L.W = w;
-        L.P = round_up(w, 32);
-        L.wp = (w + 31) / 32 + 1;
-        L.cs = (long long)h * L.P;
-        L.bits = (uint32_t*)ws.take((size_t)h * L.wp * 4);
+    const int nl = plan.nl;
+    for (int l = 0; l < nl; ++l) {
+        Level& L = lev[l];
+        L.H = plan.h[l];
+        L.W = plan.w[l];
+        L.P = round_up(L.W, 32);
+        L.wp = (L.W + 31) / 32 + 1;
+        L.cs = (long long)L.H * L.P;
+        L.bits = (uint32_t*)ws.take((size_t)L.H * L.wp * 4);
+        L.nbx = tile_count(L.W, 32, kOv);
+        L.nby = tile_count(L.H, 32, kOv);
+    }
+    counters = (unsigned long long*)ws.take(64 * 8);
+    scal = (double*)ws.take((size_t)kSlots * kMaxCh * 8);
+    flags = (unsigned*)ws.take(256 + kMaxCh * 4);
+    for (int l = 0; l < nl; ++l) {
+        Level& L = lev[l];
         L.xa = (float*)ws.take((size_t)nch_ * L.cs * 4);
         L.xb = (float*)ws.take((size_t)nch_ * L.cs * 4);
         L.b = (float*)ws.take((size_t)nch_ * L.cs * 4);
-        L.nbx = tile_count(w, 32, kOv);
-        L.nby = tile_count(h, 32, kOv);
-        ++nl;
-        if (std::max(h, w) <= 32 || nl >= kMaxLevels) break;
-        h = (h + 1) / 2;
-        w = (w + 1) / 2;
     }
     const size_t n32 = (size_t)nch_ * H_ * round_up(W_, 32);
     const int dfs[3] = {kF, kU0, kU1};
@@ -547,9 +565,6 @@ int Ctx::setup_lean(int H_, int W_, int nch_, cudaStream_t s) {
         dfv[dfs[i]].lo = dfv[dfs[i]].hi + n32;
     }
     flo2 = (float*)ws.take(n32 * 4);
-    scal = (double*)ws.take((size_t)kSlots * kMaxCh * 8);
-    counters = (unsigned long long*)ws.take(64 * 8);
-    flags = (unsigned*)ws.take(256 + kMaxCh * 4);
     if (ws.used > ws.cap) return fail(HDI_ERR_CUDA, "internal: request workspace carving exceeds its size");
     H = H_;
     W = W_;
@@ -558,9 +573,7 @@ int Ctx::setup_lean(int H_, int W_, int nch_, cudaStream_t s) {
     nlev_run = nl;
     nmask = 1;
     stream = s;
-    cudaMemsetAsync(counters, 0, 64 * 8, s);
-    cudaMemsetAsync(scal, 0, (size_t)kSlots * kMaxCh * 8, s);
-    for (int l = 0; l < nl; ++l) cudaMemsetAsync(lev[l].bits, 0, (size_t)lev[l].H * lev[l].wp * 4, s);
+    cudaMemsetAsync(ws.base, 0, plan.zero_bytes, s);   // mask bits, counters, norms, flags
     return cuda_check(cudaGetLastError(), "request workspace");
 }
 
@@ -587,13 +600,24 @@ Engine::~Engine() {
     if (partials) cudaFree(partials);
     if (tickets) cudaFree(tickets);
     if (hfin) cudaFreeHost(hfin);
+    if (hrb) cudaFreeHost(hrb);
 }
 
-// Admits one request if its workspace fits the budget: allocates it,
-// uploads and checks mask and image. FMG runs at the next step.
-int Engine::submit(const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, int64_t tag) {
+// Admits one request if its workspace fits the budget: allocates it and
+// enqueues the upload and checks of mask and image without waiting; the
+// checks are evaluated by finalize_loads (one wait for all requests loaded
+// since the last call). FMG runs at the first step after that.
+int Engine::submit_async(const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, int64_t tag) {
     if (!(tol > 0.0 && tol < 1.0)) return fail(HDI_ERR_INVALID_ARG, "tol must lie in (0, 1)");
     if (!f || !m || !u) return fail(HDI_ERR_INVALID_ARG, "null request argument");
+    if (nloading >= kReadbackSlots) return fail(HDI_ERR_OUT_OF_MEMORY, "too many requests loading at once");
+    if (!hrb) {
+        if (cudaMallocHost(&hrb, sizeof(LoadReadback) * kReadbackSlots) != cudaSuccess) {
+            cudaGetLastError();
+            hrb = nullptr;
+            return fail(HDI_ERR_OUT_OF_MEMORY, "engine: pinned readback slots");
+        }
+    }
     EngReq* r = new EngReq();
     Ctx& c = r->c;
     c.device = device;
@@ -609,6 +633,10 @@ int Engine::submit(const hdi_image* f, const hdi_mask* m, hdi_image* u, double t
         delete r;
         return fail(HDI_ERR_INVALID_ARG, "u: dtype differs from f");
     }
+    if (m->height != f->height || m->width != f->width) {
+        delete r;
+        return fail(HDI_ERR_INVALID_ARG, "mask: shape does not match the image");
+    }
     r->bytes = lean_bytes(f->height, f->width, f->channels);
     if ((double)(used + r->bytes) > budget) {
         const size_t need = r->bytes;
@@ -623,22 +651,64 @@ int Engine::submit(const hdi_image* f, const hdi_mask* m, hdi_image* u, double t
     }
     used += r->bytes;
     long long ones = 0;
-    rc = c.load_mask(m, &ones);
-    if (!rc && ones == 0) rc = c.fail(HDI_ERR_EMPTY_MASK, "empty mask: A is singular");
     c.f_lo_zero = true;
-    if (!rc) rc = c.load_image(f, c.dfv[kF], c.flo2);
+    rc = c.load_mask(m, &ones, 0, true, false);
+    if (!rc) rc = c.load_image(f, c.dfv[kF], c.flo2, 0, false);
     if (rc) {
         err = c.err;
         release(r);
         return rc;
     }
+    r->rb = nloading++;
+    c.enqueue_load_readback(&hrb[r->rb]);
     r->out = *u;
     r->tag = tag;
     r->tol = tol;
-    r->state = 0;
+    r->state = -1;
     r->t0 = std::chrono::steady_clock::now();
     reqs.push_back(r);
     return HDI_OK;
+}
+
+// Waits once for the loads enqueued by submit_async and evaluates their
+// checks; requests that fail them leave (tag and status into `failed`).
+int Engine::finalize_loads(std::vector<std::pair<int64_t, int>>* failed) {
+    if (nloading == 0) return HDI_OK;
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HDI_ERR_CUDA, "engine input upload: %s", cudaGetErrorString(e));
+    std::vector<EngReq*> keep;
+    for (EngReq* r : reqs) {
+        if (r->state != -1) {
+            keep.push_back(r);
+            continue;
+        }
+        long long ones = 0;
+        int rc = r->c.load_checks(hrb[r->rb], &ones);
+        if (!rc && ones == 0) rc = r->c.fail(HDI_ERR_EMPTY_MASK, "empty mask: A is singular");
+        r->rb = -1;
+        if (rc) {
+            err = r->c.err;
+            if (failed) failed->push_back({r->tag, rc});
+            release(r);
+            continue;
+        }
+        r->state = 0;
+        keep.push_back(r);
+    }
+    reqs = keep;
+    nloading = 0;
+    return HDI_OK;
+}
+
+// One request with its checks done before returning (a failing one returns
+// their status and is not kept).
+int Engine::submit(const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, int64_t tag) {
+    int rc = submit_async(f, m, u, tol, tag);
+    if (rc) return rc;
+    std::vector<std::pair<int64_t, int>> failed;
+    if ((rc = finalize_loads(&failed))) return rc;
+    return failed.empty() ? HDI_OK : failed.front().second;
 }
 
 // Enqueues the write of u and the read of the local-iteration counter
@@ -656,6 +726,7 @@ int Engine::finish(EngReq* r, unsigned long long* li) {
 int Engine::step(int64_t* tags, hdi_stats* stats, int cap, int* ndone) {
     *ndone = 0;
     int rc;
+    if (nloading && (rc = finalize_loads(nullptr))) return rc;   // loads left by submit_async
     if (reqs.empty()) return HDI_OK;
     std::vector<EngReq*> A, V;
     for (EngReq* r : reqs) (r->state == 0 ? A : V).push_back(r);
@@ -664,6 +735,7 @@ int Engine::step(int64_t* tags, hdi_stats* stats, int cap, int* ndone) {
     for (EngReq* r : V) nt_v += r->c.nch;
     if ((rc = ensure_norms(2 * (nt_a + nt_v)))) return rc;
     parity ^= 1;
+    const auto tp0 = std::chrono::steady_clock::now();
     // plan (twice if the staging buffer must grow)
     for (int attempt = 0; attempt < 2; ++attempt) {
         plan.clear();
@@ -686,11 +758,20 @@ int Engine::step(int64_t* tags, hdi_stats* stats, int cap, int* ndone) {
         if (cudaMalloc(&tickets, 64) != cudaSuccess) return fail(HDI_ERR_OUT_OF_MEMORY, "engine: tickets");
         cudaMemsetAsync(tickets, 0, 64, stream);
     }
+    const auto tp1 = std::chrono::steady_clock::now();
     cudaMemcpyAsync(dstage, hstage, sused, cudaMemcpyHostToDevice, stream);
     if ((rc = execute())) return rc;
     const int nn = 2 * (nt_a + nt_v);
     cudaMemcpyAsync(hnorm, dnorm[parity], (size_t)nn * 8, cudaMemcpyDeviceToHost, stream);
+    const auto tp2 = std::chrono::steady_clock::now();
     cudaError_t e = cudaStreamSynchronize(stream);
+    if (p.trace >= 0.5) {
+        const auto tp3 = std::chrono::steady_clock::now();
+        auto us = [](auto a, auto b) { return std::chrono::duration<double, std::micro>(b - a).count(); };
+        fprintf(stderr, "[hdi engine] step %d: %zu new, %zu in refinement, %zu launches, %zu table bytes; "
+                        "host plan %.0f us, enqueue %.0f us, wait %.0f us\n",
+                steps, A.size(), V.size(), plan.size(), sused, us(tp0, tp1), us(tp1, tp2), us(tp2, tp3));
+    }
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return fail(HDI_ERR_CUDA, "engine step: %s", cudaGetErrorString(e));
     ++steps;

@@ -595,7 +595,7 @@ int Ctx::check_image(const hdi_image* im, const char* name, int H_, int W_, int 
 }
 
 // Copies a caller image into the internal FP64 layout (device or host source).
-int Ctx::load_image(const hdi_image* im, DF dst, float* lo2, int c0) {
+int Ctx::load_image(const hdi_image* im, DF dst, float* lo2, int c0, bool wait) {
     const int nc = im->channels;
     if (dst.hi == dfv[kF].hi && im->dtype == HDI_F64) f_lo_zero = false;   // callers set it before loading f
     if (c0) {
@@ -622,15 +622,17 @@ int Ctx::load_image(const hdi_image* im, DF dst, float* lo2, int c0) {
         rs = W;
         cs = (long long)H * W;
     }
-    cudaMemsetAsync(flags, 0, 4, stream);
+    // flag word 1 (word 0 is the mask check's): non-finite input
+    cudaMemsetAsync(flags + 1, 0, 4, stream);
     dim3 grd((W + 127) / 128, H, nc);
     if (im->dtype == HDI_F64)
-        k_load_image<double><<<grd, 128, 0, stream>>>((const double*)src, rs, cs, arr(0), dst, lo2, flags);
+        k_load_image<double><<<grd, 128, 0, stream>>>((const double*)src, rs, cs, arr(0), dst, lo2, flags + 1);
     else
-        k_load_image<float><<<grd, 128, 0, stream>>>((const float*)src, rs, cs, arr(0), dst, lo2, flags);
+        k_load_image<float><<<grd, 128, 0, stream>>>((const float*)src, rs, cs, arr(0), dst, lo2, flags + 1);
     ++launches;
+    if (!wait) return cuda_check(cudaGetLastError(), "image upload");   // checked by load_checks
     unsigned bad = 0;
-    cudaMemcpyAsync(&bad, flags, 4, cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(&bad, flags + 1, 4, cudaMemcpyDeviceToHost, stream);
     int rc = sync("image upload");
     if (rc) return rc;
     if (bad) return fail(HDI_ERR_NONFINITE, "non-finite value in input image");
@@ -679,7 +681,7 @@ int Ctx::store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* kn
 
 // Uploads and bit-packs the mask, builds the mask pyramid; returns the number
 // of known pixels in *ones.
-int Ctx::load_mask(const hdi_mask* m, long long* ones, int plane, bool pyramid) {
+int Ctx::load_mask(const hdi_mask* m, long long* ones, int plane, bool pyramid, bool wait) {
     if (!m || !m->data) return fail(HDI_ERR_INVALID_ARG, "mask: null");
     if (m->height != H || m->width != W) return fail(HDI_ERR_INVALID_ARG, "mask: shape does not match the image");
     if (m->row_stride < m->width) return fail(HDI_ERR_INVALID_ARG, "mask: row stride too small");
@@ -704,29 +706,45 @@ int Ctx::load_mask(const hdi_mask* m, long long* ones, int plane, bool pyramid) 
                                         flags);
     ++launches;
     if (pyramid) build_mask_pyramid();
-    unsigned long long cnt = 0;
-    unsigned long long lk[kMaxLevels] = {};
-    unsigned bad = 0;
-    cudaMemcpyAsync(&cnt, counters + kCntOnes, 8, cudaMemcpyDeviceToHost, stream);
-    cudaMemcpyAsync(&bad, flags, 4, cudaMemcpyDeviceToHost, stream);
-    if (pyramid) cudaMemcpyAsync(lk, counters + kCntLevelKnown, kMaxLevels * 8, cudaMemcpyDeviceToHost, stream);
+    if (!wait) return cuda_check(cudaGetLastError(), "mask upload");   // checked by load_checks
+    LoadReadback rb;
+    enqueue_load_readback(&rb);
     int rc = sync("mask upload");
     if (rc) return rc;
-    if (bad) return fail(HDI_ERR_INVALID_ARG, "mask: values must be 0 or 1");
-    *ones = (long long)cnt;
-    mask_ones = (long long)cnt;
-    if (pyramid) {
-        // a level whose pixels are all known (every plane) has the exact
-        // coarse correction 0, and so has every level below it: the solves
-        // stop their hierarchy there (the level itself stays as the trivial
-        // coarsest level)
-        nlev_run = nlev;
-        for (int l = 1; l < nlev && p.mg_truncate >= 0.5; ++l)
-            if (lk[l] == (unsigned long long)nmask * lev[l].H * lev[l].W) {
-                nlev_run = l + 1;
-                break;
-            }
-    }
+    if (rb.flags[0]) return fail(HDI_ERR_INVALID_ARG, "mask: values must be 0 or 1");
+    *ones = (long long)rb.counters[kCntOnes];
+    mask_ones = *ones;
+    if (pyramid) set_levels_run(rb.counters + kCntLevelKnown);
+    return HDI_OK;
+}
+
+// The counters and flags the input checks leave on the device, copied to
+// `rb` (pinned or not) on the context's stream.
+void Ctx::enqueue_load_readback(LoadReadback* rb) {
+    cudaMemcpyAsync(rb->counters, counters, sizeof(rb->counters), cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(rb->flags, flags, sizeof(rb->flags), cudaMemcpyDeviceToHost, stream);
+}
+
+// A level whose pixels are all known (every plane) has the exact coarse
+// correction 0, and so has every level below it: the solves stop their
+// hierarchy there (the level itself stays as the trivial coarsest level).
+void Ctx::set_levels_run(const unsigned long long* known) {
+    nlev_run = nlev;
+    for (int l = 1; l < nlev && p.mg_truncate >= 0.5; ++l)
+        if (known[l] == (unsigned long long)nmask * lev[l].H * lev[l].W) {
+            nlev_run = l + 1;
+            break;
+        }
+}
+
+// The checks of a load_mask + load_image pair enqueued with wait = false,
+// from their readback (after the stream has reached it).
+int Ctx::load_checks(const LoadReadback& rb, long long* ones) {
+    if (rb.flags[0]) return fail(HDI_ERR_INVALID_ARG, "mask: values must be 0 or 1");
+    if (rb.flags[1]) return fail(HDI_ERR_NONFINITE, "non-finite value in input image");
+    *ones = (long long)rb.counters[kCntOnes];
+    mask_ones = *ones;
+    set_levels_run(rb.counters + kCntLevelKnown);
     return HDI_OK;
 }
 
@@ -1051,12 +1069,17 @@ int Ctx::inpaint_batch_engine(int n, const hdi_image* f, const hdi_mask* m, hdi_
     int next = 0, done = 0, worst = HDI_OK, rc;
     const int64_t l0 = e.launches;
     while (done < n) {
+        // every image that fits is loaded without waiting; one wait checks them all
         while (next < n) {
-            rc = e.submit(&f[next], &m[next], &u[next], tol, next);
+            rc = e.submit_async(&f[next], &m[next], &u[next], tol, next);
             if (rc == HDI_ERR_OUT_OF_MEMORY && !e.reqs.empty()) break;   // admitted when others finish
             if (rc) return fail(rc, "batch image %d: %s", next, e.err.c_str());
             ++next;
         }
+        std::vector<std::pair<int64_t, int>> failed;
+        if ((rc = e.finalize_loads(&failed))) return fail(rc, "batch: %s", e.err.c_str());
+        if (!failed.empty())
+            return fail(failed.front().second, "batch image %d: %s", (int)failed.front().first, e.err.c_str());
         int nd = 0;
         if ((rc = e.step(tags.data(), sts.data(), n, &nd))) return fail(rc, "batch: %s", e.err.c_str());
         for (int i = 0; i < nd; ++i) {

@@ -136,6 +136,14 @@ inline cudaError_t launch_k(bool pdl, void (*k)(K...), dim3 grid, dim3 block, cu
     return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
 }
 
+// Device-side results of the input checks (counters[0..32): ones, local
+// iterations, ..., known pixels per level; flags[0] bad mask value,
+// flags[1] non-finite image value), read back in one go.
+struct LoadReadback {
+    unsigned long long counters[32];
+    unsigned flags[2];
+};
+
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -221,10 +229,13 @@ struct Ctx {
                   bool p32 = false);
     int solve(SolveSpec& s);
     int check_image(const hdi_image* im, const char* name, int H, int W, int nch);
-    int load_image(const hdi_image* im, DF dst, float* lo2 = nullptr, int c0 = 0);
+    int load_image(const hdi_image* im, DF dst, float* lo2 = nullptr, int c0 = 0, bool wait = true);
     int store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2 = nullptr, int c0 = 0,
                     bool wait = true);
-    int load_mask(const hdi_mask* m, long long* ones, int plane = 0, bool pyramid = true);
+    int load_mask(const hdi_mask* m, long long* ones, int plane = 0, bool pyramid = true, bool wait = true);
+    void enqueue_load_readback(LoadReadback* rb);
+    void set_levels_run(const unsigned long long* known);
+    int load_checks(const LoadReadback& rb, long long* ones);
     int inpaint_batch(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, hdi_stats* st);
     int inpaint_batch_engine(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, hdi_stats* st);
     int inpaint_batch_classes(int n, const hdi_image* f, const hdi_mask* m, hdi_image* u, double tol, hdi_stats* st);
