@@ -157,6 +157,12 @@ __global__ void __launch_bounds__(32 * kVorSeg) k_vor_columns(MaskView m, int* _
     }
 }
 
+// The launch shape k_vor_columns is written for (32 columns x kVorSeg row
+// segments per block); every caller goes through this.
+inline void launch_vor_columns(const MaskView& m, int* ys, cudaStream_t s) {
+    k_vor_columns<<<(m.W + 31) / 32, dim3(32, kVorSeg), 0, s>>>(m, ys);
+}
+
 // Exact label: minimise (d^2, linear index of the site) over all columns,
 // scanning outward from x until dx^2 exceeds the best d^2.
 __global__ void k_vor_rows(const int* __restrict__ ys, int H, int W, int* __restrict__ V) {
@@ -615,7 +621,7 @@ int Ctx::densify(const hdi_image* f, hdi_mask* mask, const hdi_image* u, int64_t
                 first = full;
             }
         } else {
-            k_vor_columns<<<(W + 31) / 32, dim3(32, kVorSeg), 0, stream>>>(mv, ys);
+            launch_vor_columns(mv, ys, stream);
             k_vor_rows<<<grow, 128, 0, stream>>>(ys, H, W, V);
             launches += 2;
         }

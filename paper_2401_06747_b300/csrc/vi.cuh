@@ -161,7 +161,7 @@ int Ctx::tonal_vi(int& steps, double& mse_best, DF* u_kept) {
         den = (unsigned long long*)vws.take(N * 8);
         num = (unsigned long long*)vws.take((size_t)nch * N * 8);
         const MaskView mv = mview(0);
-        k_vor_columns<<<(W + 127) / 128, 128, 0, stream>>>(mv, ys);
+        launch_vor_columns(mv, ys, stream);
         k_vor_rows<<<dim3((W + 127) / 128, H), 128, 0, stream>>>(ys, H, W, V);
         cudaMemsetAsync(den, 0, N * 8, stream);
         cudaMemsetAsync(num, 0, (size_t)nch * N * 8, stream);
