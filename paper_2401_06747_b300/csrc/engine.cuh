@@ -57,6 +57,7 @@ struct EngLaunch {
     size_t tasks_off, cta0_off;
     size_t base_off, out_off;       // segmented reduction (r) tables
     size_t base2_off, out2_off;     // second reduction (b) of the residual
+    int level;                      // grid level of the tasks (strip launches; 0 for the residual)
     int want_b;
 };
 
@@ -184,7 +185,7 @@ struct Engine {
     // `ctas` are given; norm outputs (if any) in `outs` (one per task).
     template <typename T>
     void record(int kind, const std::vector<T>& tasks, const std::vector<int>& ctas, const std::vector<double*>* outs,
-                const std::vector<double*>* outs2 = nullptr, int want_b = 0) {
+                const std::vector<double*>* outs2 = nullptr, int want_b = 0, int level = 0) {
         if (tasks.empty()) return;
         EngLaunch L{};
         L.kind = kind;
@@ -200,10 +201,16 @@ struct Engine {
             L.out_off = put_vec(*outs);
         }
         if (outs2) {
-            L.base2_off = L.cta0_off;
+            // the second reduction's partials follow the first one's (both
+            // are committed by every CTA of the launch, so they cannot share
+            // slots: the first sum would read partials of the second)
+            std::vector<int> base2(cta0);
+            for (int& v : base2) v += L.ctas;
+            L.base2_off = put_vec(base2);
             L.out2_off = put_vec(*outs2);
         }
         L.want_b = want_b;
+        L.level = level;
         plan.push_back(L);
     }
 
@@ -286,7 +293,7 @@ struct Engine {
                 outs.push_back(c.scal + (kind == EK_RESTRICT ? l + 1 : l) * kMaxCh + ch);
             }
         }
-        record(kind, tasks, ctas, &outs);
+        record(kind, tasks, ctas, &outs, nullptr, 0, l);
     }
 
     // One V-cycle (as Ctx::vcycle with one pre- and one post-sweep) over S at level l.
@@ -419,6 +426,11 @@ struct Engine {
 
     int execute() {
         const bool pd = p.pdl >= 0.5;
+        // dynamic shared memory of the level-0 kernels that stage their row
+        // loads (`bit` of stage_loads, as in Ctx::stage_bytes)
+        auto stg = [&](const EngLaunch& L, int bit, size_t bytes) {
+            return (L.level == 0 && ((int)p.stage_loads & bit)) ? bytes : (size_t)0;
+        };
         for (const EngLaunch& L : plan) {
             const int* cta0 = (const int*)(dstage + L.cta0_off);
             const void* tk = dstage + L.tasks_off;
@@ -432,20 +444,20 @@ struct Engine {
                 k_restrict_data_b<<<grid, dim3(32, 8), 0, stream>>>((const PixTask*)tk, cta0, L.ntasks);
                 break;
             case EK_PROLONG0:
-                e = launch_k(pd, k_prolong_b<0>, grid, dim3(128), stream, (const StripTask*)tk, cta0, L.ntasks,
-                             seg(L, L.base_off, L.out_off, 0));
+                e = launch_ks(pd, stg(L, 4, PStage::bytes), k_prolong_b<0>, grid, dim3(128), stream,
+                              (const StripTask*)tk, cta0, L.ntasks, seg(L, L.base_off, L.out_off, 0));
                 break;
             case EK_PROLONG1:
-                e = launch_k(pd, k_prolong_b<1>, grid, dim3(128), stream, (const StripTask*)tk, cta0, L.ntasks,
-                             seg(L, L.base_off, L.out_off, 0));
+                e = launch_ks(pd, stg(L, 4, PStage::bytes), k_prolong_b<1>, grid, dim3(128), stream,
+                              (const StripTask*)tk, cta0, L.ntasks, seg(L, L.base_off, L.out_off, 0));
                 break;
             case EK_PROLONG2:
-                e = launch_k(pd, k_prolong_b<2>, grid, dim3(128), stream, (const StripTask*)tk, cta0, L.ntasks,
-                             seg(L, L.base_off, L.out_off, 0));
+                e = launch_ks(pd, stg(L, 4, PStage::bytes), k_prolong_b<2>, grid, dim3(128), stream,
+                              (const StripTask*)tk, cta0, L.ntasks, seg(L, L.base_off, L.out_off, 0));
                 break;
             case EK_RESTRICT:
-                e = launch_k(pd, k_restrict_residual_b, grid, dim3(128), stream, (const StripTask*)tk, cta0, L.ntasks,
-                             seg(L, L.base_off, L.out_off, 0));
+                e = launch_ks(pd, stg(L, 2, RStage::bytes), k_restrict_residual_b, grid, dim3(128), stream,
+                              (const StripTask*)tk, cta0, L.ntasks, seg(L, L.base_off, L.out_off, 0));
                 break;
             case EK_ORAS0:
                 e = launch_k(pd, k_oras_wb<true>, grid, dim3(32), stream, (const OrasTask*)tk, cta0, L.ntasks);
@@ -454,14 +466,14 @@ struct Engine {
                 e = launch_k(pd, k_oras_wb<false>, grid, dim3(32), stream, (const OrasTask*)tk, cta0, L.ntasks);
                 break;
             case EK_RES_FROM32:
-                e = launch_k(pd, k_residual_df_b<RHS_DATA, INIT_FROM32>, grid, dim3(128), stream, (const ResTask*)tk,
-                             cta0, L.ntasks, seg(L, L.base_off, L.out_off, 0), seg(L, L.base2_off, L.out2_off, 1),
-                             L.want_b);
+                e = launch_ks(pd, stg(L, 1, ResStage<RHS_DATA, INIT_FROM32, false>::bytes),
+                              k_residual_df_b<RHS_DATA, INIT_FROM32>, grid, dim3(128), stream, (const ResTask*)tk, cta0,
+                              L.ntasks, seg(L, L.base_off, L.out_off, 0), seg(L, L.base2_off, L.out2_off, 1), L.want_b);
                 break;
             case EK_RES_UPDATE:
-                e = launch_k(pd, k_residual_df_b<RHS_DATA, INIT_UPDATE>, grid, dim3(128), stream, (const ResTask*)tk,
-                             cta0, L.ntasks, seg(L, L.base_off, L.out_off, 0), seg(L, L.base2_off, L.out2_off, 1),
-                             L.want_b);
+                e = launch_ks(pd, stg(L, 1, ResStage<RHS_DATA, INIT_UPDATE, false>::bytes),
+                              k_residual_df_b<RHS_DATA, INIT_UPDATE>, grid, dim3(128), stream, (const ResTask*)tk, cta0,
+                              L.ntasks, seg(L, L.base_off, L.out_off, 0), seg(L, L.base2_off, L.out2_off, 1), L.want_b);
                 break;
             }
             ++launches;
@@ -751,9 +763,9 @@ int Engine::step(int64_t* tags, hdi_stats* stats, int cap, int* ndone) {
         if (sused <= scap) break;
         if ((rc = ensure_staging(sused))) return rc;
     }
-    int maxctas = 0;
-    for (const EngLaunch& L : plan) maxctas = std::max(maxctas, L.ctas);
-    if ((rc = ensure_partials(maxctas))) return rc;
+    int maxparts = 0;   // one partial per CTA and reduction
+    for (const EngLaunch& L : plan) maxparts = std::max(maxparts, (L.want_b ? 2 : 1) * L.ctas);
+    if ((rc = ensure_partials(maxparts))) return rc;
     if (!tickets) {
         if (cudaMalloc(&tickets, 64) != cudaSuccess) return fail(HDI_ERR_OUT_OF_MEMORY, "engine: tickets");
         cudaMemsetAsync(tickets, 0, 64, stream);

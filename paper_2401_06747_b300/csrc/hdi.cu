@@ -68,6 +68,7 @@ const ParamDef kParams[] = {
     {"tonal_fine_pre", &Params::tonal_fine_pre, 0, 4},
     {"tonal_fine_post", &Params::tonal_fine_post, 0, 4},
     {"oras_warp", &Params::oras_warp, 0, 1},
+    {"stage_loads", &Params::stage_loads, 0, 7},
     {"densify_partition", &Params::densify_partition, 0, 1},
     {"inpaint_fp32", &Params::inpaint_fp32, 0, 1},
     {"batch_engine", &Params::batch_engine, 0, 1},
@@ -378,7 +379,8 @@ void Ctx::vcycle(int l) {
         dim3 blk(128), grd = quad_grid(L.H, L.W, nch, qr);
         // read x, b and the mask bits, write a quarter value of b_H per value
         if (l == 0) tstart(kT_Restrict, 9.125 * (double)nch * L.H * L.W);
-        launch_k(p.pdl >= 0.5, k_restrict_residual, grd, blk, stream, arr(l), mview(l), (const float*)L.xa,
+        launch_ks(p.pdl >= 0.5, l == 0 ? stage_bytes(2, RStage::bytes) : 0, k_restrict_residual, grd, blk, stream,
+                  arr(l), mview(l), (const float*)L.xa,
                  (const float*)L.b, arr(l + 1), mview(l + 1), C.b, reducer(l + 1, grd.x * grd.y), qr);
         ++launches;
         if (l == 0) tstop();
@@ -392,7 +394,8 @@ void Ctx::vcycle(int l) {
         dim3 grd = quad_grid(L.H, L.W, nch, qr), blk(128);
         // read x, b, a quarter value of e_H and the mask bits, write x
         if (l == 0) tstart(kT_Prolong, 13.125 * (double)nch * L.H * L.W);
-        launch_k(p.pdl >= 0.5, k_prolong<0>, grd, blk, stream, arr(l), mview(l), (const float*)L.xa,
+        launch_ks(p.pdl >= 0.5, l == 0 ? stage_bytes(4, PStage::bytes) : 0, k_prolong<0>, grd, blk, stream, arr(l),
+                  mview(l), (const float*)L.xa,
                  (const float*)L.b, L.xb, arr(l + 1), (const float*)C.xa, reducer(l, grd.x * grd.y), qr);
         ++launches;
         if (l == 0) tstop();
@@ -485,7 +488,8 @@ static void launch_res(Ctx& c, DFc uin, DF uout, const float* x32, DFc d, DFc y,
                        (HAS_E ? 4.0 : 0.0) +
                        (RHS == RHS_SOURCE ? (a.d_lo_zero ? 4.0 : 8.0) + (y.hi ? 8.0 : 0.0) : 0.0);
     c.tstart(kT_Residual, bpv * (double)c.nch * c.H * c.W);
-    launch_k(c.p.pdl >= 0.5, k_residual_df<RHS, INIT, P32>, grd, blk, c.stream, a);
+    const size_t stg = c.stage_bytes(1, ResStage<RHS, INIT, P32>::bytes);
+    launch_ks(c.p.pdl >= 0.5, stg, k_residual_df<RHS, INIT, P32>, grd, blk, c.stream, a);
     ++c.launches;
     c.tstop();
 }

@@ -50,6 +50,8 @@ struct Params {
     double mg_truncate = 1;         // end the hierarchy at its first fully known level (exact)
     double strip_rows = 0;          // rows per warp of the quad-strip kernels (even, >= 2); 0: chosen by size
     double oras_warp = 1;           // ORAS sweep layout: 1 one warp per subdomain, 0 two warps
+    double stage_loads = 3;         // level-0 kernels that stage their next rows (cp.async), bit mask:
+                                    // 1 refinement residual, 2 restriction, 4 prolongation
 };
 
 struct Level {
@@ -121,12 +123,14 @@ enum { kF = 0, kU0, kU1, kG, kY0, kY1, kW0, kW1, kP, kNumDF };
 
 // Launch with programmatic stream serialisation (see pdl_wait in
 // common.cuh) when `pdl` is set, else a plain launch.
+// launch_ks: the same with `smem` bytes of dynamic shared memory.
 template <typename... K, typename... A>
-inline cudaError_t launch_k(bool pdl, void (*k)(K...), dim3 grid, dim3 block, cudaStream_t s, A&&... args) {
+inline cudaError_t launch_ks(bool pdl, size_t smem, void (*k)(K...), dim3 grid, dim3 block, cudaStream_t s,
+                             A&&... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -134,6 +138,10 @@ inline cudaError_t launch_k(bool pdl, void (*k)(K...), dim3 grid, dim3 block, cu
     cfg.attrs = at;
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+template <typename... K, typename... A>
+inline cudaError_t launch_k(bool pdl, void (*k)(K...), dim3 grid, dim3 block, cudaStream_t s, A&&... args) {
+    return launch_ks(pdl, 0, k, grid, block, s, std::forward<A>(args)...);
 }
 
 // Device-side results of the input checks (counters[0..32): ones, local
@@ -216,6 +224,9 @@ struct Ctx {
     int setup_lean(int H, int W, int nch, cudaStream_t s);   // one request of the batched engine (engine.cuh)
     GridReduce reducer(int slot, int nparts) const;
     // rows per warp of the quad-strip kernels: the strip_rows parameter, else by size
+    // dynamic shared memory of a level-0 kernel that stages its row loads
+    // (`bit` of stage_loads; 0 bytes: the unstaged loop)
+    size_t stage_bytes(int bit, size_t b) const { return ((int)p.stage_loads & bit) ? b : 0; }
     int qrows(int H_, int W_, int n) const { return p.strip_rows >= 2 ? ((int)p.strip_rows / 2) * 2 : quad_rows(H_, W_, n); }
     LevelArr arr(int l) const;
     MaskView mview(int l) const;

@@ -184,8 +184,11 @@ __device__ __forceinline__ StripHalo strip_halo(int lane, int px, int pxc, int W
 // take part in the shuffles with clamped loads. Rows are walked in chunks of
 // QS_CHUNK, every load of a chunk issued before its arithmetic. The kernels
 // keep one chunk buffer and run at 64-72 registers (7-8 CTAs per SM): more
-// resident warps hide the load latency better than a second buffer with the
-// next chunk's loads in flight (measured faster on the 4K RGB workload).
+// resident warps hide the load latency better than a second register buffer
+// with the next chunk's loads in flight (measured faster on the 4K RGB
+// workload). On level 0 the next chunk can instead be staged in shared
+// memory (cp.async, no registers; stage_loads), which the residual and the
+// restriction gain from.
 #define QS_COLS 128
 #define QS_CHUNK 2
 
@@ -269,6 +272,48 @@ __device__ __forceinline__ void quad_residual_interior(int lane, const float (&c
     }
 }
 
+// Read access to one field of a chunk staged in shared memory, with the
+// interface of the register chunk's arrays: element k sits k * 128 words
+// further (the [field][thread] layout of 128-thread CTAs); a field that was
+// not staged reads as zero.
+struct StagedF4 {
+    const float4* p;
+    bool on;
+    __device__ __forceinline__ float4 operator[](int k) const {
+        return on ? p[k * 128] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+};
+struct StagedU32 {
+    const uint32_t* p;
+    bool on;
+    __device__ __forceinline__ uint32_t operator[](int k) const { return on ? p[k * 128] : 0u; }
+};
+struct StagedF2 {
+    const float2* p;
+    bool on;
+    __device__ __forceinline__ float2 operator[](int k) const { return on ? p[k * 128] : make_float2(0.f, 0.f); }
+};
+struct StagedF32 {
+    const uint32_t* p;
+    bool on;
+    __device__ __forceinline__ float operator[](int k) const { return on ? __uint_as_float(p[k * 128]) : 0.f; }
+};
+// Staging layout of the restriction (dynamic shared memory, [slot][field]
+// [thread] as the residual kernel's): float4 fields x of rows yb+1, yb+2 and
+// b of rows yb, yb+1; word fields the halo's x of rows yb, yb+1, the mask
+// words of rows yb, yb+1 and the coarse mask word of row yb/2. Two slots
+// (one chunk in flight ahead) keep 7 CTAs per SM.
+struct RStage {
+    static constexpr int NV = 2 * QS_CHUNK, NW = 2 * QS_CHUNK + 1, NSLOT = 2;
+    static constexpr size_t bytes = (size_t)NSLOT * 128 * (NV * 16 + NW * 4);
+};
+struct StagedRestrict {
+    StagedF4 Xd, Bv;
+    StagedF32 Hv;
+    StagedU32 Mw;
+    uint32_t Cw;
+};
+
 // r = b - A x on level F with 2x2 sums into the coarse right-hand side
 // (restriction, Sec. 3.2), zero on coarse known pixels, and ||r_c||^2 per
 // channel. Quad strips: the lane's four columns feed two coarse columns.
@@ -294,6 +339,13 @@ __device__ __forceinline__ float restrict_residual_body(LevelArr F, MaskView fm,
     const float* xc = x + ch * F.cs;
     const float* bc = b + ch * F.cs;
     float sq = 0.f;
+    extern __shared__ float4 qs_dyn[];
+    const bool staged = dyn_smem_bytes() >= RStage::bytes;
+    auto sv = [&](int sl, int f) { return qs_dyn + ((size_t)(sl * RStage::NV + f) * 128 + threadIdx.x); };
+    auto sw = [&](int sl, int f) {
+        return reinterpret_cast<uint32_t*>(qs_dyn + (size_t)RStage::NSLOT * RStage::NV * 128) +
+               ((size_t)(sl * RStage::NW + f) * 128 + threadIdx.x);
+    };
     auto body = [&](auto in_tag) {
         constexpr bool IN = decltype(in_tag)::value;
         const uint32_t* mrow = fm.bits + q.mword;
@@ -320,7 +372,8 @@ __device__ __forceinline__ float restrict_residual_body(LevelArr F, MaskView fm,
             }
             c.Cw = cmw[(size_t)(IN ? (yb >> 1) : min(yb >> 1, C.H - 1)) * cm.wpitch];   // one coarse row
         };
-        auto compute = [&](const Chunk& c, int yb) {
+        // c: a Chunk in registers, or a StagedRestrict view of the staging slots
+        auto compute = [&](const auto& c, int yb) {
 #pragma unroll
             for (int k = 0; k < CR; ++k) {
                 const int y = yb + k;
@@ -359,10 +412,45 @@ __device__ __forceinline__ float restrict_residual_body(LevelArr F, MaskView fm,
                 }
             }
         };
-        for (int yb = y0; yb < y1; yb += CR) {
-            Chunk A;
-            load(A, yb);
-            compute(A, yb);
+        if (staged) {
+            // copies of chunk yb into slot sl, from the addresses load() reads
+            auto stage = [&](int sl, int yb) {
+#pragma unroll
+                for (int k = 0; k < CR; ++k) {
+                    const size_t ry = (size_t)rowc(yb + k) * F.pitch;
+                    cpa16(sv(sl, k), xc + (size_t)rowc(yb + k + 1) * F.pitch + q.cq);
+                    cpa16(sv(sl, CR + k), bc + ry + q.cq);
+                    if (q.hon) cpa4(sw(sl, k), xc + ry + q.hcol);
+                    cpa4(sw(sl, CR + k), mrow + (size_t)rowc(yb + k) * fm.wpitch);
+                }
+                cpa4(sw(sl, 2 * CR), cmw + (size_t)(IN ? (yb >> 1) : min(yb >> 1, C.H - 1)) * cm.wpitch);
+            };
+            auto view = [&](int sl) {
+                StagedRestrict c;
+                c.Xd = {sv(sl, 0), true};
+                c.Bv = {sv(sl, CR), true};
+                c.Hv = {sw(sl, 0), q.hon};
+                c.Mw = {sw(sl, CR), true};
+                c.Cw = *sw(sl, 2 * CR);
+                return c;
+            };
+            // two slots in rotation: the next chunk in flight while one is computed
+            stage(0, y0);
+            cpa_commit();
+            int sl = 0;
+            for (int yb = y0; yb < y1; yb += CR) {
+                if (yb + CR < y1) stage(sl ^ 1, yb + CR);
+                cpa_commit();
+                cpa_wait<1>();   // chunk yb has landed
+                compute(view(sl), yb);
+                sl ^= 1;
+            }
+        } else {
+            for (int yb = y0; yb < y1; yb += CR) {
+                Chunk A;
+                load(A, yb);
+                compute(A, yb);
+            }
         }
     };
     if (interior) body(std::true_type{});
@@ -489,6 +577,27 @@ __global__ void __launch_bounds__(128, 8) k_level_residual_norm(LevelArr F, Mask
 // are also the halo columns' cells, so lanes 0 and 31 interpolate the halo
 // column without further coarse loads. Each coarse row is interpolated once
 // and reused by the fine rows above and below it.
+// Staging layout of the prolongation (dynamic shared memory, [slot][field]
+// [thread]): float4 fields x of rows yb+1, yb+2 and b of rows yb .. yb+2;
+// float2 field the coarse cells (X0, X0+1) of row yb/2 + 1; word fields the
+// mask words of rows yb .. yb+2, then per row the halo's mask word, x and
+// b, and the edge lanes' outer coarse cell. Two slots take 32 KB per CTA,
+// which leaves 6 CTAs per SM: on the 4K RGB workload the staged form was
+// slower than the unstaged one (4.36 against 4.10 ms per step), so the
+// default stage_loads leaves this kernel unstaged.
+struct PStage {
+    static constexpr int NV = 2 * QS_CHUNK + 1, NE = QS_CHUNK / 2, NW = (QS_CHUNK + 1) + 3 * QS_CHUNK + QS_CHUNK / 2;
+    static constexpr int NSLOT = 2;
+    static constexpr size_t bytes = (size_t)NSLOT * 128 * (NV * 16 + NE * 8 + NW * 4);
+};
+struct StagedProlong {
+    StagedF4 Xd, Bd;
+    StagedU32 Mw, Hm;
+    StagedF32 Hx, Hb;
+    StagedF2 Ev;
+    StagedF32 Ee;
+};
+
 template <int MODE>
 __device__ __forceinline__ float prolong_body(LevelArr F, MaskView fm, const float* __restrict__ xin,
                                               const float* __restrict__ b, float* __restrict__ xout, LevelArr C,
@@ -507,6 +616,8 @@ __device__ __forceinline__ float prolong_body(LevelArr F, MaskView fm, const flo
     const float* ec = (MODE == 2) ? nullptr : e + ch * C.cs;
     float* xo = xout + ch * F.cs;
     float sq = 0.f;
+    extern __shared__ float4 qs_dyn[];
+    const bool staged = dyn_smem_bytes() >= PStage::bytes;
     if (y0 < F.H) {
         const uint32_t* mrow = fm.bits + q.mword;
         const uint32_t* hrow = fm.bits + (q.hcol >> 5);
@@ -606,7 +717,8 @@ __device__ __forceinline__ float prolong_body(LevelArr F, MaskView fm, const flo
                 c.Hm[k] = q.hon ? hrow[(size_t)y * fm.wpitch] : 0u;
             }
         };
-        auto compute = [&](const Chunk& c, int yb) {
+        // c: a Chunk in registers, or a StagedProlong view of the staging slots
+        auto compute = [&](const auto& c, int yb) {
 #pragma unroll
             for (int j = 0; j < NS - 2; ++j) hinterp(c.Ev[j], c.Ee[j], S[2 + j], SH[2 + j]);
 #pragma unroll
@@ -653,10 +765,77 @@ __device__ __forceinline__ float prolong_body(LevelArr F, MaskView fm, const flo
                 SH[j] = SH[NS - 2 + j];
             }
         };
-        for (int yb = y0; yb < y1; yb += CR) {
-            Chunk A;
-            load(A, yb);
-            compute(A, yb);
+        if (staged) {
+            static_assert(NS - 2 == PStage::NE, "one coarse row per chunk");
+            constexpr int NV = PStage::NV, NE = PStage::NE, NW = PStage::NW, NSL = PStage::NSLOT;
+            const int t = threadIdx.x;
+            float2* const e_base = reinterpret_cast<float2*>(qs_dyn + (size_t)NSL * NV * 128);
+            uint32_t* const w_base = reinterpret_cast<uint32_t*>(e_base + (size_t)NSL * NE * 128);
+            auto sv = [&](int sl, int f) { return qs_dyn + ((size_t)(sl * NV + f) * 128 + t); };
+            auto se = [&](int sl, int f) { return e_base + ((size_t)(sl * NE + f) * 128 + t); };
+            auto sw = [&](int sl, int f) { return w_base + ((size_t)(sl * NW + f) * 128 + t); };
+            const bool edge = lane == 0 || lane == 31;
+            // word fields: Mw [0, CR], then Hm, Hx, Hb (CR each), then Ee
+            constexpr int wHm = CR + 1, wHx = wHm + CR, wHb = wHx + CR, wEe = wHb + CR;
+            static_assert(wEe + NE == NW, "word fields");
+            // copies of chunk yb into slot sl, from the addresses load() reads
+            auto stage = [&](int sl, int yb) {
+                const int cb = (yb >> 1) - 1;
+                if (MODE != 2) {
+#pragma unroll
+                    for (int j = 0; j < NS - 2; ++j) {
+                        const float* row = ec + (size_t)min(max(cb + 2 + j, 0), C.H - 1) * C.pitch;
+                        cpa8(se(sl, j), row + Xq);
+                        if (edge) cpa4(sw(sl, wEe + j), row + Xe);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k <= CR; ++k) {
+                    const int y = min(yb + k, F.H - 1);
+                    cpa16(sv(sl, CR + k), bc + (size_t)y * F.pitch + q.cq);
+                    cpa4(sw(sl, k), mrow + (size_t)y * fm.wpitch);
+                }
+#pragma unroll
+                for (int k = 0; k < CR; ++k) {
+                    const int y = min(yb + k, F.H - 1);
+                    const size_t ry = (size_t)y * F.pitch;
+                    if (MODE == 0) cpa16(sv(sl, k), xc + (size_t)min(yb + k + 1, F.H - 1) * F.pitch + q.cq);
+                    if (MODE == 0 && q.hon) cpa4(sw(sl, wHx + k), xc + ry + q.hcol);
+                    if (q.hon) {
+                        cpa4(sw(sl, wHb + k), bc + ry + q.hcol);
+                        cpa4(sw(sl, wHm + k), hrow + (size_t)y * fm.wpitch);
+                    }
+                }
+            };
+            auto view = [&](int sl) {
+                StagedProlong c;
+                c.Xd = {sv(sl, 0), MODE == 0};
+                c.Bd = {sv(sl, CR), true};
+                c.Mw = {sw(sl, 0), true};
+                c.Hm = {sw(sl, wHm), q.hon};
+                c.Hx = {sw(sl, wHx), MODE == 0 && q.hon};
+                c.Hb = {sw(sl, wHb), q.hon};
+                c.Ev = {se(sl, 0), MODE != 2};
+                c.Ee = {sw(sl, wEe), MODE != 2 && edge};
+                return c;
+            };
+            // two slots in rotation: the next chunk in flight while one is computed
+            stage(0, y0);
+            cpa_commit();
+            int sl = 0;
+            for (int yb = y0; yb < y1; yb += CR) {
+                if (yb + CR < y1) stage(sl ^ 1, yb + CR);
+                cpa_commit();
+                cpa_wait<1>();   // chunk yb has landed
+                compute(view(sl), yb);
+                sl ^= 1;
+            }
+        } else {
+            for (int yb = y0; yb < y1; yb += CR) {
+                Chunk A;
+                load(A, yb);
+                compute(A, yb);
+            }
         }
     }
     return sq;
@@ -741,6 +920,13 @@ enum { RHS_DATA = 0, RHS_SOURCE = 1 };
 // (neighbouring tiles read uin as their halo).
 enum { INIT_KEEP = 0, INIT_UPDATE = 1, INIT_FROM32 = 2, INIT_ZERO = 3 };
 
+// The residual kernel's chunk fields as views of its staging slots.
+struct StagedRows {
+    StagedF4 Uh, Ul, E, Dh, Dl, Yh, Yl, KDh, KDl;
+    StagedU32 Mw, Hm;
+    StagedF32 HUh, HUl, HE, HDh, HDl;
+};
+
 struct ResArgs {
     LevelArr F;           // level-0 geometry
     MaskView m;
@@ -757,14 +943,43 @@ struct ResArgs {
     int d_lo_zero;        // d.lo is all zero (FP32 data): its loads are skipped
 };
 
+// Staging layout of the refinement-residual kernel (dynamic shared memory,
+// [slot][field][thread] for 128-thread CTAs: consecutive threads read
+// consecutive 16-byte or 4-byte words, conflict-free). float4 fields per
+// row: u.hi, u.lo, e, then d.hi, d.lo, y.hi, y.lo for RHS_SOURCE; word
+// fields: the mask words of rows yb .. yb+RC, then per row the halo's mask
+// word, u.hi, u.lo and e. The variants that read d only where a mask word
+// says known (LOAD_D) are not staged: those loads depend on a word of the
+// same chunk.
+template <int RHS, int INIT, bool P32>
+struct ResStage {
+    static constexpr int RC = RES_CHUNK;
+    static constexpr bool HAS_U = (INIT == INIT_KEEP || INIT == INIT_UPDATE);
+    static constexpr bool HAS_E = (INIT == INIT_UPDATE || INIT == INIT_FROM32);
+    static constexpr bool LOAD_D = (RHS == RHS_DATA) && (INIT != INIT_UPDATE);
+    static constexpr bool STAGED = !LOAD_D;
+    static constexpr int iUl = HAS_U ? 1 : 0;
+    static constexpr int iE = iUl + ((HAS_U && !P32) ? 1 : 0);
+    static constexpr int iD = iE + (HAS_E ? 1 : 0);
+    static constexpr int NV = iD + (RHS == RHS_SOURCE ? 4 : 0);
+    static constexpr int NSC = (RC + 1) + 4 * RC;
+    // two chunks in flight ahead where 7 CTAs per SM still fit, else one
+    static constexpr int NSLOT = (NV * RC <= 4) ? 3 : 2;
+    static constexpr size_t bytes = STAGED ? (size_t)NSLOT * 128 * (NV * RC * 16 + NSC * 4) : 0;
+};
+
 // Quad strips like the FP32 kernels (lane = four columns, float4 loads of
 // the hi and lo words). Known pixels take their Dirichlet value (d for
 // RHS_DATA, 0 for RHS_SOURCE). With INIT_UPDATE the input iterate already
 // holds it there (every refinement step writes it, and the V-cycle
 // correction is zero on known pixels), so d is read only by the other INIT
 // modes, once the row's mask word has arrived.
-// Seven CTAs per SM (at most 72 registers): the latency of the row loads is
-// hidden by more resident warps rather than by a second register buffer.
+// Seven CTAs per SM (at most 72 registers). Launched with
+// ResStage::bytes of dynamic shared memory, the loads of the next one or two
+// chunks are in flight while a chunk is computed: each lane copies them
+// (cp.async) into its own shared-memory slots and reads a chunk there once
+// its copy group has landed -- the same addresses and the same arithmetic,
+// so the results are bit-identical to the unstaged loop.
 //
 // P32 (plain FP32 form, RHS_DATA only): the iterate is a single FP32 word
 // (the low words are neither read nor written), the update u + e and the
@@ -789,6 +1004,16 @@ __device__ __forceinline__ float2 residual_df_body(const ResArgs& a, int bx, int
     const int lane = q.lane;
     const long long co = ch * a.F.cs;
     float rr = 0.f, bb2 = 0.f;
+    using SL = ResStage<RHS, INIT, P32>;
+    constexpr int iUl = SL::iUl, iE = SL::iE, iD = SL::iD, NV = SL::NV, NSC = SL::NSC, NSLOT = SL::NSLOT;
+    extern __shared__ float4 qs_dyn[];
+    const bool staged = SL::STAGED && dyn_smem_bytes() >= SL::bytes;
+    // slot sl, field f of this thread
+    auto sv = [&](int sl, int f) { return qs_dyn + ((size_t)(sl * NV * RC + f) * 128 + threadIdx.x); };
+    auto sw = [&](int sl, int f) {
+        return reinterpret_cast<uint32_t*>(qs_dyn + (size_t)NSLOT * NV * RC * 128) +
+               ((size_t)(sl * NSC + f) * 128 + threadIdx.x);
+    };
     auto body = [&](auto in_tag) {
         constexpr bool IN = decltype(in_tag)::value;   // no border tests, no clamped rows
         const uint32_t* mrow = m.bits + q.mword;
@@ -879,7 +1104,8 @@ __device__ __forceinline__ float2 residual_df_body(const ResArgs& a, int bx, int
                 }
             }
         };
-        auto compute = [&](const Chunk& c, int yb) {
+        // c: a Chunk in registers, or a StagedRows view of the staging slots
+        auto compute = [&](const auto& c, int yb) {
 #pragma unroll
             for (int k = 0; k < RC; ++k) {
                 const int y = yb + k;
@@ -1000,10 +1226,76 @@ __device__ __forceinline__ float2 residual_df_body(const ResArgs& a, int bx, int
                 }
             }
         };
-        for (int yb = y0; yb < y1; yb += RC) {
-            Chunk A;
-            load(A, yb);
-            compute(A, yb);
+        if (staged) {
+            // copies of chunk yb into slot sl, from the addresses load() reads
+            auto stage = [&](int sl, int yb) {
+#pragma unroll
+                for (int k = 0; k <= RC; ++k) cpa4(sw(sl, k), mrow + (size_t)rowc(yb + k) * m.wpitch);
+#pragma unroll
+                for (int k = 0; k < RC; ++k) {
+                    const size_t id = at(yb + k + 1, q.cq), ih = at(yb + k, q.hcol), ic = at(yb + k, q.cq);
+                    if (HAS_U) cpa16(sv(sl, k), a.uin.hi + id);
+                    if (HAS_U && !P32) cpa16(sv(sl, iUl * RC + k), a.uin.lo + id);
+                    if (HAS_E) cpa16(sv(sl, iE * RC + k), a.x32 + id);
+                    if (RHS == RHS_SOURCE) {
+                        cpa16(sv(sl, iD * RC + k), a.d.hi + ic);
+                        if (!a.d_lo_zero) cpa16(sv(sl, (iD + 1) * RC + k), a.d.lo + ic);
+                        if (a.y.hi) {
+                            cpa16(sv(sl, (iD + 2) * RC + k), a.y.hi + ic);
+                            cpa16(sv(sl, (iD + 3) * RC + k), a.y.lo + ic);
+                        }
+                    }
+                    if (q.hon) {
+                        cpa4(sw(sl, RC + 1 + k), hrow + (size_t)rowc(yb + k) * m.wpitch);
+                        if (HAS_U) cpa4(sw(sl, RC + 1 + RC + k), a.uin.hi + ih);
+                        if (HAS_U && !P32) cpa4(sw(sl, RC + 1 + 2 * RC + k), a.uin.lo + ih);
+                        if (HAS_E) cpa4(sw(sl, RC + 1 + 3 * RC + k), a.x32 + ih);
+                    }
+                }
+            };
+            // the chunk as load() would have filled it, read where compute uses it
+            auto view = [&](int sl) {
+                StagedRows c;
+                const float4* v = sv(sl, 0);
+                const uint32_t* w = sw(sl, 0);
+                c.Mw = {w, true};
+                c.Uh = {v, HAS_U};
+                c.Ul = {v + iUl * RC * 128, HAS_U && !P32};
+                c.E = {v + iE * RC * 128, HAS_E};
+                c.Dh = {v + iD * RC * 128, RHS == RHS_SOURCE};
+                c.Dl = {v + (iD + 1) * RC * 128, RHS == RHS_SOURCE && !a.d_lo_zero};
+                c.Yh = {v + (iD + 2) * RC * 128, RHS == RHS_SOURCE && a.y.hi != nullptr};
+                c.Yl = {v + (iD + 3) * RC * 128, RHS == RHS_SOURCE && a.y.hi != nullptr};
+                c.KDh = c.KDl = {v, false};
+                c.Hm = {w + (RC + 1) * 128, q.hon};
+                c.HUh = {w + (2 * RC + 1) * 128, HAS_U && q.hon};
+                c.HUl = {w + (3 * RC + 1) * 128, HAS_U && q.hon && !P32};
+                c.HE = {w + (4 * RC + 1) * 128, HAS_E && q.hon};
+                c.HDh = c.HDl = {w, false};
+                return c;
+            };
+            // slots in rotation; NSLOT - 1 chunks in flight ahead of the one computed
+#pragma unroll
+            for (int j = 0; j < NSLOT - 1; ++j) {
+                if (y0 + j * RC < y1) stage(j, y0 + j * RC);
+                cpa_commit();
+            }
+            int sl = 0;
+            for (int yb = y0; yb < y1; yb += RC) {
+                const int ya = yb + (NSLOT - 1) * RC;
+                // slot of chunk ya: the one chunk yb - RC used (computed in the previous pass)
+                if (ya < y1) stage(sl == 0 ? NSLOT - 1 : sl - 1, ya);
+                cpa_commit();
+                cpa_wait<NSLOT - 1>();   // chunk yb has landed
+                compute(view(sl), yb);
+                sl = (sl + 1 == NSLOT) ? 0 : sl + 1;
+            }
+        } else {
+            for (int yb = y0; yb < y1; yb += RC) {
+                Chunk A;
+                load(A, yb);
+                compute(A, yb);
+            }
         }
     };
     if (interior) body(std::true_type{});

@@ -157,3 +157,30 @@ def test_engine_errors():
     assert ei.value.code == -1
     assert e.status()["bytes_in_use"] == 0
     assert e.step() == []
+
+
+def test_engine_results_reproducible_bit_for_bit():
+    """Engines fed the same requests return the same bits: every norm comes
+    from a deterministic segmented reduction whose partials no other
+    reduction of the launch overwrites (the first refinement residual sums
+    ||r||^2 and ||b||^2 in one launch)."""
+    need_gpu()
+    import paper_2401_06747_b300 as hdi
+    data = [make(i, *s) for i, s in enumerate(SHAPES)] + [make(30, 260, 390, 3, 0.04)]
+    ref = None
+    for _ in range(5):
+        e = hdi.Engine(0, budget_gb=4.0)
+        outs = []
+        for i, (f, c) in enumerate(data):
+            o = torch.empty_like(dev(f))
+            assert e.submit(dev(f), dev(c), o, tol=1e-7, tag=i)
+            outs.append(o)
+        n = 0
+        while n < len(data):
+            n += len(e.step())
+        got = [o.cpu().numpy() for o in outs]
+        e.close()
+        if ref is None:
+            ref = got
+        for a, b in zip(ref, got):
+            np.testing.assert_array_equal(a, b)
