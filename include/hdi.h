@@ -340,8 +340,9 @@ const char* hdi_version(void);
  *                             bit for bit; 0 keeps every level down to 32 x 32
  *   strip_rows        [0]     rows per warp of the quad-strip kernels (restriction, prolongation,
  *                             residuals; even, >= 2); 0 chooses by level size
- *   oras_warp         [1]     ORAS sweep layout: 1 one warp per 32x32 subdomain (no CTA barriers),
- *                             0 two warps per subdomain
+ *   oras_warp         [1]     layout of the 32x32 local CG solves (ORAS sweeps and the tonal echoes
+ *                             on 32x32 RAS blocks): 1 one warp per solve (no CTA barriers), 0 two
+ *                             warps per solve
  *   stage_loads       [3]     level-0 kernels that copy their next rows into shared memory (cp.async)
  *                             while they compute the current ones, a bit mask: 1 refinement
  *                             residual, 2 restriction, 4 prolongation; a clear bit loads each row

@@ -105,9 +105,54 @@ struct EchoArgs {
     unsigned long long* iters;
 };
 
-// One CTA (two warps) per (subdomain, mask pixel k): solve the Neumann
-// subdomain problem L_UU x = L_UK e_k by CG; x = S e_k is stored row-major
-// over the 32x32 tile.
+// Right-hand side L_UK e_k of an echo solve at the lane's pixels: -1 at the
+// unknown 4-neighbours of the mask pixel (kx, ky) inside the subdomain. The
+// lane holds the column pair (c0, c0 + 1) over rows r0 .. r0 + NR - 1; um
+// has bit 2k + j set where pixel (r0 + k, c0 + j) is unknown and inside.
+template <int NR>
+__device__ __forceinline__ void echo_rhs(int kx, int ky, int c0, int r0, uint32_t um, float2 (&R)[NR]) {
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int y = r0 + k;
+        const bool nx = (c0 == kx && (y == ky - 1 || y == ky + 1)) || (y == ky && (c0 == kx - 1 || c0 == kx + 1));
+        const bool ny =
+            (c0 + 1 == kx && (y == ky - 1 || y == ky + 1)) || (y == ky && (c0 + 1 == kx - 1 || c0 + 1 == kx + 1));
+        R[k].x = (nx && ((um >> (2 * k)) & 1u)) ? -1.f : 0.f;
+        R[k].y = (ny && ((um >> (2 * k + 1)) & 1u)) ? -1.f : 0.f;
+    }
+}
+
+// One warp per (subdomain, mask pixel k), in the layout of the one-warp ORAS
+// sweep (oras_warp.cuh: lane = column pair x 16 rows, dot products by warp
+// butterflies, no barriers): solve the Neumann subdomain problem
+// L_UU x = L_UK e_k by CG (theta = 0 at every subdomain side) to
+// ||r|| <= rtol ||L_UK e_k||; x = S e_k is stored row-major over the 32x32
+// tile (zero on known and outside pixels). FULL: every subdomain is 32x32
+// (images of at least 32 x 32 pixels).
+template <bool FULL>
+__global__ void __launch_bounds__(32, 12) k_tonal_echo_w(EchoArgs a) {
+    __shared__ WarpShared sh;
+    const long long e = blockIdx.x;
+    if (e >= a.off[a.nb]) return;   // the whole warp (the CTA) leaves together
+    const int i = a.owner[e];
+    const int by = i / a.nbx, bx = i - by * a.nbx;
+    const int x0 = sub_origin(bx, a.m.W, a.stride), y0 = sub_origin(by, a.m.H, a.stride);
+    const WarpGeom g = make_wgeom(x0, y0, a.m.H, a.m.W, a.m, 0.f, sh);
+    const int code = a.list[e];
+    const int c0 = 2 * g.c, r0 = g.r0;
+    float2 R[kWarpRows], V[kWarpRows];
+    echo_rhs(code & 31, code >> 5, c0, r0, g.um, R);
+    const float rr0 = warp_sum_f(wdot(R, R));
+    __syncwarp();   // the mask floats of make_wgeom are read by the same lanes only
+    const int it = warp_cg<FULL>(g, sh, V, R, a.rtol2 * rr0, a.maxit);
+    if (a.iters && (threadIdx.x & 31) == 0 && it) atomicAdd(a.iters, (unsigned long long)it);
+    float* out = a.echo + (size_t)e * 1024;
+#pragma unroll
+    for (int k = 0; k < kWarpRows; ++k) *reinterpret_cast<float2*>(out + (r0 + k) * 32 + c0) = V[k];
+}
+
+// One CTA (two warps) per (subdomain, mask pixel k): the same echo solve in
+// the two-warp layout of k_oras (oras_warp = 0).
 __global__ void __launch_bounds__(kLocalThreads, 8) k_tonal_echo(EchoArgs a) {
     __shared__ LocalShared sh;
     const long long e = blockIdx.x;
@@ -123,16 +168,9 @@ __global__ void __launch_bounds__(kLocalThreads, 8) k_tonal_echo(EchoArgs a) {
     // right-hand side L_UK e_k: -1 at the unknown 4-neighbours of k inside the subdomain
     float2 R[8], V[8];
     float2 a0 = make_float2(0.f, 0.f);
+    echo_rhs(kx, ky, c0, r0, g.um, R);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int y = r0 + k;
-        const bool nx = (c0 == kx && (y == ky - 1 || y == ky + 1)) || (y == ky && (c0 == kx - 1 || c0 == kx + 1));
-        const bool ny =
-            (c0 + 1 == kx && (y == ky - 1 || y == ky + 1)) || (y == ky && (c0 + 1 == kx - 1 || c0 + 1 == kx + 1));
-        R[k].x = (nx && ((g.um >> (2 * k)) & 1u)) ? -1.f : 0.f;
-        R[k].y = (ny && ((g.um >> (2 * k + 1)) & 1u)) ? -1.f : 0.f;
-        a0 = __ffma2_rn(R[k], R[k], a0);
-    }
+    for (int k = 0; k < 8; ++k) a0 = __ffma2_rn(R[k], R[k], a0);
     const float rr0 = cta_sum2(a0.x + a0.y, sh, 3);   // slot 4 is reused right away by the CG set-up
     const int it = (g.w == 32 && g.h == 32) ? local_cg<true>(g, sh, V, R, a.rtol2 * rr0, a.maxit)
                                             : local_cg<false>(g, sh, V, R, a.rtol2 * rr0, a.maxit);
@@ -764,6 +802,10 @@ int Ctx::tonal_setup_blk(int blk) {
         ea.iters = counters + kCntEcho;
         tstart(kT_Echo);
         if (blk == 64) k_tonal_echo64<<<(unsigned)total, kL64Threads, 0, stream>>>(ea);
+        else if (p.oras_warp >= 0.5 && W >= 32 && H >= 32)
+            k_tonal_echo_w<true><<<(unsigned)total, 32, 0, stream>>>(ea);
+        else if (p.oras_warp >= 0.5)
+            k_tonal_echo_w<false><<<(unsigned)total, 32, 0, stream>>>(ea);
         else k_tonal_echo<<<(unsigned)total, kLocalThreads, 0, stream>>>(ea);
         ++launches;
         tstop();

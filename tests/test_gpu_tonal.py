@@ -155,3 +155,19 @@ def test_plain_alg2_64x64_reaches_the_optimum_at_the_oracle_rate(d, seed):
     need = int(np.argmax(hist[:, 0] <= tol))
     assert hist[need, 0] <= tol
     assert abs(st["iterations"] - need) <= 2, (st["iterations"], need)
+
+
+@pytest.mark.parametrize("oras_warp", [0, 1])
+@pytest.mark.parametrize("H,W,d,seed", [(150, 210, 0.04, 21), (31, 70, 0.05, 22)])
+def test_echo_layouts_reach_the_optimum(oras_warp, H, W, d, seed):
+    """The local echoes S e_k of Sec. 5.2 (Neumann subdomain solves on 32x32
+    RAS blocks, 3% density and above) in both kernel layouts -- one warp per
+    echo (oras_warp = 1) and two warps (0) -- including images lower than
+    one block: RAS reaches the oracle optimum with either, FP64 to 1e-10."""
+    f = synth_image(H, W, seed)
+    c = random_mask(H, W, d, seed + 100)
+    g, st = run(f, c, 1e-10, oras_warp=oras_warp, tonal_block=32)
+    assert st["rel_res"] <= 1e-10
+    assert normal_residual(f, c, g)[0] <= 2e-10
+    assert np.abs(g - tonal_ref(f, c)).max() <= 1e-5
+    assert np.all(g[c == 0] == 0)
