@@ -343,6 +343,11 @@ const char* hdi_version(void);
  *   oras_warp         [1]     layout of the 32x32 local CG solves (ORAS sweeps and the tonal echoes
  *                             on 32x32 RAS blocks): 1 one warp per solve (no CTA barriers), 0 two
  *                             warps per solve
+ *   oras_warp_waves   [2]     with oras_warp = 1, an ORAS sweep takes the one-warp layout only if
+ *                             its (subdomain, channel) solves fill the GPU at least this many times
+ *                             (12 one-warp CTAs per SM); smaller sweeps (coarse levels, small
+ *                             images) split each solve over two warps, which finishes sooner when
+ *                             there are too few solves to hide the latency of a single warp
  *   stage_loads       [3]     level-0 kernels that copy their next rows into shared memory (cp.async)
  *                             while they compute the current ones, a bit mask: 1 refinement
  *                             residual, 2 restriction, 4 prolongation; a clear bit loads each row

@@ -68,6 +68,7 @@ const ParamDef kParams[] = {
     {"tonal_fine_pre", &Params::tonal_fine_pre, 0, 4},
     {"tonal_fine_post", &Params::tonal_fine_post, 0, 4},
     {"oras_warp", &Params::oras_warp, 0, 1},
+    {"oras_warp_waves", &Params::oras_warp_waves, 0, 1e6},
     {"stage_loads", &Params::stage_loads, 0, 7},
     {"densify_partition", &Params::densify_partition, 0, 1},
     {"inpaint_fp32", &Params::inpaint_fp32, 0, 1},
@@ -328,7 +329,11 @@ void Ctx::oras(int l, bool zero, const float* xin, float* xout, const double* rn
     if (l == 0) tstart(kT_Oras, (zero ? 8.125 : 12.125) * (double)nch * L.H * L.W);
     const bool full = L.W >= 32 && L.H >= 32;
     const bool pd = p.pdl >= 0.5;
-    if (p.oras_warp >= 0.5) {   // one warp per subdomain (oras_warp.cuh)
+    // one warp per subdomain (oras_warp.cuh) where the sweep fills the GPU
+    // several times over; a sweep of fewer subdomains finishes sooner with
+    // each solve split over two warps (shorter critical path per subdomain)
+    const double waves = (double)L.nbx * L.nby * nch / (12.0 * sm_count(device));
+    if (p.oras_warp >= 0.5 && waves >= p.oras_warp_waves) {
         if (zero) {
             if (full) launch_k(pd, k_oras_w<true, true>, blocks, dim3(32), stream, a);
             else launch_k(pd, k_oras_w<true, false>, blocks, dim3(32), stream, a);

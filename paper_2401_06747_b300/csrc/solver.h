@@ -1,6 +1,7 @@
 // solver.h -- host-side context of libhdi: parameters, workspace arenas,
 // multigrid hierarchy and the solver drivers' declarations.
 #pragma once
+#include <atomic>
 #include <cstdarg>
 #include <utility>
 #include <string>
@@ -50,6 +51,8 @@ struct Params {
     double mg_truncate = 1;         // end the hierarchy at its first fully known level (exact)
     double strip_rows = 0;          // rows per warp of the quad-strip kernels (even, >= 2); 0: chosen by size
     double oras_warp = 1;           // ORAS sweep layout: 1 one warp per subdomain, 0 two warps
+    double oras_warp_waves = 2;     // one-warp layout only for sweeps of at least this many waves of
+                                    // its CTAs (12 per SM); smaller sweeps (coarse levels) take two
     double stage_loads = 3;         // level-0 kernels that stage their next rows (cp.async), bit mask:
                                     // 1 refinement residual, 2 restriction, 4 prolongation
 };
@@ -120,6 +123,21 @@ constexpr int kMaxTimed = 2048;   // timed launches buffered between flushes
 enum { kT_Oras = 0, kT_Residual, kT_Prolong, kT_Restrict, kT_Echo, kT_Gram, kT_Local, kT_Anderson, kT_Coarse };
 // double-float vectors of level-0 size
 enum { kF = 0, kU0, kU1, kG, kY0, kY1, kW0, kW1, kP, kNumDF };
+
+// Streaming multiprocessors of `device`, queried once per device (148 on a
+// B300 if the query fails).
+inline int sm_count(int device) {
+    static std::atomic<int> cache[64];
+    if (device < 0 || device >= 64) return 148;
+    int n = cache[device].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) {
+        (void)cudaGetLastError();
+        n = 148;
+    }
+    cache[device].store(n, std::memory_order_relaxed);
+    return n;
+}
 
 // Launch with programmatic stream serialisation (see pdl_wait in
 // common.cuh) when `pdl` is set, else a plain launch.

@@ -46,6 +46,23 @@ def test_ragged_rgb_fp32(H, W, d, seed):
     assert np.abs(u - ref).max() <= 1e-3
 
 
+@pytest.mark.parametrize("layout", [dict(oras_warp=1, oras_warp_waves=0), dict(oras_warp=0), {}])
+@pytest.mark.parametrize("H,W,d,seed", [(77, 131, 0.04, 11), (300, 200, 0.1, 12), (33, 33, 0.02, 13),
+                                        (1, 40, 0.1, 14), (520, 97, 0.01, 15)])
+def test_oras_layouts(layout, H, W, d, seed):
+    """The ORAS sweep (Sec. 3.1) in each kernel layout: one warp per
+    subdomain on every level (oras_warp_waves = 0), two warps on every level
+    (oras_warp = 0), and the default choice by sweep size; each reaches the
+    oracle's solution."""
+    f = synth_rgb(H, W, seeds=(seed, seed + 10, seed + 20), dtype=np.float32)
+    c = random_mask(H, W, d, seed + 100)
+    u, st = run(f, c, 1e-6, **layout)
+    ref = inpaint_ref(f.astype(np.float64), c)
+    assert st["rel_res"] <= 1e-6
+    assert rel_residual(u.astype(np.float64), f.astype(np.float64), c).max() <= 1.5e-6
+    assert np.abs(u - ref).max() <= 1e-3
+
+
 def test_full_mask_and_single_pixel():
     f = synth_image(40, 50, 9)
     u, _ = run(f, np.ones((40, 50), np.uint8), 1e-8)
