@@ -8,7 +8,9 @@ GPU and problem class by timing: each candidate set runs the real solve
 converges wins. Two stages: first the tiling and layout choices (the ORAS
 subdomain layout -- one warp or two per 32x32 subdomain --, the rows per warp
 of the streaming strip kernels, and for tonal optimisation the RAS block
-side, 32 or 64), then the scalar parameters with the best tiling. Results are
+side, 32 or 64, the sweep size below which the ORAS sweep keeps two warps per
+subdomain, and which level-0 kernels stage their rows in shared memory), then
+the scalar parameters with the best tiling. Results are
 kept in a JSON cache keyed by GPU name, size class, channel count,
 mask-density bucket and solve kind, and applied by creating a Context with
 them.
@@ -37,10 +39,14 @@ TONAL_GRID = {
 # tiling and layout (stage 1); strip_rows 0 = chosen by level size
 INPAINT_SHAPES = {
     "oras_warp": (0, 1),
+    "oras_warp_waves": (0, 2, 8),
+    "stage_loads": (0, 3),
     "strip_rows": (0, 8, 16),
 }
 TONAL_SHAPES = {
     "oras_warp": (0, 1),
+    "oras_warp_waves": (2, 8),
+    "stage_loads": (0, 3),
     "strip_rows": (0, 16),
     "tonal_block": (32, 64),
 }

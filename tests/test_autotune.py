@@ -18,9 +18,9 @@ def test_keys_and_candidates():
     c = autotune.candidates({"b": (1, 2), "a": (3,)})
     assert c == [{"a": 3, "b": 1}, {"a": 3, "b": 2}]
     assert len(autotune.candidates(autotune.INPAINT_GRID)) == 12
-    # tiling stage: subdomain layout, strip rows, RAS block side
-    assert len(autotune.candidates(autotune.INPAINT_SHAPES)) == 6
-    assert len(autotune.candidates(autotune.TONAL_SHAPES)) == 8
+    # tiling stage: subdomain layout and its size threshold, row staging, strip rows, RAS block side
+    assert len(autotune.candidates(autotune.INPAINT_SHAPES)) == 36
+    assert len(autotune.candidates(autotune.TONAL_SHAPES)) == 32
     assert {c["tonal_block"] for c in autotune.candidates(autotune.TONAL_SHAPES)} == {32, 64}
 
 
