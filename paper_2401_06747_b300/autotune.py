@@ -35,6 +35,7 @@ TONAL_GRID = {
     "tonal_oras_eta": (1e-2, 3e-2),
     "tonal_inner_ratio": (0.05, 0.1, 0.2),
     "tonal_fine_pre": (1, 2),
+    "tonal_echo_rtol": (3e-3, 1e-2),
 }
 # tiling and layout (stage 1); strip_rows 0 = chosen by level size
 INPAINT_SHAPES = {
