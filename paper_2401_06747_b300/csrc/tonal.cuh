@@ -328,44 +328,53 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
         }
     }
     __syncthreads();
-    // right-looking Cholesky on the lower triangle; thread r updates row r
-    const int r = tid;
-    for (int j = 0; j < m; ++j) {
-        if (r == j) {
-            const float d = sqrtf(G[j * gs + j]);
-            if (!(d > 0.f)) atomicOr(bad, 1u);
-            G[j * gs + j] = d;
+    // G = Lu D Lu^T (Lu unit lower triangular) by right-looking elimination:
+    // step j subtracts u_rj u_cj / d_j from the trailing entries j < c <= r
+    // (u: the column below the pivot d_j = G[j][j], kept unscaled). The
+    // trailing triangle is spread over a 16 x 16 grid of threads, so a step
+    // costs O((m - j)^2 / 256) per thread and one barrier; a step reads only
+    // column j and writes only columns after it.
+    const int tr = tid >> 4, tc = tid & 15;
+    for (int j = 0; j + 1 < m; ++j) {
+        const float pinv = 1.f / G[j * gs + j];
+        for (int r = j + 1 + tr; r < m; r += 16) {
+            const float ur = G[r * gs + j] * pinv;
+            for (int c = j + 1 + tc; c <= r; c += 16) G[r * gs + c] = fmaf(-ur, G[c * gs + j], G[r * gs + c]);
         }
         __syncthreads();
-        float lrj = 0.f;
-        if (r > j && r < m) {
-            lrj = G[r * gs + j] / G[j * gs + j];
-            G[r * gs + j] = lrj;
-        }
-        __syncthreads();
-        if (r > j && r < m)
-            for (int c = j + 1; c <= r; ++c) G[r * gs + c] = fmaf(-lrj, G[c * gs + j], G[r * gs + c]);
     }
-    __syncthreads();
-    // W = L^{-1}; thread j owns column j of W, stored as row j of W^T:
-    // Wt[j][k] = W[k][j] at G[j * gs + k] for k > j, the diagonal in dinv.
+    // Lu below the diagonal (u / d), 1 / d in dinv, the upper triangle
+    // cleared for V^T. Every pivot of the SPD G is positive.
     float* dinv = Es + gram_stage_floats(m4);
-    if (r < m) {
-        const float dj = 1.f / G[r * gs + r];
-        dinv[r] = dj;
-        for (int ii = r + 1; ii < m; ++ii) {
-            float s0 = G[ii * gs + r] * dj, s1 = 0.f;   // k = r term, then k = r+1 .. ii-1
-            int k = r + 1;
-            for (; k + 1 < ii; k += 2) {
-                s0 = fmaf(G[ii * gs + k], G[r * gs + k], s0);
-                s1 = fmaf(G[ii * gs + k + 1], G[r * gs + k + 1], s1);
-            }
-            if (k < ii) s0 = fmaf(G[ii * gs + k], G[r * gs + k], s0);
-            G[r * gs + ii] = -(s0 + s1) / G[ii * gs + ii];
+    for (int r = tr; r < m; r += 16) {
+        const float dr = G[r * gs + r];
+        for (int c = tc; c < m; c += 16) {
+            if (c < r) G[r * gs + c] = G[r * gs + c] / G[c * gs + c];
+            else if (c > r) G[r * gs + c] = 0.f;
+        }
+        if (tc == 0) {
+            if (!(dr > 0.f)) atomicOr(bad, 1u);
+            dinv[r] = 1.f / dr;
         }
     }
     __syncthreads();
-    // G^{-1}[a][b] = sum_{k >= max(a, b)} W[k][a] W[k][b], entries a >= b
+    // V = Lu^{-1} (unit lower triangular) by forward elimination on I:
+    // step k subtracts Lu[q][k] row_k(V) from the rows q > k (row k of V is
+    // final after step k - 1; its diagonal is 1). V[q][j], q > j, is kept
+    // transposed in the upper triangle, at G[j][q]; a step reads column k
+    // of both triangles and writes columns q > k of the upper one.
+    for (int k = 0; k + 1 < m; ++k) {
+        for (int q = k + 1 + tr; q < m; q += 16) {   // row q of V (i is the subdomain)
+            const float l = G[q * gs + k];
+            for (int j = tc; j <= k; j += 16) {
+                const float vkj = (j == k) ? 1.f : G[j * gs + k];
+                G[j * gs + q] = fmaf(-l, vkj, G[j * gs + q]);
+            }
+        }
+        __syncthreads();
+    }
+    // G^{-1} = V^T D^{-1} V: [a][b] = sum_{k >= max(a, b)} V[k][a] V[k][b] / d_k,
+    // entries a >= b (V[k][a] = G[a][k] for k > a, V[a][a] = 1)
     float* Gi = fac + goff[i];
     const int ne = m * (m + 1) / 2;
     for (int e = tid; e < ne; e += 256) {
@@ -373,9 +382,9 @@ __global__ void __launch_bounds__(256) k_tonal_gram(const int* __restrict__ off,
         while (ra * (ra + 1) / 2 > e) --ra;
         while ((ra + 1) * (ra + 2) / 2 <= e) ++ra;
         const int cb = e - ra * (ra + 1) / 2;
-        // k = ra term: W[ra][ra] W[ra][cb] (W[ra][cb] = Wt[cb][ra], or dinv when cb == ra)
-        float acc = dinv[ra] * ((cb == ra) ? dinv[ra] : G[cb * gs + ra]);
-        for (int k = ra + 1; k < m; ++k) acc = fmaf(G[ra * gs + k], G[cb * gs + k], acc);
+        // k = ra term: V[ra][ra] V[ra][cb] / d_ra (V[ra][cb] = G[cb][ra], or 1 when cb == ra)
+        float acc = dinv[ra] * ((cb == ra) ? 1.f : G[cb * gs + ra]);
+        for (int k = ra + 1; k < m; ++k) acc = fmaf(G[ra * gs + k] * dinv[k], G[cb * gs + k], acc);
         Gi[(size_t)ra * m + cb] = acc;
         Gi[(size_t)cb * m + ra] = acc;
     }
