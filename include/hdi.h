@@ -350,8 +350,8 @@ const char* hdi_version(void);
  *                             there are too few solves to hide the latency of a single warp
  *   stage_loads       [3]     level-0 kernels that copy their next rows into shared memory (cp.async)
  *                             while they compute the current ones, a bit mask: 1 refinement
- *                             residual, 2 restriction, 4 prolongation; a clear bit loads each row
- *                             into registers when it is needed. Bit-identical results either way
+ *                             residual, 2 restriction; a clear bit loads each row into registers
+ *                             when it is needed. Bit-identical results either way
  *   tonal_anderson    [8]     Anderson window on the RAS iteration (0 = plain Alg. 2)
  *   tonal_oras_eta    [3e-2]  oras_eta used inside the tonal inner solves
  *   fine_pre, fine_post [1, 1] ORAS sweeps before / after the coarse correction on the finest level

@@ -444,16 +444,16 @@ struct Engine {
                 k_restrict_data_b<<<grid, dim3(32, 8), 0, stream>>>((const PixTask*)tk, cta0, L.ntasks);
                 break;
             case EK_PROLONG0:
-                e = launch_ks(pd, stg(L, 4, PStage::bytes), k_prolong_b<0>, grid, dim3(128), stream,
-                              (const StripTask*)tk, cta0, L.ntasks, seg(L, L.base_off, L.out_off, 0));
+                e = launch_k(pd, k_prolong_b<0>, grid, dim3(128), stream, (const StripTask*)tk, cta0, L.ntasks,
+                             seg(L, L.base_off, L.out_off, 0));
                 break;
             case EK_PROLONG1:
-                e = launch_ks(pd, stg(L, 4, PStage::bytes), k_prolong_b<1>, grid, dim3(128), stream,
-                              (const StripTask*)tk, cta0, L.ntasks, seg(L, L.base_off, L.out_off, 0));
+                e = launch_k(pd, k_prolong_b<1>, grid, dim3(128), stream, (const StripTask*)tk, cta0, L.ntasks,
+                             seg(L, L.base_off, L.out_off, 0));
                 break;
             case EK_PROLONG2:
-                e = launch_ks(pd, stg(L, 4, PStage::bytes), k_prolong_b<2>, grid, dim3(128), stream,
-                              (const StripTask*)tk, cta0, L.ntasks, seg(L, L.base_off, L.out_off, 0));
+                e = launch_k(pd, k_prolong_b<2>, grid, dim3(128), stream, (const StripTask*)tk, cta0, L.ntasks,
+                             seg(L, L.base_off, L.out_off, 0));
                 break;
             case EK_RESTRICT:
                 e = launch_ks(pd, stg(L, 2, RStage::bytes), k_restrict_residual_b, grid, dim3(128), stream,

@@ -69,7 +69,7 @@ const ParamDef kParams[] = {
     {"tonal_fine_post", &Params::tonal_fine_post, 0, 4},
     {"oras_warp", &Params::oras_warp, 0, 1},
     {"oras_warp_waves", &Params::oras_warp_waves, 0, 1e6},
-    {"stage_loads", &Params::stage_loads, 0, 7},
+    {"stage_loads", &Params::stage_loads, 0, 3},
     {"densify_partition", &Params::densify_partition, 0, 1},
     {"inpaint_fp32", &Params::inpaint_fp32, 0, 1},
     {"batch_engine", &Params::batch_engine, 0, 1},
@@ -399,8 +399,7 @@ void Ctx::vcycle(int l) {
         dim3 grd = quad_grid(L.H, L.W, nch, qr), blk(128);
         // read x, b, a quarter value of e_H and the mask bits, write x
         if (l == 0) tstart(kT_Prolong, 13.125 * (double)nch * L.H * L.W);
-        launch_ks(p.pdl >= 0.5, l == 0 ? stage_bytes(4, PStage::bytes) : 0, k_prolong<0>, grd, blk, stream, arr(l),
-                  mview(l), (const float*)L.xa,
+        launch_k(p.pdl >= 0.5, k_prolong<0>, grd, blk, stream, arr(l), mview(l), (const float*)L.xa,
                  (const float*)L.b, L.xb, arr(l + 1), (const float*)C.xa, reducer(l, grd.x * grd.y), qr);
         ++launches;
         if (l == 0) tstop();

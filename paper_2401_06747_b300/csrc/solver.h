@@ -54,7 +54,7 @@ struct Params {
     double oras_warp_waves = 2;     // one-warp layout only for sweeps of at least this many waves of
                                     // its CTAs (12 per SM); smaller sweeps (coarse levels) take two
     double stage_loads = 3;         // level-0 kernels that stage their next rows (cp.async), bit mask:
-                                    // 1 refinement residual, 2 restriction, 4 prolongation
+                                    // 1 refinement residual, 2 restriction
 };
 
 struct Level {

@@ -288,11 +288,6 @@ struct StagedU32 {
     bool on;
     __device__ __forceinline__ uint32_t operator[](int k) const { return on ? p[k * 128] : 0u; }
 };
-struct StagedF2 {
-    const float2* p;
-    bool on;
-    __device__ __forceinline__ float2 operator[](int k) const { return on ? p[k * 128] : make_float2(0.f, 0.f); }
-};
 struct StagedF32 {
     const uint32_t* p;
     bool on;
@@ -577,27 +572,6 @@ __global__ void __launch_bounds__(128, 8) k_level_residual_norm(LevelArr F, Mask
 // are also the halo columns' cells, so lanes 0 and 31 interpolate the halo
 // column without further coarse loads. Each coarse row is interpolated once
 // and reused by the fine rows above and below it.
-// Staging layout of the prolongation (dynamic shared memory, [slot][field]
-// [thread]): float4 fields x of rows yb+1, yb+2 and b of rows yb .. yb+2;
-// float2 field the coarse cells (X0, X0+1) of row yb/2 + 1; word fields the
-// mask words of rows yb .. yb+2, then per row the halo's mask word, x and
-// b, and the edge lanes' outer coarse cell. Two slots take 32 KB per CTA,
-// which leaves 6 CTAs per SM: on the 4K RGB workload the staged form was
-// slower than the unstaged one (4.36 against 4.10 ms per step), so the
-// default stage_loads leaves this kernel unstaged.
-struct PStage {
-    static constexpr int NV = 2 * QS_CHUNK + 1, NE = QS_CHUNK / 2, NW = (QS_CHUNK + 1) + 3 * QS_CHUNK + QS_CHUNK / 2;
-    static constexpr int NSLOT = 2;
-    static constexpr size_t bytes = (size_t)NSLOT * 128 * (NV * 16 + NE * 8 + NW * 4);
-};
-struct StagedProlong {
-    StagedF4 Xd, Bd;
-    StagedU32 Mw, Hm;
-    StagedF32 Hx, Hb;
-    StagedF2 Ev;
-    StagedF32 Ee;
-};
-
 template <int MODE>
 __device__ __forceinline__ float prolong_body(LevelArr F, MaskView fm, const float* __restrict__ xin,
                                               const float* __restrict__ b, float* __restrict__ xout, LevelArr C,
@@ -616,8 +590,6 @@ __device__ __forceinline__ float prolong_body(LevelArr F, MaskView fm, const flo
     const float* ec = (MODE == 2) ? nullptr : e + ch * C.cs;
     float* xo = xout + ch * F.cs;
     float sq = 0.f;
-    extern __shared__ float4 qs_dyn[];
-    const bool staged = dyn_smem_bytes() >= PStage::bytes;
     if (y0 < F.H) {
         const uint32_t* mrow = fm.bits + q.mword;
         const uint32_t* hrow = fm.bits + (q.hcol >> 5);
@@ -717,8 +689,7 @@ __device__ __forceinline__ float prolong_body(LevelArr F, MaskView fm, const flo
                 c.Hm[k] = q.hon ? hrow[(size_t)y * fm.wpitch] : 0u;
             }
         };
-        // c: a Chunk in registers, or a StagedProlong view of the staging slots
-        auto compute = [&](const auto& c, int yb) {
+        auto compute = [&](const Chunk& c, int yb) {
 #pragma unroll
             for (int j = 0; j < NS - 2; ++j) hinterp(c.Ev[j], c.Ee[j], S[2 + j], SH[2 + j]);
 #pragma unroll
@@ -765,77 +736,10 @@ __device__ __forceinline__ float prolong_body(LevelArr F, MaskView fm, const flo
                 SH[j] = SH[NS - 2 + j];
             }
         };
-        if (staged) {
-            static_assert(NS - 2 == PStage::NE, "one coarse row per chunk");
-            constexpr int NV = PStage::NV, NE = PStage::NE, NW = PStage::NW, NSL = PStage::NSLOT;
-            const int t = threadIdx.x;
-            float2* const e_base = reinterpret_cast<float2*>(qs_dyn + (size_t)NSL * NV * 128);
-            uint32_t* const w_base = reinterpret_cast<uint32_t*>(e_base + (size_t)NSL * NE * 128);
-            auto sv = [&](int sl, int f) { return qs_dyn + ((size_t)(sl * NV + f) * 128 + t); };
-            auto se = [&](int sl, int f) { return e_base + ((size_t)(sl * NE + f) * 128 + t); };
-            auto sw = [&](int sl, int f) { return w_base + ((size_t)(sl * NW + f) * 128 + t); };
-            const bool edge = lane == 0 || lane == 31;
-            // word fields: Mw [0, CR], then Hm, Hx, Hb (CR each), then Ee
-            constexpr int wHm = CR + 1, wHx = wHm + CR, wHb = wHx + CR, wEe = wHb + CR;
-            static_assert(wEe + NE == NW, "word fields");
-            // copies of chunk yb into slot sl, from the addresses load() reads
-            auto stage = [&](int sl, int yb) {
-                const int cb = (yb >> 1) - 1;
-                if (MODE != 2) {
-#pragma unroll
-                    for (int j = 0; j < NS - 2; ++j) {
-                        const float* row = ec + (size_t)min(max(cb + 2 + j, 0), C.H - 1) * C.pitch;
-                        cpa8(se(sl, j), row + Xq);
-                        if (edge) cpa4(sw(sl, wEe + j), row + Xe);
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k <= CR; ++k) {
-                    const int y = min(yb + k, F.H - 1);
-                    cpa16(sv(sl, CR + k), bc + (size_t)y * F.pitch + q.cq);
-                    cpa4(sw(sl, k), mrow + (size_t)y * fm.wpitch);
-                }
-#pragma unroll
-                for (int k = 0; k < CR; ++k) {
-                    const int y = min(yb + k, F.H - 1);
-                    const size_t ry = (size_t)y * F.pitch;
-                    if (MODE == 0) cpa16(sv(sl, k), xc + (size_t)min(yb + k + 1, F.H - 1) * F.pitch + q.cq);
-                    if (MODE == 0 && q.hon) cpa4(sw(sl, wHx + k), xc + ry + q.hcol);
-                    if (q.hon) {
-                        cpa4(sw(sl, wHb + k), bc + ry + q.hcol);
-                        cpa4(sw(sl, wHm + k), hrow + (size_t)y * fm.wpitch);
-                    }
-                }
-            };
-            auto view = [&](int sl) {
-                StagedProlong c;
-                c.Xd = {sv(sl, 0), MODE == 0};
-                c.Bd = {sv(sl, CR), true};
-                c.Mw = {sw(sl, 0), true};
-                c.Hm = {sw(sl, wHm), q.hon};
-                c.Hx = {sw(sl, wHx), MODE == 0 && q.hon};
-                c.Hb = {sw(sl, wHb), q.hon};
-                c.Ev = {se(sl, 0), MODE != 2};
-                c.Ee = {sw(sl, wEe), MODE != 2 && edge};
-                return c;
-            };
-            // two slots in rotation: the next chunk in flight while one is computed
-            stage(0, y0);
-            cpa_commit();
-            int sl = 0;
-            for (int yb = y0; yb < y1; yb += CR) {
-                if (yb + CR < y1) stage(sl ^ 1, yb + CR);
-                cpa_commit();
-                cpa_wait<1>();   // chunk yb has landed
-                compute(view(sl), yb);
-                sl ^= 1;
-            }
-        } else {
-            for (int yb = y0; yb < y1; yb += CR) {
-                Chunk A;
-                load(A, yb);
-                compute(A, yb);
-            }
+        for (int yb = y0; yb < y1; yb += CR) {
+            Chunk A;
+            load(A, yb);
+            compute(A, yb);
         }
     }
     return sq;

@@ -1,9 +1,9 @@
-"""Staged row loads (stage_loads bits: the level-0 refinement residual,
-restriction and prolongation copy their next rows into shared memory with
-cp.async while they compute the current ones) read the same addresses and
-do the same arithmetic as the unstaged loops, so every result is
-bit-identical: inpainting, tonal optimisation (both residual forms of
-Sec. 5.1) and the batched engine."""
+"""Staged row loads (stage_loads bits: the level-0 refinement residual and
+restriction copy their next rows into shared memory with cp.async while
+they compute the current ones) read the same addresses and do the same
+arithmetic as the unstaged loops, so every result is bit-identical:
+inpainting, tonal optimisation (both residual forms of Sec. 5.1) and the
+batched engine."""
 
 import numpy as np
 import pytest
@@ -28,7 +28,7 @@ def test_inpaint_staged_equals_unstaged(H, W, ch, d):
     f, c = data(H, W, ch, d, 31)
     fd, cd = dev(f), dev(c)
     outs, stats = [], []
-    for st in (0, 7):
+    for st in (0, 3):
         o = torch.empty_like(fd)
         stats.append(ctx(stage_loads=st).inpaint(fd, cd, o, tol=1e-7))
         outs.append(o.cpu().numpy())
@@ -43,7 +43,7 @@ def test_tonal_staged_equals_unstaged(method):
     f, c = data(180, 250, 3, 0.04, 41)
     fd, cd = dev(f), dev(c)
     outs, stats = [], []
-    for st in (0, 7):
+    for st in (0, 3):
         o = torch.empty_like(fd)
         stats.append(ctx(stage_loads=st, tonal_method=method).tonal_opt(fd, cd, o, tol=1e-6))
         outs.append(o.cpu().numpy())
@@ -56,7 +56,7 @@ def test_engine_staged_equals_unstaged():
     import paper_2401_06747_b300 as hdi
     items = [data(*s, 51 + i) for i, s in enumerate(SIZES)]
     res = []
-    for st in (0, 7):
+    for st in (0, 3):
         e = hdi.Engine(0, budget_gb=4.0, stage_loads=st)
         outs = []
         for i, (f, c) in enumerate(items):
