@@ -59,11 +59,6 @@ __device__ __forceinline__ void cpa4(void* dst, const void* src) {
                  "l"(src)
                  : "memory");
 }
-__device__ __forceinline__ void cpa8(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
 // Dynamic shared memory given to this launch, in bytes: a kernel stages its
 // loads only when the launch provided the slots its layout needs.
 __device__ __forceinline__ unsigned dyn_smem_bytes() {
