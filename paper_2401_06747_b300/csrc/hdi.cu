@@ -603,7 +603,36 @@ int Ctx::check_image(const hdi_image* im, const char* name, int H_, int W_, int 
 }
 
 // Copies a caller image into the internal FP64 layout (device or host source).
-int Ctx::load_image(const hdi_image* im, DF dst, float* lo2, int c0, bool wait) {
+// A host image's copy into `stage` on the side stream, ordered after the
+// context stream's earlier use of `stage`; load_image(..., prestaged = true)
+// then converts it on the context stream once the copy has landed. Kernels
+// the context stream runs in between overlap the copy.
+int Ctx::upload_begin(const hdi_image* im) {
+    if (im->location != HDI_HOST) return HDI_OK;
+    if (!ustream) {
+        if (cudaStreamCreateWithFlags(&ustream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&uev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&uev[1], cudaEventDisableTiming) != cudaSuccess)
+            return cuda_check(cudaGetLastError(), "upload stream");
+    }
+    const size_t es = im->dtype == HDI_F64 ? 8 : 4;
+    const size_t n = (size_t)nch * H * W * es;
+    int rc = stage.reserve(*this, std::max(stage.cap, n + (size_t)H * W + 1024), "staging buffer");
+    if (rc) return rc;
+    cudaEventRecord(uev[0], stream);
+    cudaStreamWaitEvent(ustream, uev[0], 0);
+    char* st = (char*)stage.base;
+    for (int c = 0; c < im->channels; ++c) {
+        cudaError_t e = cudaMemcpy2DAsync(st + (size_t)c * H * W * es, W * es,
+                                          (const char*)im->data + (size_t)c * im->channel_stride * es,
+                                          im->row_stride * es, W * es, H, cudaMemcpyHostToDevice, ustream);
+        if (e != cudaSuccess) return cuda_check(e, "host-to-device copy");
+    }
+    cudaEventRecord(uev[1], ustream);
+    return cuda_check(cudaGetLastError(), "image upload");
+}
+
+int Ctx::load_image(const hdi_image* im, DF dst, float* lo2, int c0, bool wait, bool prestaged) {
     const int nc = im->channels;
     if (dst.hi == dfv[kF].hi && im->dtype == HDI_F64) f_lo_zero = false;   // callers set it before loading f
     if (c0) {
@@ -617,14 +646,22 @@ int Ctx::load_image(const hdi_image* im, DF dst, float* lo2, int c0, bool wait) 
     const size_t es = im->dtype == HDI_F64 ? 8 : 4;
     if (im->location == HDI_HOST) {
         const size_t n = (size_t)nch * H * W * es;
-        int rc = stage.reserve(*this, std::max(stage.cap, n + (size_t)H * W + 1024), "staging buffer");
-        if (rc) return rc;
-        char* st = (char*)stage.base;
-        for (int c = 0; c < nc; ++c) {
-            cudaError_t e = cudaMemcpy2DAsync(st + (size_t)c * H * W * es, W * es,
-                                              (const char*)src + (size_t)c * cs * es, rs * es, W * es, H,
-                                              cudaMemcpyHostToDevice, stream);
-            if (e != cudaSuccess) return cuda_check(e, "host-to-device copy");
+        char* st;
+        if (prestaged) {   // upload_begin copied it; wait for the copy
+            st = (char*)stage.base;
+            cudaStreamWaitEvent(stream, uev[1], 0);
+        } else {
+            // a side-stream upload into `stage` (one a failed call left behind) lands first
+            if (ustream) cudaStreamWaitEvent(stream, uev[1], 0);
+            int rc = stage.reserve(*this, std::max(stage.cap, n + (size_t)H * W + 1024), "staging buffer");
+            if (rc) return rc;
+            st = (char*)stage.base;
+            for (int c = 0; c < nc; ++c) {
+                cudaError_t e = cudaMemcpy2DAsync(st + (size_t)c * H * W * es, W * es,
+                                                  (const char*)src + (size_t)c * cs * es, rs * es, W * es, H,
+                                                  cudaMemcpyHostToDevice, stream);
+                if (e != cudaSuccess) return cuda_check(e, "host-to-device copy");
+            }
         }
         src = st;
         rs = W;
@@ -842,8 +879,12 @@ int hdi_destroy(hdi_ctx* h) {
     c->dws.release();
     c->vws.release();
     c->lws.release();
+    if (c->ustream) cudaStreamSynchronize(c->ustream);
     c->stage.release();
     engine_delete(c->eng);
+    if (c->ustream) cudaStreamDestroy(c->ustream);
+    for (cudaEvent_t e : c->uev)
+        if (e) cudaEventDestroy(e);
     if (c->flags) cudaFree(c->flags);
     if (c->tev) {
         for (int i = 0; i < 2 * kMaxTimed; ++i) cudaEventDestroy(c->tev[i]);

@@ -181,6 +181,16 @@ struct Ctx {
     Arena vws;     // Voronoi initialisation
     Arena lws;     // list of mask pixels (tonal optimisation)
     Arena stage;   // host staging
+    // side stream for a host image's upload into `stage` that overlaps the
+    // context stream's kernels; uev[0]: the context stream is done with
+    // `stage`, uev[1]: the upload has landed
+    cudaStream_t ustream = nullptr;
+    cudaEvent_t uev[2] = {nullptr, nullptr};
+    int upload_begin(const hdi_image* im);
+    // a host image whose upload the tonal set-up starts right before its echo
+    // kernel, after its own small host copies (which would otherwise queue
+    // behind the large one)
+    const hdi_image* pending_upload = nullptr;
     int H = 0, W = 0, nch = 0, nlev = 0;
     // levels the solves use: the hierarchy ends at its first level whose
     // pixels are all known (every coarser level's correction is exactly 0)
@@ -258,7 +268,8 @@ struct Ctx {
                   bool p32 = false);
     int solve(SolveSpec& s);
     int check_image(const hdi_image* im, const char* name, int H, int W, int nch);
-    int load_image(const hdi_image* im, DF dst, float* lo2 = nullptr, int c0 = 0, bool wait = true);
+    int load_image(const hdi_image* im, DF dst, float* lo2 = nullptr, int c0 = 0, bool wait = true,
+                   bool prestaged = false);
     int store_image(DFc src, hdi_image* im, bool zero_off_mask, const float* known_lo2 = nullptr, int c0 = 0,
                     bool wait = true);
     int load_mask(const hdi_mask* m, long long* ones, int plane = 0, bool pyramid = true, bool wait = true);

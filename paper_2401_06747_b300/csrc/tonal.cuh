@@ -809,6 +809,11 @@ int Ctx::tonal_setup_blk(int blk) {
         ea.rtol2 = (float)(p.tonal_echo_rtol * p.tonal_echo_rtol);
         ea.maxit = (int)p.tonal_echo_max_iter;
         ea.iters = counters + kCntEcho;
+        if (pending_upload) {   // Ctx::tonal's host f: copied while the echo and Gram kernels run
+            const hdi_image* im = pending_upload;
+            pending_upload = nullptr;
+            if ((rc = upload_begin(im))) return rc;
+        }
         tstart(kT_Echo);
         if (blk == 64) k_tonal_echo64<<<(unsigned)total, kL64Threads, 0, stream>>>(ea);
         else if (p.oras_warp >= 0.5 && W >= 32 && H >= 32)
@@ -1055,18 +1060,37 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     const DFc F = cview(dfv[kF]);
     DF G = dfv[kG];
     f_lo_zero = true;
-    if ((rc = load_image(f, dfv[kF]))) return rc;
-    if (g0) {
-        if ((rc = load_image(g0, G))) return rc;
+    const bool cgnr = p.tonal_method >= 0.5;
+    const bool outer = p.tonal_max_iter >= 1;   // 0: only the initial values (e.g. the Voronoi initialisation)
+    // the local factors depend on the mask only: a host f is copied to the
+    // device on the side stream while their echo and Gram kernels run
+    const bool overlap = f->location == HDI_HOST && !g0 && !cgnr && outer;
+    pending_upload = nullptr;
+    if (overlap) {
+        pending_upload = f;
     } else {
-        cudaMemcpyAsync(G.hi, F.hi, (size_t)nch * lev[0].cs * 8, cudaMemcpyDeviceToDevice, stream);
+        if ((rc = load_image(f, dfv[kF]))) return rc;
+        if (g0) {
+            if ((rc = load_image(g0, G))) return rc;
+        } else {
+            cudaMemcpyAsync(G.hi, F.hi, (size_t)nch * lev[0].cs * 8, cudaMemcpyDeviceToDevice, stream);
+        }
     }
     vcycles_run = 0;
     cudaMemsetAsync(counters + kCntLocal, 0, 16, stream);
-    const bool cgnr = p.tonal_method >= 0.5;
-    const bool outer = p.tonal_max_iter >= 1;   // 0: only the initial values (e.g. the Voronoi initialisation)
     if ((rc = mask_list())) return rc;
-    if (!cgnr && outer && (rc = tonal_setup())) return rc;
+    if (!cgnr && outer && (rc = tonal_setup())) {
+        pending_upload = nullptr;
+        return rc;
+    }
+    if (overlap) {
+        if (pending_upload) {   // the set-up did not reach its echo kernel: copy now
+            pending_upload = nullptr;
+            if ((rc = upload_begin(f))) return rc;
+        }
+        if ((rc = load_image(f, dfv[kF], nullptr, 0, true, true))) return rc;
+        cudaMemcpyAsync(G.hi, F.hi, (size_t)nch * lev[0].cs * 8, cudaMemcpyDeviceToDevice, stream);
+    }
 
     // the inner solves use their own local stop fraction (restored on exit)
     struct EtaSwap {
