@@ -499,7 +499,7 @@ __global__ void k_dens_load(const T* __restrict__ src, long long rs, long long c
     dst[(size_t)ch * H * W + (size_t)y * W + x] = (double)src[ch * cs + (size_t)y * rs + x];
 }
 
-// ------------------------------------------------------------ the driver ---
+// ------------------------------------------------------- host-side loop ---
 
 // Copies a caller image (device or host) into a plain FP64 [nch][H][W] array.
 int Ctx::dens_load(const hdi_image* im, double* dst, void* hstage) {

@@ -684,7 +684,7 @@ __global__ void __launch_bounds__(32 * kLocalWarps) k_tonal_local(LocalSolveArgs
 }
 
 
-// ------------------------------------------------------------ the driver ---
+// ------------------------------------------------------- host-side loop ---
 
 int Ctx::tonal_setup() {
     // RAS subdomain side: 64 (the paper's block) couples the subdomains

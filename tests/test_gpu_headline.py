@@ -44,7 +44,7 @@ MASK_SEED = 1001
 DENSITY = 0.04
 TOL = 1e-6
 INPAINT_TOL = 1e-7
-# tolerances of the spec gates; the FP32 output of a 1e-6 solve adds
+# tolerances of the accuracy gates; the FP32 output of a 1e-6 solve adds
 # its own rounding to the normal residual (as in the smaller tonal tests)
 U_TOL = 1e-3
 NR_TOL = 2e-6
