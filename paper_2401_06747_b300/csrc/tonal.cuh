@@ -1065,6 +1065,10 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     // the local factors depend on the mask only: a host f is copied to the
     // device on the side stream while their echo and Gram kernels run
     const bool overlap = f->location == HDI_HOST && !g0 && !cgnr && outer;
+    struct PendingClear {   // the caller's f is not referenced past this call, on any return
+        const hdi_image*& p;
+        ~PendingClear() { p = nullptr; }
+    } pending_clear{pending_upload};
     pending_upload = nullptr;
     if (overlap) {
         pending_upload = f;
@@ -1079,10 +1083,7 @@ int Ctx::tonal(const hdi_image* f, const hdi_mask* mask, const hdi_image* g0, hd
     vcycles_run = 0;
     cudaMemsetAsync(counters + kCntLocal, 0, 16, stream);
     if ((rc = mask_list())) return rc;
-    if (!cgnr && outer && (rc = tonal_setup())) {
-        pending_upload = nullptr;
-        return rc;
-    }
+    if (!cgnr && outer && (rc = tonal_setup())) return rc;
     if (overlap) {
         if (pending_upload) {   // the set-up did not reach its echo kernel: copy now
             pending_upload = nullptr;
